@@ -1,0 +1,233 @@
+"""Pins of the FP64 oracle against things other than itself: a library FFT,
+dense brute force on tiny grids, closed-form Poisson solutions, exact
+invariants of Eq. 4, the geometry of a sphere, and finite differences.
+All CPU-only."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import bruteforce as bf
+from paper_2106_03452_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _cloud(seed, N, lo=0.0, hi=1.0):
+    rng = synth.Rng(seed)
+    pts = lo + (hi - lo) * rng.uniform(N, 3)
+    nrm = rng.normal(N, 3)
+    return pts, nrm
+
+
+# --------------------------------------------------------------------------
+# FFT (Eq. A3 / A4): against numpy's FFT, round trip, Parseval.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("r", [2, 4, 8, 16])
+def test_fft3_matches_numpy(oracle, r):
+    rng = synth.Rng(7 + r)
+    g = rng.normal(r, r, r) + 1j * rng.normal(r, r, r)
+    f = oracle.fft3(g)
+    assert np.max(np.abs(f - np.fft.fftn(g))) <= 1e-12 * np.max(np.abs(f))
+    b = oracle.fft3(g, inverse=True)
+    assert np.max(np.abs(b - np.fft.ifftn(g))) <= 1e-12 * np.max(np.abs(b))
+    assert np.max(np.abs(oracle.fft3(f, inverse=True) - g)) <= 1e-12 * np.max(np.abs(g))
+    assert math.isclose(np.sum(np.abs(g) ** 2), np.sum(np.abs(f) ** 2) / r ** 3, rel_tol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Rasterization (Eq. A1-A2) against dense tent weights.
+# --------------------------------------------------------------------------
+def test_splat_and_gather_dense(oracle):
+    r = 8
+    pts, nrm = _cloud(11, 40, -0.3, 1.3)   # includes wrapped coordinates
+    pts[0] = [0.0, 0.0, 0.0]               # on a vertex
+    pts[1] = [0.125, 0.5, 0.999999]        # on cell faces, just below 1
+    pts[2] = [-1e-9, 1.0, 2.0]
+    W = bf.dense_weights(pts, r)
+    V = oracle.splat(r, pts, nrm)
+    ref = (W.T @ nrm).T.reshape(3, r, r, r)
+    assert np.max(np.abs(V - ref)) <= 1e-12
+    Wf = oracle.splat(r, pts)
+    assert np.max(np.abs(Wf.ravel() - W.sum(0))) <= 1e-12
+    G = synth.Rng(3).normal(r, r, r)
+    assert np.max(np.abs(oracle.gather(G, pts) - W @ G.ravel())) <= 1e-12
+
+
+# --------------------------------------------------------------------------
+# Whole forward against direct sums (dense weights, dense DFT, Re()).
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("r,sigma,N", [(4, 0.0, 7), (8, 0.0, 20), (8, 1.5, 20), (8, 3.0, 13)])
+def test_forward_bruteforce(oracle, r, sigma, N):
+    pts, nrm = _cloud(100 + r * 10 + N, N, -0.2, 1.2)
+    chi, chip, mu, s = oracle.forward(r, sigma, pts, nrm, full=True)
+    bchi, bchip, bmu, bs = bf.forward(pts, nrm, r, sigma)
+    sc = np.max(np.abs(bchip))
+    assert np.max(np.abs(chip - bchip)) <= 1e-12 * sc
+    assert abs(mu - bmu) <= 1e-12 * sc and abs(s - bs) <= 1e-12 * sc
+    assert np.max(np.abs(chi - bchi)) <= 1e-11
+
+
+# --------------------------------------------------------------------------
+# Closed form: a plane-wave normal field sampled exactly on the vertices.
+# V = nhat cos(2 pi (k.x - phi)) has divergence -2 pi |k| sin(2 pi (k.x - phi))
+# (nhat = k/|k|), so the periodic Poisson solution of Eq. 1 is
+# chi' = g(k) sin(2 pi (k.x - phi)) / (2 pi |k|), g(k) = exp(-2 sigma^2 |k|^2 / r^2)
+# (Eq. 3). A divergence-free field (nhat orthogonal to k) gives chi' = 0.
+# The cases and their amplitudes are in tests/golden/plane_waves.json.
+# --------------------------------------------------------------------------
+def _lattice(r):
+    j = np.stack(np.meshgrid(np.arange(r), np.arange(r), np.arange(r), indexing="ij"), -1)
+    return j.reshape(-1, 3) / r
+
+
+def test_plane_wave_closed_form(oracle):
+    with open(os.path.join(GOLDEN, "plane_waves.json")) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        r, sigma, k, nd, phi = c["r"], c["sigma"], np.array(c["k"], float), np.array(c["n"], float), c["phi"]
+        x = _lattice(r)
+        wave = np.cos(2 * np.pi * (x @ k - phi))
+        nrm = nd[None, :] * wave[:, None]
+        if c["amplitude"] == 0.0:
+            # divergence-free: chi' vanishes, so s = 0 and the layer reports a
+            # degenerate scale; check through the unnormalised splat + solve
+            # by adding a small reference wave along x that is not div-free.
+            ref = np.array([1.0, 0, 0])[None, :] * np.cos(2 * np.pi * (x[:, 0] - 0.125))[:, None]
+            _, chip_ref, _, _ = oracle.forward(r, sigma, x, ref, full=True)
+            _, chip, _, _ = oracle.forward(r, sigma, x, nrm + ref, full=True)
+            assert np.max(np.abs(chip - chip_ref)) <= 1e-13
+            continue
+        chi, chip, mu, s = oracle.forward(r, sigma, x, nrm, full=True)
+        expect = c["amplitude"] * np.sin(2 * np.pi * (x @ k - phi))
+        assert np.max(np.abs(chip.ravel() - expect)) <= 1e-13, c
+        assert abs(mu) <= 1e-13
+        assert math.isclose(s, expect[0], rel_tol=1e-10)
+
+
+# --------------------------------------------------------------------------
+# Exact invariants of the normalisation (Eq. 2, Eq. 4) and symmetries.
+# --------------------------------------------------------------------------
+def test_invariants(oracle):
+    r, sigma = 16, 2.0
+    rng = synth.Rng(5)
+    pts = 0.2 + 0.6 * rng.uniform(300, 3)
+    nrm = rng.normal(300, 3)
+    chi, chip, mu, s = oracle.forward(r, sigma, pts, nrm, full=True)
+    W = bf.dense_weights(pts, r)
+    assert abs((W @ chi.ravel()).mean()) <= 1e-12           # chi = 0 at the points on average
+    assert math.isclose(abs(chi[0, 0, 0]), 0.5, rel_tol=1e-12)
+    assert np.max(np.abs(oracle.forward(r, sigma, pts, 3.7 * nrm) - chi)) <= 1e-12
+    assert np.max(np.abs(oracle.forward(r, sigma, pts, -nrm) + chi)) <= 1e-12
+    # chi' is linear in the normals
+    n2 = rng.normal(300, 3)
+    _, c1, _, _ = oracle.forward(r, sigma, pts, nrm + n2, full=True)
+    _, c2, _, _ = oracle.forward(r, sigma, pts, n2, full=True)
+    assert np.max(np.abs(c1 - chip - c2)) <= 1e-12 * np.max(np.abs(c1))
+    # integer-voxel shift of every point circularly shifts chi'
+    sh = np.array([3, -5, 7])
+    _, cs, _, _ = oracle.forward(r, sigma, pts + sh / r, nrm, full=True)
+    assert np.max(np.abs(cs - np.roll(chip, tuple(sh), axis=(0, 1, 2)))) <= 1e-12 * np.max(np.abs(chip))
+    # swapping the x and y axes of positions and normals transposes chi'
+    _, ct, _, _ = oracle.forward(r, sigma, pts[:, [1, 0, 2]], nrm[:, [1, 0, 2]], full=True)
+    assert np.max(np.abs(ct - np.transpose(chip, (1, 0, 2)))) <= 1e-12 * np.max(np.abs(chip))
+    # sigma = 0 is allowed (no smoothing) and differs from sigma > 0
+    c0 = oracle.forward(r, 0.0, pts, nrm)
+    assert np.isfinite(c0).all() and np.max(np.abs(c0 - chi)) > 1e-3
+
+
+def test_degenerate_and_invalid(oracle):
+    pts = np.full((4, 3), 0.5)
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.forward(16, 2.0, pts, np.zeros((4, 3)))      # chi' = 0: s = 0
+    assert e.value.code == oracle.ORACLE_EDEGENERATE
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.forward(12, 2.0, pts, np.ones((4, 3)))       # r not a power of two
+    assert e.value.code == oracle.ORACLE_EINVAL
+    bad = pts.copy()
+    bad[1, 2] = np.nan
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.forward(16, 2.0, bad, np.ones((4, 3)))
+    assert e.value.code == oracle.ORACLE_EDEGENERATE
+
+
+# --------------------------------------------------------------------------
+# Geometry: a sphere of outward normals. chi is an indicator shifted to zero
+# at the points: its zero level set sits at the sphere radius, the inside is
+# negative, chi(0) = +0.5 exactly (reading: positive scale, outward normals).
+# --------------------------------------------------------------------------
+def _trilerp(grid, p):
+    r = grid.shape[0]
+    x = np.asarray(p, float) * r
+    i0 = np.floor(x).astype(int)
+    t = x - i0
+    acc = 0.0
+    for dx in (0, 1):
+        for dy in (0, 1):
+            for dz in (0, 1):
+                w = (t[0] if dx else 1 - t[0]) * (t[1] if dy else 1 - t[1]) * (t[2] if dz else 1 - t[2])
+                acc += w * grid[(i0[0] + dx) % r, (i0[1] + dy) % r, (i0[2] + dz) % r]
+    return acc
+
+
+def test_sphere_geometry(oracle):
+    w = synth.workload_sphere_r32()
+    r = w["r"]
+    chi = oracle.forward(r, w["sigma"], w["points"], w["normals"])
+    assert math.isclose(chi[0, 0, 0], 0.5, rel_tol=1e-12)
+    c = np.array([0.5, 0.5, 0.5])
+    assert chi[16, 16, 16] < -0.3                 # inside is negative
+    dirs = [np.array(d, float) for d in np.ndindex(3, 3, 3) if d != (1, 1, 1)]
+    for d in dirs:
+        d = (d - 1) / np.linalg.norm(d - 1)
+        rad = np.linspace(0.05, 0.45, 801)
+        vals = np.array([_trilerp(chi, c + q * d) for q in rad])
+        cross = np.nonzero((vals[:-1] < 0) & (vals[1:] >= 0))[0]
+        assert len(cross) >= 1
+        q0 = rad[cross[0]]
+        assert abs(q0 - 0.3) <= 1.0 / r, (d, q0)
+
+
+# --------------------------------------------------------------------------
+# Backward: central finite differences of L = <dchi, chi> in FP64.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("r,sigma", [(8, 1.0), (16, 2.0)])
+def test_backward_finite_differences(oracle, r, sigma):
+    rng = synth.Rng(31 + r)
+    N = 25
+    pts = 0.15 + 0.7 * rng.uniform(N, 3)
+    # keep every coordinate at least 1e-3 voxel away from a cell face
+    f = pts * r - np.floor(pts * r)
+    pts = (np.floor(pts * r) + np.clip(f, 0.01, 0.99)) / r
+    nrm = rng.normal(N, 3)
+    G = rng.normal(r, r, r)
+    dp, dn = oracle.backward(r, sigma, pts, nrm, G)
+    L = lambda p, n: float(np.sum(G * oracle.forward(r, sigma, p, n)))
+    h = 1e-6
+    scale_p, scale_n = np.max(np.abs(dp)), np.max(np.abs(dn))
+    for (i, d) in [(0, 0), (3, 1), (7, 2), (11, 0), (24, 2)]:
+        pp, pm = pts.copy(), pts.copy()
+        pp[i, d] += h
+        pm[i, d] -= h
+        fd = (L(pp, nrm) - L(pm, nrm)) / (2 * h)
+        assert abs(fd - dp[i, d]) <= 1e-6 * scale_p, (i, d, fd, dp[i, d])
+        npl, nmi = nrm.copy(), nrm.copy()
+        npl[i, d] += h
+        nmi[i, d] -= h
+        fd = (L(pts, npl) - L(pts, nmi)) / (2 * h)
+        assert abs(fd - dn[i, d]) <= 1e-6 * scale_n, (i, d, fd, dn[i, d])
+
+
+def test_splat_gather_adjoint(oracle):
+    """<splat(c, v), G> = <v, gather(G, c)>: the rasterization of Eq. A2 and
+    the trilinear lookup are transposes of each other."""
+    r = 16
+    rng = synth.Rng(77)
+    pts = rng.uniform(50, 3) * 3 - 1
+    v = rng.normal(50)
+    G = rng.normal(r, r, r)
+    lhs = float(np.sum(oracle.splat(r, pts, v[:, None]) * G))
+    rhs = float(np.dot(v, oracle.gather(G, pts)))
+    assert math.isclose(lhs, rhs, rel_tol=1e-12)
