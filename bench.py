@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark of the spectral DPSR layer (forward + backward) on GB300.
+
+One step = one DPSR forward + backward solve of the r = 128 workload (20 000
+points on a union of 4 random ellipsoids, sigma = 2, dchi ~ N(0, 1)) with
+every input resident in HBM. Between timed steps a 512 MiB buffer is written
+to flush L2 (the r = 128 working set would otherwise stay in the 129 MB L2);
+each step is timed with CUDA events on the stream its kernels run on.
+
+The JSON line also carries:
+  e2e        the same solve through the host-buffer entry points
+             (dpsr_forward_host / dpsr_backward_host): inputs copied from pinned
+             host memory and results copied back inside the timed region;
+  roofline   the dominant kernel's algorithmic bytes per launch over its
+             average event-timed duration, against the measured HBM copy peak;
+  r256       the r = 256 solve (100 000 points, torus + 2 ellipsoids): solves/s
+             and the fraction of the HBM roofline for the whole-solve byte
+             model 23 r^3 * 4 B + 200 N B;
+  cpu_baseline  the FP64 oracle on this host's cores on a bounded sample.
+
+--impl reference times the FP64 oracle (the only reference there is: the
+paper ships no code) on the same workload, one solve per step.
+Multi-GPU (torchrun): replicas only, each rank solves its own copy of the
+workload; value = solves of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DPSR fwd+bwd solves/s at r=128/256 (% HBM roofline); served p50/p99 ms vs per-solve loop"
+WORKLOAD = "r128: plain DPSR fwd+bwd, r=128, sigma=2, N=20000 on a union of 4 random ellipsoids"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        try:
+            rows = [ln.split(",") for ln in open(self.path).read().strip().splitlines() if ln.strip()]
+            os.unlink(self.path)
+        except Exception:
+            return out
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for i, n in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons),
+                       samples=len(sm))
+        return out
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        return dist, rank, ws, local
+    return None, rank, ws, local
+
+
+def _max_over_ranks(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------
+# byte model (per launch / per solve), see the design doc
+# ----------------------------------------------------------------------------
+def kernel_bytes(r: int, N: int):
+    U = 4 * r ** 3                      # one FP32 real grid
+    H = 8 * r * r * (r // 2 + 1)        # one complex half spectrum
+    rec = 32                            # sorted point record
+    return {
+        "plane_fwd": 3 * H + 2 * rec * N,
+        "xpass_fwd": 4 * H,
+        "plane_inv": H + U + 2 * (rec + 16) * N,
+        "plane_bfwd": 2 * U + H,
+        "xpass_bwd": 4 * H,
+        "plane_binv": 2 * H + 2 * (rec + 24) * N,
+        "bin": 2 * 24 * N + 4 * N + (rec + 4) * N,
+        "combine": (32 * 2 + 16 * 2 + 8 + 24) * N,
+    }
+
+
+def solve_bytes_model(r: int, N: int) -> float:
+    """Whole fwd+bwd solve: 23 one-grid units plus ~200 B per point."""
+    return 23 * 4 * r ** 3 + 200 * N
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2106_03452_gb300 import libdpsr as L
+    from paper_2106_03452_gb300 import synth
+    from paper_2106_03452_gb300.dpsr import Plan
+
+    dist, rank, ws, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hbm_peak, peak_kind = _peaks()
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+
+    def timed(step, K, W, flush_l2=True):
+        for _ in range(W):
+            step()
+        torch.cuda.synchronize()
+        _barrier(dist)
+        torch.cuda.synchronize()
+        evs = []
+        t0 = time.perf_counter()
+        for _ in range(K):
+            if flush_l2:
+                flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            step()
+            b.record()
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        _barrier(dist)
+        return ms, wall
+
+    # ---------------- headline: r = 128 ----------------
+    w = synth.workload_ellipsoids_r128()
+    r, N = w["r"], w["points"].shape[0]
+    plan = Plan(r, w["sigma"], device=dev, n_max=N)
+    P = torch.from_numpy(w["points"]).to(dev)
+    Nn = torch.from_numpy(w["normals"]).to(dev)
+    G = torch.from_numpy(w["dchi"]).to(dev)
+    chi = torch.empty((r, r, r), device=dev)
+    dp, dn = torch.empty_like(P), torch.empty_like(P)
+
+    def step():
+        plan.forward(P, Nn, chi)
+        plan.backward(G, dp, dn)
+
+    step()
+    st = plan.sync()
+    if st != 0:
+        raise RuntimeError(f"device status {st}: {L.dpsr_strerror(st)}")
+    clocks = Clocks(local)
+    clocks.start()
+    ms, wall = timed(step, args.steps, args.warmup)
+    clk = clocks.stop()
+    ms_max = _max_over_ranks(dist, ms)
+    value = ws * args.steps / (ms_max / 1e3)
+    launches = args.steps * 12
+
+    # per-kernel profile of the same step (events around every launch)
+    L.dpsr_plan_profile(plan.handle, True)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        step()
+    prof = L.dpsr_plan_profile_read(plan.handle)
+    L.dpsr_plan_profile(plan.handle, False)
+    kb = kernel_bytes(r, N)
+    per = {k: {"ms": v[0] / max(v[1], 1), "launches": v[1], "bytes": kb.get(k)} for k, v in prof.items() if v[1]}
+    dom = max((k for k in per if per[k]["bytes"]), key=lambda k: per[k]["ms"] * per[k]["launches"])
+    ach = per[dom]["bytes"] / (per[dom]["ms"] / 1e3) / 1e9
+
+    # ---------------- e2e through the host-buffer entry points ----------------
+    hp = torch.from_numpy(w["points"]).pin_memory()
+    hn = torch.from_numpy(w["normals"]).pin_memory()
+    hg = torch.from_numpy(w["dchi"]).pin_memory()
+    hchi = torch.empty((r, r, r)).pin_memory()
+    hdp, hdn = torch.empty_like(hp).pin_memory(), torch.empty_like(hp).pin_memory()
+    plan_h = Plan(r, w["sigma"], device=dev, n_max=N)
+    L.dpsr_plan_set_stream(plan_h.handle, torch.cuda.current_stream(dev).cuda_stream)
+
+    def step_e2e():
+        L.dpsr_forward_host(plan_h.handle, hp.data_ptr(), hn.data_ptr(), N, hchi.data_ptr())
+        L.dpsr_backward_host(plan_h.handle, hg.data_ptr(), hdp.data_ptr(), hdn.data_ptr())
+
+    ms_e2e, _ = timed(step_e2e, args.steps, args.warmup)
+    e2e_value = ws * args.steps / (_max_over_ranks(dist, ms_e2e) / 1e3)
+    h2d = 2 * 12 * N + 4 * r ** 3
+    d2h = 4 * r ** 3 + 2 * 12 * N
+
+    # ---------------- r = 256 ----------------
+    r256 = None
+    if not args.no_r256:
+        w3 = synth.workload_torus_r256()
+        r3, N3 = w3["r"], w3["points"].shape[0]
+        plan3 = Plan(r3, w3["sigma"], device=dev, n_max=N3)
+        P3 = torch.from_numpy(w3["points"]).to(dev)
+        N3t = torch.from_numpy(w3["normals"]).to(dev)
+        G3 = torch.randn((r3,) * 3, device=dev, generator=torch.Generator(device=dev).manual_seed(3))
+        chi3 = torch.empty((r3,) * 3, device=dev)
+        dp3, dn3 = torch.empty_like(P3), torch.empty_like(P3)
+
+        def step3():
+            plan3.forward(P3, N3t, chi3)
+            plan3.backward(G3, dp3, dn3)
+
+        step3()
+        if plan3.sync() != 0:
+            raise RuntimeError("r256 device status")
+        k3 = max(3, args.steps // 2)
+        ms3, _ = timed(step3, k3, args.warmup)
+        ms3 = _max_over_ranks(dist, ms3)
+        t3 = ms3 / k3 / 1e3
+        bytes3 = solve_bytes_model(r3, N3)
+        L.dpsr_plan_profile(plan3.handle, True)
+        for _ in range(k3):
+            flush.fill_(1.0)
+            step3()
+        prof3 = L.dpsr_plan_profile_read(plan3.handle)
+        L.dpsr_plan_profile(plan3.handle, False)
+        kb3 = kernel_bytes(r3, N3)
+        per3 = {k: {"ms": v[0] / max(v[1], 1), "launches": v[1], "bytes": kb3.get(k),
+                    "gbs": (kb3[k] / (v[0] / max(v[1], 1) / 1e3) / 1e9) if kb3.get(k) and v[0] > 0 else None}
+                for k, v in prof3.items() if v[1]}
+        r256 = {"workload": "r256: torus (R=0.25, tube 0.08) + 2 ellipsoids, N=100000, sigma=2, fwd+bwd",
+                "solves_per_s": ws * k3 / (ms3 / 1e3), "ms_per_step": t3 * 1e3,
+                "model_bytes_per_solve": bytes3,
+                "roofline_frac_of_model": bytes3 / t3 / 1e9 / hbm_peak,
+                "kernels": per3}
+        plan3.close()
+
+    # ---------------- CPU baseline: the oracle ----------------
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_baseline(w, budget_s=args.cpu_budget)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "r": r, "N": N, "sigma": w["sigma"],
+                       "global_batch": ws, "parallelism": f"replicas{ws}",
+                       "l2": "flushed between timed steps (512 MiB write)"},
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": ach / hbm_peak, "traffic": None, "kernel": dom,
+                         "peak_kind": peak_kind,
+                         "bytes_per_launch": per[dom]["bytes"], "ms_per_launch": per[dom]["ms"]},
+            "kernels": per,
+            "clocks": clk,
+            "r256": r256,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    plan_h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def oracle_baseline(w, budget_s=12.0):
+    """The FP64 oracle as it stands, forward + backward, on this host's cores:
+    repeats whole solves of the workload until budget_s has passed."""
+    import oracle
+    oracle.build()
+    r, sigma = w["r"], w["sigma"]
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.forward(r, sigma, w["points"], w["normals"])
+        oracle.backward(r, sigma, w["points"], w["normals"], w["dchi"])
+        n += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "solves/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{n} whole fwd+bwd solves of the r=128 workload (FP64, OpenMP over FFT pencils)"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle, one whole r=128 solve per step."""
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2106_03452_gb300 import synth
+    oracle.build()
+    w = synth.workload_ellipsoids_r128()
+    r, sigma = w["r"], w["sigma"]
+
+    def step():
+        oracle.forward(r, sigma, w["points"], w["normals"])
+        oracle.backward(r, sigma, w["points"], w["normals"], w["dchi"])
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    line = {
+        "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "r": r, "N": int(w["points"].shape[0]), "sigma": sigma,
+                   "global_batch": 1, "parallelism": "cpu"},
+        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": oracle.threads(), "kind": "oracle",
+                         "sample": f"{args.steps} whole fwd+bwd solves of the r=128 workload"},
+        "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-r256", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

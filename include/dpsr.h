@@ -1,0 +1,150 @@
+/*
+ * libdpsr: spectral Differentiable Poisson Surface Reconstruction (DPSR) on a
+ * single GB300 GPU (sm_103a). The layer of "Shape As Points" (Peng et al.,
+ * arXiv 2106.03452), Sec. 3.1, derived in supplementary Sec. A:
+ *
+ *   v    = trilinear splat of the point normals onto an r^3 grid     (Eq. A1-A2)
+ *   v~   = FFT(v)                                                     (Eq. A3)
+ *   chi~ = g(u) * (i u . v~) / (-2 pi |u|^2),
+ *          g(u) = exp(-2 sigma^2 |u|^2 / r^2)                         (Eq. 3, A7)
+ *   chi' = IFFT(chi~)                                                 (Eq. A8)
+ *   chi  = m / |chi'(0) - mu| * (chi' - mu),  mu = mean_i chi'(c_i),
+ *          m = 0.5                                                    (Eq. 4, A9)
+ *
+ * and its exact reverse-mode derivative (what Eq. 5 backpropagates through).
+ *
+ * Conventions (all calls):
+ *  - The domain is the periodic unit cube [0,1)^3 with grid origin 0 and voxel
+ *    size 1/r; vertex (ix,iy,iz) sits at (ix,iy,iz)/r. Coordinates outside
+ *    [0,1) wrap around. Frequencies are integer cycles per unit length; the
+ *    a-th term of u . v~ is zero at the Nyquist index k_a = r/2 and the DC
+ *    term of chi~ is zero. The scale uses the shifted value chi'(0) - mu, so
+ *    |chi(0)| = m exactly, with a positive factor (outside positive for
+ *    outward normals).
+ *  - points, normals, dpoints, dnormals: N x 3 row-major float32.
+ *    Normals are NOT normalised: their length weights the point.
+ *  - chi_out, dchi: r^3 float32 in C order chi[ix][iy][iz] (iz fastest);
+ *    axis 0 is the x coordinate.
+ *  - Every pointer argument of dpsr_forward / dpsr_backward is a DEVICE
+ *    pointer on the current CUDA device, owned by the caller; the library
+ *    never frees it. dpsr_forward_host / dpsr_backward_host take HOST
+ *    pointers instead and copy through the plan's stream.
+ *  - Device work is asynchronous on the plan's stream. Errors found on the
+ *    host (bad arguments, wrong call order) are returned at once and nothing
+ *    is launched. Conditions found on the device (a non-finite input, a
+ *    vanishing scale chi'(0) - mu) set a status word that dpsr_sync returns;
+ *    the outputs of that call are then unspecified.
+ *  - A plan is not thread-safe: one host thread at a time per plan.
+ */
+#ifndef DPSR_H
+#define DPSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DPSR_API __attribute__((visibility("default")))
+#else
+#define DPSR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dpsr_plan_s *dpsr_plan;
+
+enum {
+    DPSR_OK = 0,
+    DPSR_EINVAL = -1,      /* bad argument: r not a power of two in [8, 256], N < 1, NULL, ... */
+    DPSR_ENOMEM = -2,      /* device allocation failed */
+    DPSR_ECUDA = -3,       /* a CUDA runtime call failed */
+    DPSR_EDEGENERATE = -4, /* non-finite input or chi'(0) - mu == 0 (no finite scale) */
+    DPSR_ESTATE = -5,      /* backward without a forward, or N above the reserved size */
+    DPSR_ETIMEOUT = -6,    /* a bounded device wait gave up */
+    DPSR_EBUSY = -7        /* resource busy (serving admission) */
+};
+
+/* Create a plan for grid size r (a power of two, 8 <= r <= 256) and Gaussian
+ * bandwidth sigma >= 0 in grid units of Eq. 3 (sigma = 0: no smoothing).
+ * Allocates the plan's device workspace on the current device; the plan
+ * stays bound to that device. On success *out receives the plan. */
+DPSR_API int dpsr_plan_create(int r, float sigma, dpsr_plan *out);
+
+/* Free the plan and its workspace (synchronises its stream first). */
+DPSR_API int dpsr_plan_destroy(dpsr_plan plan);
+
+/* Run subsequent work on `stream` (a cudaStream_t; NULL = legacy default). */
+DPSR_API int dpsr_plan_set_stream(dpsr_plan plan, void *stream);
+
+/* Grow the point buffers to hold up to n_max points. dpsr_forward grows them
+ * on demand; reserving first keeps forward calls free of allocations (needed
+ * before capturing them in a CUDA graph). */
+DPSR_API int dpsr_plan_reserve(dpsr_plan plan, int64_t n_max);
+
+/* Device bytes a plan of size r uses with n_max points; with_bwd != 0 counts
+ * what the backward pass needs as well. Used for admission by memory budget. */
+DPSR_API size_t dpsr_plan_workspace_bytes(int r, int64_t n_max, int with_bwd);
+
+/* Forward pass of Eq. 3-4 for N oriented points (device pointers). Writes
+ * chi_out (r^3). Keeps, inside the plan, what the backward pass needs: the
+ * points sorted by x-plane, the transformed weight field of the points, the
+ * scalars mu and s, and the per-point gradient of the trilinear lookup of
+ * chi'. The caller must keep points, normals and chi_out unchanged until the
+ * matching dpsr_backward has run. */
+DPSR_API int dpsr_forward(dpsr_plan plan, const float *points, const float *normals, int64_t N,
+                 float *chi_out);
+
+/* Backward pass: given dchi = dL/dchi (r^3, device), overwrite dpoints and
+ * dnormals (N x 3, device) with dL/dpoints and dL/dnormals of the last
+ * forward pass on this plan. Returns DPSR_ESTATE if no forward pass ran. */
+DPSR_API int dpsr_backward(dpsr_plan plan, const float *dchi, float *dpoints, float *dnormals);
+
+/* Host-memory variants: the same computation with host input and output
+ * buffers; the host<->device copies run on the plan's stream inside the call,
+ * which returns after the results are on the host. */
+DPSR_API int dpsr_forward_host(dpsr_plan plan, const float *points, const float *normals, int64_t N,
+                      float *chi_out);
+DPSR_API int dpsr_backward_host(dpsr_plan plan, const float *dchi, float *dpoints, float *dnormals);
+
+/* Wait for the plan's stream; return the device status of the work queued so
+ * far (DPSR_OK, DPSR_EDEGENERATE, ...) and clear it. */
+DPSR_API int dpsr_sync(dpsr_plan plan);
+
+/* Synchronise, then read the scalars of the last forward pass:
+ * out[0] = mu (mean of chi' at the points), out[1] = s = chi'(0) - mu,
+ * out[2] = m/|s|. chi' is recovered from chi as chi/out[2] + mu. */
+DPSR_API int dpsr_get_scalars(dpsr_plan plan, double out[3]);
+
+/* Number of kernel launches the last dpsr_forward / dpsr_backward queued. */
+DPSR_API int dpsr_plan_last_launches(dpsr_plan plan);
+
+/* Per-kernel timing. With profiling on, every kernel launch of the plan is
+ * bracketed by CUDA events on the plan's stream (a small overhead per launch).
+ * dpsr_plan_profile_read synchronises, then returns, per kernel kind (the
+ * DPSR_K_* indices below), the summed device milliseconds and the number of
+ * launches since profiling was switched on or last read, and resets both.
+ * ms and launches must hold DPSR_K_COUNT entries. */
+enum {
+    DPSR_K_BIN = 0,         /* x-cell bucketing of the points (3 small kernels) */
+    DPSR_K_PLANE_FWD = 1,   /* splat + R2C(z) + FFT(y), one cluster per x-plane */
+    DPSR_K_XPASS_FWD = 2,   /* FFT(x) + spectral solve (Eq. 3) + IFFT(x) */
+    DPSR_K_FINAL_FWD = 3,   /* scalars of Eq. 4 */
+    DPSR_K_PLANE_INV = 4,   /* IFFT(y) + C2R(z) + normalisation (Eq. 4) */
+    DPSR_K_PLANE_BFWD = 5,  /* backward: R2C(z) + FFT(y) of dchi */
+    DPSR_K_FINAL_BWD = 6,   /* backward scalars */
+    DPSR_K_XPASS_BWD = 7,   /* backward: adjoint spectral solve along x */
+    DPSR_K_PLANE_BINV = 8,  /* backward: IFFT(y) + C2R(z) + point adjoint */
+    DPSR_K_COMBINE = 9,     /* backward: per-point combine */
+    DPSR_K_COUNT = 10
+};
+DPSR_API int dpsr_plan_profile(dpsr_plan plan, int enable);
+DPSR_API int dpsr_plan_profile_read(dpsr_plan plan, double *ms, int *launches);
+
+/* Static description of an error code. */
+DPSR_API const char *dpsr_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPSR_H */

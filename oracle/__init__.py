@@ -62,7 +62,9 @@ def _load():
                                                 dp, dp, dp]
             lib.oracle_dpsr_backward.argtypes = [ctypes.c_int, ctypes.c_double, i64, dp, dp,
                                                  dp, dp, dp]
-            for f in ("oracle_fft3", "oracle_splat", "oracle_gather", "oracle_dpsr_forward",
+            lib.oracle_dpsr_backward_terms.argtypes = [ctypes.c_int, ctypes.c_double, i64, dp, dp,
+                                                       dp, dp, dp, dp]
+            for f in ("oracle_dpsr_backward_terms", "oracle_fft3", "oracle_splat", "oracle_gather", "oracle_dpsr_forward",
                       "oracle_dpsr_backward", "oracle_threads"):
                 getattr(lib, f).restype = ctypes.c_int
             lib.oracle_threads.argtypes = []
@@ -143,13 +145,21 @@ def forward(r: int, sigma: float, points, normals, full: bool = False):
     return chi
 
 
-def backward(r: int, sigma: float, points, normals, dchi):
-    """DPSR backward: (dL/dpoints, dL/dnormals), each N x 3."""
+def backward(r: int, sigma: float, points, normals, dchi, mean_term: bool = False):
+    """DPSR backward: (dL/dpoints, dL/dnormals), each N x 3. With
+    mean_term=True also the part of dL/dpoints that flows through the mean of
+    Eq. 4, as a third array."""
     pts = _f64(points, (-1, 3))
     nrm = _f64(normals, (-1, 3))
     g = _f64(dchi, (r, r, r))
     dp = np.zeros_like(pts)
     dn = np.zeros_like(nrm)
+    if mean_term:
+        dm = np.zeros_like(pts)
+        _check(_load().oracle_dpsr_backward_terms(r, float(sigma), pts.shape[0], _p(pts), _p(nrm),
+                                                  _p(g), _p(dp), _p(dn), _p(dm)),
+               "oracle_dpsr_backward_terms")
+        return dp, dn, dm
     _check(_load().oracle_dpsr_backward(r, float(sigma), pts.shape[0], _p(pts), _p(nrm), _p(g),
                                         _p(dp), _p(dn)), "oracle_dpsr_backward")
     return dp, dn

@@ -389,9 +389,9 @@ int oracle_dpsr_forward(int r, double sigma, int64_t N, const double *pts,
  *   dpoints_i = sum_a n_ia d/dc (sum_j w_ij V_bar_a[j])
  *               + (mu_bar / N) d/dc (sum_j w_ij chi'_j)
  */
-int oracle_dpsr_backward(int r, double sigma, int64_t N, const double *pts,
+static int backward_impl(int r, double sigma, int64_t N, const double *pts,
                          const double *nrm, const double *dchi, double *dpts,
-                         double *dnrm)
+                         double *dnrm, double *dpts_mean)
 {
     if (!is_pow2(r) || N < 1 || !pts || !nrm || !dchi || !dpts || !dnrm ||
         !(sigma >= 0.0))
@@ -438,7 +438,7 @@ int oracle_dpsr_backward(int r, double sigma, int64_t N, const double *pts,
         stencil st;
         e = make_stencil(pts + 3 * i, r, &st);
         if (e) goto out;
-        double gn[3] = {0, 0, 0}, gc[3] = {0, 0, 0};
+        double gn[3] = {0, 0, 0}, gc[3] = {0, 0, 0}, gm[3] = {0, 0, 0};
         for (int v = 0; v < 8; v++) {
             for (int a = 0; a < 3; a++) {
                 double val = Vbar[a * n + st.idx[v]];
@@ -446,11 +446,12 @@ int oracle_dpsr_backward(int r, double sigma, int64_t N, const double *pts,
                 for (int d = 0; d < 3; d++) gc[d] += nrm[3 * i + a] * st.dw[v][d] * val;
             }
             for (int d = 0; d < 3; d++)
-                gc[d] += (mu_bar / (double)N) * st.dw[v][d] * S.chip[st.idx[v]];
+                gm[d] += (mu_bar / (double)N) * st.dw[v][d] * S.chip[st.idx[v]];
         }
         for (int d = 0; d < 3; d++) {
             dnrm[3 * i + d] = gn[d];
-            dpts[3 * i + d] = gc[d];
+            dpts[3 * i + d] = gc[d] + gm[d];
+            if (dpts_mean) dpts_mean[3 * i + d] = gm[d];
         }
     }
 out:
@@ -460,4 +461,24 @@ out:
     free(Vbar);
     free_state(&S);
     return e;
+}
+
+int oracle_dpsr_backward(int r, double sigma, int64_t N, const double *pts,
+                         const double *nrm, const double *dchi, double *dpts,
+                         double *dnrm)
+{
+    return backward_impl(r, sigma, N, pts, nrm, dchi, dpts, dnrm, NULL);
+}
+
+/* The same backward pass, also returning the part of dL/dpoints that flows
+ * through the mean of Eq. 4, (mu_bar / N) d/dc (sum_j w_ij chi'_j), on its
+ * own. With few points this part and the rest nearly cancel (moving a lone
+ * point translates chi' and its mean together), which bounds the accuracy any
+ * FP32 evaluation of their sum can reach. */
+int oracle_dpsr_backward_terms(int r, double sigma, int64_t N, const double *pts,
+                               const double *nrm, const double *dchi, double *dpts,
+                               double *dnrm, double *dpts_mean)
+{
+    if (!dpts_mean) return ORACLE_EINVAL;
+    return backward_impl(r, sigma, N, pts, nrm, dchi, dpts, dnrm, dpts_mean);
 }

@@ -1,0 +1,500 @@
+// C ABI of libdpsr: plans, workspace, and the launch sequences of the forward
+// and backward passes of the spectral DPSR layer.
+//
+// Forward (Sec. 3.1, Eq. A1-A9):
+//   bin    counting sort of the points by the x-cell of their stencil
+//   plane  per x-plane cluster: splat (Eq. A2), R2C along z, FFT along y
+//   xpass  FFT along x, spectral solve (Eq. 3), inverse FFT along x, and the
+//          spectral sums giving mu and chi'(0) (Eq. 4)
+//   final  scalars mu, s, m/|s|
+//   inv    per x-plane cluster: IFFT along y, C2R along z, chi = m/|s| (chi'-mu)
+// Backward (adjoint of the above):
+//   bfwd   R2C/y-FFT of dchi with sum(dchi) and sum(dchi chi)
+//   final  s_bar, mu_bar and the coefficients of the adjoint spectrum
+//   xpass  adjoint spectral solve, Q1 = IFFT_x(F), Q2 = IFFT_x(-i u_x F)
+//   binv   IFFT along y, C2R along z of V_bar_{x,y,z}, gather + weight
+//          derivatives at the points
+//   combine  the two plane sides of each point, in the caller's order
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "dpsr.h"
+#include "dpsr_dev.cuh"
+#include "launch.h"
+
+using dpsr::Solve;
+
+struct dpsr_plan_s {
+  int r = 0;
+  float sigma = 0.f;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int C[4] = {1, 1, 1, 1};
+  // grid workspace
+  void* grid_ws = nullptr;
+  size_t grid_bytes = 0;
+  // point workspace
+  void* pts_ws = nullptr;
+  int64_t n_cap = 0;
+  Solve s = {};
+  bool have_fwd = false;
+  int last_launches = 0;
+  // device staging for the host-buffer variants
+  void* host_io = nullptr;
+  size_t host_io_bytes = 0;
+  int64_t host_n = 0;
+  // optional per-kernel timing: an event before and after each launch
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_kind;  // kind of each recorded pair
+  size_t ev_used = 0;        // events recorded (2 per launch)
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      ok = false;
+      return;
+    }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool valid_r(int r) { return r >= 8 && r <= 256 && (r & (r - 1)) == 0; }
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t spec_bytes(int r) { return (size_t)r * r * dpsr::kpitch(r) * sizeof(float2); }
+
+int part_count(int r) {
+  const int a = dpsr::xpass_blocks(r), b = r * 8;
+  return a > b ? a : b;
+}
+
+size_t grid_ws_bytes(int r) {
+  size_t b = 4 * align256(spec_bytes(r));
+  b += align256(sizeof(float2) * r) + 3 * align256(sizeof(float) * r);
+  b += align256(sizeof(dpsr::Scalars)) + align256(sizeof(unsigned));
+  b += align256(sizeof(double) * 2 * part_count(r));
+  b += align256(sizeof(int) * (3 * r + 1));
+  return b;
+}
+
+size_t pts_ws_bytes(int64_t n) {
+  size_t b = align256(sizeof(float4) * 2 * n);  // sorted
+  b += align256(sizeof(int) * n);              // cellx
+  b += align256(sizeof(float4) * 2 * n);       // gfwd
+  b += align256(sizeof(float) * 12 * n);       // slots
+  return b;
+}
+
+int pick_cluster(int kind, int r) {
+  const int cands[4] = {1, 2, 4, 8};
+  for (int C : cands) {
+    const size_t sm = dpsr::plane_smem_bytes(kind, r, C);
+    if (sm > 0 && sm <= 227 * 1024 - 1024) return C;
+  }
+  return 0;
+}
+
+// Record an event (profiling mode only); pairs bracket one launch.
+cudaError_t prof_mark(dpsr_plan p, int kind, bool begin) {
+  if (!p->profile) return cudaSuccess;
+  if (p->ev_used == p->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+    p->ev_pool.push_back(e);
+  }
+  if (begin) p->ev_kind.push_back(kind);
+  return cudaEventRecord(p->ev_pool[p->ev_used++], p->stream);
+}
+
+int cuda_err(cudaError_t e) { return e == cudaErrorMemoryAllocation ? DPSR_ENOMEM : DPSR_ECUDA; }
+
+int grow_points(dpsr_plan p, int64_t n) {
+  if (n <= p->n_cap) return DPSR_OK;
+  int64_t cap = p->n_cap ? p->n_cap : 1024;
+  while (cap < n) cap *= 2;
+  if (p->pts_ws) {
+    cudaStreamSynchronize(p->stream);
+    cudaFree(p->pts_ws);
+    p->pts_ws = nullptr;
+    p->n_cap = 0;
+  }
+  void* w = nullptr;
+  cudaError_t e = cudaMalloc(&w, pts_ws_bytes(cap));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return DPSR_ENOMEM;
+  }
+  p->pts_ws = w;
+  p->n_cap = cap;
+  char* q = (char*)w;
+  p->s.sorted = (float4*)q;
+  q += align256(sizeof(float4) * 2 * cap);
+  p->s.cellx = (int*)q;
+  q += align256(sizeof(int) * cap);
+  p->s.gfwd = (float4*)q;
+  q += align256(sizeof(float4) * 2 * cap);
+  p->s.slots = (float*)q;
+  p->have_fwd = false;
+  return DPSR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dpsr_strerror(int st) {
+  switch (st) {
+    case DPSR_OK: return "ok";
+    case DPSR_EINVAL: return "invalid argument";
+    case DPSR_ENOMEM: return "device out of memory";
+    case DPSR_ECUDA: return "CUDA runtime error";
+    case DPSR_EDEGENERATE: return "degenerate input (non-finite value or vanishing scale chi'(0) - mu)";
+    case DPSR_ESTATE: return "invalid call order (backward without forward)";
+    case DPSR_ETIMEOUT: return "bounded device wait timed out";
+    case DPSR_EBUSY: return "resource busy";
+    default: return "unknown status";
+  }
+}
+
+size_t dpsr_plan_workspace_bytes(int r, int64_t n_max, int with_bwd) {
+  (void)with_bwd;  // the backward reuses the forward's buffers
+  if (!valid_r(r) || n_max < 0) return 0;
+  return grid_ws_bytes(r) + pts_ws_bytes(n_max > 0 ? n_max : 1);
+}
+
+int dpsr_plan_create(int r, float sigma, dpsr_plan* out) {
+  if (!out || !valid_r(r) || !(sigma >= 0.f) || !isfinite(sigma)) return DPSR_EINVAL;
+  *out = nullptr;
+  dpsr_plan p = new (std::nothrow) dpsr_plan_s();
+  if (!p) return DPSR_ENOMEM;
+  p->r = r;
+  p->sigma = sigma;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return DPSR_ECUDA;
+  }
+  for (int k = 0; k < 4; ++k) {
+    p->C[k] = pick_cluster(k, r);
+    if (!p->C[k]) {
+      delete p;
+      return DPSR_EINVAL;
+    }
+  }
+  p->grid_bytes = grid_ws_bytes(r);
+  if (cudaMalloc(&p->grid_ws, p->grid_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return DPSR_ENOMEM;
+  }
+  Solve& s = p->s;
+  s.r = r;
+  char* q = (char*)p->grid_ws;
+  for (int k = 0; k < 4; ++k) {
+    s.spec[k] = (float2*)q;
+    q += align256(spec_bytes(r));
+  }
+  float2* tw = (float2*)q;
+  q += align256(sizeof(float2) * r);
+  float* g1 = (float*)q;
+  q += align256(sizeof(float) * r);
+  float* u2 = (float*)q;
+  q += align256(sizeof(float) * r);
+  float* iu = (float*)q;
+  q += align256(sizeof(float) * r);
+  s.sc = (dpsr::Scalars*)q;
+  q += align256(sizeof(dpsr::Scalars));
+  s.status = (unsigned*)q;
+  q += align256(sizeof(unsigned));
+  s.part = (double*)q;
+  q += align256(sizeof(double) * 2 * part_count(r));
+  s.bins = (int*)q;
+  s.tw = tw;
+  s.g1 = g1;
+  s.u2 = u2;
+  s.iu = iu;
+  // Tables in FP64, rounded to FP32: twiddles exp(-2 pi i m / r); per-axis
+  // frequency u (integer cycles per unit length, |u| = r/2 at Nyquist), the
+  // per-axis factor of the Gaussian of Eq. 3, and the derivative factor u
+  // (zero at Nyquist).
+  float2* htw = (float2*)malloc(sizeof(float2) * r);
+  float* hg = (float*)malloc(sizeof(float) * 3 * r);
+  int rc = DPSR_OK;
+  if (!htw || !hg) {
+    rc = DPSR_ENOMEM;
+  } else {
+    const double pi = 3.14159265358979323846264338327950288;
+    for (int m = 0; m < r; ++m) {
+      const double ang = -2.0 * pi * (double)m / (double)r;
+      htw[m] = make_float2((float)cos(ang), (float)sin(ang));
+      const double u = m < r / 2 ? (double)m : (m == r / 2 ? (double)(r / 2) : (double)(m - r));
+      hg[m] = (float)exp(-2.0 * (double)sigma * (double)sigma * u * u / ((double)r * r));
+      hg[r + m] = (float)(u * u);
+      hg[2 * r + m] = m == r / 2 ? 0.f : (float)u;
+    }
+    if (cudaMemcpy(tw, htw, sizeof(float2) * r, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g1, hg, sizeof(float) * r, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(u2, hg + r, sizeof(float) * r, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(iu, hg + 2 * r, sizeof(float) * r, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(s.bins, 0, sizeof(int) * (3 * r + 1)) != cudaSuccess ||
+        cudaMemset(s.status, 0, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(s.sc, 0, sizeof(dpsr::Scalars)) != cudaSuccess)
+      rc = DPSR_ECUDA;
+  }
+  free(htw);
+  free(hg);
+  if (rc == DPSR_OK) rc = grow_points(p, 1024);
+  if (rc != DPSR_OK) {
+    cudaFree(p->grid_ws);
+    if (p->pts_ws) cudaFree(p->pts_ws);
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return DPSR_OK;
+}
+
+int dpsr_plan_destroy(dpsr_plan p) {
+  if (!p) return DPSR_EINVAL;
+  DeviceGuard dg(p->device);
+  cudaStreamSynchronize(p->stream);
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  cudaFree(p->grid_ws);
+  if (p->pts_ws) cudaFree(p->pts_ws);
+  if (p->host_io) cudaFree(p->host_io);
+  delete p;
+  return DPSR_OK;
+}
+
+int dpsr_plan_set_stream(dpsr_plan p, void* stream) {
+  if (!p) return DPSR_EINVAL;
+  p->stream = (cudaStream_t)stream;
+  return DPSR_OK;
+}
+
+int dpsr_plan_reserve(dpsr_plan p, int64_t n_max) {
+  if (!p || n_max < 1 || n_max > INT32_MAX / 2) return DPSR_EINVAL;
+  DeviceGuard dg(p->device);
+  if (!dg.ok) return DPSR_ECUDA;
+  return grow_points(p, n_max);
+}
+
+int dpsr_plan_last_launches(dpsr_plan p) { return p ? p->last_launches : -1; }
+
+int dpsr_plan_profile(dpsr_plan p, int enable) {
+  if (!p) return DPSR_EINVAL;
+  p->profile = enable != 0;
+  p->ev_used = 0;
+  p->ev_kind.clear();
+  return DPSR_OK;
+}
+
+int dpsr_plan_profile_read(dpsr_plan p, double* ms, int* launches) {
+  if (!p || !ms || !launches) return DPSR_EINVAL;
+  DeviceGuard dg(p->device);
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return DPSR_ECUDA;
+  for (int k = 0; k < DPSR_K_COUNT; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (size_t i = 0; i < p->ev_kind.size(); ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p->ev_pool[2 * i], p->ev_pool[2 * i + 1]) != cudaSuccess)
+      return DPSR_ECUDA;
+    ms[p->ev_kind[i]] += t;
+    launches[p->ev_kind[i]] += 1;
+  }
+  p->ev_used = 0;
+  p->ev_kind.clear();
+  return DPSR_OK;
+}
+
+int dpsr_forward(dpsr_plan p, const float* points, const float* normals, int64_t N,
+                 float* chi_out) {
+  if (!p || !points || !normals || !chi_out || N < 1 || N > INT32_MAX / 2) return DPSR_EINVAL;
+  DeviceGuard dg(p->device);
+  if (!dg.ok) return DPSR_ECUDA;
+  int rc = grow_points(p, N);
+  if (rc != DPSR_OK) return rc;
+  Solve s = p->s;
+  s.N = (int)N;
+  s.points = points;
+  s.normals = normals;
+  s.chi = chi_out;
+  const int r = p->r;
+  cudaStream_t st = p->stream;
+  cudaError_t e = cudaSuccess;
+  auto run = [&](int kind, auto&& fn) {
+    if (e == cudaSuccess) e = prof_mark(p, kind, true);
+    if (e == cudaSuccess) e = fn();
+    if (e == cudaSuccess) e = prof_mark(p, kind, false);
+  };
+  run(DPSR_K_BIN, [&] { return dpsr::launch_bin(s, nullptr, 1, (int)N, st); });
+  run(DPSR_K_PLANE_FWD, [&] { return dpsr::launch_plane(0, r, p->C[0], s, nullptr, 1, st); });
+  run(DPSR_K_XPASS_FWD, [&] { return dpsr::launch_xpass(false, r, s, nullptr, 1, st); });
+  run(DPSR_K_FINAL_FWD, [&] { return dpsr::launch_finalize(false, dpsr::xpass_blocks(r), s, nullptr, 1, st); });
+  run(DPSR_K_PLANE_INV, [&] { return dpsr::launch_plane(1, r, p->C[1], s, nullptr, 1, st); });
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p->have_fwd = false;
+    return cuda_err(e);
+  }
+  p->last_launches = 7;  // bin: 3 kernels, plane, xpass, finalize, inverse plane
+  p->s.N = s.N;
+  p->s.points = points;
+  p->s.normals = normals;
+  p->s.chi = chi_out;
+  p->have_fwd = true;
+  return DPSR_OK;
+}
+
+int dpsr_backward(dpsr_plan p, const float* dchi, float* dpoints, float* dnormals) {
+  if (!p || !dchi || !dpoints || !dnormals) return DPSR_EINVAL;
+  if (!p->have_fwd) return DPSR_ESTATE;
+  DeviceGuard dg(p->device);
+  if (!dg.ok) return DPSR_ECUDA;
+  Solve s = p->s;
+  s.dchi = dchi;
+  s.dpoints = dpoints;
+  s.dnormals = dnormals;
+  const int r = p->r;
+  cudaStream_t st = p->stream;
+  cudaError_t e = cudaSuccess;
+  auto run = [&](int kind, auto&& fn) {
+    if (e == cudaSuccess) e = prof_mark(p, kind, true);
+    if (e == cudaSuccess) e = fn();
+    if (e == cudaSuccess) e = prof_mark(p, kind, false);
+  };
+  run(DPSR_K_PLANE_BFWD, [&] { return dpsr::launch_plane(2, r, p->C[2], s, nullptr, 1, st); });
+  run(DPSR_K_FINAL_BWD, [&] { return dpsr::launch_finalize(true, r * p->C[2], s, nullptr, 1, st); });
+  run(DPSR_K_XPASS_BWD, [&] { return dpsr::launch_xpass(true, r, s, nullptr, 1, st); });
+  run(DPSR_K_PLANE_BINV, [&] { return dpsr::launch_plane(3, r, p->C[3], s, nullptr, 1, st); });
+  run(DPSR_K_COMBINE, [&] { return dpsr::launch_combine(s, nullptr, 1, s.N, st); });
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_err(e);
+  }
+  p->last_launches = 5;
+  return DPSR_OK;
+}
+
+int dpsr_sync(dpsr_plan p) {
+  if (!p) return DPSR_EINVAL;
+  DeviceGuard dg(p->device);
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return DPSR_ECUDA;
+  }
+  unsigned st = 0;
+  if (cudaMemcpy(&st, p->s.status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DPSR_ECUDA;
+  if (st) {
+    cudaMemset(p->s.status, 0, sizeof(unsigned));
+    return DPSR_EDEGENERATE;
+  }
+  return DPSR_OK;
+}
+
+int dpsr_get_scalars(dpsr_plan p, double out[3]) {
+  if (!p || !out) return DPSR_EINVAL;
+  if (!p->have_fwd) return DPSR_ESTATE;
+  DeviceGuard dg(p->device);
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return DPSR_ECUDA;
+  dpsr::Scalars sc;
+  if (cudaMemcpy(&sc, p->s.sc, sizeof(sc), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DPSR_ECUDA;
+  out[0] = sc.mu;
+  out[1] = sc.s;
+  out[2] = sc.alpha;
+  return DPSR_OK;
+}
+
+// Host-buffer variants: device staging owned by the plan.
+static int host_io_reserve(dpsr_plan p, int64_t N) {
+  const size_t need = align256(sizeof(float) * 3 * N) * 4 + align256(sizeof(float) * p->r * p->r * p->r) * 2;
+  if (need <= p->host_io_bytes) return DPSR_OK;
+  if (p->host_io) {
+    cudaStreamSynchronize(p->stream);
+    cudaFree(p->host_io);
+    p->host_io = nullptr;
+    p->host_io_bytes = 0;
+  }
+  if (cudaMalloc(&p->host_io, need) != cudaSuccess) {
+    cudaGetLastError();
+    return DPSR_ENOMEM;
+  }
+  p->host_io_bytes = need;
+  return DPSR_OK;
+}
+
+struct HostIo {
+  float *pts, *nrm, *dpts, *dnrm, *chi, *dchi;
+};
+static HostIo host_io_view(dpsr_plan p, int64_t N) {
+  HostIo v;
+  char* q = (char*)p->host_io;
+  const size_t a = align256(sizeof(float) * 3 * N), g = align256(sizeof(float) * p->r * p->r * p->r);
+  v.pts = (float*)q;
+  v.nrm = (float*)(q + a);
+  v.dpts = (float*)(q + 2 * a);
+  v.dnrm = (float*)(q + 3 * a);
+  v.chi = (float*)(q + 4 * a);
+  v.dchi = (float*)(q + 4 * a + g);
+  return v;
+}
+
+int dpsr_forward_host(dpsr_plan p, const float* points, const float* normals, int64_t N,
+                      float* chi_out) {
+  if (!p || !points || !normals || !chi_out || N < 1 || N > INT32_MAX / 2) return DPSR_EINVAL;
+  DeviceGuard dg(p->device);
+  if (!dg.ok) return DPSR_ECUDA;
+  int rc = host_io_reserve(p, N);
+  if (rc != DPSR_OK) return rc;
+  HostIo v = host_io_view(p, N);
+  const size_t nb = sizeof(float) * 3 * N, gb = sizeof(float) * p->r * p->r * p->r;
+  if (cudaMemcpyAsync(v.pts, points, nb, cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+      cudaMemcpyAsync(v.nrm, normals, nb, cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
+    return DPSR_ECUDA;
+  rc = dpsr_forward(p, v.pts, v.nrm, N, v.chi);
+  if (rc != DPSR_OK) return rc;
+  if (cudaMemcpyAsync(chi_out, v.chi, gb, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess)
+    return DPSR_ECUDA;
+  p->host_n = N;
+  return dpsr_sync(p);
+}
+
+int dpsr_backward_host(dpsr_plan p, const float* dchi, float* dpoints, float* dnormals) {
+  if (!p || !dchi || !dpoints || !dnormals) return DPSR_EINVAL;
+  if (!p->have_fwd || p->s.points != (const float*)host_io_view(p, p->host_n).pts)
+    return DPSR_ESTATE;
+  DeviceGuard dg(p->device);
+  if (!dg.ok) return DPSR_ECUDA;
+  const int64_t N = p->host_n;
+  HostIo v = host_io_view(p, N);
+  const size_t nb = sizeof(float) * 3 * N, gb = sizeof(float) * p->r * p->r * p->r;
+  if (cudaMemcpyAsync(v.dchi, dchi, gb, cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
+    return DPSR_ECUDA;
+  int rc = dpsr_backward(p, v.dchi, v.dpts, v.dnrm);
+  if (rc != DPSR_OK) return rc;
+  if (cudaMemcpyAsync(dpoints, v.dpts, nb, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+      cudaMemcpyAsync(dnormals, v.dnrm, nb, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess)
+    return DPSR_ECUDA;
+  return dpsr_sync(p);
+}
+
+}  // extern "C"

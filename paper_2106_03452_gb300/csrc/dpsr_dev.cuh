@@ -1,0 +1,289 @@
+// Device-side building blocks of libdpsr: complex arithmetic, small DFTs in
+// registers, the group FFT used by every pass, the per-solve descriptor and
+// the trilinear stencil of the point rasterization (Eq. A1).
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace dpsr {
+namespace cg = cooperative_groups;
+
+constexpr int kNT = 256;  // threads of the plane kernels
+constexpr float kM = 0.5f;  // m of Eq. 2
+
+// ---------------------------------------------------------------------------
+// complex helpers (float2 = re, im)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// a * (i u) for real u
+__device__ __forceinline__ float2 cmul_iu(float2 a, float u) { return make_float2(-a.y * u, a.x * u); }
+__device__ __forceinline__ float2 czero() { return make_float2(0.f, 0.f); }
+
+// ---------------------------------------------------------------------------
+// compile-time loops
+// ---------------------------------------------------------------------------
+template <int I, int N, class F>
+__device__ __forceinline__ void sfor(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    sfor<I + 1, N>(f);
+  }
+}
+
+// cos / sin of 2*pi*q/16: the sixteenth roots of unity.
+__host__ __device__ constexpr float cos16(int q) {
+  constexpr float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f,
+                  h = 0.70710678118654752440f;
+  switch (q & 15) {
+    case 0: return 1.f;   case 1: return c1;  case 2: return h;   case 3: return s1;
+    case 4: return 0.f;   case 5: return -s1; case 6: return -h;  case 7: return -c1;
+    case 8: return -1.f;  case 9: return -c1; case 10: return -h; case 11: return -s1;
+    case 12: return 0.f;  case 13: return s1; case 14: return h;  default: return c1;
+  }
+}
+__host__ __device__ constexpr float sin16(int q) { return cos16(q - 4); }
+
+// a * exp(DIR * 2 pi i q / 16), with the trivial factors folded at compile time.
+template <int Q, int DIR>
+__device__ __forceinline__ float2 twc(float2 a) {
+  constexpr int q = ((Q % 16) + 16) % 16;
+  if constexpr (q == 0) {
+    return a;
+  } else if constexpr (q == 8) {
+    return make_float2(-a.x, -a.y);
+  } else if constexpr (q == 4 || q == 12) {
+    constexpr float s = DIR * sin16(q);  // +-1
+    return make_float2(-a.y * s, a.x * s);
+  } else if constexpr ((q & 3) == 2) {
+    constexpr float c = cos16(q), s = DIR * sin16(q);  // |c| == |s|
+    const float p = (c == s) ? (a.x - a.y) : (a.x + a.y);
+    const float m = (c == s) ? (a.x + a.y) : (a.y - a.x);
+    return make_float2(p * c, m * c);
+  } else {
+    constexpr float c = cos16(q), s = DIR * sin16(q);
+    return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+  }
+}
+
+// In-register DFT of E points (E = 1, 2, 4, 8, 16), natural order in and out,
+// exponent sign DIR (-1 forward, +1 inverse), unnormalised. Radix-2
+// decimation in time, fully unrolled.
+template <int E, int DIR>
+struct Dft {
+  static __device__ __forceinline__ void run(float2* v) {
+    float2 ev[E / 2], od[E / 2];
+    sfor<0, E / 2>([&](auto i) {
+      ev[i] = v[2 * i];
+      od[i] = v[2 * i + 1];
+    });
+    Dft<E / 2, DIR>::run(ev);
+    Dft<E / 2, DIR>::run(od);
+    sfor<0, E / 2>([&](auto k) {
+      constexpr int q = decltype(k)::value * (16 / E);
+      const float2 t = twc<q, DIR>(od[k]);
+      v[k] = cadd(ev[k], t);
+      v[k + E / 2] = csub(ev[k], t);
+    });
+  }
+};
+template <int DIR>
+struct Dft<1, DIR> {
+  static __device__ __forceinline__ void run(float2*) {}
+};
+
+// ---------------------------------------------------------------------------
+// Group FFT of length L by T threads, each holding R1 = L / T values.
+// Distribution (in and out): thread t holds element t + T*j in v[j].
+// Two Cooley-Tukey stages L = R1 * T: an R1-point DFT per thread over the
+// stride-T subsequence, a twiddle W_L^(t*k1), an exchange through shared
+// memory (XOR-swizzled so neither side conflicts), and T-point DFTs.
+// tw[m] = exp(-2 pi i m / L), m < L (FP64-computed, rounded to FP32).
+// xch: L float2 of shared memory owned by the group. Every lane of the warp
+// must call this together (it uses __syncwarp).
+// ---------------------------------------------------------------------------
+template <int L> struct Shape;
+template <> struct Shape<8>   { static constexpr int R1 = 8,  T = 1; };
+template <> struct Shape<16>  { static constexpr int R1 = 16, T = 1; };
+template <> struct Shape<32>  { static constexpr int R1 = 8,  T = 4; };
+template <> struct Shape<64>  { static constexpr int R1 = 8,  T = 8; };
+template <> struct Shape<128> { static constexpr int R1 = 16, T = 8; };
+template <> struct Shape<256> { static constexpr int R1 = 16, T = 16; };
+
+template <int L, int DIR>
+__device__ __forceinline__ void fft(float2 (&v)[Shape<L>::R1], int t, float2* xch,
+                                    const float2* tw) {
+  constexpr int R1 = Shape<L>::R1, T = Shape<L>::T;
+  if constexpr (T == 1) {
+    Dft<L, DIR>::run(v);
+  } else {
+    Dft<R1, DIR>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) {
+      float2 w = tw[t * k1];
+      if (DIR > 0) w.y = -w.y;
+      v[k1] = cmul(v[k1], w);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) xch[k1 * T + (t ^ (k1 % T))] = v[k1];
+    __syncwarp();
+    constexpr int M = R1 / T;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      float2 u[T];
+      const int k1 = t + T * m;
+#pragma unroll
+      for (int n2 = 0; n2 < T; ++n2) u[n2] = xch[k1 * T + (n2 ^ t)];
+      Dft<T, DIR>::run(u);
+#pragma unroll
+      for (int k2 = 0; k2 < T; ++k2) v[m + M * k2] = u[k2];
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Real <-> half-complex pairs. Two real rows a, b of length L are packed as
+// z = a + i b and transformed together. Half spectra are stored "packed":
+// slot 0 holds (A[0], A[L/2]) (both real for a real row), slots 1..L/2-1 hold
+// A[1..L/2-1].
+// ---------------------------------------------------------------------------
+// Forward: ld(k) -> z[k]; sa(slot, A), sb(slot, B).
+template <int L, class Ld, class StA, class StB>
+__device__ __forceinline__ void r2c_pair(int t, float2* xch, const float2* tw, Ld ld, StA sa,
+                                         StB sb) {
+  constexpr int R1 = Shape<L>::R1, T = Shape<L>::T, H = L / 2;
+  float2 v[R1];
+#pragma unroll
+  for (int j = 0; j < R1; ++j) v[j] = ld(t + T * j);
+  fft<L, -1>(v, t, xch, tw);
+#pragma unroll
+  for (int j = 0; j < R1; ++j) xch[t + T * j] = v[j];
+  __syncwarp();
+  float2 A[R1 / 2], B[R1 / 2];
+#pragma unroll
+  for (int j = 0; j < R1 / 2; ++j) {
+    const int k = t + T * j;
+    if (k == 0) {
+      const float2 z0 = xch[0], zn = xch[H];
+      A[j] = make_float2(z0.x, zn.x);
+      B[j] = make_float2(z0.y, zn.y);
+    } else {
+      const float2 zk = xch[k], zm = cconj(xch[L - k]);
+      A[j] = cscale(cadd(zk, zm), 0.5f);
+      const float2 d = csub(zk, zm);  // B = -i d / 2
+      B[j] = make_float2(0.5f * d.y, -0.5f * d.x);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < R1 / 2; ++j) {
+    sa(t + T * j, A[j]);
+    sb(t + T * j, B[j]);
+  }
+}
+
+// Inverse: la(slot) -> packed A, lb(slot) -> packed B; st(z, (a[z], b[z]))
+// with the unnormalised inverse transform (values times L).
+template <int L, class LdA, class LdB, class St>
+__device__ __forceinline__ void c2r_pair(int t, float2* xch, const float2* tw, LdA la, LdB lb,
+                                         St st) {
+  constexpr int R1 = Shape<L>::R1, T = Shape<L>::T, H = L / 2;
+  float2 v[R1];
+#pragma unroll
+  for (int j = 0; j < R1; ++j) {
+    const int k = t + T * j;
+    if (k == 0 || k == H) {
+      const float2 a = la(0), b = lb(0);
+      v[j] = (k == 0) ? make_float2(a.x, b.x) : make_float2(a.y, b.y);
+    } else if (k < H) {
+      const float2 a = la(k), b = lb(k);
+      v[j] = make_float2(a.x - b.y, a.y + b.x);
+    } else {
+      const float2 a = la(L - k), b = lb(L - k);
+      v[j] = make_float2(a.x + b.y, b.x - a.y);
+    }
+  }
+  fft<L, +1>(v, t, xch, tw);
+#pragma unroll
+  for (int j = 0; j < R1; ++j) st(t + T * j, v[j]);
+}
+
+// Separate a packed column P = X0 + i Xn of two spectra whose inverse is real:
+// X0[k] = (P[k] + conj(P[-k])) / 2, Xn[k] = -i (P[k] - conj(P[-k])) / 2.
+__device__ __forceinline__ void unpack_dc_nyq(float2 pk, float2 pm, float2& x0, float2& xn) {
+  const float2 cm = cconj(pm);
+  x0 = cscale(cadd(pk, cm), 0.5f);
+  const float2 d = csub(pk, cm);
+  xn = make_float2(0.5f * d.y, -0.5f * d.x);
+}
+
+// ---------------------------------------------------------------------------
+// Per-solve descriptor. All pointers are device pointers.
+// ---------------------------------------------------------------------------
+struct Scalars {
+  double acc_mu, acc_s0;  // spectral sums of the forward pass
+  double mu, s, alpha;    // Eq. 4
+  double S, D, s_bar, mu_bar;
+  float a_chi, b_chi;     // chi = a_chi * y + b_chi, y = unnormalised inverse FFT
+  float g_a, g_s, g_w;    // backward: G^ = g_a * FFT(dchi) + g_s + g_w * W^
+  float c_mu;             // backward: weight of the stored lookup gradient
+};
+
+struct Solve {
+  int r;
+  int N;
+  // per call (caller-owned)
+  const float* points;
+  const float* normals;
+  float* chi;
+  const float* dchi;
+  float* dpoints;
+  float* dnormals;
+  // plan workspace
+  float4* sorted;   // 2 records per point: (x, y, z, nx), (ny, nz, orig, 0)
+  int* cellx;       // N
+  int* bins;        // count[r], off[r + 1], cursor[r]
+  float2* spec[4];  // r * r * (r/2 + 2) complex each
+  float4* gfwd;     // [2][N]: gradient of the lookup of y, per plane side
+  float* slots;     // [2][N][6]: backward partials per plane side
+  double* part;     // per-block partial sums
+  Scalars* sc;
+  unsigned* status;
+  const float2* tw;  // r
+  const float* g1;   // r: exp(-2 sigma^2 u^2 / r^2)
+  const float* u2;   // r: u^2 (|u| = r/2 at Nyquist)
+  const float* iu;   // r: u, 0 at Nyquist (factor of the spectral derivative)
+};
+
+enum : unsigned { kStBadInput = 1u, kStDegenerate = 2u };
+
+__host__ __device__ constexpr int kpitch(int r) { return r / 2 + 2; }
+
+// Trilinear stencil along one axis (Eq. A1, floor cell, periodic wrap):
+// x~ = c r (exact for r a power of two), i0 = floor(x~) mod r, t = x~ - floor(x~).
+struct Axis {
+  int i0, i1;
+  float t;
+};
+__device__ __forceinline__ Axis axis_of(float c, int r) {
+  const float x = c * (float)r;
+  const float f = floorf(x);
+  Axis a;
+  a.t = x - f;
+  const int i = (int)f;
+  a.i0 = i & (r - 1);
+  a.i1 = (i + 1) & (r - 1);
+  return a;
+}
+
+}  // namespace dpsr

@@ -1,0 +1,126 @@
+// Point kernels: bucketing of the points by the x-cell of their trilinear
+// stencil (a counting sort, so that each x-plane cluster reads only the points
+// that touch its plane), and the final combine of the backward pass.
+#include "dpsr_dev.cuh"
+#include "launch.h"
+
+namespace dpsr {
+
+__device__ __forceinline__ bool coord_ok(float c, int r) {
+  return isfinite(c) && fabsf(c * (float)r) < 1073741824.f;  // |c r| < 2^30
+}
+
+// count[i0x]++ per point; validates the inputs (non-finite or huge values
+// raise kStBadInput and are replaced by 0 so that indexing stays in range).
+__global__ void __launch_bounds__(256) k_bin_count(const __grid_constant__ Solve s0,
+                                                   const Solve* __restrict__ tab) {
+  const Solve& S = tab ? tab[blockIdx.z] : s0;
+  __shared__ int h[256];
+  const int r = S.r;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  bool bad = false;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < S.N; p += gridDim.x * blockDim.x) {
+    float x = S.points[3 * p];
+    const float y = S.points[3 * p + 1], z = S.points[3 * p + 2];
+    const float nx = S.normals[3 * p], ny = S.normals[3 * p + 1], nz = S.normals[3 * p + 2];
+    if (!(coord_ok(x, r) && coord_ok(y, r) && coord_ok(z, r) && isfinite(nx) && isfinite(ny) &&
+          isfinite(nz))) {
+      bad = true;
+      if (!coord_ok(x, r)) x = 0.f;
+    }
+    const int ix = axis_of(x, r).i0;
+    S.cellx[p] = ix;
+    atomicAdd(&h[ix], 1);
+  }
+  if (bad) atomicOr(S.status, kStBadInput);
+  __syncthreads();
+  for (int i = threadIdx.x; i < r; i += blockDim.x)
+    if (h[i]) atomicAdd(&S.bins[i], h[i]);
+}
+
+// Exclusive scan of the r counts into off[0..r] and the scatter cursors.
+__global__ void __launch_bounds__(256) k_bin_scan(const __grid_constant__ Solve s0,
+                                                  const Solve* __restrict__ tab) {
+  const Solve& S = tab ? tab[blockIdx.x] : s0;
+  __shared__ int v[256];
+  const int r = S.r, i = threadIdx.x;
+  int* count = S.bins;
+  int* off = S.bins + r;
+  int* cur = S.bins + 2 * r + 1;
+  v[i] = i < r ? count[i] : 0;
+  __syncthreads();
+  for (int d = 1; d < 256; d <<= 1) {  // Hillis-Steele inclusive scan
+    const int add = i >= d ? v[i - d] : 0;
+    __syncthreads();
+    v[i] += add;
+    __syncthreads();
+  }
+  if (i < r) {
+    const int ex = v[i] - count[i];
+    off[i] = ex;
+    cur[i] = ex;
+    count[i] = 0;  // ready for the next call
+  }
+  if (i == r - 1) off[r] = v[i];
+}
+
+__global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Solve s0,
+                                                     const Solve* __restrict__ tab) {
+  const Solve& S = tab ? tab[blockIdx.z] : s0;
+  const int r = S.r;
+  int* cur = S.bins + 2 * r + 1;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < S.N; p += gridDim.x * blockDim.x) {
+    float x = S.points[3 * p], y = S.points[3 * p + 1], z = S.points[3 * p + 2];
+    float nx = S.normals[3 * p], ny = S.normals[3 * p + 1], nz = S.normals[3 * p + 2];
+    if (!coord_ok(x, r)) x = 0.f;
+    if (!coord_ok(y, r)) y = 0.f;
+    if (!coord_ok(z, r)) z = 0.f;
+    if (!isfinite(nx)) nx = 0.f;
+    if (!isfinite(ny)) ny = 0.f;
+    if (!isfinite(nz)) nz = 0.f;
+    const int pos = atomicAdd(&cur[S.cellx[p]], 1);
+    S.sorted[2 * pos] = make_float4(x, y, z, nx);
+    S.sorted[2 * pos + 1] = make_float4(ny, nz, __int_as_float(p), 0.f);
+  }
+}
+
+cudaError_t launch_bin(const Solve& s, const Solve* tab, int count, int nmax, cudaStream_t st) {
+  const int blocks = min(max((nmax + 255) / 256, 1), 1184);
+  k_bin_count<<<dim3(blocks, 1, count), 256, 0, st>>>(s, tab);
+  k_bin_scan<<<count, 256, 0, st>>>(s, tab);
+  k_bin_scatter<<<dim3(blocks, 1, count), 256, 0, st>>>(s, tab);
+  return cudaGetLastError();
+}
+
+// dpoints = sum of the two plane sides of the weight-derivative terms
+//           + (mu_bar / (N n)) * gradient of the lookup of y (Eq. 4 adjoint);
+// dnormals = sum of the two plane sides of the gather. Written in the
+// caller's point order.
+__global__ void __launch_bounds__(256) k_combine(const __grid_constant__ Solve s0,
+                                                 const Solve* __restrict__ tab) {
+  const Solve& S = tab ? tab[blockIdx.z] : s0;
+  const float c_mu = S.sc->c_mu;
+  const size_t N = S.N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.N; i += gridDim.x * blockDim.x) {
+    const int orig = __float_as_int(S.sorted[2 * i + 1].z);
+    const float* a = S.slots + (size_t)i * 6;
+    const float* b = S.slots + (N + i) * 6;
+    const float4 ga = S.gfwd[i], gb = S.gfwd[N + i];
+    S.dnormals[3 * orig] = a[0] + b[0];
+    S.dnormals[3 * orig + 1] = a[1] + b[1];
+    S.dnormals[3 * orig + 2] = a[2] + b[2];
+    S.dpoints[3 * orig] = (a[3] + b[3]) + c_mu * (ga.x + gb.x);
+    S.dpoints[3 * orig + 1] = (a[4] + b[4]) + c_mu * (ga.y + gb.y);
+    S.dpoints[3 * orig + 2] = (a[5] + b[5]) + c_mu * (ga.z + gb.z);
+  }
+}
+
+cudaError_t launch_combine(const Solve& s, const Solve* tab, int count, int nmax,
+                           cudaStream_t st) {
+  const int blocks = min(max((nmax + 255) / 256, 1), 1184);
+  k_combine<<<dim3(blocks, 1, count), 256, 0, st>>>(s, tab);
+  return cudaGetLastError();
+}
+
+}  // namespace dpsr

@@ -1,0 +1,24 @@
+// Internal launchers of libdpsr (host side). Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "dpsr_dev.cuh"
+
+namespace dpsr {
+
+// Plane kernels: kind 0 = forward splat/z/y, 1 = forward inverse y/z + lookup
+// gradient, 2 = backward z/y of dchi, 3 = backward inverse y/z + point adjoint.
+cudaError_t launch_plane(int kind, int r, int C, const Solve& s, const Solve* tab, int count,
+                         cudaStream_t st);
+size_t plane_smem_bytes(int kind, int r, int C);
+cudaError_t launch_xpass(bool bwd, int r, const Solve& s, const Solve* tab, int count,
+                         cudaStream_t st);
+int xpass_blocks(int r);
+cudaError_t launch_finalize(bool bwd, int nparts, const Solve& s, const Solve* tab, int count,
+                            cudaStream_t st);
+// Points: x-plane bucketing (count, scan, scatter) and the backward combine.
+cudaError_t launch_bin(const Solve& s, const Solve* tab, int count, int nmax, cudaStream_t st);
+cudaError_t launch_combine(const Solve& s, const Solve* tab, int count, int nmax,
+                           cudaStream_t st);
+
+}  // namespace dpsr

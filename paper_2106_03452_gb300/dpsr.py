@@ -1,0 +1,118 @@
+"""PyTorch-facing API of libdpsr: a Plan object holding the device workspace
+for one grid size, and DPSRFunction, a torch.autograd.Function whose forward
+and backward are the library's hand-written kernels (Sec. 3.1 of Shape As
+Points and its exact adjoint). PyTorch provides device memory and streams
+only; CPU tensors are rejected.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import libdpsr as L
+
+
+def _dev_f32(t: torch.Tensor, name: str, shape=None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor (libdpsr has no CPU path)")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.contiguous()
+
+
+class Plan:
+    """A libdpsr plan: grid size r (power of two in [8, 256]) and Gaussian
+    bandwidth sigma (Eq. 3). Owns its device workspace; keeps the context of
+    its last forward pass for the backward pass."""
+
+    def __init__(self, r: int, sigma: float = 2.0, device=None, n_max: int | None = None):
+        self.r, self.sigma = int(r), float(sigma)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(self.device):
+            self.handle = L.dpsr_plan_create(self.r, self.sigma)
+            if n_max:
+                L.dpsr_plan_reserve(self.handle, int(n_max))
+        self._saved = None
+        self.generation = 0
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.dpsr_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _bind_stream(self):
+        L.dpsr_plan_set_stream(self.handle, torch.cuda.current_stream(self.device).cuda_stream)
+
+    def forward(self, points: torch.Tensor, normals: torch.Tensor, chi_out=None) -> torch.Tensor:
+        points = _dev_f32(points, "points")
+        normals = _dev_f32(normals, "normals", points.shape)
+        if points.dim() != 2 or points.shape[1] != 3:
+            raise ValueError("points must be N x 3")
+        r = self.r
+        if chi_out is None:
+            chi_out = torch.empty((r, r, r), device=points.device, dtype=torch.float32)
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            L.dpsr_forward(self.handle, points.data_ptr(), normals.data_ptr(), points.shape[0],
+                           chi_out.data_ptr())
+        # the backward reads these buffers: keep them alive
+        self._saved = (points, normals, chi_out)
+        self.generation += 1
+        return chi_out
+
+    def backward(self, dchi: torch.Tensor, dpoints=None, dnormals=None):
+        if self._saved is None:
+            raise L.DPSRError(L.DPSR_ESTATE, "dpsr_backward")
+        points = self._saved[0]
+        dchi = _dev_f32(dchi, "dchi", (self.r,) * 3)
+        if dpoints is None:
+            dpoints = torch.empty_like(points)
+        if dnormals is None:
+            dnormals = torch.empty_like(points)
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            L.dpsr_backward(self.handle, dchi.data_ptr(), dpoints.data_ptr(), dnormals.data_ptr())
+        return dpoints, dnormals
+
+    def sync(self) -> int:
+        return L.dpsr_sync(self.handle)
+
+    def check(self) -> None:
+        L.check(self.sync(), "dpsr device status")
+
+    def scalars(self):
+        """(mu, s, m/|s|) of the last forward pass (Eq. 4)."""
+        return L.dpsr_get_scalars(self.handle)
+
+    def last_launches(self) -> int:
+        return L.dpsr_plan_last_launches(self.handle)
+
+
+class DPSRFunction(torch.autograd.Function):
+    """chi = DPSR(points, normals) with the library's adjoint as backward."""
+
+    @staticmethod
+    def forward(ctx, points, normals, plan: Plan):
+        chi = plan.forward(points.detach(), normals.detach())
+        ctx.plan = plan
+        ctx.generation = plan.generation
+        return chi
+
+    @staticmethod
+    def backward(ctx, dchi):
+        if ctx.plan.generation != ctx.generation:
+            raise RuntimeError("the plan ran another forward pass since this one: one pending "
+                               "backward per plan (use one Plan per graph node)")
+        dp, dn = ctx.plan.backward(dchi.contiguous())
+        return dp, dn, None
+
+
+def dpsr(points: torch.Tensor, normals: torch.Tensor, plan: Plan) -> torch.Tensor:
+    return DPSRFunction.apply(points, normals, plan)

@@ -1,0 +1,149 @@
+"""ctypes binding of libdpsr (include/dpsr.h): the same entry points under the
+same names, argument marshalling only. Every step of the computation runs in
+the library's CUDA kernels; there is no CPU path.
+
+The shared library is built in-tree by ``paper_2106_03452_gb300.build`` (or
+``__graft_entry__.build()``); loading fails loudly when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdpsr.so")
+_lock = threading.Lock()
+_lib = None
+
+DPSR_OK = 0
+DPSR_EINVAL = -1
+DPSR_ENOMEM = -2
+DPSR_ECUDA = -3
+DPSR_EDEGENERATE = -4
+DPSR_ESTATE = -5
+DPSR_ETIMEOUT = -6
+DPSR_EBUSY = -7
+
+_c_int, _c_i64, _c_sz, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p
+_PROTOS = {
+    "dpsr_plan_create": (_c_int, [_c_int, ctypes.c_float, ctypes.POINTER(_vp)]),
+    "dpsr_plan_destroy": (_c_int, [_vp]),
+    "dpsr_plan_set_stream": (_c_int, [_vp, _vp]),
+    "dpsr_plan_reserve": (_c_int, [_vp, _c_i64]),
+    "dpsr_plan_workspace_bytes": (_c_sz, [_c_int, _c_i64, _c_int]),
+    "dpsr_forward": (_c_int, [_vp, _vp, _vp, _c_i64, _vp]),
+    "dpsr_backward": (_c_int, [_vp, _vp, _vp, _vp]),
+    "dpsr_forward_host": (_c_int, [_vp, _vp, _vp, _c_i64, _vp]),
+    "dpsr_backward_host": (_c_int, [_vp, _vp, _vp, _vp]),
+    "dpsr_sync": (_c_int, [_vp]),
+    "dpsr_get_scalars": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
+    "dpsr_plan_last_launches": (_c_int, [_vp]),
+    "dpsr_strerror": (ctypes.c_char_p, [_c_int]),
+    "dpsr_plan_profile": (_c_int, [_vp, _c_int]),
+    "dpsr_plan_profile_read": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_int)]),
+}
+
+KERNEL_KINDS = ["bin", "plane_fwd", "xpass_fwd", "final_fwd", "plane_inv", "plane_bfwd", "final_bwd",
+                "xpass_bwd", "plane_binv", "combine"]
+
+
+class DPSRError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        msg = load().dpsr_strerror(code).decode() if code is not None else "?"
+        super().__init__(f"{what}: {msg} (status {code})")
+        self.code = code
+
+
+def load():
+    """Load the in-tree libdpsr.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"libdpsr is not built ({LIB_PATH} missing): run "
+                    "`python -m paper_2106_03452_gb300.build` (needs nvcc); there is no CPU fallback")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _PROTOS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def check(code: int, what: str) -> None:
+    if code != DPSR_OK:
+        raise DPSRError(code, what)
+
+
+# Same-named thin wrappers.
+def dpsr_plan_create(r: int, sigma: float) -> int:
+    h = _vp()
+    check(load().dpsr_plan_create(int(r), float(sigma), ctypes.byref(h)), "dpsr_plan_create")
+    return h.value
+
+
+def dpsr_plan_destroy(plan: int) -> None:
+    check(load().dpsr_plan_destroy(plan), "dpsr_plan_destroy")
+
+
+def dpsr_plan_set_stream(plan: int, stream: int) -> None:
+    check(load().dpsr_plan_set_stream(plan, stream), "dpsr_plan_set_stream")
+
+
+def dpsr_plan_reserve(plan: int, n_max: int) -> None:
+    check(load().dpsr_plan_reserve(plan, int(n_max)), "dpsr_plan_reserve")
+
+
+def dpsr_plan_workspace_bytes(r: int, n_max: int, with_bwd: bool = True) -> int:
+    return int(load().dpsr_plan_workspace_bytes(int(r), int(n_max), 1 if with_bwd else 0))
+
+
+def dpsr_forward(plan: int, points: int, normals: int, N: int, chi_out: int) -> None:
+    check(load().dpsr_forward(plan, points, normals, int(N), chi_out), "dpsr_forward")
+
+
+def dpsr_backward(plan: int, dchi: int, dpoints: int, dnormals: int) -> None:
+    check(load().dpsr_backward(plan, dchi, dpoints, dnormals), "dpsr_backward")
+
+
+def dpsr_forward_host(plan: int, points: int, normals: int, N: int, chi_out: int) -> None:
+    check(load().dpsr_forward_host(plan, points, normals, int(N), chi_out), "dpsr_forward_host")
+
+
+def dpsr_backward_host(plan: int, dchi: int, dpoints: int, dnormals: int) -> None:
+    check(load().dpsr_backward_host(plan, dchi, dpoints, dnormals), "dpsr_backward_host")
+
+
+def dpsr_sync(plan: int) -> int:
+    """Returns the device status (DPSR_OK or an error code) without raising."""
+    return int(load().dpsr_sync(plan))
+
+
+def dpsr_get_scalars(plan: int):
+    out = (ctypes.c_double * 3)()
+    check(load().dpsr_get_scalars(plan, out), "dpsr_get_scalars")
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def dpsr_plan_last_launches(plan: int) -> int:
+    return int(load().dpsr_plan_last_launches(plan))
+
+
+def dpsr_strerror(code: int) -> str:
+    return load().dpsr_strerror(int(code)).decode()
+
+
+def dpsr_plan_profile(plan: int, enable: bool) -> None:
+    check(load().dpsr_plan_profile(plan, 1 if enable else 0), "dpsr_plan_profile")
+
+
+def dpsr_plan_profile_read(plan: int):
+    """{kind: (total_ms, launches)} since profiling was enabled or last read."""
+    n = len(KERNEL_KINDS)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int * n)()
+    check(load().dpsr_plan_profile_read(plan, ms, cnt), "dpsr_plan_profile_read")
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_KINDS)}

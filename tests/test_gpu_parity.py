@@ -1,0 +1,138 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, on the
+same seeded FP32 inputs. Tolerances: chi within max|d chi| / max|chi| <= 1e-5;
+dpoints and dnormals within max|d| / max|ref| <= 1e-4 per tensor."""
+import numpy as np
+import pytest
+
+from paper_2106_03452_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_CHI = 1e-5
+TOL_GRAD = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_03452_gb300 import build
+    build.build()
+
+
+def _check(oracle, r, sigma, pts, nrm, dchi, tol_chi=TOL_CHI, tol_grad=TOL_GRAD):
+    from gpu_util import gpu_fwd_bwd, relmax
+    g = gpu_fwd_bwd(r, sigma, pts, nrm, dchi)
+    assert g["status"] == 0
+    chi, chip, mu, s = oracle.forward(r, sigma, pts.astype(np.float64), nrm.astype(np.float64), full=True)
+    e = relmax(g["chi"], chi)
+    assert e <= tol_chi, f"chi parity {e:.3e}"
+    gmu, gs, galpha = g["scalars"]
+    assert abs(gmu - mu) <= 1e-5 * np.max(np.abs(chip)) and abs(gs - s) <= 1e-5 * abs(s) + 1e-6 * np.max(np.abs(chip))
+    if dchi is not None:
+        assert g["bstatus"] == 0
+        dp, dn, dm = oracle.backward(r, sigma, pts.astype(np.float64), nrm.astype(np.float64),
+                                     dchi.astype(np.float64), mean_term=True)
+        en = relmax(g["dnormals"], dn)
+        assert en <= tol_grad, f"dnormals parity {en:.3e}"
+        # dpoints is the sum of the part through the mean of Eq. 4 (dm) and the
+        # rest (dp - dm). With a handful of points the two nearly cancel, so an
+        # FP32 sum is only accurate to ~1e-6 of the larger part: the bound is
+        # 1e-4 of the result plus 2e-6 of the parts (the second term matters
+        # only when the cancellation exceeds 50x, i.e. for N of order 1).
+        scale = max(np.max(np.abs(dm)), np.max(np.abs(dp - dm)))
+        err = np.max(np.abs(g["dpoints"] - dp))
+        bound = tol_grad * np.max(np.abs(dp)) + 2e-6 * scale
+        assert err <= bound, f"dpoints parity {err / np.max(np.abs(dp)):.3e} (bound {bound:.3e})"
+    return g
+
+
+@pytest.mark.parametrize("r", [8, 16, 32, 64])
+@pytest.mark.parametrize("N,sigma", [(1, 2.0), (7, 0.0), (333, 2.0), (2049, 1.5)])
+def test_random_clouds(oracle, r, N, sigma):
+    rng = synth.Rng(1000 * r + N)
+    pts = (rng.uniform(N, 3) * 1.4 - 0.2).astype(np.float32)   # wraps around the unit cube
+    nrm = rng.normal(N, 3).astype(np.float32)
+    dchi = rng.normal(r, r, r).astype(np.float32)
+    _check(oracle, r, sigma, pts, nrm, dchi)
+
+
+def test_points_on_vertices_and_faces(oracle):
+    r = 32
+    rng = synth.Rng(4)
+    N = 500
+    pts = rng.uniform(N, 3)
+    pts[:100] = np.floor(pts[:100] * r) / r            # exactly on vertices
+    pts[100:200, 0] = np.floor(pts[100:200, 0] * r) / r  # on x faces
+    pts[200:210] = 0.0
+    pts[210:220] = np.float32(1.0) - np.float32(2 ** -24)  # just below 1
+    pts[220:230] = -np.float32(2 ** -20)                 # just below 0
+    nrm = rng.normal(N, 3)
+    nrm[300:350] = 0.0                                   # muted points (zero normals)
+    dchi = rng.normal(r, r, r)
+    _check(oracle, r, 2.0, pts.astype(np.float32), nrm.astype(np.float32), dchi.astype(np.float32))
+
+
+def test_sphere_r32(oracle):
+    w = synth.workload_sphere_r32()
+    _check(oracle, w["r"], w["sigma"], w["points"], w["normals"], w["dchi"])
+
+
+def test_ellipsoids_r128(oracle):
+    w = synth.workload_ellipsoids_r128()
+    _check(oracle, w["r"], w["sigma"], w["points"], w["normals"], w["dchi"])
+
+
+def test_torus_r256(oracle):
+    w = synth.workload_torus_r256()
+    dchi = synth.upstream_grad(synth.Rng(77), 256)
+    _check(oracle, w["r"], w["sigma"], w["points"], w["normals"], dchi)
+
+
+def test_degenerate_and_errors():
+    import torch
+    from paper_2106_03452_gb300 import libdpsr as L
+    from paper_2106_03452_gb300.dpsr import Plan
+    plan = Plan(32, 2.0)
+    with pytest.raises(L.DPSRError) as e:
+        plan.backward(torch.zeros(32, 32, 32, device="cuda"))
+    assert e.value.code == L.DPSR_ESTATE
+    P = torch.full((16, 3), 0.5, device="cuda")
+    chi = plan.forward(P, torch.zeros(16, 3, device="cuda"))
+    assert plan.sync() == L.DPSR_EDEGENERATE          # chi' = 0: no scale
+    P[3, 1] = float("nan")
+    plan.forward(P, torch.ones(16, 3, device="cuda"))
+    assert plan.sync() == L.DPSR_EDEGENERATE          # non-finite input
+    P[3, 1] = 0.25
+    plan.forward(P + torch.rand_like(P) * 0.1, torch.randn(16, 3, device="cuda"))
+    assert plan.sync() == L.DPSR_OK                   # status cleared, plan usable
+
+
+def test_autograd_function_and_host_api(oracle):
+    import torch
+    from paper_2106_03452_gb300 import libdpsr as L
+    from paper_2106_03452_gb300.dpsr import Plan, dpsr
+    w = synth.workload_sphere_r32(N=1500)
+    r = w["r"]
+    plan = Plan(r, w["sigma"])
+    P = torch.from_numpy(w["points"]).cuda().requires_grad_(True)
+    Nn = torch.from_numpy(w["normals"]).cuda().requires_grad_(True)
+    G = torch.from_numpy(w["dchi"]).cuda()
+    chi = dpsr(P, Nn, plan)
+    (chi * G).sum().backward()
+    dp, dn = oracle.backward(r, w["sigma"], w["points"], w["normals"], w["dchi"])
+    from gpu_util import relmax
+    assert relmax(P.grad.cpu().numpy(), dp) <= TOL_GRAD
+    assert relmax(Nn.grad.cpu().numpy(), dn) <= TOL_GRAD
+    # host-buffer entry points give the same numbers as the device ones
+    hp = np.ascontiguousarray(w["points"])
+    hn = np.ascontiguousarray(w["normals"])
+    hchi = np.zeros((r, r, r), np.float32)
+    L.dpsr_forward_host(plan.handle, hp.ctypes.data, hn.ctypes.data, hp.shape[0], hchi.ctypes.data)
+    assert relmax(hchi, chi.detach().cpu().numpy()) <= 1e-6
+    hg = np.ascontiguousarray(w["dchi"])
+    hdp = np.zeros_like(hp)
+    hdn = np.zeros_like(hn)
+    L.dpsr_backward_host(plan.handle, hg.ctypes.data, hdp.ctypes.data, hdn.ctypes.data)
+    assert relmax(hdp, P.grad.cpu().numpy()) <= 1e-5 and relmax(hdn, Nn.grad.cpu().numpy()) <= 1e-5
