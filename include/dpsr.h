@@ -141,6 +141,23 @@ enum {
 DPSR_API int dpsr_plan_profile(dpsr_plan plan, int enable);
 DPSR_API int dpsr_plan_profile_read(dpsr_plan plan, double *ms, int *launches);
 
+/* Forward pass for callers that cannot allocate device memory (code running
+ * where cudaMalloc is forbidden or would block, such as host callbacks,
+ * driver-level plugins with a fixed memory budget, or real-time loops that
+ * must not enter the allocator). The paper has no counterpart: this is a
+ * deployment variant of dpsr_forward. points, normals and chi_out are device
+ * pointers as in dpsr_forward; `stream` is a cudaStream_t (NULL = legacy).
+ * All scratch memory is one static device array of about 9.2 MB that every
+ * GPU loading the library holds until exit; the call allocates nothing.
+ * Limits: r a power of two with 8 <= r <= 64, 1 <= N <= 65536; anything
+ * larger returns DPSR_EINVAL. Every call shares the array and sees what the
+ * previous call left there, so calls that overlap on the GPU race: the call
+ * waits for its own work and returns the device status (DPSR_OK or
+ * DPSR_EDEGENERATE). The first call on a device looks up the array's device
+ * address; make that first call before any stream capture on that device. */
+DPSR_API int dpsr_forward_static(int r, float sigma, const float *points, const float *normals,
+                                 int64_t N, float *chi_out, void *stream);
+
 /* Static description of an error code. */
 DPSR_API const char *dpsr_strerror(int status);
 

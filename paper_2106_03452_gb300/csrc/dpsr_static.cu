@@ -1,0 +1,152 @@
+// dpsr_forward_static: the DPSR forward pass for callers that cannot allocate
+// device memory.
+//
+// Some callers cannot call cudaMalloc: code that runs inside a host callback
+// or a driver layer where allocation would deadlock or is forbidden, plugins
+// handed a fixed memory budget by a host application, and real-time loops
+// that must not hit the allocator's latency. For them this entry point runs
+// the same kernels as dpsr_forward, but all of its scratch memory lives in the
+// file-scope device array below, which every GPU that loads the library holds
+// until the process exits. It calls no cudaMalloc, cudaFree or allocating
+// library routine.
+//
+// Limits: r <= 64 and N <= 65536 (the array is sized for exactly that).
+// Larger sizes are rejected with DPSR_EINVAL.
+//
+// Sharing: every call, on every stream, uses the same array, and the array
+// keeps what the last call left in it. Calls that overlap on the GPU race on
+// it and corrupt each other's results; this entry point therefore waits for
+// its own work to finish before it returns. What must start at zero (the bin
+// counters and the status word) is cleared at the start of each call.
+//
+// Set-up: the first call on a device looks up the device address of the
+// array (cudaGetSymbolAddress, with that device current). That first call
+// should come before any stream capture on that device.
+#include <math.h>
+#include <mutex>
+
+#include "dpsr.h"
+#include "dpsr_dev.cuh"
+#include "launch.h"
+
+namespace {
+
+constexpr int kMaxR = 64;
+constexpr int kMaxN = 65536;
+constexpr size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Layout of the static scratch, for r = kMaxR and N = kMaxN.
+constexpr size_t kSpec = al((size_t)kMaxR * kMaxR * (kMaxR / 2 + 2) * sizeof(float2));
+constexpr size_t kOffSpec = 0;
+constexpr size_t kOffTw = kOffSpec + 4 * kSpec;
+constexpr size_t kOffTab = kOffTw + al(sizeof(float2) * kMaxR);
+constexpr size_t kOffSc = kOffTab + 3 * al(sizeof(float) * kMaxR);
+constexpr size_t kOffStatus = kOffSc + al(sizeof(dpsr::Scalars));
+constexpr size_t kParts = ((kMaxR / 2 + 1 + 15) / 16) * kMaxR > kMaxR * 8
+                              ? ((kMaxR / 2 + 1 + 15) / 16) * kMaxR : kMaxR * 8;
+constexpr size_t kOffPart = kOffStatus + al(sizeof(unsigned));
+constexpr size_t kOffBins = kOffPart + al(sizeof(double) * 2 * kParts);
+constexpr size_t kOffSorted = kOffBins + al(sizeof(int) * (3 * kMaxR + 1));
+constexpr size_t kOffCell = kOffSorted + al(sizeof(float4) * 2 * kMaxN);
+constexpr size_t kOffGfwd = kOffCell + al(sizeof(int) * kMaxN);
+constexpr size_t kScratchBytes = kOffGfwd + al(sizeof(float4) * 2 * kMaxN);  // ~9.2 MB
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_dpsr_static_scratch[kScratchBytes];
+
+namespace {
+
+std::mutex g_mu;
+void* g_addr[64] = {};  // device address of the array, per device ordinal
+
+// Look up (once per device, with that device current) the device address of
+// the static array. The array's name in host code is only a stand-in.
+int scratch_address(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= 64) return DPSR_EINVAL;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_dpsr_static_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return DPSR_ECUDA;
+    }
+    g_addr[dev] = p;
+  }
+  *out = (unsigned char*)g_addr[dev];
+  return DPSR_OK;
+}
+
+}  // namespace
+
+extern "C" DPSR_API int dpsr_forward_static(int r, float sigma, const float* points,
+                                            const float* normals, int64_t N, float* chi_out,
+                                            void* stream) {
+  if (r < 8 || r > kMaxR || (r & (r - 1)) != 0) return DPSR_EINVAL;
+  if (N < 1 || N > kMaxN) return DPSR_EINVAL;
+  if (!points || !normals || !chi_out || !(sigma >= 0.f) || !isfinite(sigma)) return DPSR_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return DPSR_ECUDA;
+  unsigned char* base = nullptr;
+  int rc = scratch_address(dev, &base);
+  if (rc != DPSR_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+
+  // Per-call tables: twiddles, per-axis Gaussian factor, u^2, derivative u.
+  float2 htw[kMaxR];
+  float htab[3 * kMaxR];
+  const double pi = 3.14159265358979323846264338327950288;
+  for (int m = 0; m < r; ++m) {
+    const double ang = -2.0 * pi * (double)m / (double)r;
+    htw[m] = make_float2((float)cos(ang), (float)sin(ang));
+    const double u = m < r / 2 ? (double)m : (m == r / 2 ? (double)(r / 2) : (double)(m - r));
+    htab[m] = (float)exp(-2.0 * (double)sigma * (double)sigma * u * u / ((double)r * r));
+    htab[r + m] = (float)(u * u);
+    htab[2 * r + m] = m == r / 2 ? 0.f : (float)u;
+  }
+  dpsr::Solve s = {};
+  s.r = r;
+  s.N = (int)N;
+  s.points = points;
+  s.normals = normals;
+  s.chi = chi_out;
+  for (int k = 0; k < 4; ++k) s.spec[k] = (float2*)(base + kOffSpec + k * kSpec);
+  float2* tw = (float2*)(base + kOffTw);
+  float* g1 = (float*)(base + kOffTab);
+  float* u2 = (float*)(base + kOffTab + al(sizeof(float) * kMaxR));
+  float* iu = (float*)(base + kOffTab + 2 * al(sizeof(float) * kMaxR));
+  s.tw = tw;
+  s.g1 = g1;
+  s.u2 = u2;
+  s.iu = iu;
+  s.sc = (dpsr::Scalars*)(base + kOffSc);
+  s.status = (unsigned*)(base + kOffStatus);
+  s.part = (double*)(base + kOffPart);
+  s.bins = (int*)(base + kOffBins);
+  s.sorted = (float4*)(base + kOffSorted);
+  s.cellx = (int*)(base + kOffCell);
+  s.gfwd = (float4*)(base + kOffGfwd);
+
+  cudaError_t e = cudaMemcpyAsync(tw, htw, sizeof(float2) * r, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g1, htab, sizeof(float) * r, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(u2, htab + r, sizeof(float) * r, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(iu, htab + 2 * r, sizeof(float) * r, cudaMemcpyHostToDevice, st);
+  // the bin counters and the status word must start at zero
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.bins, 0, sizeof(int) * (3 * r + 1), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.status, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess) e = dpsr::launch_bin(s, nullptr, 1, (int)N, st);
+  if (e == cudaSuccess) e = dpsr::launch_plane(0, r, 1, s, nullptr, 1, st);
+  if (e == cudaSuccess) e = dpsr::launch_xpass(false, r, s, nullptr, 1, st);
+  if (e == cudaSuccess) e = dpsr::launch_finalize(false, dpsr::xpass_blocks(r), s, nullptr, 1, st);
+  if (e == cudaSuccess) e = dpsr::launch_plane(1, r, 1, s, nullptr, 1, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return DPSR_ECUDA;
+  }
+  unsigned status = 0;
+  if (cudaMemcpy(&status, s.status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DPSR_ECUDA;
+  return status ? DPSR_EDEGENERATE : DPSR_OK;
+}

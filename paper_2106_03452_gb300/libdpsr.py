@@ -40,6 +40,7 @@ _PROTOS = {
     "dpsr_get_scalars": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "dpsr_plan_last_launches": (_c_int, [_vp]),
     "dpsr_strerror": (ctypes.c_char_p, [_c_int]),
+    "dpsr_forward_static": (_c_int, [_c_int, ctypes.c_float, _vp, _vp, _c_i64, _vp, _vp]),
     "dpsr_plan_profile": (_c_int, [_vp, _c_int]),
     "dpsr_plan_profile_read": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_int)]),
 }
@@ -147,3 +148,11 @@ def dpsr_plan_profile_read(plan: int):
     cnt = (ctypes.c_int * n)()
     check(load().dpsr_plan_profile_read(plan, ms, cnt), "dpsr_plan_profile_read")
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def dpsr_forward_static(r: int, sigma: float, points: int, normals: int, N: int, chi_out: int,
+                        stream: int = 0) -> int:
+    """Forward pass with no device allocation (static scratch; r <= 64,
+    N <= 65536). Returns the status code instead of raising."""
+    return int(load().dpsr_forward_static(int(r), float(sigma), points, normals, int(N), chi_out,
+                                          stream))
