@@ -289,6 +289,16 @@ def run_gpu(args):
                 "kernels": per3}
         plan3.close()
 
+    # ---------------- batched: 32 clouds, r in {64, 128} ----------------
+    batched = None
+    if not args.no_batch:
+        batched = bench_batched(args, dev, dist, ws, timed)
+
+    # ---------------- serving: Poisson arrivals at 200 req/s ----------------
+    serving = None
+    if not args.no_serve and rank == 0:
+        serving = bench_serving(args)
+
     # ---------------- CPU baseline: the oracle ----------------
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -312,6 +322,8 @@ def run_gpu(args):
             "kernels": per,
             "clocks": clk,
             "r256": r256,
+            "batched": batched,
+            "serving": serving,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -319,6 +331,90 @@ def run_gpu(args):
     plan_h.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def bench_batched(args, dev, dist, ws, timed):
+    """Config 4: 32 clouds (unions of 1-6 ellipsoids, N log-uniform in
+    [1000, 50000], r in {64, 128}), fwd+bwd. The batch (one CUDA graph launch
+    per step) against a per-solve launch loop of the same kernels on the same
+    GPU (one plan per cloud, called one after the other on one stream). The
+    32 working sets (about 0.7 GB) exceed L2, so no flush is needed."""
+    import torch
+
+    from paper_2106_03452_gb300 import synth
+    from paper_2106_03452_gb300.dpsr import Batch, Plan
+    inst = synth.workload_batch(count=32)
+    tens = []
+    for w in inst:
+        r = w["r"]
+        P = torch.from_numpy(w["points"]).to(dev)
+        Nn = torch.from_numpy(w["normals"]).to(dev)
+        G = torch.from_numpy(w["dchi"]).to(dev)
+        tens.append((P, Nn, G, torch.empty((r, r, r), device=dev), torch.empty_like(P), torch.empty_like(P)))
+    batch = Batch([w["r"] for w in inst], [w["sigma"] for w in inst], [w["points"].shape[0] for w in inst],
+                  device=dev)
+    for i, t in enumerate(tens):
+        batch.bind(i, *t)
+    plans = [Plan(w["r"], w["sigma"], device=dev, n_max=w["points"].shape[0]) for w in inst]
+
+    def step_batch():
+        batch.run(with_bwd=True, graph=True)
+
+    def step_loop():
+        for p, (P, Nn, G, chi, dp, dn) in zip(plans, tens):
+            p.forward(P, Nn, chi)
+            p.backward(G, dp, dn)
+
+    step_batch()
+    if batch.sync() != 0:
+        raise RuntimeError("batch device status")
+    k = max(5, args.steps)
+    ms_b, _ = timed(step_batch, k, args.warmup, flush_l2=False)
+    ms_l, _ = timed(step_loop, k, args.warmup, flush_l2=False)
+    ms_b, ms_l = _max_over_ranks(dist, ms_b), _max_over_ranks(dist, ms_l)
+    out = {"workload": "32 clouds, unions of 1-6 ellipsoids, N log-uniform [1000, 50000], r in {64,128}, "
+                       "sigma=2, fwd+bwd",
+           "solves_per_s": ws * 32 * k / (ms_b / 1e3), "ms_per_batch": ms_b / k,
+           "loop_solves_per_s": ws * 32 * k / (ms_l / 1e3), "loop_ms_per_batch": ms_l / k,
+           "speedup_vs_loop": ms_l / ms_b, "launches_per_batch": batch.launches(True),
+           "loop_launches_per_batch": 32 * 12}
+    batch.close()
+    for p in plans:
+        p.close()
+    return out
+
+
+def bench_serving(args):
+    """Config 5: Poisson arrivals at 200 req/s, each an ellipsoid-union cloud
+    with N log-uniform in [1000, 200000], r in {64, 128, 256} (0.5 / 0.35 /
+    0.15), 30% forward + backward, admitted by an 8 GB device budget. The
+    continuous-batching server (8 stream slots) against a per-solve loop (the
+    same server with one slot), first replayed in real time (latency =
+    completion - arrival), then saturated (the first 400 requests submitted
+    at once) for throughput."""
+    from paper_2106_03452_gb300 import serve, synth
+    trace = synth.serving_trace(duration_s=args.serve_seconds)
+    pool = serve.InputPool(n_clouds=6, n_max=200000)
+    keys = [(r, b) for r in (64, 128, 256) for b in (False, True)]
+    out = {"rate_per_s": 200.0, "duration_s": args.serve_seconds, "requests": len(trace),
+           "budget_bytes": 8 << 30}
+    for slots, label in ((8, "served"), (1, "loop")):
+        srv = serve.Server(8 << 30, slots)
+        serve.warm(srv, pool)
+        ring = serve.OutputRing()
+        ring.prefill(keys, slots + 2, 200000)
+        t0 = time.perf_counter()
+        res = serve.replay(trace, srv, pool, realtime=True, ring=ring)
+        wall = time.perf_counter() - t0
+        out[label] = serve.summarize(res, wall)
+        sat = trace[:400]
+        t0 = time.perf_counter()
+        res = serve.replay(sat, srv, pool, realtime=False, ring=ring)
+        out[label]["saturated_solves_per_s"] = len(sat) / (time.perf_counter() - t0)
+        out[label]["max_in_flight"] = srv.stats()["max_in_flight"]
+        srv.close()
+    out["saturated_speedup_vs_loop"] = out["served"]["saturated_solves_per_s"] / out["loop"]["saturated_solves_per_s"]
+    return out
 
 
 def oracle_baseline(w, budget_s=12.0):
@@ -384,6 +480,9 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-r256", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     args = ap.parse_args()
     if args.warmup < 3:

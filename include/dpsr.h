@@ -24,7 +24,8 @@
  *  - points, normals, dpoints, dnormals: N x 3 row-major float32.
  *    Normals are NOT normalised: their length weights the point.
  *  - chi_out, dchi: r^3 float32 in C order chi[ix][iy][iz] (iz fastest);
- *    axis 0 is the x coordinate.
+ *    axis 0 is the x coordinate. Both must start on a 16-byte boundary (they
+ *    move by bulk copies and vector loads); DPSR_EINVAL otherwise.
  *  - Every pointer argument of dpsr_forward / dpsr_backward is a DEVICE
  *    pointer on the current CUDA device, owned by the caller; the library
  *    never frees it. dpsr_forward_host / dpsr_backward_host take HOST
@@ -139,6 +140,12 @@ enum {
     DPSR_K_COUNT = 10
 };
 DPSR_API int dpsr_plan_profile(dpsr_plan plan, int enable);
+
+/* Cluster sizes (CTAs per x-plane) the plan currently uses for its four
+ * plane kernels, in the order forward, forward inverse, backward, backward
+ * inverse. An autotuner sets them on the first solve of each grid size in a
+ * process (set DPSR_TUNE=0 to keep the static choice). */
+DPSR_API int dpsr_plan_clusters(dpsr_plan plan, int *C4);
 DPSR_API int dpsr_plan_profile_read(dpsr_plan plan, double *ms, int *launches);
 
 /* Forward pass for callers that cannot allocate device memory (code running
@@ -157,6 +164,67 @@ DPSR_API int dpsr_plan_profile_read(dpsr_plan plan, double *ms, int *launches);
  * address; make that first call before any stream capture on that device. */
 DPSR_API int dpsr_forward_static(int r, float sigma, const float *points, const float *normals,
                                  int64_t N, float *chi_out, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batched solves. A batch holds `count` independent solves, instance i with
+ * grid size r[i], bandwidth sigma[i] and at most n_max[i] points. Every kernel
+ * of the forward / backward sequence runs once per distinct grid size for all
+ * instances of that size; dpsr_batch_graph_launch captures the whole
+ * sequence into one CUDA graph on first use and then replays it with one
+ * launch. Instances are numerically identical to solo dpsr_forward /
+ * dpsr_backward calls on the same inputs, up to floating-point rounding.
+ * ------------------------------------------------------------------------ */
+typedef struct dpsr_batch_s *dpsr_batch;
+DPSR_API int dpsr_batch_create(int count, const int *r, const float *sigma, const int64_t *n_max,
+                               dpsr_batch *out);
+DPSR_API int dpsr_batch_destroy(dpsr_batch batch);
+/* A non-default stream is required for dpsr_batch_graph_launch (capture). */
+DPSR_API int dpsr_batch_set_stream(dpsr_batch batch, void *stream);
+/* Bind instance i to caller-owned device buffers (layouts as for
+ * dpsr_forward / dpsr_backward; dchi, dpoints, dnormals may be NULL for a
+ * forward-only batch). N <= n_max[i], else DPSR_ESTATE. Rebinding takes effect
+ * at the next forward / backward / graph launch. */
+DPSR_API int dpsr_batch_bind(dpsr_batch batch, int i, const float *points, const float *normals,
+                             int64_t N, float *chi, const float *dchi, float *dpoints,
+                             float *dnormals);
+/* Forward (and backward) of every instance, launched on the batch stream. */
+DPSR_API int dpsr_batch_forward(dpsr_batch batch);
+DPSR_API int dpsr_batch_backward(dpsr_batch batch);
+/* Forward, and the backward if with_bwd != 0, as one CUDA graph launch. */
+DPSR_API int dpsr_batch_graph_launch(dpsr_batch batch, int with_bwd);
+/* Wait; return the worst device status over the instances (and clear them). */
+DPSR_API int dpsr_batch_sync(dpsr_batch batch);
+/* Kernel launches in one forward (+ backward) of the batch. */
+DPSR_API int dpsr_batch_launches(dpsr_batch batch, int with_bwd);
+
+/* ------------------------------------------------------------------------
+ * Serving. A server runs submitted solves concurrently on `slots` CUDA
+ * streams, admitting each request when a slot is free and its device bytes
+ * (plan workspace + staging) fit `hbm_budget_bytes` next to the requests in
+ * flight (FIFO; a request larger than the whole budget fails with
+ * DPSR_EBUSY). Plans are pooled per grid size and stay on the device between
+ * requests. All buffers of a request are HOST buffers owned by the caller
+ * until the ticket completes; page-locked buffers let the copies overlap
+ * with other requests' kernels. dchi = NULL asks for the forward pass only.
+ * A worker thread inside the server makes every CUDA call. Results equal a
+ * solo dpsr_forward_host / dpsr_backward_host of the same request up to
+ * floating-point rounding.
+ * ------------------------------------------------------------------------ */
+typedef struct dpsr_server_s *dpsr_server;
+DPSR_API int dpsr_server_create(size_t hbm_budget_bytes, int slots, float sigma,
+                                dpsr_server *out);
+DPSR_API int dpsr_server_destroy(dpsr_server server);
+DPSR_API int dpsr_server_submit(dpsr_server server, int r, const float *points,
+                                const float *normals, int64_t N, const float *dchi,
+                                float *chi_out, float *dpoints, float *dnormals,
+                                int64_t *ticket);
+/* *done = 1 once the results are in the host buffers; the return value is
+ * then the request's status and the ticket is retired. */
+DPSR_API int dpsr_server_poll(dpsr_server server, int64_t ticket, int *done);
+/* Block until the ticket completes (or timeout_s passes: DPSR_ETIMEOUT). */
+DPSR_API int dpsr_server_wait(dpsr_server server, int64_t ticket, double timeout_s);
+/* out4 = {admitted, completed, most requests in flight at once, bytes in use}. */
+DPSR_API int dpsr_server_stats(dpsr_server server, int64_t *out4);
 
 /* Static description of an error code. */
 DPSR_API const char *dpsr_strerror(int status);

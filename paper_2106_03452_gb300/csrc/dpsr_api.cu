@@ -19,8 +19,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <vector>
+
+#include <cudaTypedefs.h>
 
 #include "dpsr.h"
 #include "dpsr_dev.cuh"
@@ -47,6 +50,9 @@ struct dpsr_plan_s {
   void* host_io = nullptr;
   size_t host_io_bytes = 0;
   int64_t host_n = 0;
+  // recorded after the work of every forward / backward call: destroy waits on
+  // it, so it never touches a stream the caller may have destroyed since
+  cudaEvent_t done_ev = nullptr;
   // optional per-kernel timing: an event before and after each launch
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -79,7 +85,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 size_t spec_bytes(int r) { return (size_t)r * r * dpsr::kpitch(r) * sizeof(float2); }
 
 int part_count(int r) {
-  const int a = dpsr::xpass_blocks(r), b = r * 8;
+  const int a = dpsr::xpass_blocks(r), b = r * 16;
   return a > b ? a : b;
 }
 
@@ -100,8 +106,14 @@ size_t pts_ws_bytes(int64_t n) {
   return b;
 }
 
+// Cluster size of a plane kernel: the smallest whose CTAs fit two per SM
+// (<= 113 KB of shared memory), else the smallest that fits at all.
 int pick_cluster(int kind, int r) {
   const int cands[4] = {1, 2, 4, 8};
+  for (int C : cands) {
+    const size_t sm = dpsr::plane_smem_bytes(kind, r, C);
+    if (sm > 0 && sm <= 113 * 1024) return C;
+  }
   for (int C : cands) {
     const size_t sm = dpsr::plane_smem_bytes(kind, r, C);
     if (sm > 0 && sm <= 227 * 1024 - 1024) return C;
@@ -124,12 +136,102 @@ cudaError_t prof_mark(dpsr_plan p, int kind, bool begin) {
 
 int cuda_err(cudaError_t e) { return e == cudaErrorMemoryAllocation ? DPSR_ENOMEM : DPSR_ECUDA; }
 
+// ---------------------------------------------------------------------------
+// Autotuner: the cluster size C of each plane kernel (CTAs per x-plane) is
+// picked by timing every candidate that fits on the first solve of a given r
+// in this process. The plane kernels are idempotent (they rewrite the same
+// outputs from the same inputs), so the candidates run in place, one after
+// the other; the last run leaves the correct results. Results are cached per
+// (kernel, r) for the process. DPSR_TUNE=0 in the environment switches the
+// tuner off (the static choice of pick_cluster is used).
+// ---------------------------------------------------------------------------
+std::mutex g_tune_mu;
+int g_tuned[4][9] = {};  // [kind][log2 r]: chosen C, 0 = not tuned yet
+
+int log2i(int r) {
+  int l = 0;
+  while ((1 << l) < r) ++l;
+  return l;
+}
+
+bool tuning_enabled() {
+  const char* e = getenv("DPSR_TUNE");
+  return !(e && e[0] == '0');
+}
+
+// Launch plane kernel `kind` for every candidate C, time each with events
+// (second of two runs), record the fastest. Returns the last launch error.
+cudaError_t tune_plane(dpsr_plan p, int kind, const Solve& s, cudaStream_t st) {
+  const int r = p->r;
+  const int cands[5] = {1, 2, 4, 8, 16};
+  float best = 1e30f;
+  int bestC = p->C[kind];
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return cudaGetLastError();
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cudaGetLastError();
+  }
+  for (int C : cands) {
+    const size_t sm = dpsr::plane_smem_bytes(kind, r, C);
+    if (sm == 0 || sm > 227 * 1024 - 1024) continue;
+    cudaError_t e = dpsr::launch_plane(kind, r, C, s, nullptr, 1, st);
+    if (e != cudaSuccess) {  // e.g. a cluster shape this GPU cannot schedule
+      cudaGetLastError();
+      continue;
+    }
+    cudaEventRecord(e0, st);
+    e = dpsr::launch_plane(kind, r, C, s, nullptr, 1, st);
+    cudaEventRecord(e1, st);
+    if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      bestC = C;
+    }
+  }
+  // leave the outputs of the chosen configuration in place
+  cudaError_t e = dpsr::launch_plane(kind, r, bestC, s, nullptr, 1, st);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[kind][log2i(r)] = bestC;
+    p->C[kind] = bestC;
+  }
+  return e;
+}
+
+// Launch plane kernel `kind`, tuning it first if it has not been tuned for
+// this r (and the stream is not being captured).
+cudaError_t run_plane(dpsr_plan p, int kind, const Solve& s, cudaStream_t st) {
+  if (tuning_enabled() && p->r >= 64) {
+    int tuned;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      tuned = g_tuned[kind][log2i(p->r)];
+    }
+    if (tuned) {
+      p->C[kind] = tuned;
+    } else {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone && !p->profile)
+        return tune_plane(p, kind, s, st);
+    }
+  }
+  return dpsr::launch_plane(kind, p->r, p->C[kind], s, nullptr, 1, st);
+}
+
 int grow_points(dpsr_plan p, int64_t n) {
   if (n <= p->n_cap) return DPSR_OK;
   int64_t cap = p->n_cap ? p->n_cap : 1024;
   while (cap < n) cap *= 2;
   if (p->pts_ws) {
-    cudaStreamSynchronize(p->stream);
+    if (p->done_ev) cudaEventSynchronize(p->done_ev);
     cudaFree(p->pts_ws);
     p->pts_ws = nullptr;
     p->n_cap = 0;
@@ -154,7 +256,44 @@ int grow_points(dpsr_plan p, int64_t n) {
   return DPSR_OK;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
 }  // namespace
+
+namespace dpsr {
+// Spectral buffer k: complex (8-byte) elements [x][ky][kz], kz < r/2+1 valid
+// out of a row pitch of r/2+2. tmx: boxes of 16 kz x 1 ky x r x; tmy: boxes
+// of 16 kz x r ky x 1 x. Out-of-range kz reads as zero and is not written.
+int make_tensor_maps(Solve& s, int r) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return DPSR_ECUDA;
+  const cuuint64_t dims[3] = {(cuuint64_t)(r / 2 + 1), (cuuint64_t)r, (cuuint64_t)r};
+  const cuuint64_t strides[2] = {(cuuint64_t)kpitch(r) * 8, (cuuint64_t)r * kpitch(r) * 8};
+  const cuuint32_t boxx[3] = {16, 1, (cuuint32_t)r}, boxy[3] = {16, (cuuint32_t)r, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  for (int k = 0; k < 4; ++k) {
+    for (int w = 0; w < 2; ++w) {
+      CUresult rc = enc(w == 0 ? &s.tmx[k] : &s.tmy[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                        (void*)s.spec[k], dims, strides, w == 0 ? boxx : boxy, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (rc != CUDA_SUCCESS) return DPSR_ECUDA;
+    }
+  }
+  return DPSR_OK;
+}
+}  // namespace dpsr
 
 extern "C" {
 
@@ -258,6 +397,9 @@ int dpsr_plan_create(int r, float sigma, dpsr_plan* out) {
   }
   free(htw);
   free(hg);
+  if (rc == DPSR_OK) rc = dpsr::make_tensor_maps(s, r);
+  if (rc == DPSR_OK && cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming) != cudaSuccess)
+    rc = DPSR_ECUDA;
   if (rc == DPSR_OK) rc = grow_points(p, 1024);
   if (rc != DPSR_OK) {
     cudaFree(p->grid_ws);
@@ -272,7 +414,10 @@ int dpsr_plan_create(int r, float sigma, dpsr_plan* out) {
 int dpsr_plan_destroy(dpsr_plan p) {
   if (!p) return DPSR_EINVAL;
   DeviceGuard dg(p->device);
-  cudaStreamSynchronize(p->stream);
+  if (p->done_ev) {
+    cudaEventSynchronize(p->done_ev);
+    cudaEventDestroy(p->done_ev);
+  }
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   cudaFree(p->grid_ws);
   if (p->pts_ws) cudaFree(p->pts_ws);
@@ -295,6 +440,24 @@ int dpsr_plan_reserve(dpsr_plan p, int64_t n_max) {
 }
 
 int dpsr_plan_last_launches(dpsr_plan p) { return p ? p->last_launches : -1; }
+
+// Internal hooks for the batch driver (same library, not exported).
+const void* dpsr_internal_solve(dpsr_plan p) { return p ? (const void*)&p->s : nullptr; }
+int dpsr_internal_cluster(dpsr_plan p, int kind) {
+  if (!p || kind < 0 || kind > 3) return 1;
+  if (tuning_enabled()) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const int t = g_tuned[kind][log2i(p->r)];
+    if (t) return t;
+  }
+  return p->C[kind];
+}
+
+int dpsr_plan_clusters(dpsr_plan p, int* C4) {
+  if (!p || !C4) return DPSR_EINVAL;
+  for (int k = 0; k < 4; ++k) C4[k] = p->C[k];
+  return DPSR_OK;
+}
 
 int dpsr_plan_profile(dpsr_plan p, int enable) {
   if (!p) return DPSR_EINVAL;
@@ -327,6 +490,7 @@ int dpsr_plan_profile_read(dpsr_plan p, double* ms, int* launches) {
 int dpsr_forward(dpsr_plan p, const float* points, const float* normals, int64_t N,
                  float* chi_out) {
   if (!p || !points || !normals || !chi_out || N < 1 || N > INT32_MAX / 2) return DPSR_EINVAL;
+  if (((uintptr_t)chi_out & 15) != 0) return DPSR_EINVAL;  // read back by vector loads
   DeviceGuard dg(p->device);
   if (!dg.ok) return DPSR_ECUDA;
   int rc = grow_points(p, N);
@@ -345,16 +509,17 @@ int dpsr_forward(dpsr_plan p, const float* points, const float* normals, int64_t
     if (e == cudaSuccess) e = prof_mark(p, kind, false);
   };
   run(DPSR_K_BIN, [&] { return dpsr::launch_bin(s, nullptr, 1, (int)N, st); });
-  run(DPSR_K_PLANE_FWD, [&] { return dpsr::launch_plane(0, r, p->C[0], s, nullptr, 1, st); });
+  run(DPSR_K_PLANE_FWD, [&] { return run_plane(p, 0, s, st); });
   run(DPSR_K_XPASS_FWD, [&] { return dpsr::launch_xpass(false, r, s, nullptr, 1, st); });
   run(DPSR_K_FINAL_FWD, [&] { return dpsr::launch_finalize(false, dpsr::xpass_blocks(r), s, nullptr, 1, st); });
-  run(DPSR_K_PLANE_INV, [&] { return dpsr::launch_plane(1, r, p->C[1], s, nullptr, 1, st); });
+  run(DPSR_K_PLANE_INV, [&] { return run_plane(p, 1, s, st); });
   if (e != cudaSuccess) {
     cudaGetLastError();
     p->have_fwd = false;
     return cuda_err(e);
   }
   p->last_launches = 7;  // bin: 3 kernels, plane, xpass, finalize, inverse plane
+  cudaEventRecord(p->done_ev, st);
   p->s.N = s.N;
   p->s.points = points;
   p->s.normals = normals;
@@ -365,6 +530,7 @@ int dpsr_forward(dpsr_plan p, const float* points, const float* normals, int64_t
 
 int dpsr_backward(dpsr_plan p, const float* dchi, float* dpoints, float* dnormals) {
   if (!p || !dchi || !dpoints || !dnormals) return DPSR_EINVAL;
+  if (((uintptr_t)dchi & 15) != 0) return DPSR_EINVAL;  // rows move by bulk copies
   if (!p->have_fwd) return DPSR_ESTATE;
   DeviceGuard dg(p->device);
   if (!dg.ok) return DPSR_ECUDA;
@@ -380,16 +546,17 @@ int dpsr_backward(dpsr_plan p, const float* dchi, float* dpoints, float* dnormal
     if (e == cudaSuccess) e = fn();
     if (e == cudaSuccess) e = prof_mark(p, kind, false);
   };
-  run(DPSR_K_PLANE_BFWD, [&] { return dpsr::launch_plane(2, r, p->C[2], s, nullptr, 1, st); });
-  run(DPSR_K_FINAL_BWD, [&] { return dpsr::launch_finalize(true, r * p->C[2], s, nullptr, 1, st); });
+  run(DPSR_K_PLANE_BFWD, [&] { return run_plane(p, 2, s, st); });
+  run(DPSR_K_FINAL_BWD, [&] { return dpsr::launch_finalize(true, r * p->C[2], s, nullptr, 1, st); });  // C[2] as tuned
   run(DPSR_K_XPASS_BWD, [&] { return dpsr::launch_xpass(true, r, s, nullptr, 1, st); });
-  run(DPSR_K_PLANE_BINV, [&] { return dpsr::launch_plane(3, r, p->C[3], s, nullptr, 1, st); });
+  run(DPSR_K_PLANE_BINV, [&] { return run_plane(p, 3, s, st); });
   run(DPSR_K_COMBINE, [&] { return dpsr::launch_combine(s, nullptr, 1, s.N, st); });
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_err(e);
   }
   p->last_launches = 5;
+  cudaEventRecord(p->done_ev, st);
   return DPSR_OK;
 }
 
@@ -429,7 +596,7 @@ static int host_io_reserve(dpsr_plan p, int64_t N) {
   const size_t need = align256(sizeof(float) * 3 * N) * 4 + align256(sizeof(float) * p->r * p->r * p->r) * 2;
   if (need <= p->host_io_bytes) return DPSR_OK;
   if (p->host_io) {
-    cudaStreamSynchronize(p->stream);
+    if (p->done_ev) cudaEventSynchronize(p->done_ev);
     cudaFree(p->host_io);
     p->host_io = nullptr;
     p->host_io_bytes = 0;
@@ -456,6 +623,24 @@ static HostIo host_io_view(dpsr_plan p, int64_t N) {
   v.chi = (float*)(q + 4 * a);
   v.dchi = (float*)(q + 4 * a + g);
   return v;
+}
+
+// Internal hook for the server (same library): the plan's device staging
+// buffers for N points.
+int dpsr_internal_io(dpsr_plan p, int64_t N, float** pts, float** nrm, float** chi, float** dchi,
+                     float** dpts, float** dnrm) {
+  if (!p || N < 1) return DPSR_EINVAL;
+  DeviceGuard dg(p->device);
+  const int rc = host_io_reserve(p, N);
+  if (rc != DPSR_OK) return rc;
+  HostIo v = host_io_view(p, N);
+  *pts = v.pts;
+  *nrm = v.nrm;
+  *chi = v.chi;
+  *dchi = v.dchi;
+  *dpts = v.dpts;
+  *dnrm = v.dnrm;
+  return DPSR_OK;
 }
 
 int dpsr_forward_host(dpsr_plan p, const float* points, const float* normals, int64_t N,

@@ -1,0 +1,268 @@
+// Batched solves: many point clouds of uneven N and mixed r, each kernel of
+// the forward / backward sequence launched once per grid size for all
+// instances of that size (the instance is blockIdx.z of every kernel, its
+// descriptor read from a device table), the whole sequence capturable into
+// one CUDA graph and replayed with a single launch.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "dpsr.h"
+#include "dpsr_dev.cuh"
+#include "launch.h"
+
+using dpsr::Solve;
+
+// Internal hooks of dpsr_api.cu (same library).
+extern "C" const void* dpsr_internal_solve(dpsr_plan p);
+extern "C" int dpsr_internal_cluster(dpsr_plan p, int kind);
+
+struct BatchClass {
+  int r = 0;
+  std::vector<int> members;  // instance indices
+  Solve* dtab = nullptr;     // device table, one descriptor per member
+  int nmax = 0;
+  int C[4] = {1, 1, 1, 1};
+};
+
+struct dpsr_batch_s {
+  int count = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<dpsr_plan> plans;
+  std::vector<Solve> host;  // per instance, bound pointers
+  std::vector<int64_t> nmax;
+  std::vector<BatchClass> classes;
+  Solve* hstage = nullptr;  // pinned staging of the tables
+  cudaGraphExec_t graph = nullptr;
+  int graph_bwd = -1;
+  bool have_fwd = false;
+};
+
+namespace {
+
+int upload(dpsr_batch b) {
+  size_t off = 0;
+  for (auto& c : b->classes) {
+    for (size_t k = 0; k < c.members.size(); ++k) b->hstage[off + k] = b->host[c.members[k]];
+    if (cudaMemcpyAsync(c.dtab, b->hstage + off, sizeof(Solve) * c.members.size(),
+                        cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+      return DPSR_ECUDA;
+    off += c.members.size();
+  }
+  return DPSR_OK;
+}
+
+cudaError_t launch_fwd(dpsr_batch b) {
+  cudaStream_t st = b->stream;
+  const Solve dummy = {};
+  for (auto& c : b->classes) {
+    const int n = (int)c.members.size();
+    cudaError_t e = dpsr::launch_bin(dummy, c.dtab, n, c.nmax, st);
+    if (e == cudaSuccess) e = dpsr::launch_plane(0, c.r, c.C[0], dummy, c.dtab, n, st);
+    if (e == cudaSuccess) e = dpsr::launch_xpass(false, c.r, dummy, c.dtab, n, st);
+    if (e == cudaSuccess) e = dpsr::launch_finalize(false, dpsr::xpass_blocks(c.r), dummy, c.dtab, n, st);
+    if (e == cudaSuccess) e = dpsr::launch_plane(1, c.r, c.C[1], dummy, c.dtab, n, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_bwd(dpsr_batch b) {
+  cudaStream_t st = b->stream;
+  const Solve dummy = {};
+  for (auto& c : b->classes) {
+    const int n = (int)c.members.size();
+    cudaError_t e = dpsr::launch_plane(2, c.r, c.C[2], dummy, c.dtab, n, st);
+    if (e == cudaSuccess) e = dpsr::launch_finalize(true, c.r * c.C[2], dummy, c.dtab, n, st);
+    if (e == cudaSuccess) e = dpsr::launch_xpass(true, c.r, dummy, c.dtab, n, st);
+    if (e == cudaSuccess) e = dpsr::launch_plane(3, c.r, c.C[3], dummy, c.dtab, n, st);
+    if (e == cudaSuccess) e = dpsr::launch_combine(dummy, c.dtab, n, c.nmax, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+void drop_graph(dpsr_batch b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_bwd = -1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dpsr_batch_create(int count, const int* r, const float* sigma, const int64_t* n_max,
+                      dpsr_batch* out) {
+  if (!out || count < 1 || !r || !sigma || !n_max) return DPSR_EINVAL;
+  *out = nullptr;
+  dpsr_batch b = new (std::nothrow) dpsr_batch_s();
+  if (!b) return DPSR_ENOMEM;
+  b->count = count;
+  cudaGetDevice(&b->device);
+  b->plans.assign(count, nullptr);
+  b->host.resize(count);
+  b->nmax.assign(n_max, n_max + count);
+  int rc = DPSR_OK;
+  for (int i = 0; i < count && rc == DPSR_OK; ++i) {
+    rc = dpsr_plan_create(r[i], sigma[i], &b->plans[i]);
+    if (rc == DPSR_OK) rc = dpsr_plan_reserve(b->plans[i], n_max[i]);
+    if (rc == DPSR_OK) memcpy(&b->host[i], dpsr_internal_solve(b->plans[i]), sizeof(Solve));
+  }
+  if (rc == DPSR_OK) {
+    std::vector<int> rs(r, r + count);
+    std::sort(rs.begin(), rs.end());
+    rs.erase(std::unique(rs.begin(), rs.end()), rs.end());
+    for (int rr : rs) {
+      BatchClass c;
+      c.r = rr;
+      for (int i = 0; i < count; ++i)
+        if (r[i] == rr) {
+          c.members.push_back(i);
+          c.nmax = std::max<int>(c.nmax, (int)n_max[i]);
+        }
+      for (int k = 0; k < 4; ++k) c.C[k] = dpsr_internal_cluster(b->plans[c.members[0]], k);
+      if (cudaMalloc(&c.dtab, sizeof(Solve) * c.members.size()) != cudaSuccess) {
+        cudaGetLastError();
+        rc = DPSR_ENOMEM;
+      }
+      b->classes.push_back(c);
+    }
+  }
+  if (rc == DPSR_OK && cudaMallocHost(&b->hstage, sizeof(Solve) * count) != cudaSuccess) {
+    cudaGetLastError();
+    rc = DPSR_ENOMEM;
+  }
+  if (rc != DPSR_OK) {
+    dpsr_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return DPSR_OK;
+}
+
+int dpsr_batch_destroy(dpsr_batch b) {
+  if (!b) return DPSR_EINVAL;
+  cudaStreamSynchronize(b->stream);
+  drop_graph(b);
+  for (auto& c : b->classes)
+    if (c.dtab) cudaFree(c.dtab);
+  for (dpsr_plan p : b->plans)
+    if (p) dpsr_plan_destroy(p);
+  if (b->hstage) cudaFreeHost(b->hstage);
+  delete b;
+  return DPSR_OK;
+}
+
+int dpsr_batch_set_stream(dpsr_batch b, void* stream) {
+  if (!b) return DPSR_EINVAL;
+  b->stream = (cudaStream_t)stream;
+  for (dpsr_plan p : b->plans) dpsr_plan_set_stream(p, stream);
+  drop_graph(b);
+  return DPSR_OK;
+}
+
+int dpsr_batch_bind(dpsr_batch b, int i, const float* points, const float* normals, int64_t N,
+                    float* chi, const float* dchi, float* dpoints, float* dnormals) {
+  if (!b || i < 0 || i >= b->count || !points || !normals || !chi) return DPSR_EINVAL;
+  if (N < 1 || N > b->nmax[i]) return DPSR_ESTATE;
+  if (((uintptr_t)chi & 15) || ((uintptr_t)dchi & 15)) return DPSR_EINVAL;
+  Solve& s = b->host[i];
+  s.points = points;
+  s.normals = normals;
+  s.N = (int)N;
+  s.chi = chi;
+  s.dchi = dchi;
+  s.dpoints = dpoints;
+  s.dnormals = dnormals;
+  return DPSR_OK;
+}
+
+int dpsr_batch_forward(dpsr_batch b) {
+  if (!b) return DPSR_EINVAL;
+  int rc = upload(b);
+  if (rc != DPSR_OK) return rc;
+  if (launch_fwd(b) != cudaSuccess) {
+    cudaGetLastError();
+    return DPSR_ECUDA;
+  }
+  b->have_fwd = true;
+  return DPSR_OK;
+}
+
+int dpsr_batch_backward(dpsr_batch b) {
+  if (!b) return DPSR_EINVAL;
+  if (!b->have_fwd) return DPSR_ESTATE;
+  for (int i = 0; i < b->count; ++i)
+    if (!b->host[i].dchi || !b->host[i].dpoints || !b->host[i].dnormals) return DPSR_EINVAL;
+  int rc = upload(b);
+  if (rc != DPSR_OK) return rc;
+  if (launch_bwd(b) != cudaSuccess) {
+    cudaGetLastError();
+    return DPSR_ECUDA;
+  }
+  return DPSR_OK;
+}
+
+int dpsr_batch_graph_launch(dpsr_batch b, int with_bwd) {
+  if (!b) return DPSR_EINVAL;
+  if (with_bwd)
+    for (int i = 0; i < b->count; ++i)
+      if (!b->host[i].dchi || !b->host[i].dpoints || !b->host[i].dnormals) return DPSR_EINVAL;
+  int rc = upload(b);
+  if (rc != DPSR_OK) return rc;
+  if (!b->graph || b->graph_bwd != (with_bwd ? 1 : 0)) {
+    drop_graph(b);
+    if (b->stream == nullptr) return DPSR_EINVAL;  // capture needs a non-default stream
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return DPSR_ECUDA;
+    cudaError_t e = launch_fwd(b);
+    if (e == cudaSuccess && with_bwd) e = launch_bwd(b);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      return DPSR_ECUDA;
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b->graph = nullptr;
+      return DPSR_ECUDA;
+    }
+    b->graph_bwd = with_bwd ? 1 : 0;
+  }
+  if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return DPSR_ECUDA;
+  }
+  b->have_fwd = true;
+  return DPSR_OK;
+}
+
+int dpsr_batch_sync(dpsr_batch b) {
+  if (!b) return DPSR_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return DPSR_ECUDA;
+  }
+  int worst = DPSR_OK;
+  for (dpsr_plan p : b->plans) {
+    const int st = dpsr_sync(p);
+    if (st != DPSR_OK) worst = st;
+  }
+  return worst;
+}
+
+int dpsr_batch_launches(dpsr_batch b, int with_bwd) {
+  if (!b) return -1;
+  return (int)b->classes.size() * (with_bwd ? 12 : 7);
+}
+
+}  // extern "C"

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -119,9 +120,8 @@ template <> struct Shape<64>  { static constexpr int R1 = 8,  T = 8; };
 template <> struct Shape<128> { static constexpr int R1 = 16, T = 8; };
 template <> struct Shape<256> { static constexpr int R1 = 16, T = 16; };
 
-template <int L, int DIR>
-__device__ __forceinline__ void fft(float2 (&v)[Shape<L>::R1], int t, float2* xch,
-                                    const float2* tw) {
+template <int L, int DIR, class XA>
+__device__ __forceinline__ void fft_x(float2 (&v)[Shape<L>::R1], int t, XA xa, const float2* tw) {
   constexpr int R1 = Shape<L>::R1, T = Shape<L>::T;
   if constexpr (T == 1) {
     Dft<L, DIR>::run(v);
@@ -134,7 +134,7 @@ __device__ __forceinline__ void fft(float2 (&v)[Shape<L>::R1], int t, float2* xc
       v[k1] = cmul(v[k1], w);
     }
 #pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) xch[k1 * T + (t ^ (k1 % T))] = v[k1];
+    for (int k1 = 0; k1 < R1; ++k1) xa(k1 * T + (t ^ (k1 % T))) = v[k1];
     __syncwarp();
     constexpr int M = R1 / T;
 #pragma unroll
@@ -142,7 +142,67 @@ __device__ __forceinline__ void fft(float2 (&v)[Shape<L>::R1], int t, float2* xc
       float2 u[T];
       const int k1 = t + T * m;
 #pragma unroll
-      for (int n2 = 0; n2 < T; ++n2) u[n2] = xch[k1 * T + (n2 ^ t)];
+      for (int n2 = 0; n2 < T; ++n2) u[n2] = xa(k1 * T + (n2 ^ t));
+      Dft<T, DIR>::run(u);
+#pragma unroll
+      for (int k2 = 0; k2 < T; ++k2) v[m + M * k2] = u[k2];
+    }
+    __syncwarp();
+  }
+}
+
+template <int L, int DIR>
+__device__ __forceinline__ void fft(float2 (&v)[Shape<L>::R1], int t, float2* xch,
+                                    const float2* tw) {
+  fft_x<L, DIR>(v, t, [xch](int i) -> float2& { return xch[i]; }, tw);
+}
+
+// The stage twiddles W_L^(t*k1), k1 = 1..R1-1, of thread t held in registers
+// (the same for every transform the thread performs).
+template <int L>
+struct Twid {
+  float2 w[Shape<L>::R1];
+  __device__ __forceinline__ void load(int t, const float2* tw) {
+#pragma unroll
+    for (int k1 = 0; k1 < Shape<L>::R1; ++k1)
+      w[k1] = Shape<L>::T == 1 ? make_float2(1.f, 0.f) : tw[(t * k1) & (L - 1)];
+  }
+  __device__ __forceinline__ float2 operator()(int k1) const { return w[k1]; }
+};
+
+// The same stage twiddles read from a shared-memory table at each use
+// (fewer live registers than Twid).
+template <int L>
+struct TwTab {
+  const float2* tab;  // exp(-2 pi i m / L), m < L, in shared memory
+  int t;
+  __device__ __forceinline__ float2 operator()(int k1) const { return tab[(t * k1) & (L - 1)]; }
+};
+
+// Group FFT with register twiddles (see fft_x).
+template <int L, int DIR, class XA, class TW>
+__device__ __forceinline__ void fft_r(float2 (&v)[Shape<L>::R1], int t, XA xa, const TW& tw) {
+  constexpr int R1 = Shape<L>::R1, T = Shape<L>::T;
+  if constexpr (T == 1) {
+    Dft<L, DIR>::run(v);
+  } else {
+    Dft<R1, DIR>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < R1; ++k1) {
+      float2 w = tw(k1);
+      if (DIR > 0) w.y = -w.y;
+      v[k1] = cmul(v[k1], w);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) xa(k1 * T + (t ^ (k1 % T))) = v[k1];
+    __syncwarp();
+    constexpr int M = R1 / T;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      float2 u[T];
+      const int k1 = t + T * m;
+#pragma unroll
+      for (int n2 = 0; n2 < T; ++n2) u[n2] = xa(k1 * T + (n2 ^ t));
       Dft<T, DIR>::run(u);
 #pragma unroll
       for (int k2 = 0; k2 < T; ++k2) v[m + M * k2] = u[k2];
@@ -158,14 +218,14 @@ __device__ __forceinline__ void fft(float2 (&v)[Shape<L>::R1], int t, float2* xc
 // A[1..L/2-1].
 // ---------------------------------------------------------------------------
 // Forward: ld(k) -> z[k]; sa(slot, A), sb(slot, B).
-template <int L, class Ld, class StA, class StB>
-__device__ __forceinline__ void r2c_pair(int t, float2* xch, const float2* tw, Ld ld, StA sa,
+template <int L, class Tw, class Ld, class StA, class StB>
+__device__ __forceinline__ void r2c_pair(int t, float2* xch, const Tw& tw, Ld ld, StA sa,
                                          StB sb) {
   constexpr int R1 = Shape<L>::R1, T = Shape<L>::T, H = L / 2;
   float2 v[R1];
 #pragma unroll
   for (int j = 0; j < R1; ++j) v[j] = ld(t + T * j);
-  fft<L, -1>(v, t, xch, tw);
+  fft_r<L, -1>(v, t, [xch](int i) -> float2& { return xch[i]; }, tw);
 #pragma unroll
   for (int j = 0; j < R1; ++j) xch[t + T * j] = v[j];
   __syncwarp();
@@ -194,8 +254,8 @@ __device__ __forceinline__ void r2c_pair(int t, float2* xch, const float2* tw, L
 
 // Inverse: la(slot) -> packed A, lb(slot) -> packed B; st(z, (a[z], b[z]))
 // with the unnormalised inverse transform (values times L).
-template <int L, class LdA, class LdB, class St>
-__device__ __forceinline__ void c2r_pair(int t, float2* xch, const float2* tw, LdA la, LdB lb,
+template <int L, class Tw, class LdA, class LdB, class St>
+__device__ __forceinline__ void c2r_pair(int t, float2* xch, const Tw& tw, LdA la, LdB lb,
                                          St st) {
   constexpr int R1 = Shape<L>::R1, T = Shape<L>::T, H = L / 2;
   float2 v[R1];
@@ -213,7 +273,7 @@ __device__ __forceinline__ void c2r_pair(int t, float2* xch, const float2* tw, L
       v[j] = make_float2(a.x + b.y, b.x - a.y);
     }
   }
-  fft<L, +1>(v, t, xch, tw);
+  fft_r<L, +1>(v, t, [xch](int i) -> float2& { return xch[i]; }, tw);
 #pragma unroll
   for (int j = 0; j < R1; ++j) st(t + T * j, v[j]);
 }
@@ -240,6 +300,11 @@ struct Scalars {
 };
 
 struct Solve {
+  // TMA descriptors of the four spectral buffers (dims kz = r/2+1, ky, x):
+  // tmx boxes are 16 kz x 1 ky x r x (x-pass tiles), tmy boxes 16 kz x r ky x
+  // 1 x (plane tiles). 128-byte swizzle.
+  CUtensorMap tmx[4];
+  CUtensorMap tmy[4];
   int r;
   int N;
   // per call (caller-owned)
@@ -265,7 +330,7 @@ struct Solve {
   const float* iu;   // r: u, 0 at Nyquist (factor of the spectral derivative)
 };
 
-enum : unsigned { kStBadInput = 1u, kStDegenerate = 2u };
+enum : unsigned { kStBadInput = 1u, kStDegenerate = 2u, kStTimeout = 4u };
 
 __host__ __device__ constexpr int kpitch(int r) { return r / 2 + 2; }
 

@@ -127,6 +127,7 @@ extern "C" DPSR_API int dpsr_forward_static(int r, float sigma, const float* poi
   s.sorted = (float4*)(base + kOffSorted);
   s.cellx = (int*)(base + kOffCell);
   s.gfwd = (float4*)(base + kOffGfwd);
+  if (dpsr::make_tensor_maps(s, r) != DPSR_OK) return DPSR_ECUDA;
 
   cudaError_t e = cudaMemcpyAsync(tw, htw, sizeof(float2) * r, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(g1, htab, sizeof(float) * r, cudaMemcpyHostToDevice, st);

@@ -18,6 +18,7 @@
 //                           (gather and weight derivatives) at the points.
 #include "dpsr_dev.cuh"
 #include "launch.h"
+#include "tma.cuh"
 
 namespace dpsr {
 
@@ -27,10 +28,16 @@ struct PlaneGeo {
   static constexpr int R = L / C;        // rows per CTA
   static constexpr int H = L / 2;        // packed half-spectrum slots per channel
   static constexpr int SPC = H / C;      // slots per CTA per channel (y pass)
-  static constexpr int SP = L + 1;       // staging column pitch (float2)
+  static constexpr int CHK = G < SPC ? G : SPC;  // slots per chunk (one group each)
+  static constexpr int NB = (CHK + 15) / 16;     // TMA boxes per chunk
+  static constexpr int BOX = L * 16;             // float2 per box [ky][16 kz]
+  static constexpr int XP = L + 1;               // per-group exchange pitch (z pass)
+  static constexpr int SCR0 = NB * BOX > G * XP ? NB * BOX : G * XP;
+  static constexpr int SCR = (SCR0 + 127) / 128 * 128;  // scratch float2, whole KiB
   static constexpr int KP = L / 2 + 2;   // row pitch of the spectral buffers in HBM
   static constexpr int SWM = (H < 16 ? H : 16) - 1;
   static_assert(R >= 2 && R % 2 == 0, "at least one row pair per CTA");
+  static_assert(SPC >= 1, "at least one slot per CTA");
 };
 
 // XOR swizzle inside aligned 16-slot blocks: a column read across 16 rows and
@@ -61,102 +68,163 @@ struct PlanePoints {
 
 __device__ __forceinline__ float wsel(int d, float t) { return d ? t : 1.f - t; }
 
-// Write a chunk of y-transformed columns (staging [group][ky]) to the spectral
-// buffer dst[X][ky][kz]. Slot 0 carries the packed DC and Nyquist columns and
-// is separated into kz = 0 and kz = L/2.
+// Column `g` of the chunk boxes (box g/16, complex g%16), element row e.
+template <int L>
+__device__ __forceinline__ float2& boxcol(float2* sbox, int g, int e) {
+  return sbox[(g >> 4) * (L * 16) + bx(e, g & 15)];
+}
+
+// Dynamic shared memory: 1024-aligned scratch (TMA boxes / exchange areas),
+// then the rows of the plane, then an optional table.
+__device__ __forceinline__ float2* aligned_smem(unsigned char* raw) {
+  const uint32_t pad = (1024u - (smem_u32(raw) & 1023u)) & 1023u;
+  return reinterpret_cast<float2*>(raw + pad);
+}
+
+// The slot-0 column of a chunk holds the packed DC and Nyquist columns
+// P = X0 + i Xn. Separate them in place (column 0 <- X0) and hand Xn to
+// `nyq(ky, value)`. Run by the T threads of group 0.
+template <int L, class Nyq>
+__device__ __forceinline__ void separate_dc_nyq(float2* sbox, int t, Nyq nyq) {
+  constexpr int R1 = Shape<L>::R1, T = Shape<L>::T;
+  float2 x0[R1], xn[R1];
+#pragma unroll
+  for (int j = 0; j < R1; ++j) {
+    const int ky = t + T * j;
+    unpack_dc_nyq(boxcol<L>(sbox, 0, ky), boxcol<L>(sbox, 0, (L - ky) & (L - 1)), x0[j], xn[j]);
+  }
+  if constexpr (T > 1) __syncwarp((T == 32 ? 0xffffffffu : ((1u << T) - 1u)) << (threadIdx.x & 31 & ~(T - 1)));
+#pragma unroll
+  for (int j = 0; j < R1; ++j) {
+    boxcol<L>(sbox, 0, t + T * j) = x0[j];
+    nyq(t + T * j, xn[j]);
+  }
+}
+
+// Issue (one thread) the TMA loads / stores of a chunk's boxes.
 template <int L, int C>
-__device__ __forceinline__ void store_cols(float2* __restrict__ dst, int X, int s_first,
-                                           int nvalid, const float2* scr) {
+__device__ __forceinline__ void chunk_load(const CUtensorMap* tm, float2* sbox, int s_first, int X,
+                                           uint64_t* bar) {
   using P = PlaneGeo<L, C>;
-  for (int i = threadIdx.x; i < P::G * L; i += kNT) {
-    const int gi = i % P::G, ky = i / P::G;
-    if (gi >= nvalid) continue;
-    const int s = s_first + gi;
-    const float2* col = scr + gi * P::SP;
-    const float2 v = col[ky];
-    const size_t base = ((size_t)X * L + ky) * P::KP;
-    if (s != 0) {
-      dst[base + s] = v;
-    } else {
-      float2 x0, xn;
-      unpack_dc_nyq(v, col[(L - ky) & (L - 1)], x0, xn);
-      dst[base] = x0;
-      dst[base + P::H] = xn;
-    }
-  }
+  mbar_expect_tx(bar, P::NB * P::BOX * (uint32_t)sizeof(float2));
+  for (int b = 0; b < P::NB; ++b) tma_load_3d(sbox + b * P::BOX, tm, s_first + 16 * b, 0, X, bar);
+}
+template <int L, int C>
+__device__ __forceinline__ void chunk_store(const CUtensorMap* tm, const float2* sbox, int s_first,
+                                            int X) {
+  using P = PlaneGeo<L, C>;
+  for (int b = 0; b < P::NB; ++b) tma_store_3d(tm, s_first + 16 * b, 0, X, sbox + b * P::BOX);
+  tma_store_commit();
 }
 
-// Load a chunk of columns src[X][ky][kz] into staging [group][ky]; slot 0 is
-// packed as X0 + i Xn from kz = 0 and kz = L/2 (both transform to real rows).
-// mul(ky, s, v) may scale the value on the way in.
-template <int L, int C, class Mul>
-__device__ __forceinline__ void load_cols(const float2* __restrict__ src, int X, int s_first,
-                                          int nvalid, float2* scr, Mul mul) {
-  using P = PlaneGeo<L, C>;
-  for (int i = threadIdx.x; i < P::G * L; i += kNT) {
-    const int gi = i % P::G, ky = i / P::G;
-    if (gi >= nvalid) continue;
-    const int s = s_first + gi;
-    const size_t base = ((size_t)X * L + ky) * P::KP;
-    float2 v;
-    if (s != 0) {
-      v = src[base + s];
-    } else {
-      const float2 a = src[base], b = src[base + P::H];
-      v = make_float2(a.x - b.y, a.y + b.x);
-    }
-    scr[gi * P::SP + ky] = mul(ky, s, v);
-  }
-}
-
-// Push a chunk of y-domain columns (staging [group][y]) into the rows of their
-// owner CTAs: row y, slot `choff + s`.
+// Push a chunk of y-domain columns (boxes) into the rows of their owner CTAs:
+// row y, slot `choff + s_first + gi`.
 template <int L, int C, int RP>
-__device__ __forceinline__ void push_cols(float2* const* rb, int s_first, int nvalid, int choff,
-                                          const float2* scr) {
+__device__ __forceinline__ void push_cols(cg::cluster_group& cl, float2* rows, int s_first,
+                                          int choff, float2* sbox) {
   using P = PlaneGeo<L, C>;
-  for (int i = threadIdx.x; i < P::G * L; i += kNT) {
-    const int gi = i % P::G, y = i / P::G;
-    if (gi >= nvalid) continue;
+  for (int i = threadIdx.x; i < P::CHK * L; i += kNT) {
+    const int gi = i % P::CHK, y = i / P::CHK;
     const int q = y / P::R, lr = y % P::R;
-    rb[q][sw<RP, P::SWM>(lr, choff + s_first + gi)] = scr[gi * P::SP + y];
+    dsmem_st(dsmem_map(rows, q) + 8u * sw<RP, P::SWM>(lr, choff + s_first + gi), boxcol<L>(sbox, gi, y));
   }
 }
 
-// ===========================================================================
-// Forward plane kernel: splat + R2C(z) + FFT(y).
-// ===========================================================================
+// Bounded wait on a TMA barrier, block-uniform outcome.
+__device__ __forceinline__ bool chunk_wait(uint64_t* bar, uint32_t phase, unsigned* status) {
+  const bool ok = __syncthreads_and(mbar_wait(bar, phase));
+  if (!ok && threadIdx.x == 0) atomicOr(status, kStTimeout);
+  return ok;
+}
+
+// kind: 0 forward plane (2 channels per row + derivative table), 1 inverse
+// (1 channel), 2 backward forward-transform (1 channel), 3 backward inverse
+// (3 channels + table).
 template <int L, int C>
-__global__ void __launch_bounds__(kNT, 1)
+constexpr size_t plane_smem(int kind) {
+  using P = PlaneGeo<L, C>;
+  const int rp = kind == 0 ? L : (kind == 3 ? 3 * P::H : P::H);
+  const int table = (kind == 0 || kind == 3) ? L / 2 : 0;  // iu, as float2 units
+  return 1024 + sizeof(float2) * ((size_t)P::SCR + (size_t)P::R * rp + table + L);
+}
+
+// Two CTAs per SM where their shared memory fits (<= 113 KB each).
+template <int L, int C>
+constexpr int plane_minb(int kind) {
+  return plane_smem<L, C>(kind) <= 113 * 1024 ? 2 : 1;
+}
+
+
+// ===========================================================================
+// Forward plane kernel: splat + R2C(z) + FFT(y). 512 threads: each group of
+// T threads owns one (slot, channel) column in the y pass, so a chunk
+// transforms 16 slots of both channels of a round at once.
+// ===========================================================================
+constexpr int kNTF = 512;
+
+template <int L, int C>
+struct FwdGeo;
+template <int L, int C>
+struct FwdGeo {
+  using P = PlaneGeo<L, C>;
+  static constexpr int T = P::T, R1 = P::R1, G = kNTF / T;
+  static constexpr int CH = (G / 2 < P::SPC) ? G / 2 : P::SPC;  // slots per chunk
+  static constexpr int NB = (CH + 15) / 16;                       // boxes per channel
+  static constexpr int BOX = L * 16;
+  static constexpr int XP = L + 1;
+  static constexpr int SCR0 = 2 * NB * BOX > G * XP ? 2 * NB * BOX : G * XP;
+  static constexpr int SCR = (SCR0 + 127) / 128 * 128;
+  static_assert(T == 1 || CH == G / 2 || CH % (32 / T) == 0, "inactive groups must fill whole warps");
+};
+
+template <int L, int C>
+constexpr size_t fwd_smem() {
+  using F = FwdGeo<L, C>;
+  using P = PlaneGeo<L, C>;
+  return 1024 + sizeof(float2) * ((size_t)F::SCR + (size_t)P::R * L + L / 2 + L);
+}
+
+template <int L, int C>
+__global__ void __launch_bounds__(kNTF, 1)
     k_plane_fwd(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = PlaneGeo<L, C>;
+  using F = FwdGeo<L, C>;
   constexpr int RP = L;  // two channels of H packed slots (or L complex in real space)
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   cg::cluster_group cl = cg::this_cluster();
   const int c = (int)cl.block_rank();
   const int X = blockIdx.x / C;
-  const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
-  extern __shared__ float4 smem_raw[];
-  float2* rows = reinterpret_cast<float2*>(smem_raw);
-  float2* tw = rows + P::R * RP;
-  float* iu = reinterpret_cast<float*>(tw + L);
-  float2* scr = tw + L + L / 2;
-  float2* stg = scr + g * P::SP;
-  float2* rb[C];
+  const int tid = threadIdx.x, g = tid / F::T, t = tid % F::T;
+  extern __shared__ unsigned char smem_raw[];
+  float2* sbox = aligned_smem(smem_raw);
+  float2* rows = sbox + F::SCR;
+  float* iu = reinterpret_cast<float*>(rows + P::R * RP);
+  float2* twt = reinterpret_cast<float2*>(iu + L);
+  float2* xz = sbox + g * F::XP;  // per-group exchange area of the z pass
+  uint32_t rb[C];  // shared::cluster address of each CTA's rows
 #pragma unroll
-  for (int q = 0; q < C; ++q) rb[q] = cl.map_shared_rank(rows, q);
-  for (int i = tid; i < L; i += kNT) {
-    tw[i] = S.tw[i];
+  for (int q = 0; q < C; ++q) rb[q] = dsmem_map(rows, q);
+  for (int i = tid; i < L; i += kNTF) {
     iu[i] = S.iu[i];
+    twt[i] = S.tw[i];
   }
+  TwTab<L> twr{twt, t};
   const PlanePoints pp(S, X);
   const int y_lo = c * P::R;
+  // y pass: group g -> channel ch = g / (G/2), slot index sl = g % (G/2)
+  const int ch = g / (F::G / 2), sl = g % (F::G / 2);
+  const bool active = sl < F::CH;
+  const int slc = active ? sl : F::CH - 1;
+  float2* mybox = sbox + (ch * F::NB + slc / 16) * F::BOX;
+  auto xa = [&](int e) -> float2& { return mybox[bx(e, slc & 15)]; };
+  auto box_of = [&](int chn, int slot) { return sbox + (chn * F::NB + slot / 16) * F::BOX; };
 
   for (int round = 0; round < 2; ++round) {
-    for (int i = tid; i < P::R * RP; i += kNT) rows[i] = czero();
+    for (int i = tid; i < P::R * RP / 2; i += kNTF)
+      reinterpret_cast<float4*>(rows)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     // Rasterization (Eq. A2): round 0 splats (n_y, n_z), round 1 (n_x, 1).
-    for (int i = tid; i < pp.total(); i += kNT) {
+    for (int i = tid; i < pp.total(); i += kNTF) {
       int dx;
       const int idx = pp.index(i, dx);
       const float4 a = S.sorted[2 * idx], b = S.sorted[2 * idx + 1];
@@ -181,12 +249,12 @@ __global__ void __launch_bounds__(kNT, 1)
     }
     __syncthreads();
     // R2C along z of each row; channel B of round 0 takes the factor i u_z.
-    for (int r0 = 0; r0 < P::R; r0 += P::G) {
+    for (int r0 = 0; r0 < P::R; r0 += F::G) {
       const int row = r0 + g;
       const bool ok = row < P::R;
       const int rr = ok ? row : 0;
       r2c_pair<L>(
-          t, stg, tw, [&](int z) { return rows[sw<RP, P::SWM>(rr, z)]; },
+          t, xz, twr, [&](int z) { return rows[sw<RP, P::SWM>(rr, z)]; },
           [&](int s, float2 v) {
             if (ok) rows[sw<RP, P::SWM>(rr, s)] = v;
           },
@@ -197,47 +265,57 @@ __global__ void __launch_bounds__(kNT, 1)
           });
     }
     cl.sync();
-    // FFT along y of this CTA's slots, reading all rows of the plane.
-    for (int cb = 0; cb < P::SPC; cb += P::G) {
-      const int nvalid = min(P::G, P::SPC - cb);
+    // FFT along y of this CTA's slots (both channels at once), reading every
+    // row of the plane through DSMEM; results leave by TMA bulk stores.
+    for (int cb = 0; cb < P::SPC; cb += F::CH) {
       const int s_first = c * P::SPC + cb;
-      const int s = s_first + min(g, nvalid - 1);
-      float2 va[P::R1];
-      auto load = [&](float2(&v)[P::R1], int choff) {
+      const int s = s_first + slc;
+      // Groups without a slot skip the transform: they would share a box
+      // column with an active group. Inactivity is warp-uniform (chunks hold
+      // a multiple of 32/T slots) or T = 1 (no warp-level exchange).
+      if (active) {
+        float2 v[F::R1];
+        constexpr int RT = P::R / F::T;  // row y = t + T j lives in CTA j / RT
 #pragma unroll
-        for (int j = 0; j < P::R1; ++j) {
-          const int y = t + P::T * j;
-          v[j] = rb[y / P::R][sw<RP, P::SWM>(y % P::R, choff + s)];
+        for (int j = 0; j < F::R1; ++j)
+          v[j] = dsmem_ld(rb[j / RT] + 8u * sw<RP, P::SWM>(t + F::T * (j % RT), ch * P::H + s));
+        fft_r<L, -1>(v, t, xa, twr);
+#pragma unroll
+        for (int j = 0; j < F::R1; ++j) {
+          const int ky = t + F::T * j;
+          xa(ky) = (round == 0 && ch == 0) ? cmul_iu(v[j], iu[ky]) : v[j];
         }
-      };
-      load(va, 0);
-      fft<L, -1>(va, t, stg, tw);
-      if (round == 0) {
-        float2 vb[P::R1];
-        load(vb, P::H);
-        fft<L, -1>(vb, t, stg, tw);
-#pragma unroll
-        for (int j = 0; j < P::R1; ++j) {
-          const int ky = t + P::T * j;
-          stg[ky] = cadd(vb[j], cmul_iu(va[j], iu[ky]));
+      }
+      __syncthreads();
+      if (round == 0) {  // D = FFT_y(B) + i u_y FFT_y(A), into the channel-0 boxes
+        for (int i = tid; i < F::CH * L; i += kNTF) {
+          const int q = i % F::CH, ky = i / F::CH;
+          float2& d = box_of(0, q)[bx(ky, q & 15)];
+          d = cadd(d, box_of(1, q)[bx(ky, q & 15)]);
         }
-        __syncthreads();
-        store_cols<L, C>(S.spec[0], X, s_first, nvalid, scr);
-        __syncthreads();
-      } else {
-#pragma unroll
-        for (int j = 0; j < P::R1; ++j) stg[t + P::T * j] = va[j];
-        __syncthreads();
-        store_cols<L, C>(S.spec[1], X, s_first, nvalid, scr);
-        __syncthreads();
-        load(va, P::H);
-        fft<L, -1>(va, t, stg, tw);
-#pragma unroll
-        for (int j = 0; j < P::R1; ++j) stg[t + P::T * j] = va[j];
-        __syncthreads();
-        store_cols<L, C>(S.spec[2], X, s_first, nvalid, scr);
         __syncthreads();
       }
+      const int nch = round == 0 ? 1 : 2;
+      if (c == 0 && cb == 0 && sl == 0 && ch < nch) {
+        float2* dst = S.spec[round == 0 ? 0 : 1 + ch];
+        float2* bb = box_of(ch, 0);
+        separate_dc_nyq<L>(bb, t, [&](int ky, float2 w) {
+          if (P::H < 16) boxcol<L>(bb, P::H, ky) = w;
+          else dst[((size_t)X * L + ky) * P::KP + P::H] = w;
+        });
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        for (int k = 0; k < nch; ++k) {
+          const CUtensorMap* tm = &S.tmy[round == 0 ? 0 : 1 + k];
+          for (int b = 0; b < F::NB; ++b)
+            tma_store_3d(tm, s_first + 16 * b, 0, X, sbox + (k * F::NB + b) * F::BOX);
+        }
+        tma_store_commit();
+        tma_store_wait_read();
+      }
+      __syncthreads();
     }
     cl.sync();
   }
@@ -248,7 +326,7 @@ __global__ void __launch_bounds__(kNT, 1)
 // gradient of chi' at the points.
 // ===========================================================================
 template <int L, int C>
-__global__ void __launch_bounds__(kNT, 1)
+__global__ void __launch_bounds__(kNT, plane_minb<L, C>(1))
     k_plane_inv(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = PlaneGeo<L, C>;
   constexpr int RP = P::H;  // one channel
@@ -257,43 +335,65 @@ __global__ void __launch_bounds__(kNT, 1)
   const int c = (int)cl.block_rank();
   const int X = blockIdx.x / C;
   const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
-  extern __shared__ float4 smem_raw[];
-  float2* rows = reinterpret_cast<float2*>(smem_raw);
-  float2* tw = rows + P::R * RP;
-  float2* scr = tw + L;
-  float2* stg = scr + g * P::SP;
-  float2* rb[C];
-#pragma unroll
-  for (int q = 0; q < C; ++q) rb[q] = cl.map_shared_rank(rows, q);
-  for (int i = tid; i < L; i += kNT) tw[i] = S.tw[i];
+  extern __shared__ unsigned char smem_raw[];
+  float2* sbox = aligned_smem(smem_raw);
+  float2* rows = sbox + P::SCR;
+  float2* twt = rows + P::R * RP;
+  __shared__ uint64_t bar;
+  for (int i = tid; i < L; i += kNT) twt[i] = S.tw[i];
+  TwTab<L> twr{twt, t};
   const float a_chi = S.sc->a_chi, b_chi = S.sc->b_chi;
-
-  for (int cb = 0; cb < P::SPC; cb += P::G) {
-    const int nvalid = min(P::G, P::SPC - cb);
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  bool alive = true;
+  for (int cb = 0; cb < P::SPC && alive; cb += P::CHK) {
     const int s_first = c * P::SPC + cb;
-    load_cols<L, C>(S.spec[3], X, s_first, nvalid, scr, [](int, int, float2 v) { return v; });
-    __syncthreads();
+    if (tid == 0) chunk_load<L, C>(&S.tmy[3], sbox, s_first, X, &bar);
+    const bool head = (c == 0 && cb == 0);
+    float2 nyq[P::R1];
+    if (head && g == 0 && P::H >= 16) {
+#pragma unroll
+      for (int j = 0; j < P::R1; ++j)
+        nyq[j] = S.spec[3][((size_t)X * L + t + P::T * j) * P::KP + P::H];
+    }
+    alive = chunk_wait(&bar, phase, S.status);
+    phase ^= 1;
+    if (!alive) break;
+    auto xa = [&](int e) -> float2& { return boxcol<L>(sbox, g, e); };
     float2 v[P::R1];
 #pragma unroll
-    for (int j = 0; j < P::R1; ++j) v[j] = stg[t + P::T * j];
-    fft<L, +1>(v, t, stg, tw);
+    for (int j = 0; j < P::R1; ++j) {
+      const int ky = t + P::T * j;
+      v[j] = xa(ky);
+      if (head && g == 0) {  // pack X0 + i Xn
+        const float2 n = P::H >= 16 ? nyq[j] : boxcol<L>(sbox, P::H, ky);
+        v[j] = make_float2(v[j].x - n.y, v[j].y + n.x);
+      }
+    }
+    fft_r<L, +1>(v, t, xa, twr);
 #pragma unroll
-    for (int j = 0; j < P::R1; ++j) stg[t + P::T * j] = v[j];
+    for (int j = 0; j < P::R1; ++j) xa(t + P::T * j) = v[j];
     __syncthreads();
-    push_cols<L, C, RP>(rb, s_first, nvalid, 0, scr);
+    push_cols<L, C, RP>(cl, rows, s_first, 0, sbox);
     __syncthreads();
   }
   cl.sync();
+  if (!alive) return;
   // C2R along z of row pairs (2p, 2p+1); output written in place as pairs
   // (y_2p[z], y_2p+1[z]) at logical slot z of the pair.
   float* chi = S.chi;
+  float2* xz = sbox + g * P::XP;
   for (int p0 = 0; p0 < P::R / 2; p0 += P::G) {
     const int p = p0 + g;
     const bool ok = p < P::R / 2;
     const int pr = ok ? p : 0;
     const int ya = c * P::R + 2 * pr;
     c2r_pair<L>(
-        t, stg, tw, [&](int k) { return rows[sw<RP, P::SWM>(2 * pr, k)]; },
+        t, xz, twr, [&](int k) { return rows[sw<RP, P::SWM>(2 * pr, k)]; },
         [&](int k) { return rows[sw<RP, P::SWM>(2 * pr + 1, k)]; },
         [&](int z, float2 v) {
           if (!ok) return;
@@ -311,7 +411,7 @@ __global__ void __launch_bounds__(kNT, 1)
     const int y_lo = c * P::R;
     auto yval = [&](int y, int z) {
       const int q = y / P::R, lr = y % P::R, p2 = lr & ~1;
-      const float2 f = rb[q][sw<RP, P::SWM>(p2 + z / P::H, z % P::H)];
+      const float2 f = dsmem_ld(dsmem_map(rows, q) + 8u * sw<RP, P::SWM>(p2 + z / P::H, z % P::H));
       return (lr & 1) ? f.y : f.x;
     };
     for (int i = tid; i < pp.total(); i += kNT) {
@@ -347,7 +447,7 @@ __global__ void __launch_bounds__(kNT, 1)
 // dchi * chi needed by the adjoint of Eq. 4.
 // ===========================================================================
 template <int L, int C>
-__global__ void __launch_bounds__(kNT, 1)
+__global__ void __launch_bounds__(kNT, plane_minb<L, C>(2))
     k_plane_bfwd(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = PlaneGeo<L, C>;
   constexpr int RP = P::H;
@@ -356,35 +456,49 @@ __global__ void __launch_bounds__(kNT, 1)
   const int c = (int)cl.block_rank();
   const int X = blockIdx.x / C;
   const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
-  extern __shared__ float4 smem_raw[];
-  float2* rows = reinterpret_cast<float2*>(smem_raw);
-  float2* tw = rows + P::R * RP;
-  float2* scr = tw + L;
-  float2* stg = scr + g * P::SP;
+  extern __shared__ unsigned char smem_raw[];
+  float2* sbox = aligned_smem(smem_raw);
+  float2* rows = sbox + P::SCR;
+  float2* twt = rows + P::R * RP;
+  float2* xz = sbox + g * P::XP;
+  for (int i = tid; i < L; i += kNT) twt[i] = S.tw[i];
   __shared__ double red[2][kNT / 32];
-  float2* rb[C];
+  uint32_t rb[C];  // shared::cluster address of each CTA's rows
 #pragma unroll
-  for (int q = 0; q < C; ++q) rb[q] = cl.map_shared_rank(rows, q);
-  for (int i = tid; i < L; i += kNT) tw[i] = S.tw[i];
+  for (int q = 0; q < C; ++q) rb[q] = dsmem_map(rows, q);
+  TwTab<L> twr{twt, t};
+  __shared__ uint64_t bar;
+  // The CTA's R rows of dchi are contiguous in HBM: one bulk copy into the
+  // rows buffer (R real rows of L floats fill exactly R packed half-spectrum
+  // rows), then the sums of Eq. 4's adjoint against chi with vector loads.
+  const size_t row0 = ((size_t)X * L + c * P::R) * L;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(&bar, P::R * L * (uint32_t)sizeof(float));
+    bulk_load(rows, S.dchi + row0, P::R * L * (uint32_t)sizeof(float), &bar);
+  }
+  const float4* chi4 = reinterpret_cast<const float4*>(S.chi + row0);
   __syncthreads();
-  const float* gin = S.dchi;
-  const float* chi = S.chi;
+  const bool landed = chunk_wait(&bar, 0, S.status);
   float accS = 0.f, accD = 0.f;
-  for (int p0 = 0; p0 < P::R / 2; p0 += P::G) {
+  if (landed) {
+    const float4* g4 = reinterpret_cast<const float4*>(rows);
+#pragma unroll 4
+    for (int i = tid; i < P::R * L / 4; i += kNT) {
+      const float4 a = g4[i], b = chi4[i];
+      accS += (a.x + a.y) + (a.z + a.w);
+      accD += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+    }
+  }
+  __syncthreads();
+  const float* rf = reinterpret_cast<const float*>(rows);
+  for (int p0 = 0; p0 < P::R / 2 && landed; p0 += P::G) {
     const int p = p0 + g;
     const bool ok = p < P::R / 2;
     const int pr = ok ? p : 0;
-    const size_t o = ((size_t)X * L + c * P::R + 2 * pr) * L;
     r2c_pair<L>(
-        t, stg, tw,
-        [&](int z) {
-          const float a = gin[o + z], b = gin[o + L + z];
-          if (ok) {
-            accS += a + b;
-            accD += a * chi[o + z] + b * chi[o + L + z];
-          }
-          return make_float2(a, b);
-        },
+        t, xz, twr, [&](int z) { return make_float2(rf[2 * pr * L + z], rf[(2 * pr + 1) * L + z]); },
         [&](int s, float2 v) {
           if (ok) rows[sw<RP, P::SWM>(2 * pr, s)] = v;
         },
@@ -393,21 +507,30 @@ __global__ void __launch_bounds__(kNT, 1)
         });
   }
   cl.sync();
-  for (int cb = 0; cb < P::SPC; cb += P::G) {
-    const int nvalid = min(P::G, P::SPC - cb);
+  for (int cb = 0; cb < P::SPC; cb += P::CHK) {
     const int s_first = c * P::SPC + cb;
-    const int s = s_first + min(g, nvalid - 1);
+    const int s = s_first + min(g, P::CHK - 1);
+    auto xa = [&](int e) -> float2& { return boxcol<L>(sbox, g, e); };
     float2 v[P::R1];
+    constexpr int RT = P::R / P::T;  // row y = t + T j lives in CTA j / RT
 #pragma unroll
-    for (int j = 0; j < P::R1; ++j) {
-      const int y = t + P::T * j;
-      v[j] = rb[y / P::R][sw<RP, P::SWM>(y % P::R, s)];
-    }
-    fft<L, -1>(v, t, stg, tw);
+    for (int j = 0; j < P::R1; ++j) v[j] = dsmem_ld(rb[j / RT] + 8u * sw<RP, P::SWM>(t + P::T * (j % RT), s));
+    fft_r<L, -1>(v, t, xa, twr);
 #pragma unroll
-    for (int j = 0; j < P::R1; ++j) stg[t + P::T * j] = v[j];
+    for (int j = 0; j < P::R1; ++j) xa(t + P::T * j) = v[j];
     __syncthreads();
-    store_cols<L, C>(S.spec[3], X, s_first, nvalid, scr);
+    if (c == 0 && cb == 0 && g == 0) {
+      separate_dc_nyq<L>(sbox, t, [&](int ky, float2 w) {
+        if (P::H < 16) boxcol<L>(sbox, P::H, ky) = w;
+        else S.spec[3][((size_t)X * L + ky) * P::KP + P::H] = w;
+      });
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      chunk_store<L, C>(&S.tmy[3], sbox, s_first, X);
+      tma_store_wait_read();
+    }
     __syncthreads();
   }
   // block partial sums in FP64, fixed order
@@ -442,7 +565,7 @@ __global__ void __launch_bounds__(kNT, 1)
 // part of dpoints, per plane side.
 // ===========================================================================
 template <int L, int C>
-__global__ void __launch_bounds__(kNT, 1)
+__global__ void __launch_bounds__(kNT, plane_minb<L, C>(3))
     k_plane_binv(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = PlaneGeo<L, C>;
   constexpr int RP = 3 * P::H;  // channels X | Y | Z
@@ -451,74 +574,84 @@ __global__ void __launch_bounds__(kNT, 1)
   const int c = (int)cl.block_rank();
   const int X = blockIdx.x / C;
   const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
-  extern __shared__ float4 smem_raw[];
-  float2* rows = reinterpret_cast<float2*>(smem_raw);
-  float2* tw = rows + P::R * RP;
-  float* iu = reinterpret_cast<float*>(tw + L);
-  float2* scr = tw + L + L / 2;
-  float2* stg = scr + g * P::SP;
-  float2* rb[C];
-#pragma unroll
-  for (int q = 0; q < C; ++q) rb[q] = cl.map_shared_rank(rows, q);
+  extern __shared__ unsigned char smem_raw[];
+  float2* sbox = aligned_smem(smem_raw);
+  float2* rows = sbox + P::SCR;
+  float* iu = reinterpret_cast<float*>(rows + P::R * RP);
+  float2* twt = reinterpret_cast<float2*>(iu + L);
+  __shared__ uint64_t bar;
   for (int i = tid; i < L; i += kNT) {
-    tw[i] = S.tw[i];
     iu[i] = S.iu[i];
+    twt[i] = S.tw[i];
+  }
+  TwTab<L> twr{twt, t};
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-
-  for (int cb = 0; cb < P::SPC; cb += P::G) {
-    const int nvalid = min(P::G, P::SPC - cb);
+  uint32_t phase = 0;
+  bool alive = true;
+  for (int cb = 0; cb < P::SPC && alive; cb += P::CHK) {
     const int s_first = c * P::SPC + cb;
-    const int s = s_first + min(g, nvalid - 1);
+    const int s = s_first + min(g, P::CHK - 1);
+    const bool head = (c == 0 && cb == 0);
+    auto xa = [&](int e) -> float2& { return boxcol<L>(sbox, g, e); };
     float2 v[P::R1];
-    // X channel: Q2 = IFFT_x(-i u_x F), y-inverse as is.
-    load_cols<L, C>(S.spec[1], X, s_first, nvalid, scr, [](int, int, float2 w) { return w; });
-    __syncthreads();
+    // X channel: Q2 = IFFT_x(-i u_x F), y-inverse as is. Y and Z channels from
+    // Q1 = IFFT_x(F): -i u_y before the y-inverse, -i u_z (a constant per
+    // column) for Z.
+    for (int src = 0; src < 3 && alive; ++src) {
+      // src 0: X from Q2; src 1: Y = -i u_y Q1; src 2: Z = -i u_z Q1 (Q1 is
+      // loaded again rather than kept in registers; the second load hits L2)
+      const int buf = src == 0 ? 1 : 0;
+      if (tid == 0) chunk_load<L, C>(&S.tmy[buf], sbox, s_first, X, &bar);
+      float2 nyq[P::R1];
+      if (head && g == 0 && P::H >= 16) {
 #pragma unroll
-    for (int j = 0; j < P::R1; ++j) v[j] = stg[t + P::T * j];
-    fft<L, +1>(v, t, stg, tw);
+        for (int j = 0; j < P::R1; ++j)
+          nyq[j] = S.spec[buf][((size_t)X * L + t + P::T * j) * P::KP + P::H];
+      }
+      alive = chunk_wait(&bar, phase, S.status);
+      phase ^= 1;
+      if (!alive) break;
 #pragma unroll
-    for (int j = 0; j < P::R1; ++j) stg[t + P::T * j] = v[j];
-    __syncthreads();
-    push_cols<L, C, RP>(rb, s_first, nvalid, 0, scr);
-    __syncthreads();
-    // Y and Z channels from Q1 = IFFT_x(F): -i u_y before the y-inverse,
-    // -i u_z (a constant per column) for Z.
-    load_cols<L, C>(S.spec[0], X, s_first, nvalid, scr, [](int, int, float2 w) { return w; });
-    __syncthreads();
-    float2 q1[P::R1];
+      for (int j = 0; j < P::R1; ++j) {
+        const int ky = t + P::T * j;
+        v[j] = xa(ky);
+        if (head && g == 0) {
+          const float2 n = P::H >= 16 ? nyq[j] : boxcol<L>(sbox, P::H, ky);
+          v[j] = make_float2(v[j].x - n.y, v[j].y + n.x);
+        }
+      }
+      if (src == 1) {
 #pragma unroll
-    for (int j = 0; j < P::R1; ++j) {
-      const int ky = t + P::T * j;
-      q1[j] = stg[ky];
-      v[j] = cmul_iu(q1[j], -iu[ky]);
+        for (int j = 0; j < P::R1; ++j) v[j] = cmul_iu(v[j], -iu[t + P::T * j]);
+      } else if (src == 2) {
+        const float ez = s == 0 ? 0.f : -iu[s];
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) v[j] = cmul_iu(v[j], ez);
+      }
+      fft_r<L, +1>(v, t, xa, twr);
+#pragma unroll
+      for (int j = 0; j < P::R1; ++j) xa(t + P::T * j) = v[j];
+      __syncthreads();
+      push_cols<L, C, RP>(cl, rows, s_first, src * P::H, sbox);
+      __syncthreads();
     }
-    fft<L, +1>(v, t, stg, tw);
-#pragma unroll
-    for (int j = 0; j < P::R1; ++j) stg[t + P::T * j] = v[j];
-    __syncthreads();
-    push_cols<L, C, RP>(rb, s_first, nvalid, P::H, scr);
-    __syncthreads();
-    const float ez = s == 0 ? 0.f : -iu[s];
-#pragma unroll
-    for (int j = 0; j < P::R1; ++j) v[j] = cmul_iu(q1[j], ez);
-    fft<L, +1>(v, t, stg, tw);
-#pragma unroll
-    for (int j = 0; j < P::R1; ++j) stg[t + P::T * j] = v[j];
-    __syncthreads();
-    push_cols<L, C, RP>(rb, s_first, nvalid, 2 * P::H, scr);
-    __syncthreads();
   }
   cl.sync();
+  if (!alive) return;
   // C2R along z: rows of (X, Y) pairs in place as (Vx[z], Vy[z]); Z channel
   // by row pairs, in place as (Vz_2p[z], Vz_2p+1[z]) over the Z slots of the
   // two rows.
+  float2* xz = sbox + g * P::XP;
   for (int r0 = 0; r0 < P::R; r0 += P::G) {
     const int row = r0 + g;
     const bool ok = row < P::R;
     const int rr = ok ? row : 0;
     c2r_pair<L>(
-        t, stg, tw, [&](int k) { return rows[sw<RP, P::SWM>(rr, k)]; },
+        t, xz, twr, [&](int k) { return rows[sw<RP, P::SWM>(rr, k)]; },
         [&](int k) { return rows[sw<RP, P::SWM>(rr, P::H + k)]; },
         [&](int z, float2 w) {
           if (ok) rows[sw<RP, P::SWM>(rr, z)] = w;
@@ -529,7 +662,7 @@ __global__ void __launch_bounds__(kNT, 1)
     const bool ok = p < P::R / 2;
     const int pr = ok ? p : 0;
     c2r_pair<L>(
-        t, stg, tw, [&](int k) { return rows[sw<RP, P::SWM>(2 * pr, 2 * P::H + k)]; },
+        t, xz, twr, [&](int k) { return rows[sw<RP, P::SWM>(2 * pr, 2 * P::H + k)]; },
         [&](int k) { return rows[sw<RP, P::SWM>(2 * pr + 1, 2 * P::H + k)]; },
         [&](int z, float2 w) {
           if (ok) rows[sw<RP, P::SWM>(2 * pr + z / P::H, 2 * P::H + z % P::H)] = w;
@@ -557,8 +690,9 @@ __global__ void __launch_bounds__(kNT, 1)
         for (int dz = 0; dz < 2; ++dz) {
           const int z = dz ? az.i1 : az.i0;
           const float fz = wsel(dz, az.t), dfz = dz ? (float)L : -(float)L;
-          const float2 xy = rb[q][sw<RP, P::SWM>(lr, z)];
-          const float2 zz = rb[q][sw<RP, P::SWM>(p2 + z / P::H, 2 * P::H + z % P::H)];
+          const uint32_t rq = dsmem_map(rows, q);
+          const float2 xy = dsmem_ld(rq + 8u * sw<RP, P::SWM>(lr, z));
+          const float2 zz = dsmem_ld(rq + 8u * sw<RP, P::SWM>(p2 + z / P::H, 2 * P::H + z % P::H));
           const float vz = (lr & 1) ? zz.y : zz.x;
           const float w = fx * fy * fz;
           nb0 += w * xy.x;
@@ -586,14 +720,6 @@ __global__ void __launch_bounds__(kNT, 1)
 // Launchers
 // ---------------------------------------------------------------------------
 template <int L, int C>
-constexpr size_t plane_smem(int kind) {
-  using P = PlaneGeo<L, C>;
-  const int rp = kind == 0 ? L : (kind == 3 ? 3 * P::H : P::H);
-  const int extra = (kind == 0 || kind == 3) ? L / 2 : 0;  // iu table
-  return sizeof(float2) * ((size_t)P::R * rp + L + extra + (size_t)P::G * P::SP);
-}
-
-template <int L, int C>
 static cudaError_t launch_plane_t(int kind, const Solve& s, const Solve* tab, int count,
                                   cudaStream_t st) {
   void (*fn)(Solve, const Solve*) = nullptr;
@@ -603,18 +729,20 @@ static cudaError_t launch_plane_t(int kind, const Solve& s, const Solve* tab, in
     case 2: fn = k_plane_bfwd<L, C>; break;
     default: fn = k_plane_binv<L, C>; break;
   }
-  const size_t smem = plane_smem<L, C>(kind);
+  const size_t smem = kind == 0 ? fwd_smem<L, C>() : plane_smem<L, C>(kind);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   static bool attr_set[4] = {false, false, false, false};  // per instantiation and kind
   if (!attr_set[kind]) {
     cudaError_t e =
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && C > 8)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     attr_set[kind] = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(L * C, 1, count);
-  cfg.blockDim = dim3(kNT, 1, 1);
+  cfg.blockDim = dim3(kind == 0 ? kNTF : kNT, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -632,7 +760,8 @@ static cudaError_t launch_plane_t(int kind, const Solve& s, const Solve* tab, in
 // plane do not fit one SM's shared memory there).
 template <int L, int C>
 constexpr bool plane_inst() {
-  return L <= 64 ? C == 1 : (L == 128 ? (C == 1 || C == 2 || C == 4) : (C == 2 || C == 4 || C == 8));
+  return L <= 64 ? C == 1
+                 : (L == 128 ? (C == 1 || C == 2 || C == 4) : (C == 2 || C == 4 || C == 8 || C == 16));
 }
 
 template <int L>
@@ -643,6 +772,7 @@ static cudaError_t launch_plane_L(int kind, int C, const Solve& s, const Solve* 
     case 2: if constexpr (plane_inst<L, 2>()) return launch_plane_t<L, 2>(kind, s, tab, count, st); break;
     case 4: if constexpr (plane_inst<L, 4>()) return launch_plane_t<L, 4>(kind, s, tab, count, st); break;
     case 8: if constexpr (plane_inst<L, 8>()) return launch_plane_t<L, 8>(kind, s, tab, count, st); break;
+    case 16: if constexpr (plane_inst<L, 16>()) return launch_plane_t<L, 16>(kind, s, tab, count, st); break;
     default: break;
   }
   return cudaErrorInvalidValue;
@@ -665,10 +795,11 @@ size_t plane_smem_bytes(int kind, int r, int C) {
   auto pick = [&](auto Lc) -> size_t {
     constexpr int L = decltype(Lc)::value;
     switch (C) {
-      case 1: if constexpr (plane_inst<L, 1>()) return plane_smem<L, 1>(kind); return 0;
-      case 2: if constexpr (plane_inst<L, 2>()) return plane_smem<L, 2>(kind); return 0;
-      case 4: if constexpr (plane_inst<L, 4>()) return plane_smem<L, 4>(kind); return 0;
-      case 8: if constexpr (plane_inst<L, 8>()) return plane_smem<L, 8>(kind); return 0;
+      case 1: if constexpr (plane_inst<L, 1>()) return kind == 0 ? fwd_smem<L, 1>() : plane_smem<L, 1>(kind); return 0;
+      case 2: if constexpr (plane_inst<L, 2>()) return kind == 0 ? fwd_smem<L, 2>() : plane_smem<L, 2>(kind); return 0;
+      case 4: if constexpr (plane_inst<L, 4>()) return kind == 0 ? fwd_smem<L, 4>() : plane_smem<L, 4>(kind); return 0;
+      case 8: if constexpr (plane_inst<L, 8>()) return kind == 0 ? fwd_smem<L, 8>() : plane_smem<L, 8>(kind); return 0;
+      case 16: if constexpr (plane_inst<L, 16>()) return kind == 0 ? fwd_smem<L, 16>() : plane_smem<L, 16>(kind); return 0;
       default: return 0;
     }
   };

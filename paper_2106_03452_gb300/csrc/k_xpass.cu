@@ -1,107 +1,139 @@
 // x-axis pass: FFT along x of the partially transformed fields, the spectral
 // solve of Eq. 3 (forward) or its adjoint (backward), and the inverse FFT
-// along x, for a tile of 16 consecutive kz columns at one ky.
+// along x, for a tile of 16 consecutive kz columns at one ky, moved between
+// HBM and shared memory by TMA.
 //
 // Forward:  chi~ = G(k) (D + i u_x C),  G = g(u) / (-2 pi |u|^2),
 //           g = exp(-2 sigma^2 |u|^2 / r^2)                        (Eq. 3, A7)
 //           with the spectral sums for the mean and the value at x = 0 of
-//           Eq. 4 (Parseval over the half spectrum).
+//           Eq. 4 (Parseval over the half spectrum, and along x).
 // Backward: F = G(k) (g_a FFT(dchi) + g_s + g_w W~);  Q1 = IFFT_x(F),
 //           Q2 = IFFT_x(-i u_x F)  (the adjoint of Eq. 3, conj(H_a) = -H_a).
+// Three FFTs of length r per column in each direction.
 #include "dpsr_dev.cuh"
 #include "launch.h"
+#include "tma.cuh"
 
 namespace dpsr {
 
 template <int L>
 struct XGeo {
   static constexpr int R1 = Shape<L>::R1, T = Shape<L>::T;
-  static constexpr int KC = 16 * T >= 32 ? 16 : 32 / T;  // kz columns per CTA (>= 1 warp)
-  static constexpr int NT = KC * T;      // threads
-  static constexpr int SP = L + 1;       // smem column pitch
+  static constexpr int KC = 16;                             // kz columns per CTA (one TMA box row)
+  static constexpr int NG = KC * T >= 32 ? KC : 32 / T;     // groups (at least one warp)
+  static constexpr int NT = NG * T;                         // threads
   static constexpr int H = L / 2;
-  static constexpr int KP = L / 2 + 2;
   static constexpr int NCHUNK = (H + 1 + KC - 1) / KC;
+  static constexpr int BOX = L * KC;                        // float2 per box
 };
 
-__device__ __forceinline__ float spectral_G(int kx, int ky, int kz, const float* g1,
+// G(k) = g(k) / (-2 pi |u|^2) with g separable: g1[kx] * (g1[ky] g1[kz]);
+// gyz and u2yz are the per-thread (ky, kz) factors. Zero at k = 0.
+__device__ __forceinline__ float spectral_G(int kx, float gyz, float u2yz, const float* g1,
                                             const float* u2) {
-  const float s = u2[kx] + u2[ky] + u2[kz];
+  const float s = u2[kx] + u2yz;
   if (s == 0.f) return 0.f;
-  return g1[kx] * g1[ky] * g1[kz] / (-6.28318530717958647692f * s);
+  return __fdividef(g1[kx] * gyz, -6.28318530717958647692f * s);
 }
 
 template <int L, bool BWD>
-__global__ void __launch_bounds__(XGeo<L>::NT)
+constexpr size_t xpass_smem() {
+  using P = XGeo<L>;
+  constexpr int NCH = BWD ? 2 : 3;
+  return 1024 + sizeof(float2) * ((size_t)NCH * P::BOX + L) + 3 * sizeof(float) * L;
+}
+
+// One CTA per (kz tile of 16, ky): TMA loads the tiles [x][16 kz] of the
+// input channels (128B-swizzled boxes), each group of T threads transforms
+// one kz column along x in registers (the box column doubles as its exchange
+// buffer), and TMA stores the results.
+template <int L, bool BWD>
+__global__ void __launch_bounds__(XGeo<L>::NT, 2)
     k_xpass(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = XGeo<L>;
   constexpr int NCH = BWD ? 2 : 3;
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   const int kz0 = blockIdx.x * P::KC, ky = blockIdx.y;
   const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
-  extern __shared__ float4 smem_raw[];
-  float2* buf = reinterpret_cast<float2*>(smem_raw);  // [NCH][KC][SP]
-  float2* tw = buf + NCH * P::KC * P::SP;
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+  float2* box = reinterpret_cast<float2*>(smem_raw + pad);  // NCH boxes, 1024-aligned
+  float2* tw = box + NCH * P::BOX;
   float* g1 = reinterpret_cast<float*>(tw + L);
   float* u2 = g1 + L;
   float* iu = u2 + L;
-  __shared__ double red[2][P::NT / 32 + 1];
+  __shared__ uint64_t bar;
+  __shared__ double red[2][P::NT / 32];
+  // inputs: forward D, C, W~; backward FFT_zy(dchi), W~
+  const int src0 = BWD ? 3 : 0, src1 = BWD ? 2 : 1;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(&bar, NCH * P::BOX * (uint32_t)sizeof(float2));
+    tma_load_3d(box, &S.tmx[src0], kz0, ky, 0, &bar);
+    tma_load_3d(box + P::BOX, &S.tmx[src1], kz0, ky, 0, &bar);
+    if constexpr (!BWD) tma_load_3d(box + 2 * P::BOX, &S.tmx[2], kz0, ky, 0, &bar);
+  }
   for (int i = tid; i < L; i += P::NT) {
     tw[i] = S.tw[i];
     g1[i] = S.g1[i];
     u2[i] = S.u2[i];
     iu[i] = S.iu[i];
   }
-  const float2* src[NCH];
-  if constexpr (BWD) {
-    src[0] = S.spec[3];  // FFT_zy(dchi)
-    src[1] = S.spec[2];  // W~ (zy)
-  } else {
-    src[0] = S.spec[0];  // D
-    src[1] = S.spec[1];  // C
-    src[2] = S.spec[2];  // W~
-  }
-  for (int i = tid; i < NCH * P::KC * L; i += P::NT) {
-    const int ch = i / (P::KC * L), rem = i % (P::KC * L);
-    const int x = rem / P::KC, kzl = rem % P::KC, kz = kz0 + kzl;
-    float2 v = czero();
-    if (kz <= P::H) v = src[ch][((size_t)x * L + ky) * P::KP + kz];
-    buf[(ch * P::KC + kzl) * P::SP + x] = v;
-  }
   __syncthreads();
-  const int kz = min(kz0 + g, P::H);
-  const bool valid = kz0 + g <= P::H;
-  float2* c0 = buf + (0 * P::KC + g) * P::SP;
-  float2* c1 = buf + (1 * P::KC + g) * P::SP;
-  float2 a[P::R1], b[P::R1];
-#pragma unroll
-  for (int j = 0; j < P::R1; ++j) a[j] = c0[t + P::T * j];
-  fft<L, -1>(a, t, c0, tw);
-#pragma unroll
-  for (int j = 0; j < P::R1; ++j) b[j] = c1[t + P::T * j];
-  fft<L, -1>(b, t, c1, tw);
+  const bool landed = __syncthreads_and(mbar_wait(&bar, 0));
+  if (!landed) {
+    if (tid == 0) atomicOr(S.status, kStTimeout);
+    mbar_wait(&bar, 0);  // give copies in flight a last bounded chance before leaving
+    return;
+  }
+  const int gc = g < P::KC ? g : P::KC - 1;  // extra groups (tiny r) shadow the last column
+  const bool own = g < P::KC;
+  const int kz = min(kz0 + gc, P::H);
+  const bool valid = own && kz0 + g <= P::H;
+  Twid<L> twr;
+  twr.load(t, tw);
+  const float gyz = g1[ky] * g1[kz], u2yz = u2[ky] + u2[kz];
+  auto colref = [&](int ch) {
+    float2* b = box + ch * P::BOX;
+    return [b, gc](int e) -> float2& { return b[bx(e, gc)]; };
+  };
+  auto c0 = colref(0);
+  auto c1 = colref(1);
+  float2 a[P::R1];
   if constexpr (!BWD) {
-    float2* c2 = buf + (2 * P::KC + g) * P::SP;
-    float2 w[P::R1];
+    // chi~ = G (FFT_x(D) + i u_x FFT_x(C))
+    float2 b[P::R1];
 #pragma unroll
-    for (int j = 0; j < P::R1; ++j) w[j] = c2[t + P::T * j];
-    fft<L, -1>(w, t, c2, tw);
-    const float wz = (kz == 0 || kz == P::H) ? 1.f : 2.f;
-    float am = 0.f, as = 0.f;
+    for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
+    fft_r<L, -1>(a, t, c0, twr);
+#pragma unroll
+    for (int j = 0; j < P::R1; ++j) b[j] = c1(t + P::T * j);
+    fft_r<L, -1>(b, t, c1, twr);
 #pragma unroll
     for (int j = 0; j < P::R1; ++j) {
       const int kx = t + P::T * j;
-      const float G = spectral_G(kx, ky, kz, g1, u2);
-      const float2 chi = cscale(cadd(a[j], cmul_iu(b[j], iu[kx])), G);
-      am += w[j].x * chi.x + w[j].y * chi.y;  // Re(conj(W~) chi~)
-      as += chi.x;
-      a[j] = chi;
+      const float G = spectral_G(kx, gyz, u2yz, g1, u2);
+      a[j] = cscale(cadd(a[j], cmul_iu(b[j], iu[kx])), G);
     }
-    if (!valid) am = as = 0.f;
-    fft<L, +1>(a, t, c0, tw);
+    fft_r<L, +1>(a, t, c0, twr);  // P = unnormalised IFFT_x(chi~)
+    // Spectral sums of Eq. 4, by Parseval along x against the x-domain W~:
+    // sum_kx conj(W~(kx)) chi~(kx) = sum_x conj(W~_x(x)) P(x),
+    // sum_kx chi~(kx) = P(x = 0).
+    auto c2 = colref(2);
+    float am = 0.f, as = 0.f;
 #pragma unroll
-    for (int j = 0; j < P::R1; ++j) c0[t + P::T * j] = a[j];
-    // block partial sums (FP64, fixed order)
+    for (int j = 0; j < P::R1; ++j) {
+      const float2 w = c2(t + P::T * j);
+      am += w.x * a[j].x + w.y * a[j].y;
+    }
+    if (t == 0) as = a[0].x;
+    const float wz = (kz == 0 || kz == P::H) ? 1.f : 2.f;
+    if (!valid) am = as = 0.f;
+    if (own) {
+#pragma unroll
+      for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = a[j];
+    }
     double dm = (double)am * wz, ds = (double)as * wz;
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) {
@@ -112,8 +144,11 @@ __global__ void __launch_bounds__(XGeo<L>::NT)
       red[0][tid >> 5] = dm;
       red[1][tid >> 5] = ds;
     }
+    fence_async_smem();
     __syncthreads();
     if (tid == 0) {
+      tma_store_3d(&S.tmx[3], kz0, ky, 0, box);
+      tma_store_commit();
       double sm = 0, ss = 0;
       for (int q = 0; q < P::NT / 32; ++q) {
         sm += red[0][q];
@@ -122,37 +157,44 @@ __global__ void __launch_bounds__(XGeo<L>::NT)
       const size_t bid = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
       S.part[2 * bid] = sm;
       S.part[2 * bid + 1] = ss;
-    }
-    for (int i = tid; i < P::KC * L; i += P::NT) {
-      const int x = i / P::KC, kzl = i % P::KC, kzz = kz0 + kzl;
-      if (kzz <= P::H) S.spec[3][((size_t)x * L + ky) * P::KP + kzz] = buf[kzl * P::SP + x];
+      tma_store_wait_read();
     }
   } else {
+    // FFT_x of (g_a FFT_zy(dchi) + g_w W~ + g_s delta_{x=0}): the three terms
+    // of the adjoint spectrum combined before the transform (it is linear).
     const Scalars* sc = S.sc;
     const float ga = sc->g_a, gs = sc->g_s, gw = sc->g_w;
 #pragma unroll
     for (int j = 0; j < P::R1; ++j) {
+      const int x = t + P::T * j;
+      a[j] = cadd(cscale(c0(x), ga), cscale(c1(x), gw));
+      if (x == 0) a[j].x += gs;
+    }
+    fft_r<L, -1>(a, t, c0, twr);
+    float2 b[P::R1];
+#pragma unroll
+    for (int j = 0; j < P::R1; ++j) {
       const int kx = t + P::T * j;
-      const float G = spectral_G(kx, ky, kz, g1, u2);
-      float2 f = cadd(cscale(a[j], ga), cscale(b[j], gw));
-      f.x += gs;
-      f = cscale(f, G);
+      const float2 f = cscale(a[j], spectral_G(kx, gyz, u2yz, g1, u2));
       a[j] = f;
       b[j] = cmul_iu(f, -iu[kx]);
     }
-    fft<L, +1>(a, t, c0, tw);
-    fft<L, +1>(b, t, c1, tw);
+    fft_r<L, +1>(a, t, c0, twr);
+    fft_r<L, +1>(b, t, c1, twr);
+    if (own) {
 #pragma unroll
-    for (int j = 0; j < P::R1; ++j) {
-      c0[t + P::T * j] = a[j];
-      c1[t + P::T * j] = b[j];
+      for (int j = 0; j < P::R1; ++j) {
+        c0(t + P::T * j) = a[j];
+        c1(t + P::T * j) = b[j];
+      }
     }
+    fence_async_smem();
     __syncthreads();
-    for (int i = tid; i < 2 * P::KC * L; i += P::NT) {
-      const int ch = i / (P::KC * L), rem = i % (P::KC * L);
-      const int x = rem / P::KC, kzl = rem % P::KC, kzz = kz0 + kzl;
-      if (kzz <= P::H)
-        S.spec[ch][((size_t)x * L + ky) * P::KP + kzz] = buf[(ch * P::KC + kzl) * P::SP + x];
+    if (tid == 0) {
+      tma_store_3d(&S.tmx[0], kz0, ky, 0, box);
+      tma_store_3d(&S.tmx[1], kz0, ky, 0, box + P::BOX);
+      tma_store_commit();
+      tma_store_wait_read();
     }
   }
 }
@@ -160,8 +202,7 @@ __global__ void __launch_bounds__(XGeo<L>::NT)
 template <int L, bool BWD>
 static cudaError_t launch_xpass_t(const Solve& s, const Solve* tab, int count, cudaStream_t st) {
   using P = XGeo<L>;
-  constexpr int NCH = BWD ? 2 : 3;
-  const size_t smem = sizeof(float2) * ((size_t)NCH * P::KC * P::SP + L) + 3 * sizeof(float) * L;
+  constexpr size_t smem = xpass_smem<L, BWD>();
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_xpass<L, BWD>,

@@ -16,6 +16,9 @@ cudaError_t launch_xpass(bool bwd, int r, const Solve& s, const Solve* tab, int 
 int xpass_blocks(int r);
 cudaError_t launch_finalize(bool bwd, int nparts, const Solve& s, const Solve* tab, int count,
                             cudaStream_t st);
+// TMA descriptors of the four spectral buffers of `s` (s.spec must be set).
+// Returns 0 on success.
+int make_tensor_maps(Solve& s, int r);
 // Points: x-plane bucketing (count, scan, scatter) and the backward combine.
 cudaError_t launch_bin(const Solve& s, const Solve* tab, int count, int nmax, cudaStream_t st);
 cudaError_t launch_combine(const Solve& s, const Solve* tab, int count, int nmax,

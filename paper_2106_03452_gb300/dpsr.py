@@ -116,3 +116,57 @@ class DPSRFunction(torch.autograd.Function):
 
 def dpsr(points: torch.Tensor, normals: torch.Tensor, plan: Plan) -> torch.Tensor:
     return DPSRFunction.apply(points, normals, plan)
+
+
+class Batch:
+    """Many independent solves (mixed r, uneven N) run together: every kernel
+    launches once per grid size for all instances of that size, and with
+    graph=True the whole forward (+ backward) sequence is one CUDA graph
+    launch. Instances bind caller-owned CUDA tensors."""
+
+    def __init__(self, rs, sigmas, n_max, device=None):
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.rs = [int(r) for r in rs]
+        with torch.cuda.device(self.device):
+            self.handle = L.dpsr_batch_create(self.rs, [float(s) for s in sigmas], [int(n) for n in n_max])
+            self.stream = torch.cuda.Stream(self.device)
+        L.dpsr_batch_set_stream(self.handle, self.stream.cuda_stream)
+        self._bound = [None] * len(self.rs)
+
+    def bind(self, i, points, normals, chi, dchi=None, dpoints=None, dnormals=None):
+        r = self.rs[i]
+        points = _dev_f32(points, "points")
+        normals = _dev_f32(normals, "normals", points.shape)
+        chi = _dev_f32(chi, "chi", (r, r, r))
+        ptr = lambda t: t.data_ptr() if t is not None else 0
+        L.dpsr_batch_bind(self.handle, i, points.data_ptr(), normals.data_ptr(), points.shape[0],
+                          chi.data_ptr(), ptr(dchi), ptr(dpoints), ptr(dnormals))
+        self._bound[i] = (points, normals, chi, dchi, dpoints, dnormals)
+
+    def run(self, with_bwd=True, graph=True):
+        cur = torch.cuda.current_stream(self.device)
+        self.stream.wait_stream(cur)
+        if graph:
+            L.dpsr_batch_graph_launch(self.handle, with_bwd)
+        else:
+            L.dpsr_batch_forward(self.handle)
+            if with_bwd:
+                L.dpsr_batch_backward(self.handle)
+        cur.wait_stream(self.stream)
+
+    def sync(self) -> int:
+        return L.dpsr_batch_sync(self.handle)
+
+    def launches(self, with_bwd=True) -> int:
+        return L.dpsr_batch_launches(self.handle, with_bwd)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.dpsr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -42,6 +42,24 @@ _PROTOS = {
     "dpsr_strerror": (ctypes.c_char_p, [_c_int]),
     "dpsr_forward_static": (_c_int, [_c_int, ctypes.c_float, _vp, _vp, _c_i64, _vp, _vp]),
     "dpsr_plan_profile": (_c_int, [_vp, _c_int]),
+    "dpsr_plan_clusters": (_c_int, [_vp, ctypes.POINTER(_c_int)]),
+    "dpsr_batch_create": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float),
+                                   ctypes.POINTER(_c_i64), ctypes.POINTER(_vp)]),
+    "dpsr_batch_destroy": (_c_int, [_vp]),
+    "dpsr_batch_set_stream": (_c_int, [_vp, _vp]),
+    "dpsr_batch_bind": (_c_int, [_vp, _c_int, _vp, _vp, _c_i64, _vp, _vp, _vp, _vp]),
+    "dpsr_batch_forward": (_c_int, [_vp]),
+    "dpsr_batch_backward": (_c_int, [_vp]),
+    "dpsr_batch_graph_launch": (_c_int, [_vp, _c_int]),
+    "dpsr_batch_sync": (_c_int, [_vp]),
+    "dpsr_batch_launches": (_c_int, [_vp, _c_int]),
+    "dpsr_server_create": (_c_int, [_c_sz, _c_int, ctypes.c_float, ctypes.POINTER(_vp)]),
+    "dpsr_server_destroy": (_c_int, [_vp]),
+    "dpsr_server_submit": (_c_int, [_vp, _c_int, _vp, _vp, _c_i64, _vp, _vp, _vp, _vp,
+                                    ctypes.POINTER(_c_i64)]),
+    "dpsr_server_poll": (_c_int, [_vp, _c_i64, ctypes.POINTER(_c_int)]),
+    "dpsr_server_wait": (_c_int, [_vp, _c_i64, ctypes.c_double]),
+    "dpsr_server_stats": (_c_int, [_vp, ctypes.POINTER(_c_i64)]),
     "dpsr_plan_profile_read": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_c_int)]),
 }
 
@@ -156,3 +174,92 @@ def dpsr_forward_static(r: int, sigma: float, points: int, normals: int, N: int,
     N <= 65536). Returns the status code instead of raising."""
     return int(load().dpsr_forward_static(int(r), float(sigma), points, normals, int(N), chi_out,
                                           stream))
+
+
+def dpsr_plan_clusters(plan: int):
+    """Cluster sizes of the four plane kernels (forward, forward inverse,
+    backward, backward inverse)."""
+    out = (ctypes.c_int * 4)()
+    check(load().dpsr_plan_clusters(plan, out), "dpsr_plan_clusters")
+    return [int(x) for x in out]
+
+
+def dpsr_batch_create(r, sigma, n_max) -> int:
+    n = len(r)
+    h = _vp()
+    ra = (ctypes.c_int * n)(*[int(x) for x in r])
+    sa = (ctypes.c_float * n)(*[float(x) for x in sigma])
+    na = (ctypes.c_int64 * n)(*[int(x) for x in n_max])
+    check(load().dpsr_batch_create(n, ra, sa, na, ctypes.byref(h)), "dpsr_batch_create")
+    return h.value
+
+
+def dpsr_batch_destroy(batch: int) -> None:
+    check(load().dpsr_batch_destroy(batch), "dpsr_batch_destroy")
+
+
+def dpsr_batch_set_stream(batch: int, stream: int) -> None:
+    check(load().dpsr_batch_set_stream(batch, stream), "dpsr_batch_set_stream")
+
+
+def dpsr_batch_bind(batch: int, i: int, points: int, normals: int, N: int, chi: int, dchi: int = 0,
+                    dpoints: int = 0, dnormals: int = 0) -> None:
+    check(load().dpsr_batch_bind(batch, int(i), points, normals, int(N), chi, dchi or None,
+                                 dpoints or None, dnormals or None), "dpsr_batch_bind")
+
+
+def dpsr_batch_forward(batch: int) -> None:
+    check(load().dpsr_batch_forward(batch), "dpsr_batch_forward")
+
+
+def dpsr_batch_backward(batch: int) -> None:
+    check(load().dpsr_batch_backward(batch), "dpsr_batch_backward")
+
+
+def dpsr_batch_graph_launch(batch: int, with_bwd: bool = True) -> None:
+    check(load().dpsr_batch_graph_launch(batch, 1 if with_bwd else 0), "dpsr_batch_graph_launch")
+
+
+def dpsr_batch_sync(batch: int) -> int:
+    return int(load().dpsr_batch_sync(batch))
+
+
+def dpsr_batch_launches(batch: int, with_bwd: bool = True) -> int:
+    return int(load().dpsr_batch_launches(batch, 1 if with_bwd else 0))
+
+
+def dpsr_server_create(hbm_budget_bytes: int, slots: int = 8, sigma: float = 2.0) -> int:
+    h = _vp()
+    check(load().dpsr_server_create(int(hbm_budget_bytes), int(slots), float(sigma), ctypes.byref(h)),
+          "dpsr_server_create")
+    return h.value
+
+
+def dpsr_server_destroy(server: int) -> None:
+    check(load().dpsr_server_destroy(server), "dpsr_server_destroy")
+
+
+def dpsr_server_submit(server: int, r: int, points: int, normals: int, N: int, dchi: int, chi_out: int,
+                       dpoints: int = 0, dnormals: int = 0) -> int:
+    t = _c_i64()
+    check(load().dpsr_server_submit(server, int(r), points, normals, int(N), dchi or None, chi_out,
+                                    dpoints or None, dnormals or None, ctypes.byref(t)),
+          "dpsr_server_submit")
+    return t.value
+
+
+def dpsr_server_poll(server: int, ticket: int):
+    """(done, status)."""
+    d = _c_int()
+    st = int(load().dpsr_server_poll(server, int(ticket), ctypes.byref(d)))
+    return bool(d.value), st
+
+
+def dpsr_server_wait(server: int, ticket: int, timeout_s: float = 0.0) -> int:
+    return int(load().dpsr_server_wait(server, int(ticket), float(timeout_s)))
+
+
+def dpsr_server_stats(server: int):
+    out = (_c_i64 * 4)()
+    check(load().dpsr_server_stats(server, out), "dpsr_server_stats")
+    return dict(admitted=out[0], completed=out[1], max_in_flight=out[2], bytes_in_use=out[3])

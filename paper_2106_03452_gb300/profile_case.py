@@ -35,6 +35,11 @@ def main():
     chi = torch.empty((r,) * 3, device="cuda")
     dp, dn = torch.empty_like(P), torch.empty_like(P)
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):  # warm-up
+        plan.forward(P, Nn, chi)
+        if not a.fwd_only:
+            plan.backward(G, dp, dn)
+    torch.cuda.synchronize()
     L.dpsr_plan_profile(plan.handle, True)
     s.record()
     for _ in range(a.reps):
@@ -45,7 +50,8 @@ def main():
     torch.cuda.synchronize()
     st = plan.sync()
     prof = L.dpsr_plan_profile_read(plan.handle)
-    print(f"r={r} N={P.shape[0]} status={st} ms/solve={s.elapsed_time(e) / a.reps:.3f}")
+    print(f"r={r} N={P.shape[0]} status={st} ms/solve={s.elapsed_time(e) / a.reps:.3f} "
+          f"clusters={L.dpsr_plan_clusters(plan.handle)}")
     for k, (ms, n) in prof.items():
         if n:
             print(f"  {k:12s} {ms / n:8.4f} ms x {n}")

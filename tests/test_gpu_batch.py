@@ -1,0 +1,63 @@
+"""Batched solves (32 clouds, r in {64, 128}, N log-uniform in [1000, 50000]):
+every instance of the batch equals its solo solve, with and without the CUDA
+graph, and a sample of instances matches the FP64 oracle."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_03452_gb300 import build
+    build.build()
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def test_batch_equals_solo_and_oracle(oracle):
+    import torch
+    from paper_2106_03452_gb300 import synth
+    from paper_2106_03452_gb300.dpsr import Batch, Plan
+    inst = synth.workload_batch(count=32)
+    rs = [w["r"] for w in inst]
+    assert set(rs) == {64, 128}
+    batch = Batch(rs, [w["sigma"] for w in inst], [w["points"].shape[0] for w in inst])
+    T = []
+    for i, w in enumerate(inst):
+        r = w["r"]
+        P = torch.from_numpy(w["points"]).cuda()
+        Nn = torch.from_numpy(w["normals"]).cuda()
+        G = torch.from_numpy(w["dchi"]).cuda()
+        chi = torch.empty((r, r, r), device="cuda")
+        dp, dn = torch.empty_like(P), torch.empty_like(P)
+        batch.bind(i, P, Nn, chi, G, dp, dn)
+        T.append((P, Nn, G, chi, dp, dn))
+    for graph in (False, True, True):  # plain launches, graph capture, graph replay
+        for (_, _, _, chi, dp, dn) in T:
+            chi.fill_(float("nan")); dp.fill_(float("nan")); dn.fill_(float("nan"))
+        batch.run(with_bwd=True, graph=graph)
+        assert batch.sync() == 0
+        for i, (P, Nn, G, chi, dp, dn) in enumerate(T):
+            w = inst[i]
+            plan = Plan(w["r"], w["sigma"])
+            c0 = plan.forward(P, Nn).clone()
+            d0, n0 = plan.backward(G)
+            assert plan.sync() == 0
+            assert _rel(chi.cpu(), c0.cpu()) <= 1e-5, i
+            assert _rel(dp.cpu(), d0.cpu()) <= 1e-4 and _rel(dn.cpu(), n0.cpu()) <= 1e-4, i
+            plan.close()
+    for i in (0, 7, 31):
+        w = inst[i]
+        ref = oracle.forward(w["r"], w["sigma"], w["points"], w["normals"])
+        assert _rel(T[i][3].cpu(), ref) <= 1e-5
+        rdp, rdn = oracle.backward(w["r"], w["sigma"], w["points"], w["normals"], w["dchi"])
+        assert _rel(T[i][4].cpu(), rdp) <= 1e-4 and _rel(T[i][5].cpu(), rdn) <= 1e-4
+    assert batch.launches(True) == 2 * 12
+    batch.close()
