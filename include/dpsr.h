@@ -120,6 +120,17 @@ DPSR_API int dpsr_get_scalars(dpsr_plan plan, double out[3]);
 /* Number of kernel launches the last dpsr_forward / dpsr_backward queued. */
 DPSR_API int dpsr_plan_last_launches(dpsr_plan plan);
 
+/* Trilinear lookup of an r^3 grid (device, layout as chi) at M query points
+ * q (device, M x 3, periodic as the points of Eq. A1): out[k] = chi(q_k).
+ * Its adjoint: grid[j] (+)= sum_k w_kj vals[k], the rasterization of Eq. A2
+ * with scalar values; accumulate = 0 zeroes the grid first. Both run on
+ * `stream` (a cudaStream_t). They give a loss defined on chi at target
+ * points, such as mean_k chi(q_k)^2, and its gradient dL/dchi. */
+DPSR_API int dpsr_grid_sample(const float *grid, int r, const float *q, int64_t M, float *out,
+                              void *stream);
+DPSR_API int dpsr_grid_splat(float *grid, int r, const float *q, const float *vals, int64_t M,
+                             int accumulate, void *stream);
+
 /* Per-kernel timing. With profiling on, every kernel launch of the plan is
  * bracketed by CUDA events on the plan's stream (a small overhead per launch).
  * dpsr_plan_profile_read synchronises, then returns, per kernel kind (the

@@ -441,6 +441,26 @@ int dpsr_plan_reserve(dpsr_plan p, int64_t n_max) {
 
 int dpsr_plan_last_launches(dpsr_plan p) { return p ? p->last_launches : -1; }
 
+int dpsr_grid_sample(const float* grid, int r, const float* q, int64_t M, float* out,
+                     void* stream) {
+  if (!valid_r(r) || !grid || !q || !out || M < 0) return DPSR_EINVAL;
+  if (M == 0) return DPSR_OK;
+  return dpsr::launch_grid_sample(grid, r, q, M, out, (cudaStream_t)stream) == cudaSuccess
+             ? DPSR_OK
+             : DPSR_ECUDA;
+}
+
+int dpsr_grid_splat(float* grid, int r, const float* q, const float* vals, int64_t M,
+                    int accumulate, void* stream) {
+  if (!valid_r(r) || !grid || !q || !vals || M < 0) return DPSR_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!accumulate &&
+      cudaMemsetAsync(grid, 0, sizeof(float) * (size_t)r * r * r, st) != cudaSuccess)
+    return DPSR_ECUDA;
+  if (M == 0) return DPSR_OK;
+  return dpsr::launch_grid_splat(grid, r, q, vals, M, st) == cudaSuccess ? DPSR_OK : DPSR_ECUDA;
+}
+
 // Internal hooks for the batch driver (same library, not exported).
 const void* dpsr_internal_solve(dpsr_plan p) { return p ? (const void*)&p->s : nullptr; }
 int dpsr_internal_cluster(dpsr_plan p, int kind) {

@@ -1,6 +1,8 @@
 // Point kernels: bucketing of the points by the x-cell of their trilinear
 // stencil (a counting sort, so that each x-plane cluster reads only the points
 // that touch its plane), and the final combine of the backward pass.
+#include <algorithm>
+
 #include "dpsr_dev.cuh"
 #include "launch.h"
 
@@ -120,6 +122,60 @@ cudaError_t launch_combine(const Solve& s, const Solve* tab, int count, int nmax
                            cudaStream_t st) {
   const int blocks = min(max((nmax + 255) / 256, 1), 1184);
   k_combine<<<dim3(blocks, 1, count), 256, 0, st>>>(s, tab);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Trilinear lookup of a grid at query points and its adjoint (the same
+// periodic stencil as the rasterization of Eq. A1): used by losses defined on
+// chi at target points, e.g. mean_k chi(q_k)^2.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_grid_sample(const float* __restrict__ grid, int r,
+                                                     const float* __restrict__ q, int64_t M,
+                                                     float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const Axis ax = axis_of(q[3 * i], r), ay = axis_of(q[3 * i + 1], r), az = axis_of(q[3 * i + 2], r);
+    float acc = 0.f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const int dx = d >> 2, dy = (d >> 1) & 1, dz = d & 1;
+      const float w = (dx ? ax.t : 1.f - ax.t) * (dy ? ay.t : 1.f - ay.t) * (dz ? az.t : 1.f - az.t);
+      const size_t j = ((size_t)(dx ? ax.i1 : ax.i0) * r + (dy ? ay.i1 : ay.i0)) * r + (dz ? az.i1 : az.i0);
+      acc += w * grid[j];
+    }
+    out[i] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_grid_splat(float* __restrict__ grid, int r,
+                                                    const float* __restrict__ q,
+                                                    const float* __restrict__ vals, int64_t M) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const Axis ax = axis_of(q[3 * i], r), ay = axis_of(q[3 * i + 1], r), az = axis_of(q[3 * i + 2], r);
+    const float v = vals[i];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const int dx = d >> 2, dy = (d >> 1) & 1, dz = d & 1;
+      const float w = (dx ? ax.t : 1.f - ax.t) * (dy ? ay.t : 1.f - ay.t) * (dz ? az.t : 1.f - az.t);
+      const size_t j = ((size_t)(dx ? ax.i1 : ax.i0) * r + (dy ? ay.i1 : ay.i0)) * r + (dz ? az.i1 : az.i0);
+      atomicAdd(&grid[j], w * v);
+    }
+  }
+}
+
+cudaError_t launch_grid_sample(const float* grid, int r, const float* q, int64_t M, float* out,
+                               cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((M + 255) / 256, 4736);
+  k_grid_sample<<<std::max(blocks, 1), 256, 0, st>>>(grid, r, q, M, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grid_splat(float* grid, int r, const float* q, const float* vals, int64_t M,
+                              cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((M + 255) / 256, 4736);
+  k_grid_splat<<<std::max(blocks, 1), 256, 0, st>>>(grid, r, q, vals, M);
   return cudaGetLastError();
 }
 

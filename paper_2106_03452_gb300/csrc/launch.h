@@ -24,4 +24,10 @@ cudaError_t launch_bin(const Solve& s, const Solve* tab, int count, int nmax, cu
 cudaError_t launch_combine(const Solve& s, const Solve* tab, int count, int nmax,
                            cudaStream_t st);
 
+// Trilinear lookup of a grid at query points and its adjoint (atomic adds).
+cudaError_t launch_grid_sample(const float* grid, int r, const float* q, int64_t M, float* out,
+                               cudaStream_t st);
+cudaError_t launch_grid_splat(float* grid, int r, const float* q, const float* vals, int64_t M,
+                              cudaStream_t st);
+
 }  // namespace dpsr

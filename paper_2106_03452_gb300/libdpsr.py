@@ -41,6 +41,8 @@ _PROTOS = {
     "dpsr_plan_last_launches": (_c_int, [_vp]),
     "dpsr_strerror": (ctypes.c_char_p, [_c_int]),
     "dpsr_forward_static": (_c_int, [_c_int, ctypes.c_float, _vp, _vp, _c_i64, _vp, _vp]),
+    "dpsr_grid_sample": (_c_int, [_vp, _c_int, _vp, _c_i64, _vp, _vp]),
+    "dpsr_grid_splat": (_c_int, [_vp, _c_int, _vp, _vp, _c_i64, _c_int, _vp]),
     "dpsr_plan_profile": (_c_int, [_vp, _c_int]),
     "dpsr_plan_clusters": (_c_int, [_vp, ctypes.POINTER(_c_int)]),
     "dpsr_batch_create": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float),
@@ -263,3 +265,13 @@ def dpsr_server_stats(server: int):
     out = (_c_i64 * 4)()
     check(load().dpsr_server_stats(server, out), "dpsr_server_stats")
     return dict(admitted=out[0], completed=out[1], max_in_flight=out[2], bytes_in_use=out[3])
+
+
+def dpsr_grid_sample(grid: int, r: int, q: int, M: int, out: int, stream: int = 0) -> None:
+    check(load().dpsr_grid_sample(grid, int(r), q, int(M), out, stream), "dpsr_grid_sample")
+
+
+def dpsr_grid_splat(grid: int, r: int, q: int, vals: int, M: int, accumulate: bool = False,
+                    stream: int = 0) -> None:
+    check(load().dpsr_grid_splat(grid, int(r), q, vals, int(M), 1 if accumulate else 0, stream),
+          "dpsr_grid_splat")
