@@ -163,7 +163,7 @@ bool tuning_enabled() {
 // (second of two runs), record the fastest. Returns the last launch error.
 cudaError_t tune_plane(dpsr_plan p, int kind, const Solve& s, cudaStream_t st) {
   const int r = p->r;
-  const int cands[5] = {1, 2, 4, 8, 16};
+  const int cands[4] = {1, 2, 4, 8};
   float best = 1e30f;
   int bestC = p->C[kind];
   cudaEvent_t e0, e1;

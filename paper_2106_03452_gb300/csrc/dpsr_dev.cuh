@@ -102,6 +102,19 @@ struct Dft<1, DIR> {
   static __device__ __forceinline__ void run(float2*) {}
 };
 
+// Synchronise the T lanes of this thread's group (aligned groups of T lanes
+// within a warp); a one-thread group needs no synchronisation. Groups may
+// therefore call the FFT helpers independently of the rest of their warp.
+template <int T>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (T >= 32) {
+    __syncwarp();
+  } else if constexpr (T > 1) {
+    const unsigned lane = threadIdx.x & 31u;
+    __syncwarp(((1u << T) - 1u) << (lane & ~(unsigned)(T - 1)));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Group FFT of length L by T threads, each holding R1 = L / T values.
 // Distribution (in and out): thread t holds element t + T*j in v[j].
@@ -110,7 +123,7 @@ struct Dft<1, DIR> {
 // memory (XOR-swizzled so neither side conflicts), and T-point DFTs.
 // tw[m] = exp(-2 pi i m / L), m < L (FP64-computed, rounded to FP32).
 // xch: L float2 of shared memory owned by the group. Every lane of the warp
-// must call this together (it uses __syncwarp).
+// must call this together (they synchronise through group_sync).
 // ---------------------------------------------------------------------------
 template <int L> struct Shape;
 template <> struct Shape<8>   { static constexpr int R1 = 8,  T = 1; };
@@ -135,7 +148,7 @@ __device__ __forceinline__ void fft_x(float2 (&v)[Shape<L>::R1], int t, XA xa, c
     }
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) xa(k1 * T + (t ^ (k1 % T))) = v[k1];
-    __syncwarp();
+    group_sync<T>();
     constexpr int M = R1 / T;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
@@ -147,7 +160,7 @@ __device__ __forceinline__ void fft_x(float2 (&v)[Shape<L>::R1], int t, XA xa, c
 #pragma unroll
       for (int k2 = 0; k2 < T; ++k2) v[m + M * k2] = u[k2];
     }
-    __syncwarp();
+    group_sync<T>();
   }
 }
 
@@ -195,7 +208,7 @@ __device__ __forceinline__ void fft_r(float2 (&v)[Shape<L>::R1], int t, XA xa, c
     }
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) xa(k1 * T + (t ^ (k1 % T))) = v[k1];
-    __syncwarp();
+    group_sync<T>();
     constexpr int M = R1 / T;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
@@ -207,7 +220,7 @@ __device__ __forceinline__ void fft_r(float2 (&v)[Shape<L>::R1], int t, XA xa, c
 #pragma unroll
       for (int k2 = 0; k2 < T; ++k2) v[m + M * k2] = u[k2];
     }
-    __syncwarp();
+    group_sync<T>();
   }
 }
 
@@ -228,7 +241,7 @@ __device__ __forceinline__ void r2c_pair(int t, float2* xch, const Tw& tw, Ld ld
   fft_r<L, -1>(v, t, [xch](int i) -> float2& { return xch[i]; }, tw);
 #pragma unroll
   for (int j = 0; j < R1; ++j) xch[t + T * j] = v[j];
-  __syncwarp();
+  group_sync<T>();
   float2 A[R1 / 2], B[R1 / 2];
 #pragma unroll
   for (int j = 0; j < R1 / 2; ++j) {
@@ -244,7 +257,7 @@ __device__ __forceinline__ void r2c_pair(int t, float2* xch, const Tw& tw, Ld ld
       B[j] = make_float2(0.5f * d.y, -0.5f * d.x);
     }
   }
-  __syncwarp();
+  group_sync<T>();
 #pragma unroll
   for (int j = 0; j < R1 / 2; ++j) {
     sa(t + T * j, A[j]);

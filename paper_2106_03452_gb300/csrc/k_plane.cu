@@ -37,7 +37,7 @@ struct PlaneGeo {
   static constexpr int KP = L / 2 + 2;   // row pitch of the spectral buffers in HBM
   static constexpr int SWM = (H < 16 ? H : 16) - 1;
   static_assert(R >= 2 && R % 2 == 0, "at least one row pair per CTA");
-  static_assert(SPC >= 1, "at least one slot per CTA");
+  static_assert(SPC >= 16 || C == 1, "a CTA owns whole 16-slot TMA boxes");
 };
 
 // XOR swizzle inside aligned 16-slot blocks: a column read across 16 rows and
@@ -93,7 +93,7 @@ __device__ __forceinline__ void separate_dc_nyq(float2* sbox, int t, Nyq nyq) {
     const int ky = t + T * j;
     unpack_dc_nyq(boxcol<L>(sbox, 0, ky), boxcol<L>(sbox, 0, (L - ky) & (L - 1)), x0[j], xn[j]);
   }
-  if constexpr (T > 1) __syncwarp((T == 32 ? 0xffffffffu : ((1u << T) - 1u)) << (threadIdx.x & 31 & ~(T - 1)));
+  group_sync<T>();
 #pragma unroll
   for (int j = 0; j < R1; ++j) {
     boxcol<L>(sbox, 0, t + T * j) = x0[j];
@@ -156,40 +156,60 @@ constexpr int plane_minb(int kind) {
 
 
 // ===========================================================================
-// Forward plane kernel: splat + R2C(z) + FFT(y). 512 threads: each group of
-// T threads owns one (slot, channel) column in the y pass, so a chunk
-// transforms 16 slots of both channels of a round at once.
+// Forward plane kernel: splat + R2C(z) + FFT(y), one channel per round
+// (v_y, v_z, v_x, W). Rows of a CTA are half-spectrum rows in 16-slot blocks
+// swizzled like TMA box rows (rsw); after the z pass every CTA pushes, with
+// bulk copies into the other CTAs' shared memory, the slot segments each of
+// them transforms along y, so the y pass reads only local shared memory.
+// D = FFT_y(i u_z v~_z) + i u_y FFT_y(v~_y) accumulates in the output boxes
+// over the v_y and v_z rounds.
 // ===========================================================================
-constexpr int kNTF = 512;
+// Threads of the forward plane kernel: 512 (one CTA per SM) up to 4-CTA
+// clusters; 256 for larger clusters, whose CTAs then fit two per SM.
+template <int C>
+constexpr int fwd_threads() {
+  return C >= 8 ? 256 : 512;
+}
+
+template <int H>
+__device__ __forceinline__ int rsw(int y, int s) {
+  if constexpr (H < 16) {
+    return s;
+  } else {
+    return (s & ~15) | (((((s >> 1) ^ y) & 7)) << 1) | (s & 1);
+  }
+}
 
 template <int L, int C>
-struct FwdGeo;
-template <int L, int C>
 struct FwdGeo {
-  using P = PlaneGeo<L, C>;
-  static constexpr int T = P::T, R1 = P::R1, G = kNTF / T;
-  static constexpr int CH = (G / 2 < P::SPC) ? G / 2 : P::SPC;  // slots per chunk
-  static constexpr int NB = (CH + 15) / 16;                       // boxes per channel
+  static constexpr int NT = fwd_threads<C>();
+  static constexpr int T = Shape<L>::T, R1 = Shape<L>::R1, G = NT / T;
+  static constexpr int R = L / C, H = L / 2, SPC = H / C;
+  static constexpr int NB = (SPC + 15) / 16;  // output boxes (16 slots each)
   static constexpr int BOX = L * 16;
-  static constexpr int XP = L + 1;
-  static constexpr int SCR0 = 2 * NB * BOX > G * XP ? 2 * NB * BOX : G * XP;
-  static constexpr int SCR = (SCR0 + 127) / 128 * 128;
-  static_assert(T == 1 || CH == G / 2 || CH % (32 / T) == 0, "inactive groups must fill whole warps");
+  static constexpr int ZG = R / 2 < G ? R / 2 : G;  // groups of the z pass
+  // The boxes keep D between the v_y and v_z rounds, so the z-pass exchange
+  // areas (L per group) cannot share them: with C > 1 they live in the
+  // receive buffer (free during the z pass, exactly R/2 * L), else apart.
+  static constexpr int SCR = (NB * BOX + 127) / 128 * 128;
+  static constexpr int ROWS = R * H;               // float2 (R real rows of L floats)
+  static constexpr int RECV = C > 1 ? L * SPC : ZG * L;  // float2
+  static_assert(G >= SPC, "one y pass per round (D accumulates in the boxes)");
+  static_assert(T == 1 || SPC % (32 / T) == 0 || SPC >= G, "idle y groups must fill whole warps");
 };
 
 template <int L, int C>
 constexpr size_t fwd_smem() {
   using F = FwdGeo<L, C>;
-  using P = PlaneGeo<L, C>;
-  return 1024 + sizeof(float2) * ((size_t)F::SCR + (size_t)P::R * L + L / 2 + L);
+  return 1024 + sizeof(float2) * ((size_t)F::SCR + F::ROWS + F::RECV + L) + sizeof(float) * L;
 }
 
 template <int L, int C>
-__global__ void __launch_bounds__(kNTF, 1)
+__global__ void __launch_bounds__(fwd_threads<C>(), 512 / fwd_threads<C>())
     k_plane_fwd(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = PlaneGeo<L, C>;
   using F = FwdGeo<L, C>;
-  constexpr int RP = L;  // two channels of H packed slots (or L complex in real space)
+  constexpr int H = F::H, SPC = F::SPC;
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   cg::cluster_group cl = cg::this_cluster();
   const int c = (int)cl.block_rank();
@@ -198,127 +218,133 @@ __global__ void __launch_bounds__(kNTF, 1)
   extern __shared__ unsigned char smem_raw[];
   float2* sbox = aligned_smem(smem_raw);
   float2* rows = sbox + F::SCR;
-  float* iu = reinterpret_cast<float*>(rows + P::R * RP);
-  float2* twt = reinterpret_cast<float2*>(iu + L);
-  float2* xz = sbox + g * F::XP;  // per-group exchange area of the z pass
-  uint32_t rb[C];  // shared::cluster address of each CTA's rows
-#pragma unroll
-  for (int q = 0; q < C; ++q) rb[q] = dsmem_map(rows, q);
-  for (int i = tid; i < L; i += kNTF) {
+  float* rows_f = reinterpret_cast<float*>(rows);
+  float2* recv = rows + F::ROWS;
+  float2* twt = recv + F::RECV;
+  float* iu = reinterpret_cast<float*>(twt + L);
+  __shared__ uint64_t bar;
+  for (int i = tid; i < L; i += F::NT) {
     iu[i] = S.iu[i];
     twt[i] = S.tw[i];
   }
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
   TwTab<L> twr{twt, t};
   const PlanePoints pp(S, X);
-  const int y_lo = c * P::R;
-  // y pass: group g -> channel ch = g / (G/2), slot index sl = g % (G/2)
-  const int ch = g / (F::G / 2), sl = g % (F::G / 2);
-  const bool active = sl < F::CH;
-  const int slc = active ? sl : F::CH - 1;
-  float2* mybox = sbox + (ch * F::NB + slc / 16) * F::BOX;
-  auto xa = [&](int e) -> float2& { return mybox[bx(e, slc & 15)]; };
-  auto box_of = [&](int chn, int slot) { return sbox + (chn * F::NB + slot / 16) * F::BOX; };
+  const int y_lo = c * F::R;
+  const float2* ysrc = C > 1 ? recv : rows;  // [y][SPC] in the y pass
+  uint32_t phase = 0;
+  bool alive = true;
+  // y pass: group g -> slot sl = g of this CTA; its box column is g
+  const bool yact = g < SPC;
+  auto xa = [&](int e) -> float2& { return boxcol<L>(sbox, yact ? g : 0, e); };
+  float2* xz = recv + g * L;  // z-pass exchange (groups < ZG)
 
-  for (int round = 0; round < 2; ++round) {
-    for (int i = tid; i < P::R * RP / 2; i += kNTF)
+  for (int rd = 0; rd < 4; ++rd) {
+    const int ch = rd == 0 ? 1 : (rd == 1 ? 2 : (rd == 2 ? 0 : 3));  // v_y, v_z, v_x, W
+    for (int i = tid; i < F::ROWS / 2; i += F::NT)
       reinterpret_cast<float4*>(rows)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
-    // Rasterization (Eq. A2): round 0 splats (n_y, n_z), round 1 (n_x, 1).
-    for (int i = tid; i < pp.total(); i += kNTF) {
+    // Rasterization (Eq. A2) of one channel into real rows.
+    for (int i = tid; i < pp.total(); i += F::NT) {
       int dx;
       const int idx = pp.index(i, dx);
       const float4 a = S.sorted[2 * idx], b = S.sorted[2 * idx + 1];
+      const float val = ch == 0 ? a.w : (ch == 1 ? b.x : (ch == 2 ? b.y : 1.f));
       const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);
-      const float fx = wsel(dx, ax.t);
-      const float va = round == 0 ? b.x : a.w;
-      const float vb = round == 0 ? b.y : 1.f;
+      const float fx = wsel(dx, ax.t) * val;
 #pragma unroll
       for (int dy = 0; dy < 2; ++dy) {
         const int ly = (dy ? ay.i1 : ay.i0) - y_lo;
-        if ((unsigned)ly >= (unsigned)P::R) continue;
+        if ((unsigned)ly >= (unsigned)F::R) continue;
         const float fxy = fx * wsel(dy, ay.t);
-#pragma unroll
-        for (int dz = 0; dz < 2; ++dz) {
-          const int z = dz ? az.i1 : az.i0;
-          const float w = fxy * wsel(dz, az.t);
-          float2* cell = &rows[sw<RP, P::SWM>(ly, z)];
-          atomicAdd(&cell->x, w * va);
-          atomicAdd(&cell->y, w * vb);
-        }
+        atomicAdd(&rows_f[ly * L + az.i0], fxy * (1.f - az.t));
+        atomicAdd(&rows_f[ly * L + az.i1], fxy * az.t);
       }
     }
     __syncthreads();
-    // R2C along z of each row; channel B of round 0 takes the factor i u_z.
-    for (int r0 = 0; r0 < P::R; r0 += F::G) {
-      const int row = r0 + g;
-      const bool ok = row < P::R;
-      const int rr = ok ? row : 0;
-      r2c_pair<L>(
-          t, xz, twr, [&](int z) { return rows[sw<RP, P::SWM>(rr, z)]; },
-          [&](int s, float2 v) {
-            if (ok) rows[sw<RP, P::SWM>(rr, s)] = v;
-          },
-          [&](int s, float2 v) {
-            if (!ok) return;
-            if (round == 0) v = s == 0 ? czero() : cmul_iu(v, iu[s]);
-            rows[sw<RP, P::SWM>(rr, P::H + s)] = v;
-          });
+    // R2C along z of row pairs, in place; the v_z channel takes i u_z.
+    for (int p0 = 0; p0 < F::R / 2; p0 += F::ZG) {
+      const int p = p0 + g;
+      if (g < F::ZG) {  // whole warps (ZG a multiple of 32/T, or T = 1)
+        const bool ok = p < F::R / 2;
+        const int pr = ok ? p : 0;
+        const int ya = y_lo + 2 * pr;
+        auto put = [&](int row, int yy, int s, float2 v) {
+          if (!ok) return;
+          if (ch == 2) v = s == 0 ? czero() : cmul_iu(v, iu[s]);
+          rows[row * H + rsw<H>(yy, s)] = v;
+        };
+        r2c_pair<L>(
+            t, xz, twr,
+            [&](int z) { return make_float2(rows_f[2 * pr * L + z], rows_f[(2 * pr + 1) * L + z]); },
+            [&](int s, float2 v) { put(2 * pr, ya, s, v); },
+            [&](int s, float2 v) { put(2 * pr + 1, ya + 1, s, v); });
+      }
     }
-    cl.sync();
-    // FFT along y of this CTA's slots (both channels at once), reading every
-    // row of the plane through DSMEM; results leave by TMA bulk stores.
-    for (int cb = 0; cb < P::SPC; cb += F::CH) {
-      const int s_first = c * P::SPC + cb;
-      const int s = s_first + slc;
-      // Groups without a slot skip the transform: they would share a box
-      // column with an active group. Inactivity is warp-uniform (chunks hold
-      // a multiple of 32/T slots) or T = 1 (no warp-level exchange).
-      if (active) {
-        float2 v[F::R1];
-        constexpr int RT = P::R / F::T;  // row y = t + T j lives in CTA j / RT
-#pragma unroll
-        for (int j = 0; j < F::R1; ++j)
-          v[j] = dsmem_ld(rb[j / RT] + 8u * sw<RP, P::SWM>(t + F::T * (j % RT), ch * P::H + s));
-        fft_r<L, -1>(v, t, xa, twr);
-#pragma unroll
-        for (int j = 0; j < F::R1; ++j) {
-          const int ky = t + F::T * j;
-          xa(ky) = (round == 0 && ch == 0) ? cmul_iu(v[j], iu[ky]) : v[j];
-        }
+    if constexpr (C > 1) {
+      // Exchange: row lr's segment of CTA q's slots goes to q's receive
+      // buffer, row y_lo + lr. Arm, sync (all armed, receive buffers free),
+      // push, wait for this CTA's own segments.
+      if (tid == 0) mbar_expect_tx(&bar, L * SPC * (uint32_t)sizeof(float2));
+      fence_async_smem();
+      cl.sync();
+      for (int i = tid; i < F::R * C; i += F::NT) {
+        const int lr = i % F::R, q = i / F::R;
+        const uint32_t dst = dsmem_map(recv, q) + 8u * (uint32_t)((y_lo + lr) * SPC);
+        bulk_push(dst, rows + lr * H + q * SPC, SPC * (uint32_t)sizeof(float2), dsmem_map(&bar, q));
       }
+      alive = chunk_wait(&bar, phase, S.status) && alive;
+      phase ^= 1;
+    } else {
       __syncthreads();
-      if (round == 0) {  // D = FFT_y(B) + i u_y FFT_y(A), into the channel-0 boxes
-        for (int i = tid; i < F::CH * L; i += kNTF) {
-          const int q = i % F::CH, ky = i / F::CH;
-          float2& d = box_of(0, q)[bx(ky, q & 15)];
-          d = cadd(d, box_of(1, q)[bx(ky, q & 15)]);
-        }
-        __syncthreads();
+    }
+    // FFT along y of this CTA's SPC slots.
+    if (yact) {
+      float2 v[F::R1], part[F::R1];
+#pragma unroll
+      for (int j = 0; j < F::R1; ++j) {
+        const int y = t + F::T * j;
+        v[j] = ysrc[y * SPC + rsw<H>(y, g)];
+        // the FFT below uses the box column as its exchange buffer: take the
+        // v_y partial of D out of it first
+        if (rd == 1) part[j] = xa(y);
       }
-      const int nch = round == 0 ? 1 : 2;
-      if (c == 0 && cb == 0 && sl == 0 && ch < nch) {
-        float2* dst = S.spec[round == 0 ? 0 : 1 + ch];
-        float2* bb = box_of(ch, 0);
-        separate_dc_nyq<L>(bb, t, [&](int ky, float2 w) {
-          if (P::H < 16) boxcol<L>(bb, P::H, ky) = w;
-          else dst[((size_t)X * L + ky) * P::KP + P::H] = w;
+      fft_r<L, -1>(v, t, xa, twr);
+#pragma unroll
+      for (int j = 0; j < F::R1; ++j) {
+        const int ky = t + F::T * j;
+        if (rd == 0) xa(ky) = cmul_iu(v[j], iu[ky]);
+        else if (rd == 1) xa(ky) = cadd(part[j], v[j]);
+        else xa(ky) = v[j];
+      }
+    }
+    __syncthreads();
+    if (rd >= 1) {
+      const int buf = rd == 1 ? 0 : (rd == 2 ? 1 : 2);  // D, C, W~
+      if (c == 0 && g == 0) {
+        float2* dst = S.spec[buf];
+        separate_dc_nyq<L>(sbox, t, [&](int ky, float2 w) {
+          if (H < 16) boxcol<L>(sbox, H, ky) = w;
+          else dst[((size_t)X * L + ky) * P::KP + H] = w;
         });
       }
       fence_async_smem();
       __syncthreads();
       if (tid == 0) {
-        for (int k = 0; k < nch; ++k) {
-          const CUtensorMap* tm = &S.tmy[round == 0 ? 0 : 1 + k];
-          for (int b = 0; b < F::NB; ++b)
-            tma_store_3d(tm, s_first + 16 * b, 0, X, sbox + (k * F::NB + b) * F::BOX);
-        }
+        for (int b = 0; b < F::NB; ++b)
+          tma_store_3d(&S.tmy[buf], c * SPC + 16 * b, 0, X, sbox + b * F::BOX);
         tma_store_commit();
         tma_store_wait_read();
       }
       __syncthreads();
     }
-    cl.sync();
+    if constexpr (C > 1) cl.sync();  // receive buffers and rows are reused next round
   }
+  (void)alive;
 }
 
 // ===========================================================================
@@ -719,17 +745,40 @@ __global__ void __launch_bounds__(kNT, plane_minb<L, C>(3))
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// Cluster sizes instantiated per grid size: one CTA per plane up to r = 64,
+// 1/2/4 CTAs at r = 128, 2/4/8 CTAs at r = 256 (r^2 complex values of one
+// plane do not fit one SM's shared memory there).
+template <int L, int C>
+constexpr bool plane_inst() {
+  // every CTA must own at least 16 slots (one TMA box of kz) so that box
+  // stores never cover a neighbour's slots
+  return L <= 64 ? C == 1 : (L == 128 ? (C == 1 || C == 2 || C == 4) : (C == 2 || C == 4 || C == 8));
+}
+
+// The forward plane kernel transforms all slots of a CTA in one y pass, which
+// needs at least as many groups as slots (r = 256: C >= 4).
+template <int L, int C>
+constexpr bool fwd_inst() {
+  return plane_inst<L, C>() && (fwd_threads<C>() / Shape<L>::T) >= (L / 2) / C;
+}
+
 template <int L, int C>
 static cudaError_t launch_plane_t(int kind, const Solve& s, const Solve* tab, int count,
                                   cudaStream_t st) {
   void (*fn)(Solve, const Solve*) = nullptr;
   switch (kind) {
-    case 0: fn = k_plane_fwd<L, C>; break;
+    case 0:
+      if constexpr (fwd_inst<L, C>()) fn = k_plane_fwd<L, C>;
+      else return cudaErrorInvalidValue;
+      break;
     case 1: fn = k_plane_inv<L, C>; break;
     case 2: fn = k_plane_bfwd<L, C>; break;
     default: fn = k_plane_binv<L, C>; break;
   }
-  const size_t smem = kind == 0 ? fwd_smem<L, C>() : plane_smem<L, C>(kind);
+  size_t smem = plane_smem<L, C>(kind);
+  if constexpr (fwd_inst<L, C>()) {
+    if (kind == 0) smem = fwd_smem<L, C>();
+  }
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   static bool attr_set[4] = {false, false, false, false};  // per instantiation and kind
   if (!attr_set[kind]) {
@@ -742,7 +791,7 @@ static cudaError_t launch_plane_t(int kind, const Solve& s, const Solve* tab, in
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(L * C, 1, count);
-  cfg.blockDim = dim3(kind == 0 ? kNTF : kNT, 1, 1);
+  cfg.blockDim = dim3(kind == 0 ? fwd_threads<C>() : kNT, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -753,15 +802,6 @@ static cudaError_t launch_plane_t(int kind, const Solve& s, const Solve* tab, in
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, fn, s, tab);
-}
-
-// Cluster sizes instantiated per grid size: one CTA per plane up to r = 64,
-// 1/2/4 CTAs at r = 128, 2/4/8 CTAs at r = 256 (r^2 complex values of one
-// plane do not fit one SM's shared memory there).
-template <int L, int C>
-constexpr bool plane_inst() {
-  return L <= 64 ? C == 1
-                 : (L == 128 ? (C == 1 || C == 2 || C == 4) : (C == 2 || C == 4 || C == 8 || C == 16));
 }
 
 template <int L>
@@ -795,11 +835,11 @@ size_t plane_smem_bytes(int kind, int r, int C) {
   auto pick = [&](auto Lc) -> size_t {
     constexpr int L = decltype(Lc)::value;
     switch (C) {
-      case 1: if constexpr (plane_inst<L, 1>()) return kind == 0 ? fwd_smem<L, 1>() : plane_smem<L, 1>(kind); return 0;
-      case 2: if constexpr (plane_inst<L, 2>()) return kind == 0 ? fwd_smem<L, 2>() : plane_smem<L, 2>(kind); return 0;
-      case 4: if constexpr (plane_inst<L, 4>()) return kind == 0 ? fwd_smem<L, 4>() : plane_smem<L, 4>(kind); return 0;
-      case 8: if constexpr (plane_inst<L, 8>()) return kind == 0 ? fwd_smem<L, 8>() : plane_smem<L, 8>(kind); return 0;
-      case 16: if constexpr (plane_inst<L, 16>()) return kind == 0 ? fwd_smem<L, 16>() : plane_smem<L, 16>(kind); return 0;
+      case 1: if constexpr (plane_inst<L, 1>()) { if (kind == 0) { if constexpr (fwd_inst<L, 1>()) return fwd_smem<L, 1>(); return 0; } return plane_smem<L, 1>(kind); } return 0;
+      case 2: if constexpr (plane_inst<L, 2>()) { if (kind == 0) { if constexpr (fwd_inst<L, 2>()) return fwd_smem<L, 2>(); return 0; } return plane_smem<L, 2>(kind); } return 0;
+      case 4: if constexpr (plane_inst<L, 4>()) { if (kind == 0) { if constexpr (fwd_inst<L, 4>()) return fwd_smem<L, 4>(); return 0; } return plane_smem<L, 4>(kind); } return 0;
+      case 8: if constexpr (plane_inst<L, 8>()) { if (kind == 0) { if constexpr (fwd_inst<L, 8>()) return fwd_smem<L, 8>(); return 0; } return plane_smem<L, 8>(kind); } return 0;
+      case 16: if constexpr (plane_inst<L, 16>()) { if (kind == 0) { if constexpr (fwd_inst<L, 16>()) return fwd_smem<L, 16>(); return 0; } return plane_smem<L, 16>(kind); } return 0;
       default: return 0;
     }
   };

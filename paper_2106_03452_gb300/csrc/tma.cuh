@@ -83,6 +83,18 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       : "memory");
 }
 
+// Contiguous bulk copy from this CTA's shared memory to shared memory of a
+// CTA of the cluster (dst and bar are shared::cluster addresses of the
+// destination CTA), completion counted on the destination's barrier.
+__device__ __forceinline__ void bulk_push(uint32_t dst_cluster, const void* src, uint32_t bytes,
+                                          uint32_t bar_cluster) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst_cluster),
+      "r"(smem_u32(src)), "r"(bytes), "r"(bar_cluster)
+      : "memory");
+}
+
 // 3D tiled store shared -> global (bulk group).
 __device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, int c0, int c1, int c2,
                                              const void* src) {
