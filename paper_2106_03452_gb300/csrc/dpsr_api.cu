@@ -15,6 +15,7 @@
 //   binv   IFFT along y, C2R along z of V_bar_{x,y,z}, gather + weight
 //          derivatives at the points
 //   combine  the two plane sides of each point, in the caller's order
+#include <cstdlib>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -61,6 +62,13 @@ struct dpsr_plan_s {
 };
 
 namespace {
+
+// Per-kernel event timing (plan profiling) launches without programmatic
+// dependent launch, for the scope of one API call.
+struct PdlScope {
+  explicit PdlScope(bool off) { dpsr::pdl_suspend(off); }
+  ~PdlScope() { dpsr::pdl_suspend(false); }
+};
 
 struct DeviceGuard {
   int prev = -1;
@@ -272,6 +280,18 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }  // namespace
 
 namespace dpsr {
+static thread_local bool t_pdl_off = false;
+
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("DPSR_PDL");
+    return !(v && v[0] == '0');
+  }();
+  return on && !t_pdl_off;
+}
+
+void pdl_suspend(bool off) { t_pdl_off = off; }
+
 // Spectral buffer k: complex (8-byte) elements [x][ky][kz], kz < r/2+1 valid
 // out of a row pitch of r/2+2. tmx: boxes of 16 kz x 1 ky x r x; tmy: boxes
 // of 16 kz x r ky x 1 x. Out-of-range kz reads as zero and is not written.
@@ -515,6 +535,7 @@ int dpsr_forward(dpsr_plan p, const float* points, const float* normals, int64_t
   if (!dg.ok) return DPSR_ECUDA;
   int rc = grow_points(p, N);
   if (rc != DPSR_OK) return rc;
+  PdlScope pdl(p->profile);
   Solve s = p->s;
   s.N = (int)N;
   s.points = points;
@@ -554,6 +575,7 @@ int dpsr_backward(dpsr_plan p, const float* dchi, float* dpoints, float* dnormal
   if (!p->have_fwd) return DPSR_ESTATE;
   DeviceGuard dg(p->device);
   if (!dg.ok) return DPSR_ECUDA;
+  PdlScope pdl(p->profile);
   Solve s = p->s;
   s.dchi = dchi;
   s.dpoints = dpoints;

@@ -17,6 +17,20 @@ constexpr int kNT = 256;  // threads of the plane kernels
 constexpr float kM = 0.5f;  // m of Eq. 2
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch. Every kernel of a solve lets the next kernel
+// of its stream be scheduled once all of its own CTAs are resident
+// (pdl_trigger, first thing), and waits for the previous kernel to complete
+// and its memory to be visible (pdl_wait) before it reads or writes anything
+// that kernel produced or consumed; only plan-constant tables (twiddles,
+// frequencies) and shared memory are touched before. Both are no-ops for a
+// kernel launched without the programmatic attribute.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
 // complex helpers (float2 = re, im)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }

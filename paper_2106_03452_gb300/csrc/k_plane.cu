@@ -40,6 +40,23 @@ struct PlaneGeo {
   static_assert(SPC >= 16 || C == 1, "a CTA owns whole 16-slot TMA boxes");
 };
 
+// Cluster sizes instantiated per grid size: one CTA per plane up to r = 64,
+// 1/2/4 CTAs at r = 128, 2/4/8 CTAs at r = 256 (r^2 complex values of one
+// plane do not fit one SM's shared memory there).
+template <int L, int C>
+constexpr bool plane_inst() {
+  // every CTA must own at least 16 slots (one TMA box of kz) so that box
+  // stores never cover a neighbour's slots
+  return L <= 64 ? C == 1 : (L == 128 ? (C == 1 || C == 2 || C == 4) : (C == 2 || C == 4 || C == 8));
+}
+
+// The forward plane kernel transforms all slots of a CTA in one y pass, which
+// needs at least as many groups as slots (r = 256: C >= 4).
+template <int L, int C>
+constexpr bool fwd_inst() {
+  return plane_inst<L, C>() && (512 / Shape<L>::T) >= (L / 2) / C;
+}
+
 // XOR swizzle inside aligned 16-slot blocks: a column read across 16 rows and
 // a row read across 16 columns both touch 16 distinct bank pairs.
 template <int RP, int SWM>
@@ -67,6 +84,57 @@ struct PlanePoints {
 };
 
 __device__ __forceinline__ float wsel(int d, float t) { return d ? t : 1.f - t; }
+
+// Points of the plane whose stencil touches the rows [y_lo, y_lo + R) of a
+// CTA (row i0 only, or i0 or i1 with `both`), as entries idx | dx << 31 in
+// `list` (capacity kListCap), so that the per-channel passes over the points
+// visit only those. Returns the count, or -1 when it exceeds the capacity
+// (the caller then visits all of the plane's points). Called by all NT
+// threads of the CTA (NT a multiple of 32); the order of the entries is
+// irrelevant: every entry is processed independently of the others.
+constexpr int kListCap = 2048;
+
+template <int NT>
+__device__ int plane_list(const Solve& S, const PlanePoints& pp, int L, int y_lo, int R, bool both,
+                          unsigned* list, int* cnt) {
+  if (threadIdx.x == 0) *cnt = 0;
+  __syncthreads();
+  const float* pf = reinterpret_cast<const float*>(S.sorted);
+  const int n = pp.total();
+  const unsigned lane = threadIdx.x & 31u;
+  for (int i0 = 0; i0 < n; i0 += NT) {
+    const int i = i0 + (int)threadIdx.x;
+    bool in = false;
+    int idx = 0, dx = 0;
+    if (i < n) {
+      idx = pp.index(i, dx);
+      const Axis ay = axis_of(pf[8 * (size_t)idx + 1], L);
+      in = (unsigned)(ay.i0 - y_lo) < (unsigned)R || (both && (unsigned)(ay.i1 - y_lo) < (unsigned)R);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const int pos = base + __popc(m & ((1u << lane) - 1u));
+    if (in && pos < kListCap) list[pos] = (unsigned)idx | ((unsigned)dx << 31);
+  }
+  __syncthreads();
+  const int c = *cnt;
+  return c <= kListCap ? c : -1;
+}
+
+// Entry i of the visit: from the list, or the plane's i-th point.
+__device__ __forceinline__ int visit_point(const unsigned* list, int nlist, const PlanePoints& pp,
+                                           int i, int& dx) {
+  if (nlist >= 0) {
+    const unsigned e = list[i];
+    dx = (int)(e >> 31);
+    return (int)(e & 0x7fffffffu);
+  }
+  return pp.index(i, dx);
+}
+
+
 
 // Column `g` of the chunk boxes (box g/16, complex g%16), element row e.
 template <int L>
@@ -137,14 +205,15 @@ __device__ __forceinline__ bool chunk_wait(uint64_t* bar, uint32_t phase, unsign
   return ok;
 }
 
-// kind: 0 forward plane (2 channels per row + derivative table), 1 inverse
-// (1 channel), 2 backward forward-transform (1 channel), 3 backward inverse
-// (3 channels + table).
+// Shared memory of the inverse (kind 1) and backward forward-transform
+// (kind 2) plane kernels: scratch, one channel of R rows, twiddles. The
+// forward (kind 0) and backward inverse (kind 3) kernels have their own
+// layouts (fwd_smem, binv_smem).
 template <int L, int C>
 constexpr size_t plane_smem(int kind) {
   using P = PlaneGeo<L, C>;
-  const int rp = kind == 0 ? L : (kind == 3 ? 3 * P::H : P::H);
-  const int table = (kind == 0 || kind == 3) ? L / 2 : 0;  // iu, as float2 units
+  const int rp = P::H;
+  const int table = 0;
   return 1024 + sizeof(float2) * ((size_t)P::SCR + (size_t)P::R * rp + table + L);
 }
 
@@ -164,11 +233,16 @@ constexpr int plane_minb(int kind) {
 // D = FFT_y(i u_z v~_z) + i u_y FFT_y(v~_y) accumulates in the output boxes
 // over the v_y and v_z rounds.
 // ===========================================================================
-// Threads of the forward plane kernel: 512 (one CTA per SM) up to 4-CTA
-// clusters; 256 for larger clusters, whose CTAs then fit two per SM.
-template <int C>
+// Threads of the forward plane kernel: 256 where the configuration fits two
+// CTAs per SM (a CTA's shared memory <= 113 KB and 256 threads still cover
+// all slots of the CTA in one y pass), 512 (one CTA per SM) otherwise.
+template <int L, int C>
+constexpr size_t fwd_smem_nt(int nt);
+
+template <int L, int C>
 constexpr int fwd_threads() {
-  return C >= 8 ? 256 : 512;
+  constexpr int spc = (L / 2) / C;
+  return (fwd_smem_nt<L, C>(256) <= 113 * 1024 && 256 / Shape<L>::T >= spc) ? 256 : 512;
 }
 
 template <int H>
@@ -180,9 +254,9 @@ __device__ __forceinline__ int rsw(int y, int s) {
   }
 }
 
-template <int L, int C>
-struct FwdGeo {
-  static constexpr int NT = fwd_threads<C>();
+template <int L, int C, int NTT>
+struct FwdGeoT {
+  static constexpr int NT = NTT;
   static constexpr int T = Shape<L>::T, R1 = Shape<L>::R1, G = NT / T;
   static constexpr int R = L / C, H = L / 2, SPC = H / C;
   static constexpr int NB = (SPC + 15) / 16;  // output boxes (16 slots each)
@@ -192,20 +266,36 @@ struct FwdGeo {
   // areas (L per group) cannot share them: with C > 1 they live in the
   // receive buffer (free during the z pass, exactly R/2 * L), else apart.
   static constexpr int SCR = (NB * BOX + 127) / 128 * 128;
-  static constexpr int ROWS = R * H;               // float2 (R real rows of L floats)
+  static constexpr int ROWS = R * H;                     // float2 (R real rows of L floats)
   static constexpr int RECV = C > 1 ? L * SPC : ZG * L;  // float2
-  static_assert(G >= SPC, "one y pass per round (D accumulates in the boxes)");
-  static_assert(T == 1 || SPC % (32 / T) == 0 || SPC >= G, "idle y groups must fill whole warps");
+};
+
+template <int L, int C>
+constexpr size_t fwd_smem_nt(int nt) {
+  // the footprint does not depend on the thread count except through the
+  // z-pass exchange of C = 1 (one area per z group)
+  using A = FwdGeoT<L, C, 256>;
+  using B = FwdGeoT<L, C, 512>;
+  const int recv = nt == 256 ? A::RECV : B::RECV;
+  return 1024 + sizeof(float2) * ((size_t)A::SCR + A::ROWS + recv + L) + sizeof(float) * L +
+         sizeof(unsigned) * kListCap;
+}
+
+template <int L, int C>
+struct FwdGeo : FwdGeoT<L, C, fwd_threads<L, C>()> {
+  using B = FwdGeoT<L, C, fwd_threads<L, C>()>;
+  static_assert(B::G >= B::SPC, "one y pass per round (D accumulates in the boxes)");
+  static_assert(B::T == 1 || B::SPC % (32 / B::T) == 0 || B::SPC >= B::G,
+                "idle y groups must fill whole warps");
 };
 
 template <int L, int C>
 constexpr size_t fwd_smem() {
-  using F = FwdGeo<L, C>;
-  return 1024 + sizeof(float2) * ((size_t)F::SCR + F::ROWS + F::RECV + L) + sizeof(float) * L;
+  return fwd_smem_nt<L, C>(fwd_threads<L, C>());
 }
 
 template <int L, int C>
-__global__ void __launch_bounds__(fwd_threads<C>(), 512 / fwd_threads<C>())
+__global__ void __launch_bounds__(fwd_threads<L, C>(), 512 / fwd_threads<L, C>())
     k_plane_fwd(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = PlaneGeo<L, C>;
   using F = FwdGeo<L, C>;
@@ -222,7 +312,10 @@ __global__ void __launch_bounds__(fwd_threads<C>(), 512 / fwd_threads<C>())
   float2* recv = rows + F::ROWS;
   float2* twt = recv + F::RECV;
   float* iu = reinterpret_cast<float*>(twt + L);
+  unsigned* list = reinterpret_cast<unsigned*>(iu + L);
   __shared__ uint64_t bar;
+  __shared__ int list_n;
+  pdl_trigger();
   for (int i = tid; i < L; i += F::NT) {
     iu[i] = S.iu[i];
     twt[i] = S.tw[i];
@@ -231,10 +324,13 @@ __global__ void __launch_bounds__(fwd_threads<C>(), 512 / fwd_threads<C>())
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  pdl_wait();
   __syncthreads();
   TwTab<L> twr{twt, t};
   const PlanePoints pp(S, X);
   const int y_lo = c * F::R;
+  const int nlist = C > 1 ? plane_list<F::NT>(S, pp, L, y_lo, F::R, true, list, &list_n) : -1;
+  const int nvisit = nlist >= 0 ? nlist : pp.total();
   const float2* ysrc = C > 1 ? recv : rows;  // [y][SPC] in the y pass
   uint32_t phase = 0;
   bool alive = true;
@@ -249,9 +345,9 @@ __global__ void __launch_bounds__(fwd_threads<C>(), 512 / fwd_threads<C>())
       reinterpret_cast<float4*>(rows)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     // Rasterization (Eq. A2) of one channel into real rows.
-    for (int i = tid; i < pp.total(); i += F::NT) {
+    for (int i = tid; i < nvisit; i += F::NT) {
       int dx;
-      const int idx = pp.index(i, dx);
+      const int idx = visit_point(list, nlist, pp, i, dx);
       const float4 a = S.sorted[2 * idx], b = S.sorted[2 * idx + 1];
       const float val = ch == 0 ? a.w : (ch == 1 ? b.x : (ch == 2 ? b.y : 1.f));
       const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);
@@ -366,8 +462,10 @@ __global__ void __launch_bounds__(kNT, plane_minb<L, C>(1))
   float2* rows = sbox + P::SCR;
   float2* twt = rows + P::R * RP;
   __shared__ uint64_t bar;
+  pdl_trigger();
   for (int i = tid; i < L; i += kNT) twt[i] = S.tw[i];
   TwTab<L> twr{twt, t};
+  pdl_wait();
   const float a_chi = S.sc->a_chi, b_chi = S.sc->b_chi;
   if (tid == 0) {
     mbar_init(&bar, 1);
@@ -487,7 +585,9 @@ __global__ void __launch_bounds__(kNT, plane_minb<L, C>(2))
   float2* rows = sbox + P::SCR;
   float2* twt = rows + P::R * RP;
   float2* xz = sbox + g * P::XP;
+  pdl_trigger();
   for (int i = tid; i < L; i += kNT) twt[i] = S.tw[i];
+  pdl_wait();
   __shared__ double red[2][kNT / 32];
   uint32_t rb[C];  // shared::cluster address of each CTA's rows
 #pragma unroll
@@ -588,180 +688,253 @@ __global__ void __launch_bounds__(kNT, plane_minb<L, C>(2))
 // ===========================================================================
 // Backward inverse plane kernel: IFFT(y) + C2R(z) of the three adjoint fields
 // V_bar_x, V_bar_y, V_bar_z, then dnormals = gather and the weight-derivative
-// part of dpoints, per plane side.
+// part of dpoints, per plane side. One channel per round:
+//   y pass  : IFFT along y of this CTA's SPC columns, in their TMA boxes;
+//   push    : rows [q R, q R + R) of every box go to CTA q with one bulk copy
+//             per (box, q) (a contiguous R x 128 B run of the box);
+//   z pass  : C2R of row pairs, in place in the receive buffer (the pair's
+//             own storage is also the FFT exchange area);
+//   gather  : the channel's share of the point adjoint, read through DSMEM.
+// Both source boxes (Q2 for X, Q1 for Y and Z) are fetched by TMA at the
+// start; the Z channel's y-inverse is computed from the Q1 box in the Y
+// round (u_z is constant along a column, so it commutes with the y-inverse).
 // ===========================================================================
 template <int L, int C>
-__global__ void __launch_bounds__(kNT, plane_minb<L, C>(3))
+struct BinvGeo {
+  static constexpr int T = Shape<L>::T, R1 = Shape<L>::R1, G = kNT / T;
+  static constexpr int R = L / C, H = L / 2, SPC = H / C;
+  static constexpr int NB = (SPC + 15) / 16;
+  static constexpr int BOX = L * 16;  // float2 per box [ky][16 kz]
+  static constexpr int BUF = NB * BOX;
+  // receive buffer: R rows x H slots in blocks of 16 slots ([block][row][16],
+  // rows swizzled like box rows); with C = 1 the box buffer itself
+  static constexpr int RECV = C > 1 ? R * H : 0;
+  static constexpr int BLK = (C > 1 ? R : L) * 16;  // float2 per slot block
+  static_assert(C == 1 || (SPC % 16 == 0 && R % 8 == 0), "whole boxes, swizzle-aligned runs");
+};
+
+template <int L, int C>
+constexpr size_t binv_smem() {
+  using B = BinvGeo<L, C>;
+  return 1024 + sizeof(float2) * ((size_t)2 * B::BUF + B::RECV + L) + sizeof(float) * L +
+         sizeof(unsigned) * kListCap;
+}
+
+template <int L, int C>
+constexpr bool binv_inst() {
+  return plane_inst<L, C>() && binv_smem<L, C>() <= 227 * 1024;
+}
+
+// float2 index of (row, slot) in a block-of-16-slots buffer.
+template <int BLK>
+__device__ __forceinline__ int rb(int row, int slot) {
+  return (slot >> 4) * BLK + bx(row, slot & 15);
+}
+
+// C2R of a row pair whose storage (L float2 through `acc`: A's slots, then
+// B's) is also the exchange area and receives the output (a[z], b[z]) at z.
+template <int L, class Tw, class Acc>
+__device__ __forceinline__ void c2r_pair_ip(int t, const Tw& tw, Acc acc) {
+  constexpr int R1 = Shape<L>::R1, T = Shape<L>::T, H = L / 2;
+  float2 v[R1];
+#pragma unroll
+  for (int j = 0; j < R1; ++j) {
+    const int k = t + T * j;
+    if (k == 0 || k == H) {
+      const float2 a = acc(0), b = acc(H);
+      v[j] = (k == 0) ? make_float2(a.x, b.x) : make_float2(a.y, b.y);
+    } else if (k < H) {
+      const float2 a = acc(k), b = acc(H + k);
+      v[j] = make_float2(a.x - b.y, a.y + b.x);
+    } else {
+      const float2 a = acc(L - k), b = acc(H + L - k);
+      v[j] = make_float2(a.x + b.y, b.x - a.y);
+    }
+  }
+  group_sync<T>();  // every lane has read the pair before it becomes exchange
+  fft_r<L, +1>(v, t, acc, tw);
+#pragma unroll
+  for (int j = 0; j < R1; ++j) acc(t + T * j) = v[j];
+}
+
+template <int L, int C>
+__global__ void __launch_bounds__(kNT, binv_smem<L, C>() <= 113 * 1024 ? 2 : 1)
     k_plane_binv(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
-  using P = PlaneGeo<L, C>;
-  constexpr int RP = 3 * P::H;  // channels X | Y | Z
+  using B = BinvGeo<L, C>;
+  constexpr int H = B::H, R = B::R, SPC = B::SPC, T = B::T, R1 = B::R1, G = B::G;
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   cg::cluster_group cl = cg::this_cluster();
   const int c = (int)cl.block_rank();
   const int X = blockIdx.x / C;
-  const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
+  const int tid = threadIdx.x, g = tid / T, t = tid % T;
   extern __shared__ unsigned char smem_raw[];
-  float2* sbox = aligned_smem(smem_raw);
-  float2* rows = sbox + P::SCR;
-  float* iu = reinterpret_cast<float*>(rows + P::R * RP);
-  float2* twt = reinterpret_cast<float2*>(iu + L);
-  __shared__ uint64_t bar;
+  float2* buf0 = aligned_smem(smem_raw);
+  float2* buf1 = buf0 + B::BUF;
+  float2* recv = buf1 + B::BUF;
+  float2* twt = recv + B::RECV;
+  float* iu = reinterpret_cast<float*>(twt + L);
+  unsigned* list = reinterpret_cast<unsigned*>(iu + L);
+  __shared__ uint64_t barL[2], barR;
+  __shared__ int list_n;
+  pdl_trigger();
   for (int i = tid; i < L; i += kNT) {
     iu[i] = S.iu[i];
     twt[i] = S.tw[i];
   }
-  TwTab<L> twr{twt, t};
+  pdl_wait();
+  const int s_first = c * SPC;
   if (tid == 0) {
-    mbar_init(&bar, 1);
+    mbar_init(&barL[0], 1);
+    mbar_init(&barL[1], 1);
+    mbar_init(&barR, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // X channel from Q2 = IFFT_x(-i u_x F), Y and Z from Q1 = IFFT_x(F):
+    // the NB boxes of this CTA's SPC slots (x coordinate even: 16-B aligned)
+    for (int k = 0; k < 2; ++k) {
+      mbar_expect_tx(&barL[k], B::NB * B::BOX * (uint32_t)sizeof(float2));
+      for (int b = 0; b < B::NB; ++b)
+        tma_load_3d((k ? buf1 : buf0) + b * B::BOX, &S.tmy[k ? 0 : 1], s_first + 16 * b, 0, X, &barL[k]);
+    }
   }
   __syncthreads();
-  uint32_t phase = 0;
+  TwTab<L> twr{twt, t};
+  const PlanePoints pp(S, X);
+  const int y_lo = c * R;
+  // (overlaps the box loads in flight)
+  const int nlist = C > 1 ? plane_list<kNT>(S, pp, L, y_lo, R, false, list, &list_n) : -1;
+  const int nvisit = nlist >= 0 ? nlist : pp.total();
+  uint32_t phR = 0;
   bool alive = true;
-  for (int cb = 0; cb < P::SPC && alive; cb += P::CHK) {
-    const int s_first = c * P::SPC + cb;
-    const int s = s_first + min(g, P::CHK - 1);
-    const bool head = (c == 0 && cb == 0);
-    auto xa = [&](int e) -> float2& { return boxcol<L>(sbox, g, e); };
-    float2 v[P::R1];
-    // X channel: Q2 = IFFT_x(-i u_x F), y-inverse as is. Y and Z channels from
-    // Q1 = IFFT_x(F): -i u_y before the y-inverse, -i u_z (a constant per
-    // column) for Z.
-    for (int src = 0; src < 3 && alive; ++src) {
-      // src 0: X from Q2; src 1: Y = -i u_y Q1; src 2: Z = -i u_z Q1 (Q1 is
-      // loaded again rather than kept in registers; the second load hits L2)
-      const int buf = src == 0 ? 1 : 0;
-      if (tid == 0) chunk_load<L, C>(&S.tmy[buf], sbox, s_first, X, &bar);
-      float2 nyq[P::R1];
-      if (head && g == 0 && P::H >= 16) {
-#pragma unroll
-        for (int j = 0; j < P::R1; ++j)
-          nyq[j] = S.spec[buf][((size_t)X * L + t + P::T * j) * P::KP + P::H];
-      }
-      alive = chunk_wait(&bar, phase, S.status);
-      phase ^= 1;
-      if (!alive) break;
-#pragma unroll
-      for (int j = 0; j < P::R1; ++j) {
-        const int ky = t + P::T * j;
-        v[j] = xa(ky);
-        if (head && g == 0) {
-          const float2 n = P::H >= 16 ? nyq[j] : boxcol<L>(sbox, P::H, ky);
-          v[j] = make_float2(v[j].x - n.y, v[j].y + n.x);
+  // y-domain column `sl` of a box buffer
+  auto col = [](float2* bf, int sl, int e) -> float2& { return bf[(sl >> 4) * B::BOX + bx(e, sl & 15)]; };
+
+#pragma unroll 1
+  for (int ch = 0; ch < 3; ++ch) {
+    float2* src = ch == 1 ? buf1 : buf0;  // y-inverse of channel ch (push source)
+    float2* dst = C > 1 ? recv : src;     // this CTA's rows of channel ch
+    if (ch < 2) {
+      if constexpr (C == 1) __syncthreads();  // buf0 was read by the last gather
+      alive = chunk_wait(&barL[ch], 0, S.status) && alive;
+      if (alive && c == 0 && g == 0) {
+        // column kz = 0 becomes P = X0 + i Xn (Xn: the Nyquist column); the
+        // same lanes read these elements again in the y pass below
+        const float2* nq = S.spec[ch == 0 ? 1 : 0] + (size_t)X * L * (H + 2) + H;
+        for (int j = 0; j < R1; ++j) {
+          const int ky = t + T * j;
+          const float2 n = H >= 16 ? nq[(size_t)ky * (H + 2)] : col(src, H, ky);
+          const float2 x0 = col(src, 0, ky);
+          col(src, 0, ky) = make_float2(x0.x - n.y, x0.y + n.x);
         }
       }
-      if (src == 1) {
+      if (alive) {
+        for (int sl0 = 0; sl0 < SPC; sl0 += G) {
+          const int sl = sl0 + g;
+          if (sl < SPC) {  // whole groups; T-lane syncs only
+            const int s = s_first + sl;
+            float2 v[R1];
 #pragma unroll
-        for (int j = 0; j < P::R1; ++j) v[j] = cmul_iu(v[j], -iu[t + P::T * j]);
-      } else if (src == 2) {
-        const float ez = s == 0 ? 0.f : -iu[s];
+            for (int j = 0; j < R1; ++j) v[j] = col(src, sl, t + T * j);
+            if (ch == 1) {
 #pragma unroll
-        for (int j = 0; j < P::R1; ++j) v[j] = cmul_iu(v[j], ez);
-      }
-      fft_r<L, +1>(v, t, xa, twr);
+              for (int j = 0; j < R1; ++j) col(buf0, sl, t + T * j) = v[j];  // Q1 for Z
 #pragma unroll
-      for (int j = 0; j < P::R1; ++j) xa(t + P::T * j) = v[j];
-      __syncthreads();
-      push_cols<L, C, RP>(cl, rows, s_first, src * P::H, sbox);
-      __syncthreads();
-    }
-  }
-  cl.sync();
-  if (!alive) return;
-  // C2R along z: rows of (X, Y) pairs in place as (Vx[z], Vy[z]); Z channel
-  // by row pairs, in place as (Vz_2p[z], Vz_2p+1[z]) over the Z slots of the
-  // two rows.
-  float2* xz = sbox + g * P::XP;
-  for (int r0 = 0; r0 < P::R; r0 += P::G) {
-    const int row = r0 + g;
-    const bool ok = row < P::R;
-    const int rr = ok ? row : 0;
-    c2r_pair<L>(
-        t, xz, twr, [&](int k) { return rows[sw<RP, P::SWM>(rr, k)]; },
-        [&](int k) { return rows[sw<RP, P::SWM>(rr, P::H + k)]; },
-        [&](int z, float2 w) {
-          if (ok) rows[sw<RP, P::SWM>(rr, z)] = w;
-        });
-  }
-  for (int p0 = 0; p0 < P::R / 2; p0 += P::G) {
-    const int p = p0 + g;
-    const bool ok = p < P::R / 2;
-    const int pr = ok ? p : 0;
-    c2r_pair<L>(
-        t, xz, twr, [&](int k) { return rows[sw<RP, P::SWM>(2 * pr, 2 * P::H + k)]; },
-        [&](int k) { return rows[sw<RP, P::SWM>(2 * pr + 1, 2 * P::H + k)]; },
-        [&](int z, float2 w) {
-          if (ok) rows[sw<RP, P::SWM>(2 * pr + z / P::H, 2 * P::H + z % P::H)] = w;
-        });
-  }
-  cl.sync();
-  {
-    const PlanePoints pp(S, X);
-    const int y_lo = c * P::R;
-    for (int i = tid; i < pp.total(); i += kNT) {
-      int dx;
-      const int idx = pp.index(i, dx);
-      const float4 a = S.sorted[2 * idx], b = S.sorted[2 * idx + 1];
-      const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);
-      if (ay.i0 - y_lo < 0 || ay.i0 - y_lo >= P::R) continue;
-      const float n0 = a.w, n1 = b.x, n2 = b.y;
-      const float fx = wsel(dx, ax.t), dfx = dx ? (float)L : -(float)L;
-      float nb0 = 0.f, nb1 = 0.f, nb2 = 0.f, cb0 = 0.f, cb1 = 0.f, cb2 = 0.f;
+              for (int j = 0; j < R1; ++j) v[j] = cmul_iu(v[j], -iu[t + T * j]);
+            }
+            fft_r<L, +1>(v, t, [&](int e) -> float2& { return col(src, sl, e); }, twr);
 #pragma unroll
-      for (int dy = 0; dy < 2; ++dy) {
-        const int y = dy ? ay.i1 : ay.i0;
-        const int q = y / P::R, lr = y % P::R, p2 = lr & ~1;
-        const float fy = wsel(dy, ay.t), dfy = dy ? (float)L : -(float)L;
+            for (int j = 0; j < R1; ++j) col(src, sl, t + T * j) = v[j];
+            if (ch == 1) {
+              group_sync<T>();
 #pragma unroll
-        for (int dz = 0; dz < 2; ++dz) {
-          const int z = dz ? az.i1 : az.i0;
-          const float fz = wsel(dz, az.t), dfz = dz ? (float)L : -(float)L;
-          const uint32_t rq = dsmem_map(rows, q);
-          const float2 xy = dsmem_ld(rq + 8u * sw<RP, P::SWM>(lr, z));
-          const float2 zz = dsmem_ld(rq + 8u * sw<RP, P::SWM>(p2 + z / P::H, 2 * P::H + z % P::H));
-          const float vz = (lr & 1) ? zz.y : zz.x;
-          const float w = fx * fy * fz;
-          nb0 += w * xy.x;
-          nb1 += w * xy.y;
-          nb2 += w * vz;
-          const float sdot = n0 * xy.x + n1 * xy.y + n2 * vz;
-          cb0 += dfx * fy * fz * sdot;
-          cb1 += fx * dfy * fz * sdot;
-          cb2 += fx * fy * dfz * sdot;
+              for (int j = 0; j < R1; ++j) v[j] = col(buf0, sl, t + T * j);
+              fft_r<L, +1>(v, t, [&](int e) -> float2& { return col(buf0, sl, e); }, twr);
+              const float ez = s == 0 ? 0.f : -iu[s];
+#pragma unroll
+              for (int j = 0; j < R1; ++j) col(buf0, sl, t + T * j) = cmul_iu(v[j], ez);
+            }
+          }
         }
       }
-      float* o = S.slots + ((size_t)dx * S.N + idx) * 6;
-      o[0] = nb0;
-      o[1] = nb1;
-      o[2] = nb2;
-      o[3] = cb0;
-      o[4] = cb1;
-      o[5] = cb2;
+    }
+    if constexpr (C > 1) {
+      // Arm, make the boxes visible to the async proxy, sync (every receive
+      // buffer is free and armed), push, wait for this CTA's rows.
+      if (tid == 0) mbar_expect_tx(&barR, R * H * (uint32_t)sizeof(float2));
+      fence_async_smem();
+      cl.sync();
+      if (tid < C * B::NB) {
+        const int q = tid / B::NB, b = tid % B::NB;
+        const int blk = s_first / 16 + b;  // slot block of the receiver
+        bulk_push(dsmem_map(recv + blk * B::BLK, q), src + b * B::BOX + q * R * 16,
+                  R * 16 * (uint32_t)sizeof(float2), dsmem_map(&barR, q));
+      }
+      alive = chunk_wait(&barR, phR, S.status) && alive;
+      phR ^= 1;
+    } else {
+      __syncthreads();
+    }
+    // C2R along z of row pairs, in place.
+    if (alive) {
+      for (int p0 = 0; p0 < R / 2; p0 += G) {
+        const int p = p0 + g;
+        if (p < R / 2) {
+          c2r_pair_ip<L>(t, twr, [&](int i) -> float2& { return dst[rb<B::BLK>(2 * p + i / H, i % H)]; });
+        }
+      }
+    }
+    if constexpr (C > 1) cl.sync(); else __syncthreads();
+    // This channel's share of the point adjoint: dnormals_ch = gather of
+    // V_ch, and d/dp of the weights times n_ch V_ch.
+    if (alive) {
+      for (int i = tid; i < nvisit; i += kNT) {
+        int dx;
+        const int idx = visit_point(list, nlist, pp, i, dx);
+        const float4 a = S.sorted[2 * idx];
+        const Axis ay = axis_of(a.y, L);
+        if ((unsigned)(ay.i0 - y_lo) >= (unsigned)R) continue;
+        const Axis ax = axis_of(a.x, L), az = axis_of(a.z, L);
+        const float nch = ch == 0 ? a.w : (ch == 1 ? S.sorted[2 * idx + 1].x : S.sorted[2 * idx + 1].y);
+        const float fx = wsel(dx, ax.t), dfx = dx ? (float)L : -(float)L;
+        float nb = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+          const int y = dy ? ay.i1 : ay.i0;
+          const int q = y / R, lr = y % R, p2 = lr & ~1;
+          const float fy = wsel(dy, ay.t), dfy = dy ? (float)L : -(float)L;
+          const uint32_t base = dsmem_map(dst, q);
+#pragma unroll
+          for (int dz = 0; dz < 2; ++dz) {
+            const int z = dz ? az.i1 : az.i0;
+            const float fz = wsel(dz, az.t), dfz = dz ? (float)L : -(float)L;
+            const float2 f = dsmem_ld(base + 8u * rb<B::BLK>(p2 + z / H, z % H));
+            const float V = (lr & 1) ? f.y : f.x;
+            const float sv = nch * V;
+            nb += fx * fy * fz * V;
+            c0 += dfx * fy * fz * sv;
+            c1 += fx * dfy * fz * sv;
+            c2 += fx * fy * dfz * sv;
+          }
+        }
+        float* o = S.slots + ((size_t)dx * S.N + idx) * 6;
+        o[ch] = nb;
+        if (ch == 0) {
+          o[3] = c0;
+          o[4] = c1;
+          o[5] = c2;
+        } else {
+          o[3] += c0;
+          o[4] += c1;
+          o[5] += c2;
+        }
+      }
     }
   }
-  cl.sync();
+  if constexpr (C > 1) cl.sync();  // peers may still read this CTA's rows
 }
 
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-// Cluster sizes instantiated per grid size: one CTA per plane up to r = 64,
-// 1/2/4 CTAs at r = 128, 2/4/8 CTAs at r = 256 (r^2 complex values of one
-// plane do not fit one SM's shared memory there).
-template <int L, int C>
-constexpr bool plane_inst() {
-  // every CTA must own at least 16 slots (one TMA box of kz) so that box
-  // stores never cover a neighbour's slots
-  return L <= 64 ? C == 1 : (L == 128 ? (C == 1 || C == 2 || C == 4) : (C == 2 || C == 4 || C == 8));
-}
-
-// The forward plane kernel transforms all slots of a CTA in one y pass, which
-// needs at least as many groups as slots (r = 256: C >= 4).
-template <int L, int C>
-constexpr bool fwd_inst() {
-  return plane_inst<L, C>() && (fwd_threads<C>() / Shape<L>::T) >= (L / 2) / C;
-}
-
 template <int L, int C>
 static cudaError_t launch_plane_t(int kind, const Solve& s, const Solve* tab, int count,
                                   cudaStream_t st) {
@@ -773,12 +946,16 @@ static cudaError_t launch_plane_t(int kind, const Solve& s, const Solve* tab, in
       break;
     case 1: fn = k_plane_inv<L, C>; break;
     case 2: fn = k_plane_bfwd<L, C>; break;
-    default: fn = k_plane_binv<L, C>; break;
+    default:
+      if constexpr (binv_inst<L, C>()) fn = k_plane_binv<L, C>;
+      else return cudaErrorInvalidValue;
+      break;
   }
   size_t smem = plane_smem<L, C>(kind);
   if constexpr (fwd_inst<L, C>()) {
     if (kind == 0) smem = fwd_smem<L, C>();
   }
+  if (kind == 3) smem = binv_smem<L, C>();
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   static bool attr_set[4] = {false, false, false, false};  // per instantiation and kind
   if (!attr_set[kind]) {
@@ -789,19 +966,11 @@ static cudaError_t launch_plane_t(int kind, const Solve& s, const Solve* tab, in
     if (e != cudaSuccess) return e;
     attr_set[kind] = true;
   }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(L * C, 1, count);
-  cfg.blockDim = dim3(kind == 0 ? fwd_threads<C>() : kNT, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fn, s, tab);
+  dim3 block(kNT);
+  if constexpr (fwd_inst<L, C>()) {
+    if (kind == 0) block = dim3(fwd_threads<L, C>());
+  }
+  return launch_k(fn, dim3(L * C, 1, count), block, smem, st, C, s, tab);
 }
 
 template <int L>
@@ -812,7 +981,6 @@ static cudaError_t launch_plane_L(int kind, int C, const Solve& s, const Solve* 
     case 2: if constexpr (plane_inst<L, 2>()) return launch_plane_t<L, 2>(kind, s, tab, count, st); break;
     case 4: if constexpr (plane_inst<L, 4>()) return launch_plane_t<L, 4>(kind, s, tab, count, st); break;
     case 8: if constexpr (plane_inst<L, 8>()) return launch_plane_t<L, 8>(kind, s, tab, count, st); break;
-    case 16: if constexpr (plane_inst<L, 16>()) return launch_plane_t<L, 16>(kind, s, tab, count, st); break;
     default: break;
   }
   return cudaErrorInvalidValue;
@@ -831,15 +999,31 @@ cudaError_t launch_plane(int kind, int r, int C, const Solve& s, const Solve* ta
   }
 }
 
+template <int L, int C>
+static size_t kind_smem(int kind) {
+  if constexpr (!plane_inst<L, C>()) {
+    return 0;
+  } else {
+    if (kind == 0) {
+      if constexpr (fwd_inst<L, C>()) return fwd_smem<L, C>();
+      return 0;
+    }
+    if (kind == 3) {
+      if constexpr (binv_inst<L, C>()) return binv_smem<L, C>();
+      return 0;
+    }
+    return plane_smem<L, C>(kind);
+  }
+}
+
 size_t plane_smem_bytes(int kind, int r, int C) {
   auto pick = [&](auto Lc) -> size_t {
     constexpr int L = decltype(Lc)::value;
     switch (C) {
-      case 1: if constexpr (plane_inst<L, 1>()) { if (kind == 0) { if constexpr (fwd_inst<L, 1>()) return fwd_smem<L, 1>(); return 0; } return plane_smem<L, 1>(kind); } return 0;
-      case 2: if constexpr (plane_inst<L, 2>()) { if (kind == 0) { if constexpr (fwd_inst<L, 2>()) return fwd_smem<L, 2>(); return 0; } return plane_smem<L, 2>(kind); } return 0;
-      case 4: if constexpr (plane_inst<L, 4>()) { if (kind == 0) { if constexpr (fwd_inst<L, 4>()) return fwd_smem<L, 4>(); return 0; } return plane_smem<L, 4>(kind); } return 0;
-      case 8: if constexpr (plane_inst<L, 8>()) { if (kind == 0) { if constexpr (fwd_inst<L, 8>()) return fwd_smem<L, 8>(); return 0; } return plane_smem<L, 8>(kind); } return 0;
-      case 16: if constexpr (plane_inst<L, 16>()) { if (kind == 0) { if constexpr (fwd_inst<L, 16>()) return fwd_smem<L, 16>(); return 0; } return plane_smem<L, 16>(kind); } return 0;
+      case 1: return kind_smem<L, 1>(kind);
+      case 2: return kind_smem<L, 2>(kind);
+      case 4: return kind_smem<L, 4>(kind);
+      case 8: return kind_smem<L, 8>(kind);
       default: return 0;
     }
   };

@@ -16,10 +16,12 @@ __device__ __forceinline__ bool coord_ok(float c, int r) {
 // raise kStBadInput and are replaced by 0 so that indexing stays in range).
 __global__ void __launch_bounds__(256) k_bin_count(const __grid_constant__ Solve s0,
                                                    const Solve* __restrict__ tab) {
+  pdl_trigger();
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   __shared__ int h[256];
   const int r = S.r;
   for (int i = threadIdx.x; i < r; i += blockDim.x) h[i] = 0;
+  pdl_wait();
   __syncthreads();
   bool bad = false;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < S.N; p += gridDim.x * blockDim.x) {
@@ -44,6 +46,8 @@ __global__ void __launch_bounds__(256) k_bin_count(const __grid_constant__ Solve
 // Exclusive scan of the r counts into off[0..r] and the scatter cursors.
 __global__ void __launch_bounds__(256) k_bin_scan(const __grid_constant__ Solve s0,
                                                   const Solve* __restrict__ tab) {
+  pdl_trigger();
+  pdl_wait();
   const Solve& S = tab ? tab[blockIdx.x] : s0;
   __shared__ int v[256];
   const int r = S.r, i = threadIdx.x;
@@ -69,6 +73,8 @@ __global__ void __launch_bounds__(256) k_bin_scan(const __grid_constant__ Solve 
 
 __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Solve s0,
                                                      const Solve* __restrict__ tab) {
+  pdl_trigger();
+  pdl_wait();
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   const int r = S.r;
   int* cur = S.bins + 2 * r + 1;
@@ -89,10 +95,10 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Sol
 
 cudaError_t launch_bin(const Solve& s, const Solve* tab, int count, int nmax, cudaStream_t st) {
   const int blocks = min(max((nmax + 255) / 256, 1), 1184);
-  k_bin_count<<<dim3(blocks, 1, count), 256, 0, st>>>(s, tab);
-  k_bin_scan<<<count, 256, 0, st>>>(s, tab);
-  k_bin_scatter<<<dim3(blocks, 1, count), 256, 0, st>>>(s, tab);
-  return cudaGetLastError();
+  cudaError_t e = launch_k(k_bin_count, dim3(blocks, 1, count), dim3(256), 0, st, 0, s, tab);
+  if (e == cudaSuccess) e = launch_k(k_bin_scan, dim3(count), dim3(256), 0, st, 0, s, tab);
+  if (e == cudaSuccess) e = launch_k(k_bin_scatter, dim3(blocks, 1, count), dim3(256), 0, st, 0, s, tab);
+  return e;
 }
 
 // dpoints = sum of the two plane sides of the weight-derivative terms
@@ -101,6 +107,8 @@ cudaError_t launch_bin(const Solve& s, const Solve* tab, int count, int nmax, cu
 // caller's point order.
 __global__ void __launch_bounds__(256) k_combine(const __grid_constant__ Solve s0,
                                                  const Solve* __restrict__ tab) {
+  pdl_trigger();
+  pdl_wait();
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   const float c_mu = S.sc->c_mu;
   const size_t N = S.N;
@@ -121,8 +129,7 @@ __global__ void __launch_bounds__(256) k_combine(const __grid_constant__ Solve s
 cudaError_t launch_combine(const Solve& s, const Solve* tab, int count, int nmax,
                            cudaStream_t st) {
   const int blocks = min(max((nmax + 255) / 256, 1), 1184);
-  k_combine<<<dim3(blocks, 1, count), 256, 0, st>>>(s, tab);
-  return cudaGetLastError();
+  return launch_k(k_combine, dim3(blocks, 1, count), dim3(256), 0, st, 0, s, tab);
 }
 
 // ---------------------------------------------------------------------------

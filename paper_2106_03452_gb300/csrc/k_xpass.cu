@@ -66,6 +66,8 @@ __global__ void __launch_bounds__(XGeo<L>::NT, 2)
   __shared__ double red[2][P::NT / 32];
   // inputs: forward D, C, W~; backward FFT_zy(dchi), W~
   const int src0 = BWD ? 3 : 0, src1 = BWD ? 2 : 1;
+  pdl_trigger();
+  pdl_wait();
   if (tid == 0) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -210,8 +212,7 @@ static cudaError_t launch_xpass_t(const Solve& s, const Solve* tab, int count, c
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_xpass<L, BWD><<<dim3(P::NCHUNK, L, count), P::NT, smem, st>>>(s, tab);
-  return cudaGetLastError();
+  return launch_k(k_xpass<L, BWD>, dim3(P::NCHUNK, L, count), dim3(P::NT), smem, st, 0, s, tab);
 }
 
 cudaError_t launch_xpass(bool bwd, int r, const Solve& s, const Solve* tab, int count,
@@ -267,6 +268,8 @@ __device__ void reduce_parts(const double* part, int n, double& a, double& b) {
 __global__ void __launch_bounds__(256) k_finalize(const __grid_constant__ Solve s0,
                                                   const Solve* __restrict__ tab, int nparts,
                                                   int bwd) {
+  pdl_trigger();
+  pdl_wait();
   const Solve& S = tab ? tab[blockIdx.x] : s0;
   double a, b;
   reduce_parts(S.part, nparts, a, b);
@@ -314,8 +317,7 @@ __global__ void __launch_bounds__(256) k_finalize(const __grid_constant__ Solve 
 
 cudaError_t launch_finalize(bool bwd, int nparts, const Solve& s, const Solve* tab, int count,
                             cudaStream_t st) {
-  k_finalize<<<count, 256, 0, st>>>(s, tab, nparts, bwd ? 1 : 0);
-  return cudaGetLastError();
+  return launch_k(k_finalize, dim3(count), dim3(256), 0, st, 0, s, tab, nparts, bwd ? 1 : 0);
 }
 
 }  // namespace dpsr

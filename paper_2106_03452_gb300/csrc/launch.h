@@ -2,9 +2,47 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "dpsr_dev.cuh"
 
 namespace dpsr {
+
+// Whether solve kernels are launched with programmatic stream serialization
+// (on unless the environment sets DPSR_PDL=0, or the calling thread has
+// suspended it: per-kernel event timing wants each kernel to start after the
+// previous one has completed).
+bool pdl_enabled();
+void pdl_suspend(bool off);
+
+// cudaLaunchKernelEx with an optional cluster size (x) and the programmatic
+// launch attribute.
+template <class... KArgs, class... Args>
+cudaError_t launch_k(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     int cluster, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  int n = 0;
+  if (cluster > 0) {
+    attr[n].id = cudaLaunchAttributeClusterDimension;
+    attr[n].val.clusterDim.x = cluster;
+    attr[n].val.clusterDim.y = 1;
+    attr[n].val.clusterDim.z = 1;
+    ++n;
+  }
+  if (pdl_enabled()) {
+    attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[n].val.programmaticStreamSerializationAllowed = 1;
+    ++n;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = n;
+  return cudaLaunchKernelEx(&cfg, fn, std::forward<Args>(args)...);
+}
 
 // Plane kernels: kind 0 = forward splat/z/y, 1 = forward inverse y/z + lookup
 // gradient, 2 = backward z/y of dchi, 3 = backward inverse y/z + point adjoint.
