@@ -206,7 +206,10 @@ def run_gpu(args):
         plan.forward(P, Nn, chi)
         plan.backward(G, dp, dn)
 
-    step()
+    plan.forward(P, Nn, chi)
+    per_step = plan.last_launches()
+    plan.backward(G, dp, dn)
+    per_step += plan.last_launches()
     st = plan.sync()
     if st != 0:
         raise RuntimeError(f"device status {st}: {L.dpsr_strerror(st)}")
@@ -216,7 +219,7 @@ def run_gpu(args):
     clk = clocks.stop()
     ms_max = _max_over_ranks(dist, ms)
     value = ws * args.steps / (ms_max / 1e3)
-    launches = args.steps * 12
+    launches = args.steps * per_step
 
     # per-kernel profile of the same step (events around every launch)
     L.dpsr_plan_profile(plan.handle, True)
@@ -365,6 +368,11 @@ def bench_batched(args, dev, dist, ws, timed):
             p.forward(P, Nn, chi)
             p.backward(G, dp, dn)
 
+    P0, Nn0, G0, chi0, dp0, dn0 = tens[0]
+    plans[0].forward(P0, Nn0, chi0)
+    loop_launches = plans[0].last_launches()
+    plans[0].backward(G0, dp0, dn0)
+    loop_launches += plans[0].last_launches()
     step_batch()
     if batch.sync() != 0:
         raise RuntimeError("batch device status")
@@ -377,7 +385,7 @@ def bench_batched(args, dev, dist, ws, timed):
            "solves_per_s": ws * 32 * k / (ms_b / 1e3), "ms_per_batch": ms_b / k,
            "loop_solves_per_s": ws * 32 * k / (ms_l / 1e3), "loop_ms_per_batch": ms_l / k,
            "speedup_vs_loop": ms_l / ms_b, "launches_per_batch": batch.launches(True),
-           "loop_launches_per_batch": 32 * 12}
+           "loop_launches_per_batch": 32 * loop_launches}
     batch.close()
     for p in plans:
         p.close()

@@ -98,11 +98,11 @@ int part_count(int r) {
 }
 
 size_t grid_ws_bytes(int r) {
-  size_t b = 4 * align256(spec_bytes(r));
+  size_t b = dpsr::kNSpec * align256(spec_bytes(r));
   b += align256(sizeof(float2) * r) + 3 * align256(sizeof(float) * r);
   b += align256(sizeof(dpsr::Scalars)) + align256(sizeof(unsigned));
   b += align256(sizeof(double) * 2 * part_count(r));
-  b += align256(sizeof(int) * (3 * r + 1));
+  b += align256(sizeof(int) * dpsr::bins_ints(r));
   return b;
 }
 
@@ -154,7 +154,7 @@ int cuda_err(cudaError_t e) { return e == cudaErrorMemoryAllocation ? DPSR_ENOME
 // tuner off (the static choice of pick_cluster is used).
 // ---------------------------------------------------------------------------
 std::mutex g_tune_mu;
-int g_tuned[4][9] = {};  // [kind][log2 r]: chosen C, 0 = not tuned yet
+int g_tuned[4][9] = {};  // [kind][log2 r]: 1 + chosen C (0 = pencil path), 0 = not tuned yet
 
 int log2i(int r) {
   int l = 0;
@@ -167,11 +167,21 @@ bool tuning_enabled() {
   return !(e && e[0] == '0');
 }
 
+// DPSR_PLANE_PATH in the environment fixes the plane path of every kind:
+// 0 = pencil passes, 1/2/4/8 = cluster size (for tests and measurements).
+// Returns -1 when unset.
+int forced_path() {
+  const char* e = getenv("DPSR_PLANE_PATH");
+  if (!e || !*e) return -1;
+  const int c = atoi(e);
+  return (c == 0 || c == 1 || c == 2 || c == 4 || c == 8) ? c : -1;
+}
+
 // Launch plane kernel `kind` for every candidate C, time each with events
 // (second of two runs), record the fastest. Returns the last launch error.
 cudaError_t tune_plane(dpsr_plan p, int kind, const Solve& s, cudaStream_t st) {
   const int r = p->r;
-  const int cands[4] = {1, 2, 4, 8};
+  const int cands[5] = {0, 1, 2, 4, 8};  // 0: the z/y pencil passes
   float best = 1e30f;
   int bestC = p->C[kind];
   cudaEvent_t e0, e1;
@@ -208,7 +218,7 @@ cudaError_t tune_plane(dpsr_plan p, int kind, const Solve& s, cudaStream_t st) {
   cudaEventDestroy(e1);
   if (e == cudaSuccess) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tuned[kind][log2i(r)] = bestC;
+    g_tuned[kind][log2i(r)] = bestC + 1;
     p->C[kind] = bestC;
   }
   return e;
@@ -217,6 +227,11 @@ cudaError_t tune_plane(dpsr_plan p, int kind, const Solve& s, cudaStream_t st) {
 // Launch plane kernel `kind`, tuning it first if it has not been tuned for
 // this r (and the stream is not being captured).
 cudaError_t run_plane(dpsr_plan p, int kind, const Solve& s, cudaStream_t st) {
+  const int forced = forced_path();
+  if (forced >= 0) {
+    p->C[kind] = forced;
+    return dpsr::launch_plane(kind, p->r, forced, s, nullptr, 1, st);
+  }
   if (tuning_enabled() && p->r >= 64) {
     int tuned;
     {
@@ -224,7 +239,7 @@ cudaError_t run_plane(dpsr_plan p, int kind, const Solve& s, cudaStream_t st) {
       tuned = g_tuned[kind][log2i(p->r)];
     }
     if (tuned) {
-      p->C[kind] = tuned;
+      p->C[kind] = tuned - 1;
     } else {
       cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
       if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone && !p->profile)
@@ -302,7 +317,7 @@ int make_tensor_maps(Solve& s, int r) {
   const cuuint64_t strides[2] = {(cuuint64_t)kpitch(r) * 8, (cuuint64_t)r * kpitch(r) * 8};
   const cuuint32_t boxx[3] = {16, 1, (cuuint32_t)r}, boxy[3] = {16, (cuuint32_t)r, 1};
   const cuuint32_t es[3] = {1, 1, 1};
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < kNSpec; ++k) {
     for (int w = 0; w < 2; ++w) {
       CUresult rc = enc(w == 0 ? &s.tmx[k] : &s.tmy[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
                         (void*)s.spec[k], dims, strides, w == 0 ? boxx : boxy, es,
@@ -364,7 +379,7 @@ int dpsr_plan_create(int r, float sigma, dpsr_plan* out) {
   Solve& s = p->s;
   s.r = r;
   char* q = (char*)p->grid_ws;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < dpsr::kNSpec; ++k) {
     s.spec[k] = (float2*)q;
     q += align256(spec_bytes(r));
   }
@@ -410,7 +425,7 @@ int dpsr_plan_create(int r, float sigma, dpsr_plan* out) {
         cudaMemcpy(g1, hg, sizeof(float) * r, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(u2, hg + r, sizeof(float) * r, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(iu, hg + 2 * r, sizeof(float) * r, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(s.bins, 0, sizeof(int) * (3 * r + 1)) != cudaSuccess ||
+        cudaMemset(s.bins, 0, sizeof(int) * dpsr::bins_ints(r)) != cudaSuccess ||
         cudaMemset(s.status, 0, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(s.sc, 0, sizeof(dpsr::Scalars)) != cudaSuccess)
       rc = DPSR_ECUDA;
@@ -485,10 +500,12 @@ int dpsr_grid_splat(float* grid, int r, const float* q, const float* vals, int64
 const void* dpsr_internal_solve(dpsr_plan p) { return p ? (const void*)&p->s : nullptr; }
 int dpsr_internal_cluster(dpsr_plan p, int kind) {
   if (!p || kind < 0 || kind > 3) return 1;
+  const int forced = forced_path();
+  if (forced >= 0) return forced;
   if (tuning_enabled()) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     const int t = g_tuned[kind][log2i(p->r)];
-    if (t) return t;
+    if (t) return t - 1;
   }
   return p->C[kind];
 }
@@ -552,14 +569,14 @@ int dpsr_forward(dpsr_plan p, const float* points, const float* normals, int64_t
   run(DPSR_K_BIN, [&] { return dpsr::launch_bin(s, nullptr, 1, (int)N, st); });
   run(DPSR_K_PLANE_FWD, [&] { return run_plane(p, 0, s, st); });
   run(DPSR_K_XPASS_FWD, [&] { return dpsr::launch_xpass(false, r, s, nullptr, 1, st); });
-  run(DPSR_K_FINAL_FWD, [&] { return dpsr::launch_finalize(false, dpsr::xpass_blocks(r), s, nullptr, 1, st); });
   run(DPSR_K_PLANE_INV, [&] { return run_plane(p, 1, s, st); });
   if (e != cudaSuccess) {
     cudaGetLastError();
     p->have_fwd = false;
     return cuda_err(e);
   }
-  p->last_launches = 7;  // bin: 3 kernels, plane, xpass, finalize, inverse plane
+  // bin: 3 kernels, plane pass(es), x-pass (+ scalars), inverse plane pass(es)
+  p->last_launches = 4 + dpsr::plane_launches(p->C[0]) + dpsr::plane_launches(p->C[1]);
   cudaEventRecord(p->done_ev, st);
   p->s.N = s.N;
   p->s.points = points;
@@ -589,7 +606,6 @@ int dpsr_backward(dpsr_plan p, const float* dchi, float* dpoints, float* dnormal
     if (e == cudaSuccess) e = prof_mark(p, kind, false);
   };
   run(DPSR_K_PLANE_BFWD, [&] { return run_plane(p, 2, s, st); });
-  run(DPSR_K_FINAL_BWD, [&] { return dpsr::launch_finalize(true, r * p->C[2], s, nullptr, 1, st); });  // C[2] as tuned
   run(DPSR_K_XPASS_BWD, [&] { return dpsr::launch_xpass(true, r, s, nullptr, 1, st); });
   run(DPSR_K_PLANE_BINV, [&] { return run_plane(p, 3, s, st); });
   run(DPSR_K_COMBINE, [&] { return dpsr::launch_combine(s, nullptr, 1, s.N, st); });
@@ -597,7 +613,8 @@ int dpsr_backward(dpsr_plan p, const float* dchi, float* dpoints, float* dnormal
     cudaGetLastError();
     return cuda_err(e);
   }
-  p->last_launches = 5;
+  // plane pass(es) (+ scalars), x-pass, inverse plane pass(es), combine
+  p->last_launches = 2 + dpsr::plane_launches(p->C[2]) + dpsr::plane_launches(p->C[3]);
   cudaEventRecord(p->done_ev, st);
   return DPSR_OK;
 }

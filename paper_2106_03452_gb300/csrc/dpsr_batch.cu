@@ -64,7 +64,6 @@ cudaError_t launch_fwd(dpsr_batch b) {
     cudaError_t e = dpsr::launch_bin(dummy, c.dtab, n, c.nmax, st);
     if (e == cudaSuccess) e = dpsr::launch_plane(0, c.r, c.C[0], dummy, c.dtab, n, st);
     if (e == cudaSuccess) e = dpsr::launch_xpass(false, c.r, dummy, c.dtab, n, st);
-    if (e == cudaSuccess) e = dpsr::launch_finalize(false, dpsr::xpass_blocks(c.r), dummy, c.dtab, n, st);
     if (e == cudaSuccess) e = dpsr::launch_plane(1, c.r, c.C[1], dummy, c.dtab, n, st);
     if (e != cudaSuccess) return e;
   }
@@ -77,7 +76,6 @@ cudaError_t launch_bwd(dpsr_batch b) {
   for (auto& c : b->classes) {
     const int n = (int)c.members.size();
     cudaError_t e = dpsr::launch_plane(2, c.r, c.C[2], dummy, c.dtab, n, st);
-    if (e == cudaSuccess) e = dpsr::launch_finalize(true, c.r * c.C[2], dummy, c.dtab, n, st);
     if (e == cudaSuccess) e = dpsr::launch_xpass(true, c.r, dummy, c.dtab, n, st);
     if (e == cudaSuccess) e = dpsr::launch_plane(3, c.r, c.C[3], dummy, c.dtab, n, st);
     if (e == cudaSuccess) e = dpsr::launch_combine(dummy, c.dtab, n, c.nmax, st);
@@ -262,7 +260,12 @@ int dpsr_batch_sync(dpsr_batch b) {
 
 int dpsr_batch_launches(dpsr_batch b, int with_bwd) {
   if (!b) return -1;
-  return (int)b->classes.size() * (with_bwd ? 12 : 7);
+  int n = 0;
+  for (const auto& c : b->classes) {
+    n += 4 + dpsr::plane_launches(c.C[0]) + dpsr::plane_launches(c.C[1]);
+    if (with_bwd) n += 2 + dpsr::plane_launches(c.C[2]) + dpsr::plane_launches(c.C[3]);
+  }
+  return n;
 }
 
 }  // extern "C"

@@ -324,14 +324,21 @@ struct Scalars {
   float a_chi, b_chi;     // chi = a_chi * y + b_chi, y = unnormalised inverse FFT
   float g_a, g_s, g_w;    // backward: G^ = g_a * FFT(dchi) + g_s + g_w * W^
   float c_mu;             // backward: weight of the stored lookup gradient
+  // arrival counters of the last-block reductions: [0] forward x-pass,
+  // [1] backward plane pass (reset by the binning of every forward)
+  unsigned ticket[2];
 };
 
+// Spectral buffers of a solve: four channels of the plane/x passes plus one
+// for the inverse y passes of the pencil path.
+constexpr int kNSpec = 5;
+
 struct Solve {
-  // TMA descriptors of the four spectral buffers (dims kz = r/2+1, ky, x):
-  // tmx boxes are 16 kz x 1 ky x r x (x-pass tiles), tmy boxes 16 kz x r ky x
+  // TMA descriptors of the spectral buffers (dims kz = r/2+1, ky, x): tmx
+  // boxes are 16 kz x 1 ky x r x (x-pass tiles), tmy boxes 16 kz x r ky x
   // 1 x (plane tiles). 128-byte swizzle.
-  CUtensorMap tmx[4];
-  CUtensorMap tmy[4];
+  CUtensorMap tmx[kNSpec];
+  CUtensorMap tmy[kNSpec];
   int r;
   int N;
   // per call (caller-owned)
@@ -344,8 +351,8 @@ struct Solve {
   // plan workspace
   float4* sorted;   // 2 records per point: (x, y, z, nx), (ny, nz, orig, 0)
   int* cellx;       // N
-  int* bins;        // count[r], off[r + 1], cursor[r]
-  float2* spec[4];  // r * r * (r/2 + 2) complex each
+  int* bins;        // count[r*r], off[r*r + 1], cursor[r*r] (see nbins)
+  float2* spec[kNSpec];  // r * r * (r/2 + 2) complex each
   float4* gfwd;     // [2][N]: gradient of the lookup of y, per plane side
   float* slots;     // [2][N][6]: backward partials per plane side
   double* part;     // per-block partial sums
@@ -363,6 +370,16 @@ __host__ __device__ constexpr int kpitch(int r) { return r / 2 + 2; }
 
 // Trilinear stencil along one axis (Eq. A1, floor cell, periodic wrap):
 // x~ = c r (exact for r a power of two), i0 = floor(x~) mod r, t = x~ - floor(x~).
+// Point bins: a counting sort of the points by the x-cell of their stencil
+// origin and the block of ybin(r) y-rows its y-cell falls in, key
+// x * nybins(r) + y / ybin(r), so that the points of an x-plane, and of a
+// block of y-rows within it, are contiguous. S.bins holds count[nbins],
+// off[nbins + 1] (exclusive prefix sums) and cur[nbins] (scatter cursors).
+__host__ __device__ constexpr int ybin(int r) { return r < 16 ? r : 16; }
+__host__ __device__ constexpr int nybins(int r) { return r / ybin(r); }
+__host__ __device__ constexpr int nbins(int r) { return r * nybins(r); }
+__host__ __device__ constexpr size_t bins_ints(int r) { return 3 * (size_t)nbins(r) + 1; }
+
 struct Axis {
   int i0, i1;
   float t;

@@ -38,7 +38,7 @@ constexpr size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 // Layout of the static scratch, for r = kMaxR and N = kMaxN.
 constexpr size_t kSpec = al((size_t)kMaxR * kMaxR * (kMaxR / 2 + 2) * sizeof(float2));
 constexpr size_t kOffSpec = 0;
-constexpr size_t kOffTw = kOffSpec + 4 * kSpec;
+constexpr size_t kOffTw = kOffSpec + dpsr::kNSpec * kSpec;
 constexpr size_t kOffTab = kOffTw + al(sizeof(float2) * kMaxR);
 constexpr size_t kOffSc = kOffTab + 3 * al(sizeof(float) * kMaxR);
 constexpr size_t kOffStatus = kOffSc + al(sizeof(dpsr::Scalars));
@@ -46,7 +46,7 @@ constexpr size_t kParts = ((kMaxR / 2 + 1 + 15) / 16) * kMaxR > kMaxR * 8
                               ? ((kMaxR / 2 + 1 + 15) / 16) * kMaxR : kMaxR * 8;
 constexpr size_t kOffPart = kOffStatus + al(sizeof(unsigned));
 constexpr size_t kOffBins = kOffPart + al(sizeof(double) * 2 * kParts);
-constexpr size_t kOffSorted = kOffBins + al(sizeof(int) * (3 * kMaxR + 1));
+constexpr size_t kOffSorted = kOffBins + al(sizeof(int) * dpsr::bins_ints(kMaxR));
 constexpr size_t kOffCell = kOffSorted + al(sizeof(float4) * 2 * kMaxN);
 constexpr size_t kOffGfwd = kOffCell + al(sizeof(int) * kMaxN);
 constexpr size_t kScratchBytes = kOffGfwd + al(sizeof(float4) * 2 * kMaxN);  // ~9.2 MB
@@ -111,7 +111,7 @@ extern "C" DPSR_API int dpsr_forward_static(int r, float sigma, const float* poi
   s.points = points;
   s.normals = normals;
   s.chi = chi_out;
-  for (int k = 0; k < 4; ++k) s.spec[k] = (float2*)(base + kOffSpec + k * kSpec);
+  for (int k = 0; k < dpsr::kNSpec; ++k) s.spec[k] = (float2*)(base + kOffSpec + k * kSpec);
   float2* tw = (float2*)(base + kOffTw);
   float* g1 = (float*)(base + kOffTab);
   float* u2 = (float*)(base + kOffTab + al(sizeof(float) * kMaxR));
@@ -134,12 +134,11 @@ extern "C" DPSR_API int dpsr_forward_static(int r, float sigma, const float* poi
   if (e == cudaSuccess) e = cudaMemcpyAsync(u2, htab + r, sizeof(float) * r, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(iu, htab + 2 * r, sizeof(float) * r, cudaMemcpyHostToDevice, st);
   // the bin counters and the status word must start at zero
-  if (e == cudaSuccess) e = cudaMemsetAsync(s.bins, 0, sizeof(int) * (3 * r + 1), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.bins, 0, sizeof(int) * dpsr::bins_ints(r), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s.status, 0, sizeof(unsigned), st);
   if (e == cudaSuccess) e = dpsr::launch_bin(s, nullptr, 1, (int)N, st);
   if (e == cudaSuccess) e = dpsr::launch_plane(0, r, 1, s, nullptr, 1, st);
   if (e == cudaSuccess) e = dpsr::launch_xpass(false, r, s, nullptr, 1, st);
-  if (e == cudaSuccess) e = dpsr::launch_finalize(false, dpsr::xpass_blocks(r), s, nullptr, 1, st);
   if (e == cudaSuccess) e = dpsr::launch_plane(1, r, 1, s, nullptr, 1, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {

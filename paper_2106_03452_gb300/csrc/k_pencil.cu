@@ -1,0 +1,798 @@
+// Pencil kernels: the (y, z) transforms of a plane split into a z pass over
+// blocks of YB y-rows and a y pass over chunks of 16 kz columns, with the
+// intermediate spectra in the spectral buffers (L2-resident up to r = 128).
+// Each CTA is independent (no cluster, no DSMEM), so thousands of small CTAs
+// keep every SM busy; the plane kernels of k_plane.cu instead keep a plane in
+// the shared memory of a cluster. The autotuner picks between the two per
+// kernel kind (cluster size 0 = this path).
+//
+//   forward   k_zfwd  splat (Eq. A2) of v_y, v_z, v_x, w into YB rows, R2C
+//                     along z (v_z times i u_z)  -> spec[0..3] (y, kz)
+//             k_yfwd  FFT along y of the four channels, D = FFT(i u_z v_z)
+//                     + i u_y FFT(v_y), C, W~        -> spec[0..2] (ky, kz)
+//   inverse   k_yinv  IFFT along y of chi~ (spec[3]) -> spec[4] (y, kz)
+//             k_zinv  C2R along z, chi = a y + b (Eq. 4), lookup gradient
+//   backward  k_zbfwd sums of Eq. 4's adjoint, R2C along z of dchi -> spec[3]
+//             k_yfwd  FFT along y of spec[3] (one channel)
+//   adjoint   k_yinv  IFFT along y of Q2, -i u_y Q1, -i u_z Q1 -> spec[2,3,4]
+//             k_zinv3 C2R along z of the three fields, adjoint of the splat
+//
+// Half spectra along z are stored "packed" between the passes: slot 0 holds
+// the DC and Nyquist terms of a real row as one complex number.
+#include "dpsr_dev.cuh"
+#include "finalize.cuh"
+#include "launch.h"
+#include "tma.cuh"
+
+namespace dpsr {
+
+template <int L>
+struct Pen {
+  static constexpr int T = Shape<L>::T, R1 = Shape<L>::R1;
+  static constexpr int H = L / 2, KP = H + 2;
+  static constexpr int YB = L < 16 ? L : 16;  // y-rows per z-pass CTA
+  static constexpr int NYB = L / YB;
+  static constexpr int NCOL = H < 16 ? H : 16;  // kz columns per y-pass CTA
+  static constexpr int NKC = H / NCOL;          // y-pass CTAs per plane
+  static constexpr int BOX = L * 16;            // float2 per TMA box [ky][16 kz]
+  static constexpr int ZNT = 256;               // threads of the z-pass kernels
+  static constexpr int ZG = ZNT / T;
+  static_assert(YB == ybin(L) && NYB == nybins(L), "one point bin per z-pass CTA");
+};
+
+// 1D weight of the trilinear stencil (Eq. A1): corner d of the cell, offset t.
+__device__ __forceinline__ float tri_w(int d, float t) { return d ? t : 1.f - t; }
+
+// Column 0 of a box holds P = X0 + i Xn, the transforms of the DC and Nyquist
+// columns packed together. Split them in place (column 0 <- X0) and hand Xn
+// to nyq(ky, value). Run by the T threads of one group.
+template <int L, class Nyq>
+__device__ __forceinline__ void split_dc_nyq(float2* b, int t, Nyq nyq) {
+  constexpr int R1 = Shape<L>::R1, T = Shape<L>::T;
+  float2 x0[R1], xn[R1];
+#pragma unroll
+  for (int j = 0; j < R1; ++j) {
+    const int ky = t + T * j;
+    unpack_dc_nyq(b[bx(ky, 0)], b[bx((L - ky) & (L - 1), 0)], x0[j], xn[j]);
+  }
+  group_sync<T>();
+#pragma unroll
+  for (int j = 0; j < R1; ++j) {
+    b[bx(t + T * j, 0)] = x0[j];
+    nyq(t + T * j, xn[j]);
+  }
+}
+
+// Sorted-point index range of point bin (x-cell xc, y-block yb): the points
+// whose stencil origin lies in rows [yb * YB, yb * YB + YB) of x-cell xc.
+__device__ __forceinline__ int2 bin_range(const Solve& S, int xc, int yb) {
+  const int* off = S.bins + nbins(S.r);
+  const int k = xc * nybins(S.r) + yb;
+  return make_int2(off[k], off[k + 1]);
+}
+
+// R2C of two real rows a = p[0..L), b = p[L..2L) in place: afterwards the
+// storage, seen as L float2, holds A's packed half spectrum in [0, H) and B's
+// in [H, L). The storage is also the FFT exchange area.
+template <int L, class Tw>
+__device__ __forceinline__ void r2c_pair_ip(int t, const Tw& tw, float* p) {
+  constexpr int R1 = Shape<L>::R1, T = Shape<L>::T, H = L / 2;
+  float2 v[R1];
+#pragma unroll
+  for (int j = 0; j < R1; ++j) v[j] = make_float2(p[t + T * j], p[L + t + T * j]);
+  group_sync<T>();
+  float2* x = reinterpret_cast<float2*>(p);
+  fft_r<L, -1>(v, t, [x](int i) -> float2& { return x[i]; }, tw);
+#pragma unroll
+  for (int j = 0; j < R1; ++j) x[t + T * j] = v[j];
+  group_sync<T>();
+  float2 A[R1 / 2], B[R1 / 2];
+#pragma unroll
+  for (int j = 0; j < R1 / 2; ++j) {
+    const int k = t + T * j;
+    if (k == 0) {
+      const float2 z0 = x[0], zn = x[H];
+      A[j] = make_float2(z0.x, zn.x);
+      B[j] = make_float2(z0.y, zn.y);
+    } else {
+      const float2 zk = x[k], zm = cconj(x[L - k]);
+      A[j] = cscale(cadd(zk, zm), 0.5f);
+      const float2 d = csub(zk, zm);  // B = -i d / 2
+      B[j] = make_float2(0.5f * d.y, -0.5f * d.x);
+    }
+  }
+  group_sync<T>();
+#pragma unroll
+  for (int j = 0; j < R1 / 2; ++j) {
+    x[t + T * j] = A[j];
+    x[H + t + T * j] = B[j];
+  }
+}
+
+// C2R of two packed half spectra in place (A in [0, H), B in [H, L) of the
+// L float2 at x); afterwards x[z] = (a[z], b[z]), unnormalised.
+template <int L, class Tw>
+__device__ __forceinline__ void c2r_pair_ip2(int t, const Tw& tw, float2* x) {
+  constexpr int R1 = Shape<L>::R1, T = Shape<L>::T, H = L / 2;
+  float2 v[R1];
+#pragma unroll
+  for (int j = 0; j < R1; ++j) {
+    const int k = t + T * j;
+    if (k == 0 || k == H) {
+      const float2 a = x[0], b = x[H];
+      v[j] = (k == 0) ? make_float2(a.x, b.x) : make_float2(a.y, b.y);
+    } else if (k < H) {
+      const float2 a = x[k], b = x[H + k];
+      v[j] = make_float2(a.x - b.y, a.y + b.x);
+    } else {
+      const float2 a = x[L - k], b = x[H + L - k];
+      v[j] = make_float2(a.x + b.y, b.x - a.y);
+    }
+  }
+  group_sync<T>();
+  fft_r<L, +1>(v, t, [x](int i) -> float2& { return x[i]; }, tw);
+#pragma unroll
+  for (int j = 0; j < R1; ++j) x[t + T * j] = v[j];
+}
+
+// ===========================================================================
+// Forward z pass: splat of the four channels into YB rows of plane X, R2C.
+// ===========================================================================
+template <int L>
+constexpr size_t zfwd_smem() {
+  using P = Pen<L>;
+  return sizeof(float) * (4 * P::YB * L + L) + sizeof(float2) * L;
+}
+
+template <int L>
+__global__ void __launch_bounds__(Pen<L>::ZNT) k_zfwd(const __grid_constant__ Solve s0,
+                                                      const Solve* __restrict__ tab) {
+  using P = Pen<L>;
+  constexpr int YB = P::YB, H = P::H;
+  const Solve& S = tab ? tab[blockIdx.z] : s0;
+  const int X = blockIdx.x / P::NYB, y0 = (blockIdx.x % P::NYB) * YB;
+  const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
+  extern __shared__ float4 smem4[];
+  float* rows = reinterpret_cast<float*>(smem4);  // [4][YB][L]: v_y, v_z, v_x, w
+  float2* twt = reinterpret_cast<float2*>(rows + 4 * YB * L);
+  float* iu = reinterpret_cast<float*>(twt + L);
+  pdl_trigger();
+  for (int i = tid; i < L; i += P::ZNT) {
+    twt[i] = S.tw[i];
+    iu[i] = S.iu[i];
+  }
+  for (int i = tid; i < YB * L; i += P::ZNT) smem4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  pdl_wait();
+  __syncthreads();
+  // Rasterization (Eq. A2): points of x-cells X (dx = 0) and X - 1 (dx = 1)
+  // whose stencil rows i0 or i1 fall in [y0, y0 + YB), i.e. i0 in
+  // [y0 - 1, y0 + YB - 1] (mod L): the CTA's own bin, and the points of the
+  // previous y-block's bin in its last row.
+  const int yb = y0 / YB, ylast = (y0 - 1) & (L - 1);
+  for (int side = 0; side < 2; ++side) {
+    const int xc = (X - side) & (L - 1);
+    for (int part = 0; part < 2; ++part) {
+      if (part == 1 && YB == L) continue;  // one bin holds the whole plane
+      const int2 rg = bin_range(S, xc, part == 0 ? yb : (yb + P::NYB - 1) % P::NYB);
+      for (int i = rg.x + tid; i < rg.y; i += P::ZNT) {
+        const float4 a = S.sorted[2 * i];
+        const Axis ay = axis_of(a.y, L);
+        if (part == 1 && ay.i0 != ylast) continue;
+        const float4 b = S.sorted[2 * i + 1];
+        const Axis ax = axis_of(a.x, L), az = axis_of(a.z, L);
+        const float wx = tri_w(side, ax.t);
+        const float val[4] = {b.x, b.y, a.w, 1.f};
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+          const int ly = (dy ? ay.i1 : ay.i0) - y0;
+          if ((unsigned)ly >= (unsigned)YB) continue;
+          const float f = wx * tri_w(dy, ay.t);
+          const float f0 = f * (1.f - az.t), f1 = f * az.t;
+#pragma unroll
+          for (int ch = 0; ch < 4; ++ch) {
+            float* row = rows + (ch * YB + ly) * L;
+            atomicAdd(row + az.i0, f0 * val[ch]);
+            atomicAdd(row + az.i1, f1 * val[ch]);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  TwTab<L> twr{twt, t};
+  constexpr int NP = 4 * YB / 2;
+  for (int p0 = 0; p0 < NP; p0 += P::ZG) {
+    const int pi = p0 + g;
+    if (pi < NP) r2c_pair_ip<L>(t, twr, rows + 2 * pi * L);  // whole groups
+  }
+  __syncthreads();
+  // Packed rows out; the v_z channel takes i u_z (zero at DC and Nyquist).
+  constexpr int Q = H / 2;  // float4 per row
+  for (int i = tid; i < 4 * YB * Q; i += P::ZNT) {
+    const int ch = i / (YB * Q), rem = i % (YB * Q), ly = rem / Q, q = rem % Q;
+    float4 v = smem4[(ch * YB + ly) * Q + q];
+    if (ch == 1) {
+      const int s = 2 * q;
+      const float2 a = s == 0 ? czero() : cmul_iu(make_float2(v.x, v.y), iu[s]);
+      const float2 b = cmul_iu(make_float2(v.z, v.w), iu[s + 1]);
+      v = make_float4(a.x, a.y, b.x, b.y);
+    }
+    reinterpret_cast<float4*>(S.spec[ch] + ((size_t)X * L + y0 + ly) * P::KP)[q] = v;
+  }
+}
+
+// ===========================================================================
+// Forward y pass over 16 kz columns of plane X. NCH = 4: the forward
+// channels (D, C, W~ out); NCH = 1: the backward transform of spec[3].
+// ===========================================================================
+template <int L, int NCH>
+struct YfGeo {
+  static constexpr int T = Shape<L>::T;
+  static constexpr int NG = NCH == 4 ? 32 : 16;  // groups: column (+ channel pair)
+  static constexpr int NT = NG * T >= 32 ? NG * T : 32;
+};
+
+template <int L, int NCH>
+constexpr size_t yfwd_smem() {
+  return 1024 + sizeof(float2) * ((size_t)NCH * Pen<L>::BOX + L) + sizeof(float) * L;
+}
+
+template <int L, int NCH>
+__global__ void __launch_bounds__(YfGeo<L, NCH>::NT) k_yfwd(const __grid_constant__ Solve s0,
+                                                            const Solve* __restrict__ tab) {
+  using P = Pen<L>;
+  using Y = YfGeo<L, NCH>;
+  constexpr int H = P::H;
+  const Solve& S = tab ? tab[blockIdx.z] : s0;
+  const int X = blockIdx.x / P::NKC, kz0 = (blockIdx.x % P::NKC) * P::NCOL;
+  const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+  float2* box = reinterpret_cast<float2*>(smem_raw + pad);  // NCH boxes
+  float2* twt = box + NCH * P::BOX;
+  float* iu = reinterpret_cast<float*>(twt + L);
+  __shared__ uint64_t bar;
+  pdl_trigger();
+  for (int i = tid; i < L; i += Y::NT) {
+    twt[i] = S.tw[i];
+    iu[i] = S.iu[i];
+  }
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  pdl_wait();
+  __syncthreads();
+  if (tid == 0) {
+    mbar_expect_tx(&bar, NCH * P::BOX * (uint32_t)sizeof(float2));
+    for (int k = 0; k < NCH; ++k) tma_load_3d(box + k * P::BOX, &S.tmy[NCH == 4 ? k : 3], kz0, 0, X, &bar);
+  }
+  const bool landed = __syncthreads_and(mbar_wait(&bar, 0));
+  if (!landed) {
+    if (tid == 0) atomicOr(S.status, kStTimeout);
+    mbar_wait(&bar, 0);  // a last bounded chance for copies in flight
+    return;
+  }
+  TwTab<L> twr{twt, t};
+  const int col = g % 16;
+  if (g < Y::NG && col < P::NCOL) {  // whole groups
+    auto cref = [&](int k) {
+      float2* b = box + k * P::BOX;
+      return [b, col](int e) -> float2& { return b[bx(e, col)]; };
+    };
+    float2 a[P::R1];
+    if (NCH == 1 || g < 16) {
+      auto c0 = cref(0);
+#pragma unroll
+      for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
+      fft_r<L, -1>(a, t, c0, twr);
+      if constexpr (NCH == 4) {
+        // D = FFT(i u_z v_z) + i u_y FFT(v_y)
+        auto c1 = cref(1);
+        float2 b[P::R1];
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) b[j] = c1(t + P::T * j);
+        fft_r<L, -1>(b, t, c1, twr);
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) a[j] = cadd(b[j], cmul_iu(a[j], iu[t + P::T * j]));
+      }
+#pragma unroll
+      for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = a[j];
+    } else {
+      // C = FFT(v_x), W~ = FFT(w)
+#pragma unroll
+      for (int k = 2; k < 4; ++k) {
+        auto ck = cref(k);
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) a[j] = ck(t + P::T * j);
+        fft_r<L, -1>(a, t, ck, twr);
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) ck(t + P::T * j) = a[j];
+      }
+    }
+  }
+  __syncthreads();
+  // outputs: NCH = 4: D (box 0) -> spec[0], C (box 2) -> spec[1], W~ (box 3)
+  // -> spec[2]; NCH = 1: box 0 -> spec[3]
+  constexpr int NOUT = NCH == 4 ? 3 : 1;
+  if (kz0 == 0 && g < NOUT) {
+    // column 0 holds X0 + i Xn of the DC and Nyquist columns: split them
+    const int bi = g == 0 ? 0 : g + 1, buf = NCH == 4 ? g : 3;
+    float2* b = box + bi * P::BOX;
+    float2* dst = S.spec[buf];
+    split_dc_nyq<L>(b, t, [&](int ky, float2 w) {
+      if (H < 16) b[bx(ky, H)] = w;
+      else dst[((size_t)X * L + ky) * P::KP + H] = w;
+    });
+  }
+  fence_async_smem();
+  __syncthreads();
+  if (tid == 0) {
+    if constexpr (NCH == 4) {
+      tma_store_3d(&S.tmy[0], kz0, 0, X, box);
+      tma_store_3d(&S.tmy[1], kz0, 0, X, box + 2 * P::BOX);
+      tma_store_3d(&S.tmy[2], kz0, 0, X, box + 3 * P::BOX);
+    } else {
+      tma_store_3d(&S.tmy[3], kz0, 0, X, box);
+    }
+    tma_store_commit();
+    tma_store_wait_read();
+  }
+}
+
+// ===========================================================================
+// Inverse y pass over 16 kz columns of plane X. NCH = 1: chi~ (spec[3]) ->
+// spec[4]. NCH = 3: the adjoint fields V_bar_x = IFFT_y(Q2) -> spec[2],
+// V_bar_y = IFFT_y(-i u_y Q1) -> spec[3], V_bar_z = -i u_z IFFT_y(Q1) ->
+// spec[4], with Q1 in spec[0] and Q2 in spec[1].
+// ===========================================================================
+template <int L, int NCH>
+constexpr size_t yinv_smem() {
+  return 1024 + sizeof(float2) * ((size_t)NCH * Pen<L>::BOX + L) + sizeof(float) * L;
+}
+
+template <int L, int NCH>
+__global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32)
+    k_yinv(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
+  using P = Pen<L>;
+  constexpr int H = P::H, NT = 16 * P::T >= 32 ? 16 * P::T : 32;
+  const Solve& S = tab ? tab[blockIdx.z] : s0;
+  const int X = blockIdx.x / P::NKC, kz0 = (blockIdx.x % P::NKC) * P::NCOL;
+  const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+  float2* box = reinterpret_cast<float2*>(smem_raw + pad);
+  float2* twt = box + NCH * P::BOX;
+  float* iu = reinterpret_cast<float*>(twt + L);
+  __shared__ uint64_t bar;
+  pdl_trigger();
+  for (int i = tid; i < L; i += NT) {
+    twt[i] = S.tw[i];
+    iu[i] = S.iu[i];
+  }
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  pdl_wait();
+  __syncthreads();
+  // NCH = 1: box 0 <- spec[3]; NCH = 3: box 0 <- Q2 (spec[1]), box 1 <- Q1
+  constexpr int NIN = NCH == 1 ? 1 : 2;
+  if (tid == 0) {
+    mbar_expect_tx(&bar, NIN * P::BOX * (uint32_t)sizeof(float2));
+    if constexpr (NCH == 1) {
+      tma_load_3d(box, &S.tmy[3], kz0, 0, X, &bar);
+    } else {
+      tma_load_3d(box, &S.tmy[1], kz0, 0, X, &bar);
+      tma_load_3d(box + P::BOX, &S.tmy[0], kz0, 0, X, &bar);
+    }
+  }
+  const bool landed = __syncthreads_and(mbar_wait(&bar, 0));
+  if (!landed) {
+    if (tid == 0) atomicOr(S.status, kStTimeout);
+    mbar_wait(&bar, 0);
+    return;
+  }
+  TwTab<L> twr{twt, t};
+  if (kz0 == 0 && g < NIN) {
+    // column 0 becomes X0 + i Xn (Xn: the Nyquist column); the same lanes
+    // read these elements again below
+    float2* b = box + g * P::BOX;
+    const float2* nq = S.spec[NCH == 1 ? 3 : (g == 0 ? 1 : 0)] + (size_t)X * L * P::KP + H;
+    for (int j = 0; j < P::R1; ++j) {
+      const int ky = t + P::T * j;
+      const float2 n = H >= 16 ? nq[(size_t)ky * P::KP] : b[bx(ky, H)];
+      const float2 x0 = b[bx(ky, 0)];
+      b[bx(ky, 0)] = make_float2(x0.x - n.y, x0.y + n.x);
+    }
+  }
+  __syncthreads();
+  if (g < P::NCOL) {
+    const int s = kz0 + g;
+    auto cref = [&](int k) {
+      float2* b = box + k * P::BOX;
+      return [b, g](int e) -> float2& { return b[bx(e, g)]; };
+    };
+    float2 v[P::R1];
+    auto c0 = cref(0);
+#pragma unroll
+    for (int j = 0; j < P::R1; ++j) v[j] = c0(t + P::T * j);
+    fft_r<L, +1>(v, t, c0, twr);
+#pragma unroll
+    for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = v[j];
+    if constexpr (NCH == 3) {
+      auto c1 = cref(1);
+      auto c2 = cref(2);
+#pragma unroll
+      for (int j = 0; j < P::R1; ++j) {
+        v[j] = c1(t + P::T * j);
+        c2(t + P::T * j) = v[j];
+        v[j] = cmul_iu(v[j], -iu[t + P::T * j]);
+      }
+      fft_r<L, +1>(v, t, c1, twr);
+#pragma unroll
+      for (int j = 0; j < P::R1; ++j) c1(t + P::T * j) = v[j];
+      group_sync<P::T>();
+#pragma unroll
+      for (int j = 0; j < P::R1; ++j) v[j] = c2(t + P::T * j);
+      fft_r<L, +1>(v, t, c2, twr);
+      const float ez = s == 0 ? 0.f : -iu[s];
+#pragma unroll
+      for (int j = 0; j < P::R1; ++j) c2(t + P::T * j) = cmul_iu(v[j], ez);
+    }
+  }
+  fence_async_smem();
+  __syncthreads();
+  if (tid == 0) {
+    // out of place, so that the pass can run again on the same inputs
+    if constexpr (NCH == 1) {
+      tma_store_3d(&S.tmy[4], kz0, 0, X, box);
+    } else {
+      tma_store_3d(&S.tmy[2], kz0, 0, X, box);
+      tma_store_3d(&S.tmy[3], kz0, 0, X, box + P::BOX);
+      tma_store_3d(&S.tmy[4], kz0, 0, X, box + 2 * P::BOX);
+    }
+    tma_store_commit();
+    tma_store_wait_read();
+  }
+}
+
+// ===========================================================================
+// Inverse z passes over YB rows of plane X (+ 2 halo rows for the stencil's
+// row i0 + 1): load the packed rows, C2R in place.
+// ===========================================================================
+// Rows y0 .. y0 + YB + 1 (mod L) of `src` into rows[(ch, ly)] (H float2 each).
+template <int L>
+__device__ __forceinline__ void load_rows(const float2* src, int X, int y0, float4* dst, int nthreads) {
+  using P = Pen<L>;
+  constexpr int Q = P::H / 2, NR = P::YB + 2;
+  for (int i = threadIdx.x; i < NR * Q; i += nthreads) {
+    const int ly = i / Q, q = i % Q;
+    const int y = (y0 + ly) & (L - 1);
+    dst[ly * Q + q] = reinterpret_cast<const float4*>(src + ((size_t)X * L + y) * P::KP)[q];
+  }
+}
+
+template <int L, int NCH>
+constexpr size_t zinv_smem() {
+  return sizeof(float2) * ((size_t)NCH * (Pen<L>::YB + 2) * (L / 2) + L);
+}
+
+// Forward: chi = a_chi y + b_chi for the CTA's rows, and the gradient of the
+// trilinear lookup of y at the points whose stencil row i0 is one of them
+// (this plane's share, delta_x fixed by the plane).
+template <int L>
+__global__ void __launch_bounds__(Pen<L>::ZNT) k_zinv(const __grid_constant__ Solve s0,
+                                                      const Solve* __restrict__ tab) {
+  using P = Pen<L>;
+  constexpr int YB = P::YB, H = P::H, NR = YB + 2;
+  const Solve& S = tab ? tab[blockIdx.z] : s0;
+  const int X = blockIdx.x / P::NYB, y0 = (blockIdx.x % P::NYB) * YB;
+  const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
+  extern __shared__ float4 smem4[];
+  float2* rows = reinterpret_cast<float2*>(smem4);  // NR rows of H float2
+  float2* twt = rows + NR * H;
+  pdl_trigger();
+  for (int i = tid; i < L; i += P::ZNT) twt[i] = S.tw[i];
+  pdl_wait();
+  load_rows<L>(S.spec[4], X, y0, smem4, P::ZNT);
+  const float a_chi = S.sc->a_chi, b_chi = S.sc->b_chi;
+  __syncthreads();
+  TwTab<L> twr{twt, t};
+  for (int p0 = 0; p0 < NR / 2; p0 += P::ZG) {
+    const int pi = p0 + g;
+    if (pi < NR / 2) c2r_pair_ip2<L>(t, twr, rows + pi * L);
+  }
+  __syncthreads();
+  // value of row ly (0 .. NR-1), column z: pair ly / 2, component ly & 1
+  auto yv = [&](int ly, int z) {
+    const float2 f = rows[(ly >> 1) * L + z];
+    return (ly & 1) ? f.y : f.x;
+  };
+  float* chi = S.chi;
+  for (int i = tid; i < YB * L / 4; i += P::ZNT) {
+    const int ly = i / (L / 4), z4 = (i % (L / 4)) * 4;
+    const float4 o = make_float4(fmaf(a_chi, yv(ly, z4), b_chi), fmaf(a_chi, yv(ly, z4 + 1), b_chi),
+                                 fmaf(a_chi, yv(ly, z4 + 2), b_chi), fmaf(a_chi, yv(ly, z4 + 3), b_chi));
+    reinterpret_cast<float4*>(chi + ((size_t)X * L + y0 + ly) * L)[z4 / 4] = o;
+  }
+  for (int side = 0; side < 2; ++side) {
+    const int xc = (X - side) & (L - 1);
+    const int2 rg = bin_range(S, xc, y0 / YB);
+    for (int i = rg.x + tid; i < rg.y; i += P::ZNT) {
+      const float4 a = S.sorted[2 * i];
+      const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);
+      const int ly0 = ay.i0 - y0;  // in [0, YB); row i1 is ly0 + 1 (a halo row at most)
+      const float fx = tri_w(side, ax.t), dfx = side ? (float)L : -(float)L;
+      float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const float fy = tri_w(dy, ay.t), dfy = dy ? (float)L : -(float)L;
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz) {
+          const int z = dz ? az.i1 : az.i0;
+          const float fz = tri_w(dz, az.t), dfz = dz ? (float)L : -(float)L;
+          const float val = yv(ly0 + dy, z);
+          gx += dfx * fy * fz * val;
+          gy += fx * dfy * fz * val;
+          gz += fx * fy * dfz * val;
+        }
+      }
+      S.gfwd[(size_t)side * S.N + i] = make_float4(gx, gy, gz, 0.f);
+    }
+  }
+}
+
+// Backward: C2R of V_bar_x (spec[2]), V_bar_y (spec[3]), V_bar_z (spec[4]);
+// at each point whose stencil row i0 is one of the CTA's rows, the gather of
+// the three fields (dnormals share) and the weight derivatives times n . V
+// (dpoints share) of this plane side.
+template <int L>
+__global__ void __launch_bounds__(Pen<L>::ZNT) k_zinv3(const __grid_constant__ Solve s0,
+                                                       const Solve* __restrict__ tab) {
+  using P = Pen<L>;
+  constexpr int YB = P::YB, H = P::H, NR = YB + 2;
+  const Solve& S = tab ? tab[blockIdx.z] : s0;
+  const int X = blockIdx.x / P::NYB, y0 = (blockIdx.x % P::NYB) * YB;
+  const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
+  extern __shared__ float4 smem4[];
+  float2* rows = reinterpret_cast<float2*>(smem4);  // [3][NR][H]: x, y, z
+  float2* twt = rows + 3 * NR * H;
+  pdl_trigger();
+  for (int i = tid; i < L; i += P::ZNT) twt[i] = S.tw[i];
+  pdl_wait();
+  load_rows<L>(S.spec[2], X, y0, smem4, P::ZNT);
+  load_rows<L>(S.spec[3], X, y0, smem4 + NR * H / 2, P::ZNT);
+  load_rows<L>(S.spec[4], X, y0, smem4 + 2 * NR * H / 2, P::ZNT);
+  __syncthreads();
+  TwTab<L> twr{twt, t};
+  constexpr int NP = 3 * NR / 2;
+  for (int p0 = 0; p0 < NP; p0 += P::ZG) {
+    const int pi = p0 + g;
+    if (pi < NP) c2r_pair_ip2<L>(t, twr, rows + pi * L);
+  }
+  __syncthreads();
+  auto vv = [&](int ch, int ly, int z) {
+    const float2 f = rows[(ch * NR / 2 + (ly >> 1)) * L + z];
+    return (ly & 1) ? f.y : f.x;
+  };
+  for (int side = 0; side < 2; ++side) {
+    const int xc = (X - side) & (L - 1);
+    const int2 rg = bin_range(S, xc, y0 / YB);
+    for (int i = rg.x + tid; i < rg.y; i += P::ZNT) {
+      const float4 a = S.sorted[2 * i], b = S.sorted[2 * i + 1];
+      const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);
+      const int ly0 = ay.i0 - y0;
+      const float n0 = a.w, n1 = b.x, n2 = b.y;
+      const float fx = tri_w(side, ax.t), dfx = side ? (float)L : -(float)L;
+      float nb0 = 0.f, nb1 = 0.f, nb2 = 0.f, cb0 = 0.f, cb1 = 0.f, cb2 = 0.f;
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const float fy = tri_w(dy, ay.t), dfy = dy ? (float)L : -(float)L;
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz) {
+          const int z = dz ? az.i1 : az.i0;
+          const float fz = tri_w(dz, az.t), dfz = dz ? (float)L : -(float)L;
+          const float vx = vv(0, ly0 + dy, z), vy = vv(1, ly0 + dy, z), vz = vv(2, ly0 + dy, z);
+          const float w = fx * fy * fz;
+          nb0 += w * vx;
+          nb1 += w * vy;
+          nb2 += w * vz;
+          const float sdot = n0 * vx + n1 * vy + n2 * vz;
+          cb0 += dfx * fy * fz * sdot;
+          cb1 += fx * dfy * fz * sdot;
+          cb2 += fx * fy * dfz * sdot;
+        }
+      }
+      float* o = S.slots + ((size_t)side * S.N + i) * 6;
+      o[0] = nb0;
+      o[1] = nb1;
+      o[2] = nb2;
+      o[3] = cb0;
+      o[4] = cb1;
+      o[5] = cb2;
+    }
+  }
+}
+
+// ===========================================================================
+// Backward z pass: the sums S = sum dchi and sum dchi * chi of the CTA's
+// rows (block partials, reduced by the last CTA into the adjoint scalars),
+// and the R2C along z of dchi -> spec[3].
+// ===========================================================================
+template <int L>
+constexpr size_t zbfwd_smem() {
+  return sizeof(float) * Pen<L>::YB * L + sizeof(float2) * L;
+}
+
+template <int L>
+__global__ void __launch_bounds__(Pen<L>::ZNT) k_zbfwd(const __grid_constant__ Solve s0,
+                                                       const Solve* __restrict__ tab) {
+  using P = Pen<L>;
+  constexpr int YB = P::YB, H = P::H;
+  const Solve& S = tab ? tab[blockIdx.z] : s0;
+  const int X = blockIdx.x / P::NYB, y0 = (blockIdx.x % P::NYB) * YB;
+  const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
+  extern __shared__ float4 smem4[];
+  float* rows = reinterpret_cast<float*>(smem4);  // [YB][L]
+  float2* twt = reinterpret_cast<float2*>(rows + YB * L);
+  __shared__ double red[2][P::ZNT / 32];
+  pdl_trigger();
+  for (int i = tid; i < L; i += P::ZNT) twt[i] = S.tw[i];
+  pdl_wait();
+  const size_t row0 = ((size_t)X * L + y0) * L;
+  const float4* g4 = reinterpret_cast<const float4*>(S.dchi + row0);
+  const float4* c4 = reinterpret_cast<const float4*>(S.chi + row0);
+  float accS = 0.f, accD = 0.f;
+  for (int i = tid; i < YB * L / 4; i += P::ZNT) {
+    const float4 a = g4[i], b = c4[i];
+    smem4[i] = a;
+    accS += (a.x + a.y) + (a.z + a.w);
+    accD += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+  }
+  {
+    double dS = accS, dD = accD;
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+      dS += __shfl_xor_sync(0xffffffffu, dS, m);
+      dD += __shfl_xor_sync(0xffffffffu, dD, m);
+    }
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = dS;
+      red[1][tid >> 5] = dD;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < P::ZNT / 32; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    const size_t bid = (size_t)blockIdx.x;
+    S.part[2 * bid] = a;
+    S.part[2 * bid + 1] = b;
+  }
+  TwTab<L> twr{twt, t};
+  for (int p0 = 0; p0 < YB / 2; p0 += P::ZG) {
+    const int pi = p0 + g;
+    if (pi < YB / 2) r2c_pair_ip<L>(t, twr, rows + 2 * pi * L);
+  }
+  __syncthreads();
+  constexpr int Q = H / 2;
+  for (int i = tid; i < YB * Q; i += P::ZNT) {
+    const int ly = i / Q, q = i % Q;
+    reinterpret_cast<float4*>(S.spec[3] + ((size_t)X * L + y0 + ly) * P::KP)[q] = smem4[ly * Q + q];
+  }
+  last_block_finalize(S, 1, (int)gridDim.x, true);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers: kind 0 forward (z, y), 1 inverse (y, z), 2 backward (z, y),
+// 3 adjoint (y, z).
+// ---------------------------------------------------------------------------
+template <class K>
+static cudaError_t set_smem(K fn, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int L>
+static cudaError_t launch_pencil_t(int kind, const Solve& s, const Solve* tab, int count,
+                                   cudaStream_t st) {
+  using P = Pen<L>;
+  const dim3 gz(L * P::NYB, 1, count), gy(L * P::NKC, 1, count);
+  static bool attr_set[4] = {false, false, false, false};
+  cudaError_t e = cudaSuccess;
+  switch (kind) {
+    case 0: {
+      constexpr size_t a = zfwd_smem<L>(), b = yfwd_smem<L, 4>();
+      if (!attr_set[0]) {
+        e = set_smem(k_zfwd<L>, a);
+        if (e == cudaSuccess) e = set_smem(k_yfwd<L, 4>, b);
+        if (e != cudaSuccess) return e;
+        attr_set[0] = true;
+      }
+      e = launch_k(k_zfwd<L>, gz, dim3(P::ZNT), a, st, 0, s, tab);
+      if (e == cudaSuccess) e = launch_k(k_yfwd<L, 4>, gy, dim3(YfGeo<L, 4>::NT), b, st, 0, s, tab);
+      return e;
+    }
+    case 1: {
+      constexpr size_t a = yinv_smem<L, 1>(), b = zinv_smem<L, 1>();
+      constexpr int nt = 16 * P::T >= 32 ? 16 * P::T : 32;
+      if (!attr_set[1]) {
+        e = set_smem(k_yinv<L, 1>, a);
+        if (e == cudaSuccess) e = set_smem(k_zinv<L>, b);
+        if (e != cudaSuccess) return e;
+        attr_set[1] = true;
+      }
+      e = launch_k(k_yinv<L, 1>, gy, dim3(nt), a, st, 0, s, tab);
+      if (e == cudaSuccess) e = launch_k(k_zinv<L>, gz, dim3(P::ZNT), b, st, 0, s, tab);
+      return e;
+    }
+    case 2: {
+      constexpr size_t a = zbfwd_smem<L>(), b = yfwd_smem<L, 1>();
+      if (!attr_set[2]) {
+        e = set_smem(k_zbfwd<L>, a);
+        if (e == cudaSuccess) e = set_smem(k_yfwd<L, 1>, b);
+        if (e != cudaSuccess) return e;
+        attr_set[2] = true;
+      }
+      e = launch_k(k_zbfwd<L>, gz, dim3(P::ZNT), a, st, 0, s, tab);
+      if (e == cudaSuccess) e = launch_k(k_yfwd<L, 1>, gy, dim3(YfGeo<L, 1>::NT), b, st, 0, s, tab);
+      return e;
+    }
+    default: {
+      constexpr size_t a = yinv_smem<L, 3>(), b = zinv_smem<L, 3>();
+      constexpr int nt = 16 * P::T >= 32 ? 16 * P::T : 32;
+      if (!attr_set[3]) {
+        e = set_smem(k_yinv<L, 3>, a);
+        if (e == cudaSuccess) e = set_smem(k_zinv3<L>, b);
+        if (e != cudaSuccess) return e;
+        attr_set[3] = true;
+      }
+      e = launch_k(k_yinv<L, 3>, gy, dim3(nt), a, st, 0, s, tab);
+      if (e == cudaSuccess) e = launch_k(k_zinv3<L>, gz, dim3(P::ZNT), b, st, 0, s, tab);
+      return e;
+    }
+  }
+}
+
+cudaError_t launch_pencil(int kind, int r, const Solve& s, const Solve* tab, int count,
+                          cudaStream_t st) {
+  switch (r) {
+    case 8: return launch_pencil_t<8>(kind, s, tab, count, st);
+    case 16: return launch_pencil_t<16>(kind, s, tab, count, st);
+    case 32: return launch_pencil_t<32>(kind, s, tab, count, st);
+    case 64: return launch_pencil_t<64>(kind, s, tab, count, st);
+    case 128: return launch_pencil_t<128>(kind, s, tab, count, st);
+    case 256: return launch_pencil_t<256>(kind, s, tab, count, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Largest dynamic shared memory of the two kernels of a kind (for the tuner).
+size_t pencil_smem_bytes(int kind, int r) {
+  auto pick = [&](auto Lc) -> size_t {
+    constexpr int L = decltype(Lc)::value;
+    size_t a = 0, b = 0;
+    switch (kind) {
+      case 0: a = zfwd_smem<L>(); b = yfwd_smem<L, 4>(); break;
+      case 1: a = yinv_smem<L, 1>(); b = zinv_smem<L, 1>(); break;
+      case 2: a = zbfwd_smem<L>(); b = yfwd_smem<L, 1>(); break;
+      default: a = yinv_smem<L, 3>(); b = zinv_smem<L, 3>(); break;
+    }
+    return a > b ? a : b;
+  };
+  switch (r) {
+    case 8: return pick(std::integral_constant<int, 8>{});
+    case 16: return pick(std::integral_constant<int, 16>{});
+    case 32: return pick(std::integral_constant<int, 32>{});
+    case 64: return pick(std::integral_constant<int, 64>{});
+    case 128: return pick(std::integral_constant<int, 128>{});
+    case 256: return pick(std::integral_constant<int, 256>{});
+    default: return 0;
+  }
+}
+
+}  // namespace dpsr

@@ -17,6 +17,7 @@
 //                           fields V_bar_a, then the adjoint of the splat
 //                           (gather and weight derivatives) at the points.
 #include "dpsr_dev.cuh"
+#include "finalize.cuh"
 #include "launch.h"
 #include "tma.cuh"
 
@@ -69,12 +70,13 @@ __device__ __forceinline__ int sw(int row, int col) {
 struct PlanePoints {
   int b0, n0, b1, n1;
   __device__ PlanePoints(const Solve& S, int X) {
-    const int* off = S.bins + S.r;
+    const int* off = S.bins + nbins(S.r);
     const int Xm = (X - 1) & (S.r - 1);
-    b0 = off[X];
-    n0 = off[X + 1] - b0;
-    b1 = off[Xm];
-    n1 = off[Xm + 1] - b1;
+    const int ny = nybins(S.r);
+    b0 = off[X * ny];
+    n0 = off[(X + 1) * ny] - b0;
+    b1 = off[Xm * ny];
+    n1 = off[(Xm + 1) * ny] - b1;
   }
   __device__ int total() const { return n0 + n1; }
   __device__ int index(int i, int& dx) const {
@@ -682,6 +684,8 @@ __global__ void __launch_bounds__(kNT, plane_minb<L, C>(2))
       S.part[2 * blockIdx.x + 1] = b;
     }
   }
+  // the last CTA of the solve turns the sums into the adjoint scalars
+  last_block_finalize(S, 1, (int)gridDim.x, true);
   cl.sync();
 }
 
@@ -988,6 +992,7 @@ static cudaError_t launch_plane_L(int kind, int C, const Solve& s, const Solve* 
 
 cudaError_t launch_plane(int kind, int r, int C, const Solve& s, const Solve* tab, int count,
                          cudaStream_t st) {
+  if (C == 0) return launch_pencil(kind, r, s, tab, count, st);
   switch (r) {
     case 8: return launch_plane_L<8>(kind, C, s, tab, count, st);
     case 16: return launch_plane_L<16>(kind, C, s, tab, count, st);
@@ -1017,6 +1022,7 @@ static size_t kind_smem(int kind) {
 }
 
 size_t plane_smem_bytes(int kind, int r, int C) {
+  if (C == 0) return pencil_smem_bytes(kind, r);
   auto pick = [&](auto Lc) -> size_t {
     constexpr int L = decltype(Lc)::value;
     switch (C) {

@@ -12,63 +12,98 @@ __device__ __forceinline__ bool coord_ok(float c, int r) {
   return isfinite(c) && fabsf(c * (float)r) < 1073741824.f;  // |c r| < 2^30
 }
 
-// count[i0x]++ per point; validates the inputs (non-finite or huge values
-// raise kStBadInput and are replaced by 0 so that indexing stays in range).
+// count[key]++ per point (see nbins for the key); validates the inputs
+// (non-finite or huge values raise kStBadInput and are replaced by 0 so that
+// indexing stays in range). Per-block histogram in shared memory, then one
+// global add per touched bin.
+__device__ __forceinline__ int bin_key(float x, float y, int r) {
+  return axis_of(x, r).i0 * nybins(r) + axis_of(y, r).i0 / ybin(r);
+}
+
 __global__ void __launch_bounds__(256) k_bin_count(const __grid_constant__ Solve s0,
                                                    const Solve* __restrict__ tab) {
+  static_assert(nbins(256) == 4096, "histogram size");
+  __shared__ int h[4096];
   pdl_trigger();
   const Solve& S = tab ? tab[blockIdx.z] : s0;
-  __shared__ int h[256];
-  const int r = S.r;
-  for (int i = threadIdx.x; i < r; i += blockDim.x) h[i] = 0;
+  const int r = S.r, nb = nbins(r);
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = 0;
   pdl_wait();
   __syncthreads();
   bool bad = false;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < S.N; p += gridDim.x * blockDim.x) {
-    float x = S.points[3 * p];
-    const float y = S.points[3 * p + 1], z = S.points[3 * p + 2];
+    float x = S.points[3 * p], y = S.points[3 * p + 1];
+    const float z = S.points[3 * p + 2];
     const float nx = S.normals[3 * p], ny = S.normals[3 * p + 1], nz = S.normals[3 * p + 2];
     if (!(coord_ok(x, r) && coord_ok(y, r) && coord_ok(z, r) && isfinite(nx) && isfinite(ny) &&
           isfinite(nz))) {
       bad = true;
       if (!coord_ok(x, r)) x = 0.f;
+      if (!coord_ok(y, r)) y = 0.f;
     }
-    const int ix = axis_of(x, r).i0;
-    S.cellx[p] = ix;
-    atomicAdd(&h[ix], 1);
+    const int key = bin_key(x, y, r);
+    S.cellx[p] = key;
+    atomicAdd(&h[key], 1);
   }
   if (bad) atomicOr(S.status, kStBadInput);
   __syncthreads();
-  for (int i = threadIdx.x; i < r; i += blockDim.x)
+  for (int i = threadIdx.x; i < nb; i += blockDim.x)
     if (h[i]) atomicAdd(&S.bins[i], h[i]);
 }
 
-// Exclusive scan of the r counts into off[0..r] and the scatter cursors.
-__global__ void __launch_bounds__(256) k_bin_scan(const __grid_constant__ Solve s0,
-                                                  const Solve* __restrict__ tab) {
+// Exclusive scan of the nbins counts into off[0..nbins] and the scatter
+// cursors: one block of 1024 threads per solve, four consecutive bins per
+// thread (coalesced 16-byte accesses).
+__global__ void __launch_bounds__(1024) k_bin_scan(const __grid_constant__ Solve s0,
+                                                   const Solve* __restrict__ tab) {
   pdl_trigger();
   pdl_wait();
   const Solve& S = tab ? tab[blockIdx.x] : s0;
-  __shared__ int v[256];
-  const int r = S.r, i = threadIdx.x;
+  __shared__ int wsum[32];
+  const int r = S.r, nb = nbins(r), i = threadIdx.x;
   int* count = S.bins;
-  int* off = S.bins + r;
-  int* cur = S.bins + 2 * r + 1;
-  v[i] = i < r ? count[i] : 0;
+  int* off = S.bins + nb;
+  int* cur = off + nb + 1;
+  int c[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (4 * i + k < nb) c[k] = count[4 * i + k];
+  const int sum = c[0] + c[1] + c[2] + c[3];
+  // block-wide exclusive scan of the per-thread sums
+  const int lane = i & 31, w = i >> 5;
+  int incl = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += v;
+  }
+  if (lane == 31) wsum[w] = incl;
   __syncthreads();
-  for (int d = 1; d < 256; d <<= 1) {  // Hillis-Steele inclusive scan
-    const int add = i >= d ? v[i - d] : 0;
-    __syncthreads();
-    v[i] += add;
-    __syncthreads();
+  if (w == 0) {
+    int v = wsum[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d) v += u;
+    }
+    wsum[lane] = v;  // inclusive over warps
   }
-  if (i < r) {
-    const int ex = v[i] - count[i];
-    off[i] = ex;
-    cur[i] = ex;
-    count[i] = 0;  // ready for the next call
+  __syncthreads();
+  int run = incl - sum + (w > 0 ? wsum[w - 1] : 0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (4 * i + k < nb) {
+      off[4 * i + k] = run;
+      cur[4 * i + k] = run;
+      count[4 * i + k] = 0;  // ready for the next call
+      run += c[k];
+    }
   }
-  if (i == r - 1) off[r] = v[i];
+  if (i == 1023) off[nb] = wsum[31];
+  if (i == 0) {  // arrival counters of this solve's last-block reductions
+    S.sc->ticket[0] = 0;
+    S.sc->ticket[1] = 0;
+  }
 }
 
 __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Solve s0,
@@ -77,7 +112,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Sol
   pdl_wait();
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   const int r = S.r;
-  int* cur = S.bins + 2 * r + 1;
+  int* cur = S.bins + 2 * nbins(r) + 1;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < S.N; p += gridDim.x * blockDim.x) {
     float x = S.points[3 * p], y = S.points[3 * p + 1], z = S.points[3 * p + 2];
     float nx = S.normals[3 * p], ny = S.normals[3 * p + 1], nz = S.normals[3 * p + 2];
@@ -87,7 +122,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Sol
     if (!isfinite(nx)) nx = 0.f;
     if (!isfinite(ny)) ny = 0.f;
     if (!isfinite(nz)) nz = 0.f;
-    const int pos = atomicAdd(&cur[S.cellx[p]], 1);
+    const int pos = atomicAdd(&cur[S.cellx[p]], 1);  // key of k_bin_count
     S.sorted[2 * pos] = make_float4(x, y, z, nx);
     S.sorted[2 * pos + 1] = make_float4(ny, nz, __int_as_float(p), 0.f);
   }
@@ -96,7 +131,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Sol
 cudaError_t launch_bin(const Solve& s, const Solve* tab, int count, int nmax, cudaStream_t st) {
   const int blocks = min(max((nmax + 255) / 256, 1), 1184);
   cudaError_t e = launch_k(k_bin_count, dim3(blocks, 1, count), dim3(256), 0, st, 0, s, tab);
-  if (e == cudaSuccess) e = launch_k(k_bin_scan, dim3(count), dim3(256), 0, st, 0, s, tab);
+  if (e == cudaSuccess) e = launch_k(k_bin_scan, dim3(count), dim3(1024), 0, st, 0, s, tab);
   if (e == cudaSuccess) e = launch_k(k_bin_scatter, dim3(blocks, 1, count), dim3(256), 0, st, 0, s, tab);
   return e;
 }

@@ -12,6 +12,7 @@
 // Three FFTs of length r per column in each direction.
 #include "dpsr_dev.cuh"
 #include "launch.h"
+#include "finalize.cuh"
 #include "tma.cuh"
 
 namespace dpsr {
@@ -161,6 +162,7 @@ __global__ void __launch_bounds__(XGeo<L>::NT, 2)
       S.part[2 * bid + 1] = ss;
       tma_store_wait_read();
     }
+    last_block_finalize(S, 0, (int)(gridDim.x * gridDim.y), false);
   } else {
     // FFT_x of (g_a FFT_zy(dchi) + g_w W~ + g_s delta_{x=0}): the three terms
     // of the adjoint spectrum combined before the transform (it is linear).
@@ -238,86 +240,6 @@ int xpass_blocks(int r) {
     case 256: return XGeo<256>::NCHUNK * 256;
     default: return 0;
   }
-}
-
-// ---------------------------------------------------------------------------
-// Scalar finalisation (one block): fixed-order FP64 reduction of the block
-// partials, then the scalars of Eq. 4 (forward) or of its adjoint (backward).
-// ---------------------------------------------------------------------------
-__device__ void reduce_parts(const double* part, int n, double& a, double& b) {
-  __shared__ double ra[256], rb[256];
-  double x = 0, y = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    x += part[2 * i];
-    y += part[2 * i + 1];
-  }
-  ra[threadIdx.x] = x;
-  rb[threadIdx.x] = y;
-  __syncthreads();
-  for (int m = blockDim.x / 2; m > 0; m >>= 1) {
-    if ((int)threadIdx.x < m) {
-      ra[threadIdx.x] += ra[threadIdx.x + m];
-      rb[threadIdx.x] += rb[threadIdx.x + m];
-    }
-    __syncthreads();
-  }
-  a = ra[0];
-  b = rb[0];
-}
-
-__global__ void __launch_bounds__(256) k_finalize(const __grid_constant__ Solve s0,
-                                                  const Solve* __restrict__ tab, int nparts,
-                                                  int bwd) {
-  pdl_trigger();
-  pdl_wait();
-  const Solve& S = tab ? tab[blockIdx.x] : s0;
-  double a, b;
-  reduce_parts(S.part, nparts, a, b);
-  if (threadIdx.x != 0) return;
-  Scalars* sc = S.sc;
-  const double n = (double)S.r * S.r * S.r;
-  if (!bwd) {
-    // mu = <W, chi'> / N, chi'(0) = sum_k chi~ / n, s = chi'(0) - mu (Eq. 4)
-    const double mu = a / ((double)S.N * n);
-    const double chi0 = b / n;
-    const double s = chi0 - mu;
-    sc->acc_mu = a;
-    sc->acc_s0 = b;
-    sc->mu = mu;
-    sc->s = s;
-    const bool bad = !isfinite(s) || !(fabs(s) > 1e-7 * (fabs(chi0) + fabs(mu)) + 1e-37);
-    if (bad) {
-      atomicOr(S.status, kStDegenerate);
-      sc->alpha = 0;
-      sc->a_chi = 0.f;
-      sc->b_chi = 0.f;
-    } else {
-      const double alpha = (double)kM / fabs(s);
-      sc->alpha = alpha;
-      sc->a_chi = (float)(alpha / n);
-      sc->b_chi = (float)(-alpha * mu);
-    }
-  } else {
-    // a = sum dchi, b = sum dchi * chi = alpha * sum dchi (chi' - mu)
-    const double alpha = sc->alpha, s = sc->s;
-    const double Ssum = a;
-    const double D = alpha > 0 ? b / alpha : 0.0;
-    const double s_bar = -(double)kM * (s > 0 ? 1.0 : -1.0) * D / (s * s);
-    const double mu_bar = -alpha * Ssum - s_bar;
-    sc->S = Ssum;
-    sc->D = D;
-    sc->s_bar = s_bar;
-    sc->mu_bar = mu_bar;
-    sc->g_a = (float)(alpha / n);
-    sc->g_s = (float)(s_bar / n);
-    sc->g_w = (float)(mu_bar / ((double)S.N * n));
-    sc->c_mu = (float)(mu_bar / ((double)S.N * n));
-  }
-}
-
-cudaError_t launch_finalize(bool bwd, int nparts, const Solve& s, const Solve* tab, int count,
-                            cudaStream_t st) {
-  return launch_k(k_finalize, dim3(count), dim3(256), 0, st, 0, s, tab, nparts, bwd ? 1 : 0);
 }
 
 }  // namespace dpsr

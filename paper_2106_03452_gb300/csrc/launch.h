@@ -49,11 +49,17 @@ cudaError_t launch_k(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, c
 cudaError_t launch_plane(int kind, int r, int C, const Solve& s, const Solve* tab, int count,
                          cudaStream_t st);
 size_t plane_smem_bytes(int kind, int r, int C);
+// The same four kinds as z and y passes of independent CTAs (two launches
+// each; "cluster size 0" to the tuner).
+cudaError_t launch_pencil(int kind, int r, const Solve& s, const Solve* tab, int count,
+                          cudaStream_t st);
+size_t pencil_smem_bytes(int kind, int r);
+// Kernel launches of one plane kind with path C (0: two pencil passes).
+inline int plane_launches(int C) { return C == 0 ? 2 : 1; }
 cudaError_t launch_xpass(bool bwd, int r, const Solve& s, const Solve* tab, int count,
                          cudaStream_t st);
 int xpass_blocks(int r);
-cudaError_t launch_finalize(bool bwd, int nparts, const Solve& s, const Solve* tab, int count,
-                            cudaStream_t st);
+
 // TMA descriptors of the four spectral buffers of `s` (s.spec must be set).
 // Returns 0 on success.
 int make_tensor_maps(Solve& s, int r);

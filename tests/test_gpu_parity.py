@@ -21,19 +21,46 @@ def _cuda():
     build.build()
 
 
-def _check(oracle, r, sigma, pts, nrm, dchi, tol_chi=TOL_CHI, tol_grad=TOL_GRAD):
+# Plane paths: "pencil" = independent z and y passes, "cluster" = one
+# thread-block cluster per x-plane (the smallest cluster size valid for r),
+# "tuned" = whatever the autotuner picks per kernel kind.
+PATHS = ["pencil", "cluster"]
+
+
+def _set_path(monkeypatch, path, r):
+    if path == "pencil":
+        monkeypatch.setenv("DPSR_PLANE_PATH", "0")
+    elif path == "cluster":
+        monkeypatch.setenv("DPSR_PLANE_PATH", "4" if r == 256 else "1")
+    else:
+        monkeypatch.delenv("DPSR_PLANE_PATH", raising=False)
+
+
+_ORACLE_CACHE = {}
+
+
+def _check(oracle, r, sigma, pts, nrm, dchi, tol_chi=TOL_CHI, tol_grad=TOL_GRAD, key=None):
     from gpu_util import gpu_fwd_bwd, relmax
     g = gpu_fwd_bwd(r, sigma, pts, nrm, dchi)
     assert g["status"] == 0
-    chi, chip, mu, s = oracle.forward(r, sigma, pts.astype(np.float64), nrm.astype(np.float64), full=True)
+    ref = _ORACLE_CACHE.get(key) if key else None
+    if ref is None:
+        fwd = oracle.forward(r, sigma, pts.astype(np.float64), nrm.astype(np.float64), full=True)
+        bwd = None
+        if dchi is not None:
+            bwd = oracle.backward(r, sigma, pts.astype(np.float64), nrm.astype(np.float64),
+                                  dchi.astype(np.float64), mean_term=True)
+        ref = (fwd, bwd)
+        if key:
+            _ORACLE_CACHE[key] = ref
+    chi, chip, mu, s = ref[0]
     e = relmax(g["chi"], chi)
     assert e <= tol_chi, f"chi parity {e:.3e}"
     gmu, gs, galpha = g["scalars"]
     assert abs(gmu - mu) <= 1e-5 * np.max(np.abs(chip)) and abs(gs - s) <= 1e-5 * abs(s) + 1e-6 * np.max(np.abs(chip))
     if dchi is not None:
         assert g["bstatus"] == 0
-        dp, dn, dm = oracle.backward(r, sigma, pts.astype(np.float64), nrm.astype(np.float64),
-                                     dchi.astype(np.float64), mean_term=True)
+        dp, dn, dm = ref[1]
         en = relmax(g["dnormals"], dn)
         assert en <= tol_grad, f"dnormals parity {en:.3e}"
         # dpoints is the sum of the part through the mean of Eq. 4 (dm) and the
@@ -48,9 +75,11 @@ def _check(oracle, r, sigma, pts, nrm, dchi, tol_chi=TOL_CHI, tol_grad=TOL_GRAD)
     return g
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("r", [8, 16, 32, 64])
 @pytest.mark.parametrize("N,sigma", [(1, 2.0), (7, 0.0), (333, 2.0), (2049, 1.5)])
-def test_random_clouds(oracle, r, N, sigma):
+def test_random_clouds(oracle, monkeypatch, path, r, N, sigma):
+    _set_path(monkeypatch, path, r)
     rng = synth.Rng(1000 * r + N)
     pts = (rng.uniform(N, 3) * 1.4 - 0.2).astype(np.float32)   # wraps around the unit cube
     nrm = rng.normal(N, 3).astype(np.float32)
@@ -58,8 +87,10 @@ def test_random_clouds(oracle, r, N, sigma):
     _check(oracle, r, sigma, pts, nrm, dchi)
 
 
-def test_points_on_vertices_and_faces(oracle):
+@pytest.mark.parametrize("path", PATHS)
+def test_points_on_vertices_and_faces(oracle, monkeypatch, path):
     r = 32
+    _set_path(monkeypatch, path, r)
     rng = synth.Rng(4)
     N = 500
     pts = rng.uniform(N, 3)
@@ -79,15 +110,19 @@ def test_sphere_r32(oracle):
     _check(oracle, w["r"], w["sigma"], w["points"], w["normals"], w["dchi"])
 
 
-def test_ellipsoids_r128(oracle):
+@pytest.mark.parametrize("path", PATHS + ["tuned"])
+def test_ellipsoids_r128(oracle, monkeypatch, path):
     w = synth.workload_ellipsoids_r128()
-    _check(oracle, w["r"], w["sigma"], w["points"], w["normals"], w["dchi"])
+    _set_path(monkeypatch, path, w["r"])
+    _check(oracle, w["r"], w["sigma"], w["points"], w["normals"], w["dchi"], key="ellipsoids_r128")
 
 
-def test_torus_r256(oracle):
+@pytest.mark.parametrize("path", PATHS + ["tuned"])
+def test_torus_r256(oracle, monkeypatch, path):
     w = synth.workload_torus_r256()
+    _set_path(monkeypatch, path, w["r"])
     dchi = synth.upstream_grad(synth.Rng(77), 256)
-    _check(oracle, w["r"], w["sigma"], w["points"], w["normals"], dchi)
+    _check(oracle, w["r"], w["sigma"], w["points"], w["normals"], dchi, key="torus_r256")
 
 
 def test_degenerate_and_errors():
