@@ -329,9 +329,18 @@ struct Scalars {
   unsigned ticket[2];
 };
 
-// Spectral buffers of a solve: four channels of the plane/x passes plus one
-// for the inverse y passes of the pencil path.
-constexpr int kNSpec = 5;
+// Spectral buffers of a solve (Solve::spec) and what they hold between the
+// passes (complex [x][ky][kz], kz pitch r/2 + 2):
+//   kSpD   forward D; backward FFT_zy(dchi), then Q1 = IFFT_x(F)
+//   kSpChi forward chi~ after the x-pass; backward Q2 = IFFT_x(-i u_x F)
+//   kSpC   forward C; adjoint (pencil) V_bar_x
+//   kSpW   W~, kept from the forward for every backward
+//   kSpYa  pencil: y-domain chi~; adjoint V_bar_y
+//   kSpYb  pencil: adjoint V_bar_z
+// The pencil forward holds v_y, i u_z v_z, v_x, w (y-domain) in buffers
+// 0..3 before its y pass.
+constexpr int kSpD = 0, kSpChi = 1, kSpC = 2, kSpW = 3, kSpYa = 4, kSpYb = 5;
+constexpr int kNSpec = 6;
 
 struct Solve {
   // TMA descriptors of the spectral buffers (dims kz = r/2+1, ky, x): tmx
@@ -366,7 +375,10 @@ struct Solve {
 
 enum : unsigned { kStBadInput = 1u, kStDegenerate = 2u, kStTimeout = 4u };
 
-__host__ __device__ constexpr int kpitch(int r) { return r / 2 + 2; }
+// Row pitch (complex values) of the spectral buffers along kz: the r/2 + 1
+// valid slots padded so that, from r = 32 on, every row starts on a 128-byte
+// line (the 16-slot tiles of the plane and x passes are then one line each).
+__host__ __device__ constexpr int kpitch(int r) { return r / 2 < 16 ? r / 2 + 2 : r / 2 + 16; }
 
 // Trilinear stencil along one axis (Eq. A1, floor cell, periodic wrap):
 // x~ = c r (exact for r a power of two), i0 = floor(x~) mod r, t = x~ - floor(x~).

@@ -36,7 +36,7 @@ constexpr int kMaxN = 65536;
 constexpr size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Layout of the static scratch, for r = kMaxR and N = kMaxN.
-constexpr size_t kSpec = al((size_t)kMaxR * kMaxR * (kMaxR / 2 + 2) * sizeof(float2));
+constexpr size_t kSpec = al((size_t)kMaxR * kMaxR * dpsr::kpitch(kMaxR) * sizeof(float2));
 constexpr size_t kOffSpec = 0;
 constexpr size_t kOffTw = kOffSpec + dpsr::kNSpec * kSpec;
 constexpr size_t kOffTab = kOffTw + al(sizeof(float2) * kMaxR);

@@ -7,15 +7,17 @@
 // kernel kind (cluster size 0 = this path).
 //
 //   forward   k_zfwd  splat (Eq. A2) of v_y, v_z, v_x, w into YB rows, R2C
-//                     along z (v_z times i u_z)  -> spec[0..3] (y, kz)
-//             k_yfwd  FFT along y of the four channels, D = FFT(i u_z v_z)
-//                     + i u_y FFT(v_y), C, W~        -> spec[0..2] (ky, kz)
-//   inverse   k_yinv  IFFT along y of chi~ (spec[3]) -> spec[4] (y, kz)
-//             k_zinv  C2R along z, chi = a y + b (Eq. 4), lookup gradient
-//   backward  k_zbfwd sums of Eq. 4's adjoint, R2C along z of dchi -> spec[3]
-//             k_yfwd  FFT along y of spec[3] (one channel)
-//   adjoint   k_yinv  IFFT along y of Q2, -i u_y Q1, -i u_z Q1 -> spec[2,3,4]
-//             k_zinv3 C2R along z of the three fields, adjoint of the splat
+//                     along z (v_z times i u_z)   -> buffers 0..3 (y, kz)
+//             k_yfwd  FFT along y: D = FFT(i u_z v_z) + i u_y FFT(v_y) -> kSpD,
+//                     C -> kSpC, W~ -> kSpW         (ky, kz)
+//   inverse   k_yinv  IFFT along y of chi~ (kSpChi) -> kSpYa (y, kz)
+//             k_zinv<1> C2R along z, chi = a y + b (Eq. 4), lookup gradient
+//   backward  k_zbfwd sums of Eq. 4's adjoint, R2C along z of dchi -> kSpD
+//             k_yfwd  FFT along y of kSpD in place
+//   adjoint   k_yinv  IFFT along y of Q2, -i u_y Q1, -i u_z Q1 -> kSpC, kSpYa,
+//                     kSpYb
+//             k_zinv<3> C2R along z of the three fields, adjoint of the splat
+// The buffer roles are listed with kNSpec.
 //
 // Half spectra along z are stored "packed" between the passes: slot 0 holds
 // the DC and Nyquist terms of a real row as one complex number.
@@ -29,7 +31,7 @@ namespace dpsr {
 template <int L>
 struct Pen {
   static constexpr int T = Shape<L>::T, R1 = Shape<L>::R1;
-  static constexpr int H = L / 2, KP = H + 2;
+  static constexpr int H = L / 2, KP = kpitch(L);
   static constexpr int YB = L < 16 ? L : 16;  // y-rows per z-pass CTA
   static constexpr int NYB = L / YB;
   static constexpr int NCOL = H < 16 ? H : 16;  // kz columns per y-pass CTA
@@ -49,18 +51,17 @@ __device__ __forceinline__ float tri_w(int d, float t) { return d ? t : 1.f - t;
 template <int L, class Nyq>
 __device__ __forceinline__ void split_dc_nyq(float2* b, int t, Nyq nyq) {
   constexpr int R1 = Shape<L>::R1, T = Shape<L>::T;
-  float2 x0[R1], xn[R1];
+  float2 x0[R1];
 #pragma unroll
   for (int j = 0; j < R1; ++j) {
     const int ky = t + T * j;
-    unpack_dc_nyq(b[bx(ky, 0)], b[bx((L - ky) & (L - 1), 0)], x0[j], xn[j]);
+    float2 xn;
+    unpack_dc_nyq(b[bx(ky, 0)], b[bx((L - ky) & (L - 1), 0)], x0[j], xn);
+    nyq(ky, xn);  // never column 0
   }
   group_sync<T>();
 #pragma unroll
-  for (int j = 0; j < R1; ++j) {
-    b[bx(t + T * j, 0)] = x0[j];
-    nyq(t + T * j, xn[j]);
-  }
+  for (int j = 0; j < R1; ++j) b[bx(t + T * j, 0)] = x0[j];
 }
 
 // Sorted-point index range of point bin (x-cell xc, y-block yb): the points
@@ -109,30 +110,47 @@ __device__ __forceinline__ void r2c_pair_ip(int t, const Tw& tw, float* p) {
   }
 }
 
-// C2R of two packed half spectra in place (A in [0, H), B in [H, L) of the
-// L float2 at x); afterwards x[z] = (a[z], b[z]), unnormalised.
-template <int L, class Tw>
-__device__ __forceinline__ void c2r_pair_ip2(int t, const Tw& tw, float2* x) {
+// C2R of two packed half spectra A, B in place, through an accessor: x(i),
+// i < L, addresses the pair's storage (A's slots for i < H, B's for
+// i >= H); it is also the FFT exchange area and receives (a[z], b[z]) at
+// x(z), unnormalised.
+template <int L, class Tw, class Acc>
+__device__ __forceinline__ void c2r_acc(int t, const Tw& tw, Acc x) {
   constexpr int R1 = Shape<L>::R1, T = Shape<L>::T, H = L / 2;
   float2 v[R1];
 #pragma unroll
   for (int j = 0; j < R1; ++j) {
     const int k = t + T * j;
     if (k == 0 || k == H) {
-      const float2 a = x[0], b = x[H];
+      const float2 a = x(0), b = x(H);
       v[j] = (k == 0) ? make_float2(a.x, b.x) : make_float2(a.y, b.y);
     } else if (k < H) {
-      const float2 a = x[k], b = x[H + k];
+      const float2 a = x(k), b = x(H + k);
       v[j] = make_float2(a.x - b.y, a.y + b.x);
     } else {
-      const float2 a = x[L - k], b = x[H + L - k];
+      const float2 a = x(L - k), b = x(H + L - k);
       v[j] = make_float2(a.x + b.y, b.x - a.y);
     }
   }
   group_sync<T>();
-  fft_r<L, +1>(v, t, [x](int i) -> float2& { return x[i]; }, tw);
+  fft_r<L, +1>(v, t, x, tw);
 #pragma unroll
-  for (int j = 0; j < R1; ++j) x[t + T * j] = v[j];
+  for (int j = 0; j < R1; ++j) x(t + T * j) = v[j];
+}
+
+// Persistent CTAs: the number of CTAs that fit the GPU at once (at most
+// `tiles`), for a kernel that loops over tiles with a stride of gridDim.x.
+template <class K>
+static int persistent_ctas(K fn, int nthreads, size_t smem, int tiles, int count) {
+  int dev = 0, sms = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nthreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return tiles;
+  }
+  const int n = (sms * (occ > 0 ? occ : 1)) / (count > 0 ? count : 1);
+  return n < 1 ? 1 : (n < tiles ? n : tiles);
 }
 
 // ===========================================================================
@@ -145,7 +163,7 @@ constexpr size_t zfwd_smem() {
 }
 
 template <int L>
-__global__ void __launch_bounds__(Pen<L>::ZNT) k_zfwd(const __grid_constant__ Solve s0,
+__global__ void __launch_bounds__(Pen<L>::ZNT, 3) k_zfwd(const __grid_constant__ Solve s0,
                                                       const Solve* __restrict__ tab) {
   using P = Pen<L>;
   constexpr int YB = P::YB, H = P::H;
@@ -222,38 +240,39 @@ __global__ void __launch_bounds__(Pen<L>::ZNT) k_zfwd(const __grid_constant__ So
 }
 
 // ===========================================================================
-// Forward y pass over 16 kz columns of plane X. NCH = 4: the forward
-// channels (D, C, W~ out); NCH = 1: the backward transform of spec[3].
+// Forward y pass over 16 kz columns of plane X, one output per CTA
+// (blockIdx.y): 0: D = FFT(i u_z v_z) + i u_y FFT(v_y) from buffers 0 and 1
+// into kSpD; 1: C = FFT(v_x) in place in kSpC; 2: W~ = FFT(w) in place in
+// kSpW. BWD: FFT of the z-transformed dchi in place in kSpD.
 // ===========================================================================
-template <int L, int NCH>
-struct YfGeo {
-  static constexpr int T = Shape<L>::T;
-  static constexpr int NG = NCH == 4 ? 32 : 16;  // groups: column (+ channel pair)
-  static constexpr int NT = NG * T >= 32 ? NG * T : 32;
-};
-
-template <int L, int NCH>
-constexpr size_t yfwd_smem() {
-  return 1024 + sizeof(float2) * ((size_t)NCH * Pen<L>::BOX + L) + sizeof(float) * L;
+template <int L>
+constexpr int ynt() {
+  return 16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32;  // one group per column
 }
 
-template <int L, int NCH>
-__global__ void __launch_bounds__(YfGeo<L, NCH>::NT) k_yfwd(const __grid_constant__ Solve s0,
-                                                            const Solve* __restrict__ tab) {
+template <int L, bool BWD>
+constexpr size_t yfwd_smem() {
+  return 1024 + sizeof(float2) * ((size_t)(BWD ? 1 : 2) * Pen<L>::BOX + L) + sizeof(float) * L;
+}
+
+template <int L, bool BWD>
+__global__ void __launch_bounds__(ynt<L>(), BWD ? 4 : 3) k_yfwd(const __grid_constant__ Solve s0,
+                                                   const Solve* __restrict__ tab) {
   using P = Pen<L>;
-  using Y = YfGeo<L, NCH>;
-  constexpr int H = P::H;
+  constexpr int H = P::H, NT = ynt<L>();
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   const int X = blockIdx.x / P::NKC, kz0 = (blockIdx.x % P::NKC) * P::NCOL;
+  const int kind = BWD ? 3 : (int)blockIdx.y;
+  const int buf = kind == 1 ? kSpC : (kind == 2 ? kSpW : kSpD);  // input and output
   const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
-  float2* box = reinterpret_cast<float2*>(smem_raw + pad);  // NCH boxes
-  float2* twt = box + NCH * P::BOX;
+  float2* box = reinterpret_cast<float2*>(smem_raw + pad);  // 1 or 2 boxes
+  float2* twt = box + (BWD ? 1 : 2) * P::BOX;
   float* iu = reinterpret_cast<float*>(twt + L);
   __shared__ uint64_t bar;
   pdl_trigger();
-  for (int i = tid; i < L; i += Y::NT) {
+  for (int i = tid; i < L; i += NT) {
     twt[i] = S.tw[i];
     iu[i] = S.iu[i];
   }
@@ -264,8 +283,10 @@ __global__ void __launch_bounds__(YfGeo<L, NCH>::NT) k_yfwd(const __grid_constan
   pdl_wait();
   __syncthreads();
   if (tid == 0) {
-    mbar_expect_tx(&bar, NCH * P::BOX * (uint32_t)sizeof(float2));
-    for (int k = 0; k < NCH; ++k) tma_load_3d(box + k * P::BOX, &S.tmy[NCH == 4 ? k : 3], kz0, 0, X, &bar);
+    const int nin = kind == 0 ? 2 : 1;
+    mbar_expect_tx(&bar, nin * P::BOX * (uint32_t)sizeof(float2));
+    tma_load_3d(box, &S.tmy[buf], kz0, 0, X, &bar);
+    if (kind == 0) tma_load_3d(box + P::BOX, &S.tmy[1], kz0, 0, X, &bar);  // i u_z v_z
   }
   const bool landed = __syncthreads_and(mbar_wait(&bar, 0));
   if (!landed) {
@@ -274,77 +295,50 @@ __global__ void __launch_bounds__(YfGeo<L, NCH>::NT) k_yfwd(const __grid_constan
     return;
   }
   TwTab<L> twr{twt, t};
-  const int col = g % 16;
-  if (g < Y::NG && col < P::NCOL) {  // whole groups
-    auto cref = [&](int k) {
-      float2* b = box + k * P::BOX;
-      return [b, col](int e) -> float2& { return b[bx(e, col)]; };
-    };
+  if (g < P::NCOL) {  // whole groups
+    float2* b0 = box;
+    auto c0 = [b0, g](int e) -> float2& { return b0[bx(e, g)]; };
     float2 a[P::R1];
-    if (NCH == 1 || g < 16) {
-      auto c0 = cref(0);
 #pragma unroll
-      for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
-      fft_r<L, -1>(a, t, c0, twr);
-      if constexpr (NCH == 4) {
-        // D = FFT(i u_z v_z) + i u_y FFT(v_y)
-        auto c1 = cref(1);
-        float2 b[P::R1];
+    for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
+    fft_r<L, -1>(a, t, c0, twr);
+    if (kind == 0) {
+      float2* b1 = box + P::BOX;
+      auto c1 = [b1, g](int e) -> float2& { return b1[bx(e, g)]; };
+      float2 b[P::R1];
 #pragma unroll
-        for (int j = 0; j < P::R1; ++j) b[j] = c1(t + P::T * j);
-        fft_r<L, -1>(b, t, c1, twr);
+      for (int j = 0; j < P::R1; ++j) b[j] = c1(t + P::T * j);
+      fft_r<L, -1>(b, t, c1, twr);
 #pragma unroll
-        for (int j = 0; j < P::R1; ++j) a[j] = cadd(b[j], cmul_iu(a[j], iu[t + P::T * j]));
-      }
-#pragma unroll
-      for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = a[j];
-    } else {
-      // C = FFT(v_x), W~ = FFT(w)
-#pragma unroll
-      for (int k = 2; k < 4; ++k) {
-        auto ck = cref(k);
-#pragma unroll
-        for (int j = 0; j < P::R1; ++j) a[j] = ck(t + P::T * j);
-        fft_r<L, -1>(a, t, ck, twr);
-#pragma unroll
-        for (int j = 0; j < P::R1; ++j) ck(t + P::T * j) = a[j];
-      }
+      for (int j = 0; j < P::R1; ++j) a[j] = cadd(b[j], cmul_iu(a[j], iu[t + P::T * j]));
     }
+#pragma unroll
+    for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = a[j];
   }
   __syncthreads();
-  // outputs: NCH = 4: D (box 0) -> spec[0], C (box 2) -> spec[1], W~ (box 3)
-  // -> spec[2]; NCH = 1: box 0 -> spec[3]
-  constexpr int NOUT = NCH == 4 ? 3 : 1;
-  if (kz0 == 0 && g < NOUT) {
+  if (kz0 == 0 && g == 0) {
     // column 0 holds X0 + i Xn of the DC and Nyquist columns: split them
-    const int bi = g == 0 ? 0 : g + 1, buf = NCH == 4 ? g : 3;
-    float2* b = box + bi * P::BOX;
     float2* dst = S.spec[buf];
-    split_dc_nyq<L>(b, t, [&](int ky, float2 w) {
-      if (H < 16) b[bx(ky, H)] = w;
+    split_dc_nyq<L>(box, t, [&](int ky, float2 w) {
+      if (H < 16) box[bx(ky, H)] = w;
       else dst[((size_t)X * L + ky) * P::KP + H] = w;
     });
   }
   fence_async_smem();
   __syncthreads();
   if (tid == 0) {
-    if constexpr (NCH == 4) {
-      tma_store_3d(&S.tmy[0], kz0, 0, X, box);
-      tma_store_3d(&S.tmy[1], kz0, 0, X, box + 2 * P::BOX);
-      tma_store_3d(&S.tmy[2], kz0, 0, X, box + 3 * P::BOX);
-    } else {
-      tma_store_3d(&S.tmy[3], kz0, 0, X, box);
-    }
+    tma_store_3d(&S.tmy[buf], kz0, 0, X, box);
     tma_store_commit();
     tma_store_wait_read();
   }
 }
 
 // ===========================================================================
-// Inverse y pass over 16 kz columns of plane X. NCH = 1: chi~ (spec[3]) ->
-// spec[4]. NCH = 3: the adjoint fields V_bar_x = IFFT_y(Q2) -> spec[2],
-// V_bar_y = IFFT_y(-i u_y Q1) -> spec[3], V_bar_z = -i u_z IFFT_y(Q1) ->
-// spec[4], with Q1 in spec[0] and Q2 in spec[1].
+// Inverse y pass over 16 kz columns of plane X, out of place (the pass can
+// run again on the same inputs). NCH = 1: chi~ (kSpChi) -> kSpYa. NCH = 3:
+// the adjoint fields V_bar_x = IFFT_y(Q2) -> kSpC, V_bar_y = IFFT_y(-i u_y
+// Q1) -> kSpYa, V_bar_z = -i u_z IFFT_y(Q1) -> kSpYb, with Q1 in kSpD and
+// Q2 in kSpChi.
 // ===========================================================================
 template <int L, int NCH>
 constexpr size_t yinv_smem() {
@@ -352,7 +346,7 @@ constexpr size_t yinv_smem() {
 }
 
 template <int L, int NCH>
-__global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32)
+__global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32, NCH == 1 ? 4 : 2)
     k_yinv(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = Pen<L>;
   constexpr int H = P::H, NT = 16 * P::T >= 32 ? 16 * P::T : 32;
@@ -376,16 +370,12 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
   }
   pdl_wait();
   __syncthreads();
-  // NCH = 1: box 0 <- spec[3]; NCH = 3: box 0 <- Q2 (spec[1]), box 1 <- Q1
+  // NCH = 1: box 0 <- chi~; NCH = 3: box 0 <- Q2, box 1 <- Q1
   constexpr int NIN = NCH == 1 ? 1 : 2;
   if (tid == 0) {
     mbar_expect_tx(&bar, NIN * P::BOX * (uint32_t)sizeof(float2));
-    if constexpr (NCH == 1) {
-      tma_load_3d(box, &S.tmy[3], kz0, 0, X, &bar);
-    } else {
-      tma_load_3d(box, &S.tmy[1], kz0, 0, X, &bar);
-      tma_load_3d(box + P::BOX, &S.tmy[0], kz0, 0, X, &bar);
-    }
+    tma_load_3d(box, &S.tmy[kSpChi], kz0, 0, X, &bar);
+    if constexpr (NCH == 3) tma_load_3d(box + P::BOX, &S.tmy[kSpD], kz0, 0, X, &bar);
   }
   const bool landed = __syncthreads_and(mbar_wait(&bar, 0));
   if (!landed) {
@@ -398,7 +388,7 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
     // column 0 becomes X0 + i Xn (Xn: the Nyquist column); the same lanes
     // read these elements again below
     float2* b = box + g * P::BOX;
-    const float2* nq = S.spec[NCH == 1 ? 3 : (g == 0 ? 1 : 0)] + (size_t)X * L * P::KP + H;
+    const float2* nq = S.spec[g == 0 ? kSpChi : kSpD] + (size_t)X * L * P::KP + H;
     for (int j = 0; j < P::R1; ++j) {
       const int ky = t + P::T * j;
       const float2 n = H >= 16 ? nq[(size_t)ky * P::KP] : b[bx(ky, H)];
@@ -444,13 +434,12 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
   fence_async_smem();
   __syncthreads();
   if (tid == 0) {
-    // out of place, so that the pass can run again on the same inputs
     if constexpr (NCH == 1) {
-      tma_store_3d(&S.tmy[4], kz0, 0, X, box);
+      tma_store_3d(&S.tmy[kSpYa], kz0, 0, X, box);
     } else {
-      tma_store_3d(&S.tmy[2], kz0, 0, X, box);
-      tma_store_3d(&S.tmy[3], kz0, 0, X, box + P::BOX);
-      tma_store_3d(&S.tmy[4], kz0, 0, X, box + 2 * P::BOX);
+      tma_store_3d(&S.tmy[kSpC], kz0, 0, X, box);
+      tma_store_3d(&S.tmy[kSpYa], kz0, 0, X, box + P::BOX);
+      tma_store_3d(&S.tmy[kSpYb], kz0, 0, X, box + 2 * P::BOX);
     }
     tma_store_commit();
     tma_store_wait_read();
@@ -458,167 +447,181 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
 }
 
 // ===========================================================================
-// Inverse z passes over YB rows of plane X (+ 2 halo rows for the stencil's
-// row i0 + 1): load the packed rows, C2R in place.
+// Inverse z passes over tiles of YB rows of plane X (+ 2 halo rows for the
+// stencil's row i0 + 1): persistent CTAs, each loading tile i + 1 by bulk
+// copies (two stages) while it transforms tile i. Per tile: C2R of row pairs
+// in place, then
+//   NCH = 1 (forward): chi = a_chi y + b_chi for the YB rows, and the
+//     gradient of the trilinear lookup of y at the points whose stencil row
+//     i0 is one of them (this plane's share, delta_x fixed by the plane);
+//   NCH = 3 (adjoint): C2R of V_bar_x (kSpC), V_bar_y (kSpYa), V_bar_z
+//     (kSpYb); at those points the gather of the three fields (dnormals
+//     share) and the weight derivatives times n . V (dpoints share).
 // ===========================================================================
-// Rows y0 .. y0 + YB + 1 (mod L) of `src` into rows[(ch, ly)] (H float2 each).
-template <int L>
-__device__ __forceinline__ void load_rows(const float2* src, int X, int y0, float4* dst, int nthreads) {
-  using P = Pen<L>;
-  constexpr int Q = P::H / 2, NR = P::YB + 2;
-  for (int i = threadIdx.x; i < NR * Q; i += nthreads) {
-    const int ly = i / Q, q = i % Q;
-    const int y = (y0 + ly) & (L - 1);
-    dst[ly * Q + q] = reinterpret_cast<const float4*>(src + ((size_t)X * L + y) * P::KP)[q];
-  }
-}
+template <int L, int NCH>
+struct ZiGeo {
+  static constexpr int NR = Pen<L>::YB + 2;              // rows per tile
+  static constexpr int STAGE = NCH * NR * Pen<L>::KP;     // float2 per stage
+  static constexpr int NT = NCH == 1 ? 256 : 512;
+};
 
 template <int L, int NCH>
 constexpr size_t zinv_smem() {
-  return sizeof(float2) * ((size_t)NCH * (Pen<L>::YB + 2) * (L / 2) + L);
+  return sizeof(float2) * ((size_t)2 * ZiGeo<L, NCH>::STAGE + L);
 }
 
-// Forward: chi = a_chi y + b_chi for the CTA's rows, and the gradient of the
-// trilinear lookup of y at the points whose stencil row i0 is one of them
-// (this plane's share, delta_x fixed by the plane).
-template <int L>
-__global__ void __launch_bounds__(Pen<L>::ZNT) k_zinv(const __grid_constant__ Solve s0,
-                                                      const Solve* __restrict__ tab) {
+template <int L, int NCH>
+__global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : 1)
+    k_zinv(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = Pen<L>;
-  constexpr int YB = P::YB, H = P::H, NR = YB + 2;
+  using Z = ZiGeo<L, NCH>;
+  constexpr int YB = P::YB, H = P::H, NR = Z::NR, KP = P::KP, NT = Z::NT, G = NT / P::T;
   const Solve& S = tab ? tab[blockIdx.z] : s0;
-  const int X = blockIdx.x / P::NYB, y0 = (blockIdx.x % P::NYB) * YB;
   const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
   extern __shared__ float4 smem4[];
-  float2* rows = reinterpret_cast<float2*>(smem4);  // NR rows of H float2
-  float2* twt = rows + NR * H;
+  float2* stg = reinterpret_cast<float2*>(smem4);  // 2 stages of [NCH][NR][KP]
+  float2* twt = stg + 2 * Z::STAGE;
+  __shared__ uint64_t bar[2];
   pdl_trigger();
-  for (int i = tid; i < L; i += P::ZNT) twt[i] = S.tw[i];
+  for (int i = tid; i < L; i += NT) twt[i] = S.tw[i];
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   pdl_wait();
-  load_rows<L>(S.spec[4], X, y0, smem4, P::ZNT);
-  const float a_chi = S.sc->a_chi, b_chi = S.sc->b_chi;
   __syncthreads();
-  TwTab<L> twr{twt, t};
-  for (int p0 = 0; p0 < NR / 2; p0 += P::ZG) {
-    const int pi = p0 + g;
-    if (pi < NR / 2) c2r_pair_ip2<L>(t, twr, rows + pi * L);
-  }
-  __syncthreads();
-  // value of row ly (0 .. NR-1), column z: pair ly / 2, component ly & 1
-  auto yv = [&](int ly, int z) {
-    const float2 f = rows[(ly >> 1) * L + z];
-    return (ly & 1) ? f.y : f.x;
+  constexpr int ntiles = L * P::NYB;
+  auto issue = [&](int tile, int st) {  // thread 0: the tile's rows into stage st
+    const int X = tile / P::NYB, y0 = (tile % P::NYB) * YB;
+    const int n1 = NR < L - y0 ? NR : L - y0;  // rows before the wrap to row 0
+    mbar_expect_tx(&bar[st], NCH * NR * KP * (uint32_t)sizeof(float2));
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) {
+      const int buf = NCH == 1 ? kSpYa : (ch == 0 ? kSpC : (ch == 1 ? kSpYa : kSpYb));
+      const float2* base = S.spec[buf] + (size_t)X * L * KP;
+      float2* dst = stg + st * Z::STAGE + ch * NR * KP;
+      bulk_load(dst, base + (size_t)y0 * KP, n1 * KP * (uint32_t)sizeof(float2), &bar[st]);
+      if (n1 < NR) bulk_load(dst + n1 * KP, base, (NR - n1) * KP * (uint32_t)sizeof(float2), &bar[st]);
+    }
   };
-  float* chi = S.chi;
-  for (int i = tid; i < YB * L / 4; i += P::ZNT) {
-    const int ly = i / (L / 4), z4 = (i % (L / 4)) * 4;
-    const float4 o = make_float4(fmaf(a_chi, yv(ly, z4), b_chi), fmaf(a_chi, yv(ly, z4 + 1), b_chi),
-                                 fmaf(a_chi, yv(ly, z4 + 2), b_chi), fmaf(a_chi, yv(ly, z4 + 3), b_chi));
-    reinterpret_cast<float4*>(chi + ((size_t)X * L + y0 + ly) * L)[z4 / 4] = o;
+  float a_chi = 0.f, b_chi = 0.f;
+  if constexpr (NCH == 1) {
+    a_chi = S.sc->a_chi;
+    b_chi = S.sc->b_chi;
   }
-  for (int side = 0; side < 2; ++side) {
-    const int xc = (X - side) & (L - 1);
-    const int2 rg = bin_range(S, xc, y0 / YB);
-    for (int i = rg.x + tid; i < rg.y; i += P::ZNT) {
-      const float4 a = S.sorted[2 * i];
-      const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);
-      const int ly0 = ay.i0 - y0;  // in [0, YB); row i1 is ly0 + 1 (a halo row at most)
-      const float fx = tri_w(side, ax.t), dfx = side ? (float)L : -(float)L;
-      float gx = 0.f, gy = 0.f, gz = 0.f;
+  TwTab<L> twr{twt, t};
+  uint32_t ph = 0u;  // bit st: parity of stage st's next completion
+  int tile = blockIdx.x;
+  if (tid == 0 && tile < ntiles) issue(tile, 0);
+  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    const int st = it & 1;
+    const int next = tile + gridDim.x;
+    if (tid == 0 && next < ntiles) issue(next, st ^ 1);  // released at the end of the last iteration
+    const bool ok = __syncthreads_and(mbar_wait(&bar[st], (ph >> st) & 1u));
+    ph ^= 1u << st;
+    if (!ok) {
+      if (tid == 0) {
+        atomicOr(S.status, kStTimeout);
+        if (next < ntiles) mbar_wait(&bar[st ^ 1], (ph >> (st ^ 1)) & 1u);  // the prefetch, bounded
+      }
+      break;
+    }
+    float2* sb = stg + st * Z::STAGE;
+    const int X = tile / P::NYB, y0 = (tile % P::NYB) * YB;
+    // pair p of channel ch: rows 2p (A) and 2p + 1 (B) of the stage
+    auto pair = [&](int ch, int p) {
+      float2* ra = sb + (ch * NR + 2 * p) * KP;
+      return [ra](int i) -> float2& { return i < H ? ra[i] : ra[KP + i - H]; };
+    };
+    constexpr int NP = NCH * NR / 2;
+    for (int p0 = 0; p0 < NP; p0 += G) {
+      const int pi = p0 + g;
+      if (pi < NP) c2r_acc<L>(t, twr, pair(pi / (NR / 2), pi % (NR / 2)));  // whole groups
+    }
+    __syncthreads();
+    // value of channel ch, tile row ly, column z
+    auto val = [&](int ch, int ly, int z) {
+      const float2 f = pair(ch, ly >> 1)(z);
+      return (ly & 1) ? f.y : f.x;
+    };
+    if constexpr (NCH == 1) {
+      float* chi = S.chi;
+      for (int i = tid; i < YB * L / 4; i += NT) {
+        const int ly = i / (L / 4), z4 = (i % (L / 4)) * 4;
+        float4 o;
+        o.x = fmaf(a_chi, val(0, ly, z4), b_chi);
+        o.y = fmaf(a_chi, val(0, ly, z4 + 1), b_chi);
+        o.z = fmaf(a_chi, val(0, ly, z4 + 2), b_chi);
+        o.w = fmaf(a_chi, val(0, ly, z4 + 3), b_chi);
+        reinterpret_cast<float4*>(chi + ((size_t)X * L + y0 + ly) * L)[z4 / 4] = o;
+      }
+    }
+    for (int side = 0; side < 2; ++side) {
+      const int xc = (X - side) & (L - 1);
+      const int2 rg = bin_range(S, xc, y0 / YB);
+      for (int i = rg.x + tid; i < rg.y; i += NT) {
+        const float4 a = S.sorted[2 * i];
+        const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);
+        const int ly0 = ay.i0 - y0;  // in [0, YB); row i1 is ly0 + 1 (a halo row at most)
+        const float fx = tri_w(side, ax.t), dfx = side ? (float)L : -(float)L;
+        if constexpr (NCH == 1) {
+          float gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
-      for (int dy = 0; dy < 2; ++dy) {
-        const float fy = tri_w(dy, ay.t), dfy = dy ? (float)L : -(float)L;
+          for (int dy = 0; dy < 2; ++dy) {
+            const float fy = tri_w(dy, ay.t), dfy = dy ? (float)L : -(float)L;
 #pragma unroll
-        for (int dz = 0; dz < 2; ++dz) {
-          const int z = dz ? az.i1 : az.i0;
-          const float fz = tri_w(dz, az.t), dfz = dz ? (float)L : -(float)L;
-          const float val = yv(ly0 + dy, z);
-          gx += dfx * fy * fz * val;
-          gy += fx * dfy * fz * val;
-          gz += fx * fy * dfz * val;
+            for (int dz = 0; dz < 2; ++dz) {
+              const int z = dz ? az.i1 : az.i0;
+              const float fz = tri_w(dz, az.t), dfz = dz ? (float)L : -(float)L;
+              const float v = val(0, ly0 + dy, z);
+              gx += dfx * fy * fz * v;
+              gy += fx * dfy * fz * v;
+              gz += fx * fy * dfz * v;
+            }
+          }
+          S.gfwd[(size_t)side * S.N + i] = make_float4(gx, gy, gz, 0.f);
+        } else {
+          const float4 b = S.sorted[2 * i + 1];
+          const float n0 = a.w, n1 = b.x, n2 = b.y;
+          float nb0 = 0.f, nb1 = 0.f, nb2 = 0.f, cb0 = 0.f, cb1 = 0.f, cb2 = 0.f;
+#pragma unroll
+          for (int dy = 0; dy < 2; ++dy) {
+            const float fy = tri_w(dy, ay.t), dfy = dy ? (float)L : -(float)L;
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz) {
+              const int z = dz ? az.i1 : az.i0;
+              const float fz = tri_w(dz, az.t), dfz = dz ? (float)L : -(float)L;
+              const float vx = val(0, ly0 + dy, z), vy = val(1, ly0 + dy, z), vz = val(2, ly0 + dy, z);
+              const float w = fx * fy * fz;
+              nb0 += w * vx;
+              nb1 += w * vy;
+              nb2 += w * vz;
+              const float sdot = n0 * vx + n1 * vy + n2 * vz;
+              cb0 += dfx * fy * fz * sdot;
+              cb1 += fx * dfy * fz * sdot;
+              cb2 += fx * fy * dfz * sdot;
+            }
+          }
+          float* o = S.slots + ((size_t)side * S.N + i) * 6;
+          o[0] = nb0;
+          o[1] = nb1;
+          o[2] = nb2;
+          o[3] = cb0;
+          o[4] = cb1;
+          o[5] = cb2;
         }
       }
-      S.gfwd[(size_t)side * S.N + i] = make_float4(gx, gy, gz, 0.f);
     }
-  }
-}
-
-// Backward: C2R of V_bar_x (spec[2]), V_bar_y (spec[3]), V_bar_z (spec[4]);
-// at each point whose stencil row i0 is one of the CTA's rows, the gather of
-// the three fields (dnormals share) and the weight derivatives times n . V
-// (dpoints share) of this plane side.
-template <int L>
-__global__ void __launch_bounds__(Pen<L>::ZNT) k_zinv3(const __grid_constant__ Solve s0,
-                                                       const Solve* __restrict__ tab) {
-  using P = Pen<L>;
-  constexpr int YB = P::YB, H = P::H, NR = YB + 2;
-  const Solve& S = tab ? tab[blockIdx.z] : s0;
-  const int X = blockIdx.x / P::NYB, y0 = (blockIdx.x % P::NYB) * YB;
-  const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
-  extern __shared__ float4 smem4[];
-  float2* rows = reinterpret_cast<float2*>(smem4);  // [3][NR][H]: x, y, z
-  float2* twt = rows + 3 * NR * H;
-  pdl_trigger();
-  for (int i = tid; i < L; i += P::ZNT) twt[i] = S.tw[i];
-  pdl_wait();
-  load_rows<L>(S.spec[2], X, y0, smem4, P::ZNT);
-  load_rows<L>(S.spec[3], X, y0, smem4 + NR * H / 2, P::ZNT);
-  load_rows<L>(S.spec[4], X, y0, smem4 + 2 * NR * H / 2, P::ZNT);
-  __syncthreads();
-  TwTab<L> twr{twt, t};
-  constexpr int NP = 3 * NR / 2;
-  for (int p0 = 0; p0 < NP; p0 += P::ZG) {
-    const int pi = p0 + g;
-    if (pi < NP) c2r_pair_ip2<L>(t, twr, rows + pi * L);
-  }
-  __syncthreads();
-  auto vv = [&](int ch, int ly, int z) {
-    const float2 f = rows[(ch * NR / 2 + (ly >> 1)) * L + z];
-    return (ly & 1) ? f.y : f.x;
-  };
-  for (int side = 0; side < 2; ++side) {
-    const int xc = (X - side) & (L - 1);
-    const int2 rg = bin_range(S, xc, y0 / YB);
-    for (int i = rg.x + tid; i < rg.y; i += P::ZNT) {
-      const float4 a = S.sorted[2 * i], b = S.sorted[2 * i + 1];
-      const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);
-      const int ly0 = ay.i0 - y0;
-      const float n0 = a.w, n1 = b.x, n2 = b.y;
-      const float fx = tri_w(side, ax.t), dfx = side ? (float)L : -(float)L;
-      float nb0 = 0.f, nb1 = 0.f, nb2 = 0.f, cb0 = 0.f, cb1 = 0.f, cb2 = 0.f;
-#pragma unroll
-      for (int dy = 0; dy < 2; ++dy) {
-        const float fy = tri_w(dy, ay.t), dfy = dy ? (float)L : -(float)L;
-#pragma unroll
-        for (int dz = 0; dz < 2; ++dz) {
-          const int z = dz ? az.i1 : az.i0;
-          const float fz = tri_w(dz, az.t), dfz = dz ? (float)L : -(float)L;
-          const float vx = vv(0, ly0 + dy, z), vy = vv(1, ly0 + dy, z), vz = vv(2, ly0 + dy, z);
-          const float w = fx * fy * fz;
-          nb0 += w * vx;
-          nb1 += w * vy;
-          nb2 += w * vz;
-          const float sdot = n0 * vx + n1 * vy + n2 * vz;
-          cb0 += dfx * fy * fz * sdot;
-          cb1 += fx * dfy * fz * sdot;
-          cb2 += fx * fy * dfz * sdot;
-        }
-      }
-      float* o = S.slots + ((size_t)side * S.N + i) * 6;
-      o[0] = nb0;
-      o[1] = nb1;
-      o[2] = nb2;
-      o[3] = cb0;
-      o[4] = cb1;
-      o[5] = cb2;
-    }
+    fence_async_smem();  // this stage is refilled by a bulk copy two tiles on
+    __syncthreads();
   }
 }
 
 // ===========================================================================
 // Backward z pass: the sums S = sum dchi and sum dchi * chi of the CTA's
 // rows (block partials, reduced by the last CTA into the adjoint scalars),
-// and the R2C along z of dchi -> spec[3].
+// and the R2C along z of dchi -> kSpD.
 // ===========================================================================
 template <int L>
 constexpr size_t zbfwd_smem() {
@@ -626,7 +629,7 @@ constexpr size_t zbfwd_smem() {
 }
 
 template <int L>
-__global__ void __launch_bounds__(Pen<L>::ZNT) k_zbfwd(const __grid_constant__ Solve s0,
+__global__ void __launch_bounds__(Pen<L>::ZNT, 4) k_zbfwd(const __grid_constant__ Solve s0,
                                                        const Solve* __restrict__ tab) {
   using P = Pen<L>;
   constexpr int YB = P::YB, H = P::H;
@@ -682,7 +685,7 @@ __global__ void __launch_bounds__(Pen<L>::ZNT) k_zbfwd(const __grid_constant__ S
   constexpr int Q = H / 2;
   for (int i = tid; i < YB * Q; i += P::ZNT) {
     const int ly = i / Q, q = i % Q;
-    reinterpret_cast<float4*>(S.spec[3] + ((size_t)X * L + y0 + ly) * P::KP)[q] = smem4[ly * Q + q];
+    reinterpret_cast<float4*>(S.spec[kSpD] + ((size_t)X * L + y0 + ly) * P::KP)[q] = smem4[ly * Q + q];
   }
   last_block_finalize(S, 1, (int)gridDim.x, true);
 }
@@ -706,53 +709,60 @@ static cudaError_t launch_pencil_t(int kind, const Solve& s, const Solve* tab, i
   cudaError_t e = cudaSuccess;
   switch (kind) {
     case 0: {
-      constexpr size_t a = zfwd_smem<L>(), b = yfwd_smem<L, 4>();
+      constexpr size_t a = zfwd_smem<L>(), b = yfwd_smem<L, false>();
       if (!attr_set[0]) {
         e = set_smem(k_zfwd<L>, a);
-        if (e == cudaSuccess) e = set_smem(k_yfwd<L, 4>, b);
+        if (e == cudaSuccess) e = set_smem(k_yfwd<L, false>, b);
         if (e != cudaSuccess) return e;
         attr_set[0] = true;
       }
       e = launch_k(k_zfwd<L>, gz, dim3(P::ZNT), a, st, 0, s, tab);
-      if (e == cudaSuccess) e = launch_k(k_yfwd<L, 4>, gy, dim3(YfGeo<L, 4>::NT), b, st, 0, s, tab);
+      if (e == cudaSuccess)
+        e = launch_k(k_yfwd<L, false>, dim3(L * P::NKC, 3, count), dim3(ynt<L>()), b, st, 0, s, tab);
       return e;
     }
     case 1: {
       constexpr size_t a = yinv_smem<L, 1>(), b = zinv_smem<L, 1>();
       constexpr int nt = 16 * P::T >= 32 ? 16 * P::T : 32;
+      static int nz = 0;
       if (!attr_set[1]) {
         e = set_smem(k_yinv<L, 1>, a);
-        if (e == cudaSuccess) e = set_smem(k_zinv<L>, b);
+        if (e == cudaSuccess) e = set_smem(k_zinv<L, 1>, b);
         if (e != cudaSuccess) return e;
+        nz = persistent_ctas(k_zinv<L, 1>, ZiGeo<L, 1>::NT, b, L * P::NYB, 1);
         attr_set[1] = true;
       }
       e = launch_k(k_yinv<L, 1>, gy, dim3(nt), a, st, 0, s, tab);
-      if (e == cudaSuccess) e = launch_k(k_zinv<L>, gz, dim3(P::ZNT), b, st, 0, s, tab);
+      if (e == cudaSuccess)
+        e = launch_k(k_zinv<L, 1>, dim3(nz, 1, count), dim3(ZiGeo<L, 1>::NT), b, st, 0, s, tab);
       return e;
     }
     case 2: {
-      constexpr size_t a = zbfwd_smem<L>(), b = yfwd_smem<L, 1>();
+      constexpr size_t a = zbfwd_smem<L>(), b = yfwd_smem<L, true>();
       if (!attr_set[2]) {
         e = set_smem(k_zbfwd<L>, a);
-        if (e == cudaSuccess) e = set_smem(k_yfwd<L, 1>, b);
+        if (e == cudaSuccess) e = set_smem(k_yfwd<L, true>, b);
         if (e != cudaSuccess) return e;
         attr_set[2] = true;
       }
       e = launch_k(k_zbfwd<L>, gz, dim3(P::ZNT), a, st, 0, s, tab);
-      if (e == cudaSuccess) e = launch_k(k_yfwd<L, 1>, gy, dim3(YfGeo<L, 1>::NT), b, st, 0, s, tab);
+      if (e == cudaSuccess) e = launch_k(k_yfwd<L, true>, gy, dim3(ynt<L>()), b, st, 0, s, tab);
       return e;
     }
     default: {
       constexpr size_t a = yinv_smem<L, 3>(), b = zinv_smem<L, 3>();
       constexpr int nt = 16 * P::T >= 32 ? 16 * P::T : 32;
+      static int nz = 0;
       if (!attr_set[3]) {
         e = set_smem(k_yinv<L, 3>, a);
-        if (e == cudaSuccess) e = set_smem(k_zinv3<L>, b);
+        if (e == cudaSuccess) e = set_smem(k_zinv<L, 3>, b);
         if (e != cudaSuccess) return e;
+        nz = persistent_ctas(k_zinv<L, 3>, ZiGeo<L, 3>::NT, b, L * P::NYB, 1);
         attr_set[3] = true;
       }
       e = launch_k(k_yinv<L, 3>, gy, dim3(nt), a, st, 0, s, tab);
-      if (e == cudaSuccess) e = launch_k(k_zinv3<L>, gz, dim3(P::ZNT), b, st, 0, s, tab);
+      if (e == cudaSuccess)
+        e = launch_k(k_zinv<L, 3>, dim3(nz, 1, count), dim3(ZiGeo<L, 3>::NT), b, st, 0, s, tab);
       return e;
     }
   }
@@ -777,9 +787,9 @@ size_t pencil_smem_bytes(int kind, int r) {
     constexpr int L = decltype(Lc)::value;
     size_t a = 0, b = 0;
     switch (kind) {
-      case 0: a = zfwd_smem<L>(); b = yfwd_smem<L, 4>(); break;
+      case 0: a = zfwd_smem<L>(); b = yfwd_smem<L, false>(); break;
       case 1: a = yinv_smem<L, 1>(); b = zinv_smem<L, 1>(); break;
-      case 2: a = zbfwd_smem<L>(); b = yfwd_smem<L, 1>(); break;
+      case 2: a = zbfwd_smem<L>(); b = yfwd_smem<L, true>(); break;
       default: a = yinv_smem<L, 3>(); b = zinv_smem<L, 3>(); break;
     }
     return a > b ? a : b;

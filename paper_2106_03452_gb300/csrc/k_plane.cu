@@ -35,7 +35,7 @@ struct PlaneGeo {
   static constexpr int XP = L + 1;               // per-group exchange pitch (z pass)
   static constexpr int SCR0 = NB * BOX > G * XP ? NB * BOX : G * XP;
   static constexpr int SCR = (SCR0 + 127) / 128 * 128;  // scratch float2, whole KiB
-  static constexpr int KP = L / 2 + 2;   // row pitch of the spectral buffers in HBM
+  static constexpr int KP = kpitch(L);   // row pitch of the spectral buffers in HBM
   static constexpr int SWM = (H < 16 ? H : 16) - 1;
   static_assert(R >= 2 && R % 2 == 0, "at least one row pair per CTA");
   static_assert(SPC >= 16 || C == 1, "a CTA owns whole 16-slot TMA boxes");
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(fwd_threads<L, C>(), 512 / fwd_threads<L, C>()
     }
     __syncthreads();
     if (rd >= 1) {
-      const int buf = rd == 1 ? 0 : (rd == 2 ? 1 : 2);  // D, C, W~
+      const int buf = rd == 1 ? kSpD : (rd == 2 ? kSpC : kSpW);
       if (c == 0 && g == 0) {
         float2* dst = S.spec[buf];
         separate_dc_nyq<L>(sbox, t, [&](int ky, float2 w) {
@@ -478,13 +478,13 @@ __global__ void __launch_bounds__(kNT, plane_minb<L, C>(1))
   bool alive = true;
   for (int cb = 0; cb < P::SPC && alive; cb += P::CHK) {
     const int s_first = c * P::SPC + cb;
-    if (tid == 0) chunk_load<L, C>(&S.tmy[3], sbox, s_first, X, &bar);
+    if (tid == 0) chunk_load<L, C>(&S.tmy[kSpChi], sbox, s_first, X, &bar);
     const bool head = (c == 0 && cb == 0);
     float2 nyq[P::R1];
     if (head && g == 0 && P::H >= 16) {
 #pragma unroll
       for (int j = 0; j < P::R1; ++j)
-        nyq[j] = S.spec[3][((size_t)X * L + t + P::T * j) * P::KP + P::H];
+        nyq[j] = S.spec[kSpChi][((size_t)X * L + t + P::T * j) * P::KP + P::H];
     }
     alive = chunk_wait(&bar, phase, S.status);
     phase ^= 1;
@@ -650,13 +650,13 @@ __global__ void __launch_bounds__(kNT, plane_minb<L, C>(2))
     if (c == 0 && cb == 0 && g == 0) {
       separate_dc_nyq<L>(sbox, t, [&](int ky, float2 w) {
         if (P::H < 16) boxcol<L>(sbox, P::H, ky) = w;
-        else S.spec[3][((size_t)X * L + ky) * P::KP + P::H] = w;
+        else S.spec[kSpD][((size_t)X * L + ky) * P::KP + P::H] = w;
       });
     }
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
-      chunk_store<L, C>(&S.tmy[3], sbox, s_first, X);
+      chunk_store<L, C>(&S.tmy[kSpD], sbox, s_first, X);
       tma_store_wait_read();
     }
     __syncthreads();
@@ -797,7 +797,7 @@ __global__ void __launch_bounds__(kNT, binv_smem<L, C>() <= 113 * 1024 ? 2 : 1)
     for (int k = 0; k < 2; ++k) {
       mbar_expect_tx(&barL[k], B::NB * B::BOX * (uint32_t)sizeof(float2));
       for (int b = 0; b < B::NB; ++b)
-        tma_load_3d((k ? buf1 : buf0) + b * B::BOX, &S.tmy[k ? 0 : 1], s_first + 16 * b, 0, X, &barL[k]);
+        tma_load_3d((k ? buf1 : buf0) + b * B::BOX, &S.tmy[k ? kSpD : kSpChi], s_first + 16 * b, 0, X, &barL[k]);
     }
   }
   __syncthreads();
@@ -822,10 +822,10 @@ __global__ void __launch_bounds__(kNT, binv_smem<L, C>() <= 113 * 1024 ? 2 : 1)
       if (alive && c == 0 && g == 0) {
         // column kz = 0 becomes P = X0 + i Xn (Xn: the Nyquist column); the
         // same lanes read these elements again in the y pass below
-        const float2* nq = S.spec[ch == 0 ? 1 : 0] + (size_t)X * L * (H + 2) + H;
+        const float2* nq = S.spec[ch == 0 ? kSpChi : kSpD] + (size_t)X * L * kpitch(L) + H;
         for (int j = 0; j < R1; ++j) {
           const int ky = t + T * j;
-          const float2 n = H >= 16 ? nq[(size_t)ky * (H + 2)] : col(src, H, ky);
+          const float2 n = H >= 16 ? nq[(size_t)ky * kpitch(L)] : col(src, H, ky);
           const float2 x0 = col(src, 0, ky);
           col(src, 0, ky) = make_float2(x0.x - n.y, x0.y + n.x);
         }

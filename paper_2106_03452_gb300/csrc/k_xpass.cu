@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(XGeo<L>::NT, 2)
   __shared__ uint64_t bar;
   __shared__ double red[2][P::NT / 32];
   // inputs: forward D, C, W~; backward FFT_zy(dchi), W~
-  const int src0 = BWD ? 3 : 0, src1 = BWD ? 2 : 1;
+  const int src0 = kSpD, src1 = BWD ? kSpW : kSpC;
   pdl_trigger();
   pdl_wait();
   if (tid == 0) {
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(XGeo<L>::NT, 2)
     mbar_expect_tx(&bar, NCH * P::BOX * (uint32_t)sizeof(float2));
     tma_load_3d(box, &S.tmx[src0], kz0, ky, 0, &bar);
     tma_load_3d(box + P::BOX, &S.tmx[src1], kz0, ky, 0, &bar);
-    if constexpr (!BWD) tma_load_3d(box + 2 * P::BOX, &S.tmx[2], kz0, ky, 0, &bar);
+    if constexpr (!BWD) tma_load_3d(box + 2 * P::BOX, &S.tmx[kSpW], kz0, ky, 0, &bar);
   }
   for (int i = tid; i < L; i += P::NT) {
     tw[i] = S.tw[i];
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(XGeo<L>::NT, 2)
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
-      tma_store_3d(&S.tmx[3], kz0, ky, 0, box);
+      tma_store_3d(&S.tmx[kSpChi], kz0, ky, 0, box);
       tma_store_commit();
       double sm = 0, ss = 0;
       for (int q = 0; q < P::NT / 32; ++q) {
@@ -195,8 +195,8 @@ __global__ void __launch_bounds__(XGeo<L>::NT, 2)
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
-      tma_store_3d(&S.tmx[0], kz0, ky, 0, box);
-      tma_store_3d(&S.tmx[1], kz0, ky, 0, box + P::BOX);
+      tma_store_3d(&S.tmx[kSpD], kz0, ky, 0, box);          // Q1
+      tma_store_3d(&S.tmx[kSpChi], kz0, ky, 0, box + P::BOX);  // Q2
       tma_store_commit();
       tma_store_wait_read();
     }
