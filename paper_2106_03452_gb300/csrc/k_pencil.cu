@@ -184,35 +184,49 @@ __global__ void __launch_bounds__(Pen<L>::ZNT, 3) k_zfwd(const __grid_constant__
   __syncthreads();
   // Rasterization (Eq. A2): points of x-cells X (dx = 0) and X - 1 (dx = 1)
   // whose stencil rows i0 or i1 fall in [y0, y0 + YB), i.e. i0 in
-  // [y0 - 1, y0 + YB - 1] (mod L): the CTA's own bin, and the points of the
-  // previous y-block's bin in its last row.
+  // [y0 - 1, y0 + YB - 1] (mod L): per side the CTA's own bin and the
+  // previous y-block's bin (its last row only). The four ranges are read up
+  // front and visited as one sequence, so that their loads overlap.
   const int yb = y0 / YB, ylast = (y0 - 1) & (L - 1);
-  for (int side = 0; side < 2; ++side) {
-    const int xc = (X - side) & (L - 1);
-    for (int part = 0; part < 2; ++part) {
-      if (part == 1 && YB == L) continue;  // one bin holds the whole plane
-      const int2 rg = bin_range(S, xc, part == 0 ? yb : (yb + P::NYB - 1) % P::NYB);
-      for (int i = rg.x + tid; i < rg.y; i += P::ZNT) {
-        const float4 a = S.sorted[2 * i];
-        const Axis ay = axis_of(a.y, L);
-        if (part == 1 && ay.i0 != ylast) continue;
-        const float4 b = S.sorted[2 * i + 1];
-        const Axis ax = axis_of(a.x, L), az = axis_of(a.z, L);
-        const float wx = tri_w(side, ax.t);
-        const float val[4] = {b.x, b.y, a.w, 1.f};
+  int q0, q1, q2, q3, c1, c2, c3, c4;  // range starts, cumulative counts
+  {
+    const int* off = S.bins + nbins(L);
+    auto key = [&](int k) {
+      return ((X - (k >> 1)) & (L - 1)) * P::NYB + ((k & 1) ? (yb + P::NYB - 1) % P::NYB : yb);
+    };
+    const bool prev = YB < L;  // with YB == L one bin holds the whole plane
+    const int k0 = key(0), k1 = key(1), k2 = key(2), k3 = key(3);
+    q0 = off[k0];
+    q1 = prev ? off[k1] : 0;
+    q2 = off[k2];
+    q3 = prev ? off[k3] : 0;
+    const int e0 = off[k0 + 1], e1 = prev ? off[k1 + 1] : 0, e2 = off[k2 + 1], e3 = prev ? off[k3 + 1] : 0;
+    c1 = e0 - q0;
+    c2 = c1 + (e1 - q1);
+    c3 = c2 + (e2 - q2);
+    c4 = c3 + (e3 - q3);
+  }
+  for (int v = tid; v < c4; v += P::ZNT) {
+    const int k = v < c1 ? 0 : (v < c2 ? 1 : (v < c3 ? 2 : 3));
+    const int i = k == 0 ? q0 + v : (k == 1 ? q1 + (v - c1) : (k == 2 ? q2 + (v - c2) : q3 + (v - c3)));
+    const int side = k >> 1, part = k & 1;
+    const float4 a = S.sorted[2 * i], b = S.sorted[2 * i + 1];
+    const Axis ay = axis_of(a.y, L);
+    if (part == 1 && ay.i0 != ylast) continue;
+    const Axis ax = axis_of(a.x, L), az = axis_of(a.z, L);
+    const float wx = tri_w(side, ax.t);
+    const float val[4] = {b.x, b.y, a.w, 1.f};
 #pragma unroll
-        for (int dy = 0; dy < 2; ++dy) {
-          const int ly = (dy ? ay.i1 : ay.i0) - y0;
-          if ((unsigned)ly >= (unsigned)YB) continue;
-          const float f = wx * tri_w(dy, ay.t);
-          const float f0 = f * (1.f - az.t), f1 = f * az.t;
+    for (int dy = 0; dy < 2; ++dy) {
+      const int ly = (dy ? ay.i1 : ay.i0) - y0;
+      if ((unsigned)ly >= (unsigned)YB) continue;
+      const float f = wx * tri_w(dy, ay.t);
+      const float f0 = f * (1.f - az.t), f1 = f * az.t;
 #pragma unroll
-          for (int ch = 0; ch < 4; ++ch) {
-            float* row = rows + (ch * YB + ly) * L;
-            atomicAdd(row + az.i0, f0 * val[ch]);
-            atomicAdd(row + az.i1, f1 * val[ch]);
-          }
-        }
+      for (int ch = 0; ch < 4; ++ch) {
+        float* row = rows + (ch * YB + ly) * L;
+        atomicAdd(row + az.i0, f0 * val[ch]);
+        atomicAdd(row + az.i1, f1 * val[ch]);
       }
     }
   }
@@ -557,10 +571,13 @@ __global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : 1)
         reinterpret_cast<float4*>(chi + ((size_t)X * L + y0 + ly) * L)[z4 / 4] = o;
       }
     }
-    for (int side = 0; side < 2; ++side) {
-      const int xc = (X - side) & (L - 1);
-      const int2 rg = bin_range(S, xc, y0 / YB);
-      for (int i = rg.x + tid; i < rg.y; i += NT) {
+    // both plane sides' bins as one sequence (their loads overlap)
+    const int2 r0 = bin_range(S, X, y0 / YB), r1 = bin_range(S, (X - 1) & (L - 1), y0 / YB);
+    const int n0 = r0.y - r0.x, nv = n0 + (r1.y - r1.x);
+    for (int v = tid; v < nv; v += NT) {
+      const int side = v < n0 ? 0 : 1;
+      const int i = side ? r1.x + (v - n0) : r0.x + v;
+      {
         const float4 a = S.sorted[2 * i];
         const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);
         const int ly0 = ay.i0 - y0;  // in [0, YB); row i1 is ly0 + 1 (a halo row at most)
@@ -619,73 +636,110 @@ __global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : 1)
 }
 
 // ===========================================================================
-// Backward z pass: the sums S = sum dchi and sum dchi * chi of the CTA's
-// rows (block partials, reduced by the last CTA into the adjoint scalars),
-// and the R2C along z of dchi -> kSpD.
+// Backward z pass over tiles of YB rows: the sums S = sum dchi and
+// sum dchi * chi (per-CTA partials, reduced by the last CTA into the adjoint
+// scalars) and the R2C along z of dchi -> kSpD. Persistent CTAs, each loading
+// the next tile's dchi and chi rows by bulk copies while it transforms the
+// current one.
 // ===========================================================================
 template <int L>
 constexpr size_t zbfwd_smem() {
-  return sizeof(float) * Pen<L>::YB * L + sizeof(float2) * L;
+  return sizeof(float) * 2 * 2 * Pen<L>::YB * L + sizeof(float2) * L;
 }
 
 template <int L>
-__global__ void __launch_bounds__(Pen<L>::ZNT, 4) k_zbfwd(const __grid_constant__ Solve s0,
-                                                       const Solve* __restrict__ tab) {
+__global__ void __launch_bounds__(Pen<L>::ZNT, 3) k_zbfwd(const __grid_constant__ Solve s0,
+                                                          const Solve* __restrict__ tab) {
   using P = Pen<L>;
-  constexpr int YB = P::YB, H = P::H;
+  constexpr int YB = P::YB, H = P::H, NT = P::ZNT, STAGE = 2 * YB * L;  // floats: dchi, chi
   const Solve& S = tab ? tab[blockIdx.z] : s0;
-  const int X = blockIdx.x / P::NYB, y0 = (blockIdx.x % P::NYB) * YB;
   const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
   extern __shared__ float4 smem4[];
-  float* rows = reinterpret_cast<float*>(smem4);  // [YB][L]
-  float2* twt = reinterpret_cast<float2*>(rows + YB * L);
-  __shared__ double red[2][P::ZNT / 32];
+  float* stg = reinterpret_cast<float*>(smem4);
+  float2* twt = reinterpret_cast<float2*>(stg + 2 * STAGE);
+  __shared__ uint64_t bar[2];
+  __shared__ double red[2][NT / 32];
   pdl_trigger();
-  for (int i = tid; i < L; i += P::ZNT) twt[i] = S.tw[i];
-  pdl_wait();
-  const size_t row0 = ((size_t)X * L + y0) * L;
-  const float4* g4 = reinterpret_cast<const float4*>(S.dchi + row0);
-  const float4* c4 = reinterpret_cast<const float4*>(S.chi + row0);
-  float accS = 0.f, accD = 0.f;
-  for (int i = tid; i < YB * L / 4; i += P::ZNT) {
-    const float4 a = g4[i], b = c4[i];
-    smem4[i] = a;
-    accS += (a.x + a.y) + (a.z + a.w);
-    accD += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+  for (int i = tid; i < L; i += NT) twt[i] = S.tw[i];
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  {
-    double dS = accS, dD = accD;
+  pdl_wait();
+  __syncthreads();
+  constexpr int ntiles = L * P::NYB;
+  constexpr uint32_t kRowBytes = YB * L * sizeof(float);
+  auto issue = [&](int tile, int st) {  // thread 0: dchi and chi rows of the tile
+    const size_t row0 = (size_t)tile * YB * L;  // tiles are consecutive blocks of rows
+    mbar_expect_tx(&bar[st], 2 * kRowBytes);
+    bulk_load(stg + st * STAGE, S.dchi + row0, kRowBytes, &bar[st]);
+    bulk_load(stg + st * STAGE + YB * L, S.chi + row0, kRowBytes, &bar[st]);
+  };
+  TwTab<L> twr{twt, t};
+  double dS = 0.0, dD = 0.0;
+  uint32_t ph = 0u;
+  int tile = blockIdx.x;
+  if (tid == 0 && tile < ntiles) issue(tile, 0);
+  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    const int st = it & 1;
+    const int next = tile + gridDim.x;
+    if (tid == 0 && next < ntiles) issue(next, st ^ 1);
+    const bool ok = __syncthreads_and(mbar_wait(&bar[st], (ph >> st) & 1u));
+    ph ^= 1u << st;
+    if (!ok) {
+      if (tid == 0) {
+        atomicOr(S.status, kStTimeout);
+        if (next < ntiles) mbar_wait(&bar[st ^ 1], (ph >> (st ^ 1)) & 1u);
+      }
+      break;
+    }
+    float* rows = stg + st * STAGE;  // dchi rows, then chi rows
+    const float4* g4 = reinterpret_cast<const float4*>(rows);
+    const float4* c4 = reinterpret_cast<const float4*>(rows + YB * L);
+    float accS = 0.f, accD = 0.f;
+    for (int i = tid; i < YB * L / 4; i += NT) {
+      const float4 a = g4[i], b = c4[i];
+      accS += (a.x + a.y) + (a.z + a.w);
+      accD += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+    }
+    dS += accS;
+    dD += accD;
+    __syncthreads();  // the sums have read the rows before the R2C rewrites them
+    for (int p0 = 0; p0 < YB / 2; p0 += P::ZG) {
+      const int pi = p0 + g;
+      if (pi < YB / 2) r2c_pair_ip<L>(t, twr, rows + 2 * pi * L);  // whole groups
+    }
+    __syncthreads();
+    constexpr int Q = H / 2;
+    const int X = tile / P::NYB, y0 = (tile % P::NYB) * YB;
+    const float4* r4 = reinterpret_cast<const float4*>(rows);
+    for (int i = tid; i < YB * Q; i += NT) {
+      const int ly = i / Q, q = i % Q;
+      reinterpret_cast<float4*>(S.spec[kSpD] + ((size_t)X * L + y0 + ly) * P::KP)[q] = r4[ly * Q + q];
+    }
+    fence_async_smem();  // this stage is refilled by a bulk copy two tiles on
+    __syncthreads();
+  }
+  // this CTA's partial sums in FP64, fixed order; the last CTA finalises
 #pragma unroll
-    for (int m = 16; m > 0; m >>= 1) {
-      dS += __shfl_xor_sync(0xffffffffu, dS, m);
-      dD += __shfl_xor_sync(0xffffffffu, dD, m);
-    }
-    if ((tid & 31) == 0) {
-      red[0][tid >> 5] = dS;
-      red[1][tid >> 5] = dD;
-    }
+  for (int m = 16; m > 0; m >>= 1) {
+    dS += __shfl_xor_sync(0xffffffffu, dS, m);
+    dD += __shfl_xor_sync(0xffffffffu, dD, m);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = dS;
+    red[1][tid >> 5] = dD;
   }
   __syncthreads();
   if (tid == 0) {
     double a = 0, b = 0;
-    for (int w = 0; w < P::ZNT / 32; ++w) {
+    for (int w = 0; w < NT / 32; ++w) {
       a += red[0][w];
       b += red[1][w];
     }
-    const size_t bid = (size_t)blockIdx.x;
-    S.part[2 * bid] = a;
-    S.part[2 * bid + 1] = b;
-  }
-  TwTab<L> twr{twt, t};
-  for (int p0 = 0; p0 < YB / 2; p0 += P::ZG) {
-    const int pi = p0 + g;
-    if (pi < YB / 2) r2c_pair_ip<L>(t, twr, rows + 2 * pi * L);
-  }
-  __syncthreads();
-  constexpr int Q = H / 2;
-  for (int i = tid; i < YB * Q; i += P::ZNT) {
-    const int ly = i / Q, q = i % Q;
-    reinterpret_cast<float4*>(S.spec[kSpD] + ((size_t)X * L + y0 + ly) * P::KP)[q] = smem4[ly * Q + q];
+    S.part[2 * blockIdx.x] = a;
+    S.part[2 * blockIdx.x + 1] = b;
   }
   last_block_finalize(S, 1, (int)gridDim.x, true);
 }
@@ -739,13 +793,15 @@ static cudaError_t launch_pencil_t(int kind, const Solve& s, const Solve* tab, i
     }
     case 2: {
       constexpr size_t a = zbfwd_smem<L>(), b = yfwd_smem<L, true>();
+      static int nz = 0;
       if (!attr_set[2]) {
         e = set_smem(k_zbfwd<L>, a);
         if (e == cudaSuccess) e = set_smem(k_yfwd<L, true>, b);
         if (e != cudaSuccess) return e;
+        nz = persistent_ctas(k_zbfwd<L>, P::ZNT, a, L * P::NYB, 1);
         attr_set[2] = true;
       }
-      e = launch_k(k_zbfwd<L>, gz, dim3(P::ZNT), a, st, 0, s, tab);
+      e = launch_k(k_zbfwd<L>, dim3(nz, 1, count), dim3(P::ZNT), a, st, 0, s, tab);
       if (e == cudaSuccess) e = launch_k(k_yfwd<L, true>, gy, dim3(ynt<L>()), b, st, 0, s, tab);
       return e;
     }
