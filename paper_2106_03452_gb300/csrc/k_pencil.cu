@@ -238,18 +238,21 @@ __global__ void __launch_bounds__(Pen<L>::ZNT, 3) k_zfwd(const __grid_constant__
     if (pi < NP) r2c_pair_ip<L>(t, twr, rows + 2 * pi * L);  // whole groups
   }
   __syncthreads();
-  // Packed rows out; the v_z channel takes i u_z (zero at DC and Nyquist).
-  constexpr int Q = H / 2;  // float4 per row
-  for (int i = tid; i < 4 * YB * Q; i += P::ZNT) {
-    const int ch = i / (YB * Q), rem = i % (YB * Q), ly = rem / Q, q = rem % Q;
-    float4 v = smem4[(ch * YB + ly) * Q + q];
-    if (ch == 1) {
-      const int s = 2 * q;
-      const float2 a = s == 0 ? czero() : cmul_iu(make_float2(v.x, v.y), iu[s]);
-      const float2 b = cmul_iu(make_float2(v.z, v.w), iu[s + 1]);
-      v = make_float4(a.x, a.y, b.x, b.y);
-    }
-    reinterpret_cast<float4*>(S.spec[ch] + ((size_t)X * L + y0 + ly) * P::KP)[q] = v;
+  // The v_z channel takes i u_z (zero at DC and Nyquist), then the packed rows
+  // go out by bulk copies, one row per thread.
+  float2* vz = reinterpret_cast<float2*>(rows + YB * L);
+  for (int i = tid; i < YB * H; i += P::ZNT) {
+    const int sl = i % H;
+    vz[i] = sl == 0 ? czero() : cmul_iu(vz[i], iu[sl]);
+  }
+  fence_async_smem();
+  __syncthreads();
+  if (tid < 4 * YB) {
+    const int ch = tid / YB, ly = tid % YB;
+    bulk_store(S.spec[ch] + ((size_t)X * L + y0 + ly) * P::KP, rows + (ch * YB + ly) * L,
+               H * (uint32_t)sizeof(float2));
+    tma_store_commit();
+    tma_store_wait_read();  // shared memory stays valid until read
   }
 }
 
@@ -475,8 +478,8 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
 template <int L, int NCH>
 struct ZiGeo {
   static constexpr int NR = Pen<L>::YB + 2;              // rows per tile
-  static constexpr int STAGE = NCH * NR * Pen<L>::KP;     // float2 per stage
-  static constexpr int NT = NCH == 1 ? 256 : 512;
+  static constexpr int STAGE = NCH * NR * (L / 2);        // float2 per stage (row pitch H)
+  static constexpr int NT = 256;
 };
 
 template <int L, int NCH>
@@ -485,7 +488,7 @@ constexpr size_t zinv_smem() {
 }
 
 template <int L, int NCH>
-__global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : 1)
+__global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : 2)
     k_zinv(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = Pen<L>;
   using Z = ZiGeo<L, NCH>;
@@ -506,17 +509,17 @@ __global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : 1)
   pdl_wait();
   __syncthreads();
   constexpr int ntiles = L * P::NYB;
-  auto issue = [&](int tile, int st) {  // thread 0: the tile's rows into stage st
+  auto issue = [&](int tile, int st) {  // thread 0: the tile's rows (H slots each) into stage st
     const int X = tile / P::NYB, y0 = (tile % P::NYB) * YB;
-    const int n1 = NR < L - y0 ? NR : L - y0;  // rows before the wrap to row 0
-    mbar_expect_tx(&bar[st], NCH * NR * KP * (uint32_t)sizeof(float2));
+    mbar_expect_tx(&bar[st], NCH * NR * H * (uint32_t)sizeof(float2));
 #pragma unroll
     for (int ch = 0; ch < NCH; ++ch) {
       const int buf = NCH == 1 ? kSpYa : (ch == 0 ? kSpC : (ch == 1 ? kSpYa : kSpYb));
       const float2* base = S.spec[buf] + (size_t)X * L * KP;
-      float2* dst = stg + st * Z::STAGE + ch * NR * KP;
-      bulk_load(dst, base + (size_t)y0 * KP, n1 * KP * (uint32_t)sizeof(float2), &bar[st]);
-      if (n1 < NR) bulk_load(dst + n1 * KP, base, (NR - n1) * KP * (uint32_t)sizeof(float2), &bar[st]);
+      float2* dst = stg + st * Z::STAGE + ch * NR * H;
+      for (int ly = 0; ly < NR; ++ly)  // row y0 + ly, wrapping to rows 0, 1
+        bulk_load(dst + ly * H, base + (size_t)((y0 + ly) & (L - 1)) * KP, H * (uint32_t)sizeof(float2),
+                  &bar[st]);
     }
   };
   float a_chi = 0.f, b_chi = 0.f;
@@ -543,10 +546,10 @@ __global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : 1)
     }
     float2* sb = stg + st * Z::STAGE;
     const int X = tile / P::NYB, y0 = (tile % P::NYB) * YB;
-    // pair p of channel ch: rows 2p (A) and 2p + 1 (B) of the stage
+    // pair p of channel ch: rows 2p (A) and 2p + 1 (B) of the stage, L float2
     auto pair = [&](int ch, int p) {
-      float2* ra = sb + (ch * NR + 2 * p) * KP;
-      return [ra](int i) -> float2& { return i < H ? ra[i] : ra[KP + i - H]; };
+      float2* ra = sb + (ch * NR + 2 * p) * H;
+      return [ra](int i) -> float2& { return ra[i]; };
     };
     constexpr int NP = NCH * NR / 2;
     for (int p0 = 0; p0 < NP; p0 += G) {
@@ -684,7 +687,10 @@ __global__ void __launch_bounds__(Pen<L>::ZNT, 3) k_zbfwd(const __grid_constant_
   for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
     const int st = it & 1;
     const int next = tile + gridDim.x;
-    if (tid == 0 && next < ntiles) issue(next, st ^ 1);
+    if (tid == 0 && next < ntiles) {
+      tma_store_wait_read();  // the rows stored from stage st ^ 1 last tile have been read
+      issue(next, st ^ 1);
+    }
     const bool ok = __syncthreads_and(mbar_wait(&bar[st], (ph >> st) & 1u));
     ph ^= 1u << st;
     if (!ok) {
@@ -710,17 +716,17 @@ __global__ void __launch_bounds__(Pen<L>::ZNT, 3) k_zbfwd(const __grid_constant_
       const int pi = p0 + g;
       if (pi < YB / 2) r2c_pair_ip<L>(t, twr, rows + 2 * pi * L);  // whole groups
     }
+    fence_async_smem();
     __syncthreads();
-    constexpr int Q = H / 2;
-    const int X = tile / P::NYB, y0 = (tile % P::NYB) * YB;
-    const float4* r4 = reinterpret_cast<const float4*>(rows);
-    for (int i = tid; i < YB * Q; i += NT) {
-      const int ly = i / Q, q = i % Q;
-      reinterpret_cast<float4*>(S.spec[kSpD] + ((size_t)X * L + y0 + ly) * P::KP)[q] = r4[ly * Q + q];
+    if (tid == 0) {  // packed rows out by bulk copies; waited for before the refill
+      const int X = tile / P::NYB, y0 = (tile % P::NYB) * YB;
+      for (int ly = 0; ly < YB; ++ly)
+        bulk_store(S.spec[kSpD] + ((size_t)X * L + y0 + ly) * P::KP, rows + ly * L,
+                   H * (uint32_t)sizeof(float2));
+      tma_store_commit();
     }
-    fence_async_smem();  // this stage is refilled by a bulk copy two tiles on
-    __syncthreads();
   }
+  if (tid == 0) tma_store_wait_read();  // shared memory stays valid until read
   // this CTA's partial sums in FP64, fixed order; the last CTA finalises
 #pragma unroll
   for (int m = 16; m > 0; m >>= 1) {

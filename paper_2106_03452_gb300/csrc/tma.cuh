@@ -104,6 +104,14 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, int c0, int 
       : "memory");
 }
 
+// Contiguous bulk copy shared -> global (bulk group of the issuing thread;
+// both addresses 16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+               "r"(smem_u32(ssrc)), "r"(bytes)
+               : "memory");
+}
+
 __device__ __forceinline__ void tma_store_commit() {
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
