@@ -11,14 +11,23 @@ namespace dpsr {
 // the block partials: a fixed-order FP64 reduction of the partials, then the
 // scalars of Eq. 4 (forward) or of its adjoint (backward).
 // ---------------------------------------------------------------------------
-// Sums of the n partial pairs: thread-strided sums, a warp tree, then the
-// warps in order (the same order on every run). Every thread of the block
-// calls it; the result is valid in thread 0. The partials come from other
+// Sums of the n partial pairs by one warp: lane-strided sums (the loads of a
+// lane issued together), then a butterfly over the lanes, the same order on
+// every run; the result is valid in every lane. The partials come from other
 // blocks of this grid, so they are read past L1.
-__device__ inline void reduce_parts(const double* part, int n, double& a, double& b) {
-  __shared__ double wa[32], wb[32];
+__device__ inline void reduce_parts_warp(const double* part, int n, double& a, double& b) {
+  const int lane = threadIdx.x & 31;
   double x = 0, y = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  int i = lane;
+  for (; i + 96 < n; i += 128) {
+    const double x0 = __ldcg(part + 2 * i), y0 = __ldcg(part + 2 * i + 1);
+    const double x1 = __ldcg(part + 2 * i + 64), y1 = __ldcg(part + 2 * i + 65);
+    const double x2 = __ldcg(part + 2 * i + 128), y2 = __ldcg(part + 2 * i + 129);
+    const double x3 = __ldcg(part + 2 * i + 192), y3 = __ldcg(part + 2 * i + 193);
+    x += ((x0 + x1) + (x2 + x3));
+    y += ((y0 + y1) + (y2 + y3));
+  }
+  for (; i < n; i += 32) {
     x += __ldcg(part + 2 * i);
     y += __ldcg(part + 2 * i + 1);
   }
@@ -27,19 +36,8 @@ __device__ inline void reduce_parts(const double* part, int n, double& a, double
     x += __shfl_xor_sync(0xffffffffu, x, m);
     y += __shfl_xor_sync(0xffffffffu, y, m);
   }
-  if ((threadIdx.x & 31) == 0) {
-    wa[threadIdx.x >> 5] = x;
-    wb[threadIdx.x >> 5] = y;
-  }
-  __syncthreads();
-  a = 0;
-  b = 0;
-  if (threadIdx.x == 0) {
-    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) {
-      a += wa[w];
-      b += wb[w];
-    }
-  }
+  a = x;
+  b = y;
 }
 
 // Thread 0: the scalars from the reduced sums.
@@ -85,21 +83,22 @@ __device__ inline void finalize_scalars(const Solve& S, double a, double b, bool
   }
 }
 
-// Every thread of a block calls this after its thread 0 has written the
-// block's partials to S.part[2 * bid, 2 * bid + 1]; the last of the
-// `nblocks` blocks of the solve reduces them and writes the scalars.
+// Warp 0 of every block calls this after its lane 0 has written the block's
+// partials to S.part[2 * bid, 2 * bid + 1]; the last of the `nblocks` blocks
+// of the solve to arrive reduces them and writes the scalars. The other
+// warps of the block need not wait.
 __device__ inline void last_block_finalize(const Solve& S, int ticket, int nblocks, bool bwd) {
-  __shared__ bool last;
-  if (threadIdx.x == 0) {
+  unsigned last = 0;
+  if ((threadIdx.x & 31) == 0) {
     __threadfence();  // this block's partials before its arrival
-    last = atomicAdd(&S.sc->ticket[ticket], 1u) == (unsigned)nblocks - 1u;
+    last = atomicAdd(&S.sc->ticket[ticket], 1u) == (unsigned)nblocks - 1u ? 1u : 0u;
   }
-  __syncthreads();
+  last = __shfl_sync(0xffffffffu, last, 0);
   if (!last) return;
   __threadfence();
   double a, b;
-  reduce_parts(S.part, nblocks, a, b);
-  if (threadIdx.x == 0) {
+  reduce_parts_warp(S.part, nblocks, a, b);
+  if ((threadIdx.x & 31) == 0) {
     finalize_scalars(S, a, b, bwd);
     S.sc->ticket[ticket] = 0;
   }

@@ -747,7 +747,7 @@ __global__ void __launch_bounds__(Pen<L>::ZNT, 3) k_zbfwd(const __grid_constant_
     S.part[2 * blockIdx.x] = a;
     S.part[2 * blockIdx.x + 1] = b;
   }
-  last_block_finalize(S, 1, (int)gridDim.x, true);
+  if (tid < 32) last_block_finalize(S, 1, (int)gridDim.x, true);
 }
 
 // ---------------------------------------------------------------------------

@@ -685,7 +685,7 @@ __global__ void __launch_bounds__(kNT, plane_minb<L, C>(2))
     }
   }
   // the last CTA of the solve turns the sums into the adjoint scalars
-  last_block_finalize(S, 1, (int)gridDim.x, true);
+  if (tid < 32) last_block_finalize(S, 1, (int)gridDim.x, true);
   cl.sync();
 }
 

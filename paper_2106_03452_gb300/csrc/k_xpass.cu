@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(XGeo<L>::NT, 2)
       S.part[2 * bid + 1] = ss;
       tma_store_wait_read();
     }
-    last_block_finalize(S, 0, (int)(gridDim.x * gridDim.y), false);
+    if (tid < 32) last_block_finalize(S, 0, (int)(gridDim.x * gridDim.y), false);
   } else {
     // FFT_x of (g_a FFT_zy(dchi) + g_w W~ + g_s delta_{x=0}): the three terms
     // of the adjoint spectrum combined before the transform (it is linear).
