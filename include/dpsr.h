@@ -165,7 +165,7 @@ DPSR_API int dpsr_plan_profile_read(dpsr_plan plan, double *ms, int *launches);
  * must not enter the allocator). The paper has no counterpart: this is a
  * deployment variant of dpsr_forward. points, normals and chi_out are device
  * pointers as in dpsr_forward; `stream` is a cudaStream_t (NULL = legacy).
- * All scratch memory is one static device array of about 9.2 MB that every
+ * All scratch memory is one static device array of about 14 MB that every
  * GPU loading the library holds until exit; the call allocates nothing.
  * Limits: r a power of two with 8 <= r <= 64, 1 <= N <= 65536; anything
  * larger returns DPSR_EINVAL. Every call shares the array and sees what the

@@ -49,7 +49,7 @@ constexpr size_t kOffBins = kOffPart + al(sizeof(double) * 2 * kParts);
 constexpr size_t kOffSorted = kOffBins + al(sizeof(int) * dpsr::bins_ints(kMaxR));
 constexpr size_t kOffCell = kOffSorted + al(sizeof(float4) * 2 * kMaxN);
 constexpr size_t kOffGfwd = kOffCell + al(sizeof(int) * kMaxN);
-constexpr size_t kScratchBytes = kOffGfwd + al(sizeof(float4) * 2 * kMaxN);  // ~9.2 MB
+constexpr size_t kScratchBytes = kOffGfwd + al(sizeof(float4) * 2 * kMaxN);  // ~14 MB
 
 }  // namespace
 
