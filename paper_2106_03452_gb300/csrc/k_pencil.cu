@@ -138,21 +138,6 @@ __device__ __forceinline__ void c2r_acc(int t, const Tw& tw, Acc x) {
   for (int j = 0; j < R1; ++j) x(t + T * j) = v[j];
 }
 
-// Persistent CTAs: the number of CTAs that fit the GPU at once (at most
-// `tiles`), for a kernel that loops over tiles with a stride of gridDim.x.
-template <class K>
-static int persistent_ctas(K fn, int nthreads, size_t smem, int tiles, int count) {
-  int dev = 0, sms = 0, occ = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nthreads, smem) != cudaSuccess) {
-    cudaGetLastError();
-    return tiles;
-  }
-  const int n = (sms * (occ > 0 ? occ : 1)) / (count > 0 ? count : 1);
-  return n < 1 ? 1 : (n < tiles ? n : tiles);
-}
-
 // ===========================================================================
 // Forward z pass: splat of the four channels into YB rows of plane X, R2C.
 // ===========================================================================

@@ -54,6 +54,21 @@ size_t plane_smem_bytes(int kind, int r, int C);
 cudaError_t launch_pencil(int kind, int r, const Solve& s, const Solve* tab, int count,
                           cudaStream_t st);
 size_t pencil_smem_bytes(int kind, int r);
+// Persistent CTAs: the number of CTAs that fit the GPU at once (at most
+// `tiles`), for a kernel that loops over tiles with a stride of gridDim.x.
+template <class K>
+inline int persistent_ctas(K fn, int nthreads, size_t smem, int tiles, int count) {
+  int dev = 0, sms = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nthreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return tiles;
+  }
+  const int n = (sms * (occ > 0 ? occ : 1)) / (count > 0 ? count : 1);
+  return n < 1 ? 1 : (n < tiles ? n : tiles);
+}
+
 // Kernel launches of one plane kind with path C (0: two pencil passes).
 inline int plane_launches(int C) { return C == 0 ? 2 : 1; }
 cudaError_t launch_xpass(bool bwd, int r, const Solve& s, const Solve* tab, int count,
