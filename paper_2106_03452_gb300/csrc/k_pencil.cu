@@ -148,7 +148,7 @@ constexpr size_t zfwd_smem() {
 }
 
 template <int L>
-__global__ void __launch_bounds__(Pen<L>::ZNT, 3) k_zfwd(const __grid_constant__ Solve s0,
+__global__ void __launch_bounds__(Pen<L>::ZNT, L >= 256 ? 3 : 4) k_zfwd(const __grid_constant__ Solve s0,
                                                       const Solve* __restrict__ tab) {
   using P = Pen<L>;
   constexpr int YB = P::YB, H = P::H;
@@ -258,7 +258,7 @@ constexpr size_t yfwd_smem() {
 }
 
 template <int L, bool BWD>
-__global__ void __launch_bounds__(ynt<L>(), BWD ? 4 : 3) k_yfwd(const __grid_constant__ Solve s0,
+__global__ void __launch_bounds__(ynt<L>(), BWD ? 4 : (L >= 256 ? 3 : 5)) k_yfwd(const __grid_constant__ Solve s0,
                                                    const Solve* __restrict__ tab) {
   using P = Pen<L>;
   constexpr int H = P::H, NT = ynt<L>();
@@ -473,7 +473,7 @@ constexpr size_t zinv_smem() {
 }
 
 template <int L, int NCH>
-__global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : 2)
+__global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : (L >= 256 ? 2 : 3))
     k_zinv(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = Pen<L>;
   using Z = ZiGeo<L, NCH>;

@@ -49,7 +49,7 @@ constexpr size_t xpass_smem() {
 // one kz column along x in registers (the box column doubles as its exchange
 // buffer), and TMA stores the results.
 template <int L, bool BWD>
-__global__ void __launch_bounds__(XGeo<L>::NT, 2)
+__global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 4)
     k_xpass(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = XGeo<L>;
   constexpr int NCH = BWD ? 2 : 3;
