@@ -138,7 +138,7 @@ DPSR_API int dpsr_grid_splat(float *grid, int r, const float *q, const float *va
  * launches since profiling was switched on or last read, and resets both.
  * ms and launches must hold DPSR_K_COUNT entries. */
 enum {
-    DPSR_K_BIN = 0,         /* x-cell bucketing of the points (3 small kernels) */
+    DPSR_K_BIN = 0,         /* bucketing of the points (2 small kernels) */
     DPSR_K_PLANE_FWD = 1,   /* splat + R2C(z) + FFT(y), one cluster per x-plane */
     DPSR_K_XPASS_FWD = 2,   /* FFT(x) + spectral solve (Eq. 3) + IFFT(x) */
     DPSR_K_FINAL_FWD = 3,   /* scalars of Eq. 4 */

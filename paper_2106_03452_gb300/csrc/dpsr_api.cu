@@ -575,8 +575,8 @@ int dpsr_forward(dpsr_plan p, const float* points, const float* normals, int64_t
     p->have_fwd = false;
     return cuda_err(e);
   }
-  // bin: 3 kernels, plane pass(es), x-pass (+ scalars), inverse plane pass(es)
-  p->last_launches = 4 + dpsr::plane_launches(p->C[0]) + dpsr::plane_launches(p->C[1]);
+  // bin: count (+ scan) and scatter, plane pass(es), x-pass (+ scalars), inverse plane pass(es)
+  p->last_launches = 3 + dpsr::plane_launches(p->C[0]) + dpsr::plane_launches(p->C[1]);
   cudaEventRecord(p->done_ev, st);
   p->s.N = s.N;
   p->s.points = points;

@@ -262,7 +262,7 @@ int dpsr_batch_launches(dpsr_batch b, int with_bwd) {
   if (!b) return -1;
   int n = 0;
   for (const auto& c : b->classes) {
-    n += 4 + dpsr::plane_launches(c.C[0]) + dpsr::plane_launches(c.C[1]);
+    n += 3 + dpsr::plane_launches(c.C[0]) + dpsr::plane_launches(c.C[1]);
     if (with_bwd) n += 2 + dpsr::plane_launches(c.C[2]) + dpsr::plane_launches(c.C[3]);
   }
   return n;

@@ -325,8 +325,9 @@ struct Scalars {
   float g_a, g_s, g_w;    // backward: G^ = g_a * FFT(dchi) + g_s + g_w * W^
   float c_mu;             // backward: weight of the stored lookup gradient
   // arrival counters of the last-block reductions: [0] forward x-pass,
-  // [1] backward plane pass (reset by the binning of every forward)
-  unsigned ticket[2];
+  // [1] backward plane pass (both reset by the binning of every forward),
+  // [2] the binning's count pass (reset by its last block)
+  unsigned ticket[3];
 };
 
 // Spectral buffers of a solve (Solve::spec) and what they hold between the

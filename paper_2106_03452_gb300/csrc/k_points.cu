@@ -12,18 +12,78 @@ __device__ __forceinline__ bool coord_ok(float c, int r) {
   return isfinite(c) && fabsf(c * (float)r) < 1073741824.f;  // |c r| < 2^30
 }
 
-// count[key]++ per point (see nbins for the key); validates the inputs
-// (non-finite or huge values raise kStBadInput and are replaced by 0 so that
-// indexing stays in range). Per-block histogram in shared memory, then one
-// global add per touched bin.
+// Bin key of a point (see nbins).
 __device__ __forceinline__ int bin_key(float x, float y, int r) {
   return axis_of(x, r).i0 * nybins(r) + axis_of(y, r).i0 / ybin(r);
 }
 
+// Exclusive scan of the nbins counts into off[0..nbins] and the scatter
+// cursors, by one block of NT threads (consecutive bins per thread, then a
+// block-wide scan of the per-thread sums); resets the counts and the
+// last-block arrival counters for the next call.
+template <int NT>
+__device__ void scan_bins(const Solve& S) {
+  static_assert(NT % 32 == 0 && NT <= 1024, "block of whole warps");
+  __shared__ int wsum[NT / 32];
+  constexpr int SEG = (4096 + NT - 1) / NT;  // bins per thread at r = 256
+  const int r = S.r, nb = nbins(r), i = threadIdx.x;
+  int* count = S.bins;
+  int* off = S.bins + nb;
+  int* cur = off + nb + 1;
+  const int lo = i * SEG;
+  int c[SEG];
+  int sum = 0;
+#pragma unroll
+  for (int k = 0; k < SEG; ++k) {
+    c[k] = lo + k < nb ? __ldcg(count + lo + k) : 0;
+    sum += c[k];
+  }
+  const int lane = i & 31, w = i >> 5;
+  int incl = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += v;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int v = lane < NT / 32 ? wsum[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d) v += u;
+    }
+    if (lane < NT / 32) wsum[lane] = v;  // inclusive over warps
+  }
+  __syncthreads();
+  int run = incl - sum + (w > 0 ? wsum[w - 1] : 0);
+#pragma unroll
+  for (int k = 0; k < SEG; ++k) {
+    if (lo + k < nb) {
+      off[lo + k] = run;
+      cur[lo + k] = run;
+      count[lo + k] = 0;  // ready for the next call
+      run += c[k];
+    }
+  }
+  if (i == NT - 1) off[nb] = wsum[NT / 32 - 1];
+  if (i == 0) {  // arrival counters of this solve's last-block reductions
+    S.sc->ticket[0] = 0;
+    S.sc->ticket[1] = 0;
+    S.sc->ticket[2] = 0;
+  }
+}
+
+// count[key]++ per point (see nbins for the key); validates the inputs
+// (non-finite or huge values raise kStBadInput and are replaced by 0 so that
+// indexing stays in range). Per-block histogram in shared memory, then one
+// global add per touched bin; the last block to finish scans the counts.
 __global__ void __launch_bounds__(256) k_bin_count(const __grid_constant__ Solve s0,
                                                    const Solve* __restrict__ tab) {
   static_assert(nbins(256) == 4096, "histogram size");
   __shared__ int h[4096];
+  __shared__ bool last;
   pdl_trigger();
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   const int r = S.r, nb = nbins(r);
@@ -49,61 +109,13 @@ __global__ void __launch_bounds__(256) k_bin_count(const __grid_constant__ Solve
   __syncthreads();
   for (int i = threadIdx.x; i < nb; i += blockDim.x)
     if (h[i]) atomicAdd(&S.bins[i], h[i]);
-}
-
-// Exclusive scan of the nbins counts into off[0..nbins] and the scatter
-// cursors: one block of 1024 threads per solve, four consecutive bins per
-// thread (coalesced 16-byte accesses).
-__global__ void __launch_bounds__(1024) k_bin_scan(const __grid_constant__ Solve s0,
-                                                   const Solve* __restrict__ tab) {
-  pdl_trigger();
-  pdl_wait();
-  const Solve& S = tab ? tab[blockIdx.x] : s0;
-  __shared__ int wsum[32];
-  const int r = S.r, nb = nbins(r), i = threadIdx.x;
-  int* count = S.bins;
-  int* off = S.bins + nb;
-  int* cur = off + nb + 1;
-  int c[4] = {0, 0, 0, 0};
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    if (4 * i + k < nb) c[k] = count[4 * i + k];
-  const int sum = c[0] + c[1] + c[2] + c[3];
-  // block-wide exclusive scan of the per-thread sums
-  const int lane = i & 31, w = i >> 5;
-  int incl = sum;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int v = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= d) incl += v;
-  }
-  if (lane == 31) wsum[w] = incl;
+  __threadfence();  // this thread's counts before the block's arrival
   __syncthreads();
-  if (w == 0) {
-    int v = wsum[lane];
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int u = __shfl_up_sync(0xffffffffu, v, d);
-      if (lane >= d) v += u;
-    }
-    wsum[lane] = v;  // inclusive over warps
-  }
+  if (threadIdx.x == 0) last = atomicAdd(&S.sc->ticket[2], 1u) == gridDim.x - 1u;
   __syncthreads();
-  int run = incl - sum + (w > 0 ? wsum[w - 1] : 0);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (4 * i + k < nb) {
-      off[4 * i + k] = run;
-      cur[4 * i + k] = run;
-      count[4 * i + k] = 0;  // ready for the next call
-      run += c[k];
-    }
-  }
-  if (i == 1023) off[nb] = wsum[31];
-  if (i == 0) {  // arrival counters of this solve's last-block reductions
-    S.sc->ticket[0] = 0;
-    S.sc->ticket[1] = 0;
-  }
+  if (!last) return;
+  __threadfence();
+  scan_bins<256>(S);
 }
 
 __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Solve s0,
@@ -131,7 +143,6 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Sol
 cudaError_t launch_bin(const Solve& s, const Solve* tab, int count, int nmax, cudaStream_t st) {
   const int blocks = min(max((nmax + 255) / 256, 1), 1184);
   cudaError_t e = launch_k(k_bin_count, dim3(blocks, 1, count), dim3(256), 0, st, 0, s, tab);
-  if (e == cudaSuccess) e = launch_k(k_bin_scan, dim3(count), dim3(1024), 0, st, 0, s, tab);
   if (e == cudaSuccess) e = launch_k(k_bin_scatter, dim3(blocks, 1, count), dim3(256), 0, st, 0, s, tab);
   return e;
 }

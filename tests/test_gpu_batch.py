@@ -64,8 +64,8 @@ def test_batch_equals_solo_and_oracle(oracle, monkeypatch, path):
         assert _rel(T[i][3].cpu(), ref) <= 1e-5
         rdp, rdn = oracle.backward(w["r"], w["sigma"], w["points"], w["normals"], w["dchi"])
         assert _rel(T[i][4].cpu(), rdp) <= 1e-4 and _rel(T[i][5].cpu(), rdn) <= 1e-4
-    # per grid size: bin (3), x-passes (2), combine, and one (cluster) or two
+    # per grid size: bin (2), x-passes (2), combine, and one (cluster) or two
     # (pencil) launches for each of the four plane kinds
     n = batch.launches(True)
-    assert 2 * 10 <= n <= 2 * 14 and (path != "pencil" or n == 2 * 14)
+    assert 2 * 9 <= n <= 2 * 13 and (path != "pencil" or n == 2 * 13)
     batch.close()
