@@ -26,6 +26,12 @@ struct XGeo {
   static constexpr int H = L / 2;
   static constexpr int NCHUNK = (H + 1 + KC - 1) / KC;
   static constexpr int BOX = L * KC;                        // float2 per box
+  static constexpr int KP = kpitch(L);                      // row pitch of the spectral buffers
+  // Up to r = 128 the forward reads W~ straight from L2 (the spectra stay
+  // resident there): two tiles per CTA instead of three, more CTAs per SM.
+  static constexpr bool WL2 = L <= 128;
+  template <bool BWD>
+  static constexpr int nch() { return BWD ? 2 : (WL2 ? 2 : 3); }
 };
 
 // G(k) = g(k) / (-2 pi |u|^2) with g separable: g1[kx] * (g1[ky] g1[kz]);
@@ -37,10 +43,22 @@ __device__ __forceinline__ float spectral_G(int kx, float gyz, float u2yz, const
   return __fdividef(g1[kx] * gyz, -6.28318530717958647692f * s);
 }
 
+// Stage twiddles of the thread (see Twid / TwTab).
+template <int L, class Tw>
+__device__ __forceinline__ Tw make_tw(const float2* tw, int t) {
+  if constexpr (std::is_same<Tw, Twid<L>>::value) {
+    Tw w;
+    w.load(t, tw);
+    return w;
+  } else {
+    return Tw{tw, t};
+  }
+}
+
 template <int L, bool BWD>
 constexpr size_t xpass_smem() {
   using P = XGeo<L>;
-  constexpr int NCH = BWD ? 2 : 3;
+  constexpr int NCH = P::template nch<BWD>();
   return 1024 + sizeof(float2) * ((size_t)NCH * P::BOX + L) + 3 * sizeof(float) * L;
 }
 
@@ -49,10 +67,10 @@ constexpr size_t xpass_smem() {
 // one kz column along x in registers (the box column doubles as its exchange
 // buffer), and TMA stores the results.
 template <int L, bool BWD>
-__global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 4)
+__global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
     k_xpass(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = XGeo<L>;
-  constexpr int NCH = BWD ? 2 : 3;
+  constexpr int NCH = P::template nch<BWD>();
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   const int kz0 = blockIdx.x * P::KC, ky = blockIdx.y;
   const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
@@ -75,7 +93,7 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 4)
     mbar_expect_tx(&bar, NCH * P::BOX * (uint32_t)sizeof(float2));
     tma_load_3d(box, &S.tmx[src0], kz0, ky, 0, &bar);
     tma_load_3d(box + P::BOX, &S.tmx[src1], kz0, ky, 0, &bar);
-    if constexpr (!BWD) tma_load_3d(box + 2 * P::BOX, &S.tmx[kSpW], kz0, ky, 0, &bar);
+    if constexpr (NCH == 3) tma_load_3d(box + 2 * P::BOX, &S.tmx[kSpW], kz0, ky, 0, &bar);
   }
   for (int i = tid; i < L; i += P::NT) {
     tw[i] = S.tw[i];
@@ -94,8 +112,10 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 4)
   const bool own = g < P::KC;
   const int kz = min(kz0 + gc, P::H);
   const bool valid = own && kz0 + g <= P::H;
-  Twid<L> twr;
-  twr.load(t, tw);
+  // r = 256: register twiddles and both column arrays live (two CTAs per
+  // SM); below, shared-memory twiddles and one array (more CTAs per SM)
+  using Tw = typename std::conditional<(L >= 256), Twid<L>, TwTab<L>>::type;
+  Tw twr = make_tw<L, Tw>(tw, t);
   const float gyz = g1[ky] * g1[kz], u2yz = u2[ky] + u2[kz];
   auto colref = [&](int ch) {
     float2* b = box + ch * P::BOX;
@@ -105,30 +125,63 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 4)
   auto c1 = colref(1);
   float2 a[P::R1];
   if constexpr (!BWD) {
-    // chi~ = G (FFT_x(D) + i u_x FFT_x(C))
-    float2 b[P::R1];
+    if constexpr (L >= 256) {
+      // chi~ = G (FFT_x(D) + i u_x FFT_x(C))
+      float2 b[P::R1];
 #pragma unroll
-    for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
-    fft_r<L, -1>(a, t, c0, twr);
+      for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
+      fft_r<L, -1>(a, t, c0, twr);
 #pragma unroll
-    for (int j = 0; j < P::R1; ++j) b[j] = c1(t + P::T * j);
-    fft_r<L, -1>(b, t, c1, twr);
+      for (int j = 0; j < P::R1; ++j) b[j] = c1(t + P::T * j);
+      fft_r<L, -1>(b, t, c1, twr);
 #pragma unroll
-    for (int j = 0; j < P::R1; ++j) {
-      const int kx = t + P::T * j;
-      const float G = spectral_G(kx, gyz, u2yz, g1, u2);
-      a[j] = cscale(cadd(a[j], cmul_iu(b[j], iu[kx])), G);
+      for (int j = 0; j < P::R1; ++j) {
+        const int kx = t + P::T * j;
+        const float G = spectral_G(kx, gyz, u2yz, g1, u2);
+        a[j] = cscale(cadd(a[j], cmul_iu(b[j], iu[kx])), G);
+      }
+    } else {
+      // chi~ = G (FFT_x(D) + i u_x FFT_x(C)); one column array live at a time:
+      // FFT_x(D) goes back to its column, FFT_x(C) meets it there.
+#pragma unroll
+      for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
+      fft_r<L, -1>(a, t, c0, twr);
+      if (own) {  // groups past the last column (tiny r) only shadow it
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = a[j];
+      }
+#pragma unroll
+      for (int j = 0; j < P::R1; ++j) a[j] = c1(t + P::T * j);
+      fft_r<L, -1>(a, t, c1, twr);
+#pragma unroll
+      for (int j = 0; j < P::R1; ++j) {
+        const int kx = t + P::T * j;  // this lane wrote c0(kx) above
+        const float G = spectral_G(kx, gyz, u2yz, g1, u2);
+        a[j] = cscale(cadd(c0(kx), cmul_iu(a[j], iu[kx])), G);
+      }
     }
     fft_r<L, +1>(a, t, c0, twr);  // P = unnormalised IFFT_x(chi~)
-    // Spectral sums of Eq. 4, by Parseval along x against the x-domain W~:
+    // Spectral sums of Eq. 4, by Parseval along x against the x-domain W~
+    // (its tile, or up to r = 128 its column straight from L2):
     // sum_kx conj(W~(kx)) chi~(kx) = sum_x conj(W~_x(x)) P(x),
     // sum_kx chi~(kx) = P(x = 0).
-    auto c2 = colref(2);
     float am = 0.f, as = 0.f;
+    if (valid) {
+      if constexpr (NCH == 3) {
+        auto c2 = colref(2);
 #pragma unroll
-    for (int j = 0; j < P::R1; ++j) {
-      const float2 w = c2(t + P::T * j);
-      am += w.x * a[j].x + w.y * a[j].y;
+        for (int j = 0; j < P::R1; ++j) {
+          const float2 w = c2(t + P::T * j);
+          am += w.x * a[j].x + w.y * a[j].y;
+        }
+      } else {
+        const float2* wc = S.spec[kSpW] + (size_t)ky * P::KP + kz;
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) {
+          const float2 w = __ldcg(wc + (size_t)(t + P::T * j) * L * P::KP);
+          am += w.x * a[j].x + w.y * a[j].y;
+        }
+      }
     }
     if (t == 0) as = a[0].x;
     const float wz = (kz == 0 || kz == P::H) ? 1.f : 2.f;
@@ -175,21 +228,45 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 4)
       if (x == 0) a[j].x += gs;
     }
     fft_r<L, -1>(a, t, c0, twr);
-    float2 b[P::R1];
-#pragma unroll
-    for (int j = 0; j < P::R1; ++j) {
-      const int kx = t + P::T * j;
-      const float2 f = cscale(a[j], spectral_G(kx, gyz, u2yz, g1, u2));
-      a[j] = f;
-      b[j] = cmul_iu(f, -iu[kx]);
-    }
-    fft_r<L, +1>(a, t, c0, twr);
-    fft_r<L, +1>(b, t, c1, twr);
-    if (own) {
+    if constexpr (L >= 256) {
+      float2 b[P::R1];
 #pragma unroll
       for (int j = 0; j < P::R1; ++j) {
-        c0(t + P::T * j) = a[j];
-        c1(t + P::T * j) = b[j];
+        const int kx = t + P::T * j;
+        const float2 f = cscale(a[j], spectral_G(kx, gyz, u2yz, g1, u2));
+        a[j] = f;
+        b[j] = cmul_iu(f, -iu[kx]);
+      }
+      fft_r<L, +1>(a, t, c0, twr);
+      fft_r<L, +1>(b, t, c1, twr);
+      if (own) {
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) {
+          c0(t + P::T * j) = a[j];
+          c1(t + P::T * j) = b[j];
+        }
+      }
+    } else {
+      // F = G (.); Q2's input -i u_x F goes to the column of W~ (read above by
+      // this group), Q1 = IFFT_x(F) is transformed from registers first
+#pragma unroll
+      for (int j = 0; j < P::R1; ++j) {
+        const int kx = t + P::T * j;
+        a[j] = cscale(a[j], spectral_G(kx, gyz, u2yz, g1, u2));
+        if (own) c1(kx) = cmul_iu(a[j], -iu[kx]);
+      }
+      fft_r<L, +1>(a, t, c0, twr);
+      if (own) {
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = a[j];
+      }
+      group_sync<P::T>();
+#pragma unroll
+      for (int j = 0; j < P::R1; ++j) a[j] = c1(t + P::T * j);
+      fft_r<L, +1>(a, t, c1, twr);
+      if (own) {
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) c1(t + P::T * j) = a[j];
       }
     }
     fence_async_smem();
