@@ -26,6 +26,10 @@ struct BatchClass {
   Solve* dtab = nullptr;     // device table, one descriptor per member
   int nmax = 0;
   int C[4] = {1, 1, 1, 1};
+  // Classes run side by side: each on its own stream, forked from and
+  // joined back into the batch stream (also inside a captured graph).
+  cudaStream_t st = nullptr;
+  cudaEvent_t join = nullptr;
 };
 
 struct dpsr_batch_s {
@@ -37,6 +41,7 @@ struct dpsr_batch_s {
   std::vector<int64_t> nmax;
   std::vector<BatchClass> classes;
   Solve* hstage = nullptr;  // pinned staging of the tables
+  cudaEvent_t fork = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_bwd = -1;
   bool have_fwd = false;
@@ -56,32 +61,44 @@ int upload(dpsr_batch b) {
   return DPSR_OK;
 }
 
-cudaError_t launch_fwd(dpsr_batch b) {
-  cudaStream_t st = b->stream;
-  const Solve dummy = {};
+// Launch `body(class, stream)` for every class on the class's stream, after
+// everything queued on the batch stream, and make the batch stream wait for
+// all of them.
+template <class F>
+cudaError_t per_class(dpsr_batch b, F body) {
+  cudaError_t e = cudaEventRecord(b->fork, b->stream);
   for (auto& c : b->classes) {
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c.st, b->fork, 0);
+    if (e == cudaSuccess) e = body(c, c.st);
+    if (e == cudaSuccess) e = cudaEventRecord(c.join, c.st);
+  }
+  for (auto& c : b->classes)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, c.join, 0);
+  return e;
+}
+
+cudaError_t launch_fwd(dpsr_batch b) {
+  const Solve dummy = {};
+  return per_class(b, [&](BatchClass& c, cudaStream_t st) {
     const int n = (int)c.members.size();
     cudaError_t e = dpsr::launch_bin(dummy, c.dtab, n, c.nmax, st);
     if (e == cudaSuccess) e = dpsr::launch_plane(0, c.r, c.C[0], dummy, c.dtab, n, st);
     if (e == cudaSuccess) e = dpsr::launch_xpass(false, c.r, dummy, c.dtab, n, st);
     if (e == cudaSuccess) e = dpsr::launch_plane(1, c.r, c.C[1], dummy, c.dtab, n, st);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+    return e;
+  });
 }
 
 cudaError_t launch_bwd(dpsr_batch b) {
-  cudaStream_t st = b->stream;
   const Solve dummy = {};
-  for (auto& c : b->classes) {
+  return per_class(b, [&](BatchClass& c, cudaStream_t st) {
     const int n = (int)c.members.size();
     cudaError_t e = dpsr::launch_plane(2, c.r, c.C[2], dummy, c.dtab, n, st);
     if (e == cudaSuccess) e = dpsr::launch_xpass(true, c.r, dummy, c.dtab, n, st);
     if (e == cudaSuccess) e = dpsr::launch_plane(3, c.r, c.C[3], dummy, c.dtab, n, st);
     if (e == cudaSuccess) e = dpsr::launch_combine(dummy, c.dtab, n, c.nmax, st);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+    return e;
+  });
 }
 
 void drop_graph(dpsr_batch b) {
@@ -124,12 +141,18 @@ int dpsr_batch_create(int count, const int* r, const float* sigma, const int64_t
           c.nmax = std::max<int>(c.nmax, (int)n_max[i]);
         }
       for (int k = 0; k < 4; ++k) c.C[k] = dpsr_internal_cluster(b->plans[c.members[0]], k);
-      if (cudaMalloc(&c.dtab, sizeof(Solve) * c.members.size()) != cudaSuccess) {
+      if (cudaMalloc(&c.dtab, sizeof(Solve) * c.members.size()) != cudaSuccess ||
+          cudaStreamCreateWithFlags(&c.st, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c.join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         rc = DPSR_ENOMEM;
       }
       b->classes.push_back(c);
     }
+  }
+  if (rc == DPSR_OK && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    rc = DPSR_ENOMEM;
   }
   if (rc == DPSR_OK && cudaMallocHost(&b->hstage, sizeof(Solve) * count) != cudaSuccess) {
     cudaGetLastError();
@@ -147,8 +170,13 @@ int dpsr_batch_destroy(dpsr_batch b) {
   if (!b) return DPSR_EINVAL;
   cudaStreamSynchronize(b->stream);
   drop_graph(b);
-  for (auto& c : b->classes)
+  for (auto& c : b->classes) {
+    if (c.st) cudaStreamSynchronize(c.st);
+    if (c.join) cudaEventDestroy(c.join);
+    if (c.st) cudaStreamDestroy(c.st);
     if (c.dtab) cudaFree(c.dtab);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   for (dpsr_plan p : b->plans)
     if (p) dpsr_plan_destroy(p);
   if (b->hstage) cudaFreeHost(b->hstage);
