@@ -396,7 +396,7 @@ def bench_serving(args):
     """Config 5: Poisson arrivals at 200 req/s, each an ellipsoid-union cloud
     with N log-uniform in [1000, 200000], r in {64, 128, 256} (0.5 / 0.35 /
     0.15), 30% forward + backward, admitted by an 8 GB device budget. The
-    continuous-batching server (8 stream slots) against a per-solve loop (the
+    continuous-batching server (--serve-slots stream slots) against a per-solve loop (the
     same server with one slot), first replayed in real time (latency =
     completion - arrival), then saturated (the first 400 requests submitted
     at once) for throughput."""
@@ -406,7 +406,8 @@ def bench_serving(args):
     keys = [(r, b) for r in (64, 128, 256) for b in (False, True)]
     out = {"rate_per_s": 200.0, "duration_s": args.serve_seconds, "requests": len(trace),
            "budget_bytes": 8 << 30}
-    for slots, label in ((8, "served"), (1, "loop")):
+    out["slots"] = args.serve_slots
+    for slots, label in ((args.serve_slots, "served"), (1, "loop")):
         srv = serve.Server(8 << 30, slots)
         serve.warm(srv, pool)
         ring = serve.OutputRing()
@@ -491,6 +492,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     args = ap.parse_args()
     if args.warmup < 3:
