@@ -125,48 +125,50 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
   auto c1 = colref(1);
   float2 a[P::R1];
   if constexpr (!BWD) {
-    if constexpr (L >= 256) {
-      // chi~ = G (FFT_x(D) + i u_x FFT_x(C))
-      float2 b[P::R1];
-#pragma unroll
-      for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
-      fft_r<L, -1>(a, t, c0, twr);
-#pragma unroll
-      for (int j = 0; j < P::R1; ++j) b[j] = c1(t + P::T * j);
-      fft_r<L, -1>(b, t, c1, twr);
-#pragma unroll
-      for (int j = 0; j < P::R1; ++j) {
-        const int kx = t + P::T * j;
-        const float G = spectral_G(kx, gyz, u2yz, g1, u2);
-        a[j] = cscale(cadd(a[j], cmul_iu(b[j], iu[kx])), G);
-      }
-    } else {
-      // chi~ = G (FFT_x(D) + i u_x FFT_x(C)); one column array live at a time:
-      // FFT_x(D) goes back to its column, FFT_x(C) meets it there.
-#pragma unroll
-      for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
-      fft_r<L, -1>(a, t, c0, twr);
-      if (own) {  // groups past the last column (tiny r) only shadow it
-#pragma unroll
-        for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = a[j];
-      }
-#pragma unroll
-      for (int j = 0; j < P::R1; ++j) a[j] = c1(t + P::T * j);
-      fft_r<L, -1>(a, t, c1, twr);
-#pragma unroll
-      for (int j = 0; j < P::R1; ++j) {
-        const int kx = t + P::T * j;  // this lane wrote c0(kx) above
-        const float G = spectral_G(kx, gyz, u2yz, g1, u2);
-        a[j] = cscale(cadd(c0(kx), cmul_iu(a[j], iu[kx])), G);
-      }
-    }
-    fft_r<L, +1>(a, t, c0, twr);  // P = unnormalised IFFT_x(chi~)
-    // Spectral sums of Eq. 4, by Parseval along x against the x-domain W~
-    // (its tile, or up to r = 128 its column straight from L2):
-    // sum_kx conj(W~(kx)) chi~(kx) = sum_x conj(W~_x(x)) P(x),
-    // sum_kx chi~(kx) = P(x = 0).
-    float am = 0.f, as = 0.f;
+    // Columns past Nyquist (the last kz tile) hold zeros and are not stored:
+    // their groups skip the transforms.
+    float am = 0.f, as = 0.f, wz = 0.f;
     if (valid) {
+      if constexpr (L >= 256) {
+        // chi~ = G (FFT_x(D) + i u_x FFT_x(C))
+        float2 b[P::R1];
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
+        fft_r<L, -1>(a, t, c0, twr);
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) b[j] = c1(t + P::T * j);
+        fft_r<L, -1>(b, t, c1, twr);
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) {
+          const int kx = t + P::T * j;
+          const float G = spectral_G(kx, gyz, u2yz, g1, u2);
+          a[j] = cscale(cadd(a[j], cmul_iu(b[j], iu[kx])), G);
+        }
+      } else {
+        // chi~ = G (FFT_x(D) + i u_x FFT_x(C)); one column array live at a time:
+        // FFT_x(D) goes back to its column, FFT_x(C) meets it there.
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
+        fft_r<L, -1>(a, t, c0, twr);
+        if (own) {  // groups past the last column (tiny r) only shadow it
+#pragma unroll
+          for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = a[j];
+        }
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) a[j] = c1(t + P::T * j);
+        fft_r<L, -1>(a, t, c1, twr);
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) {
+          const int kx = t + P::T * j;  // this lane wrote c0(kx) above
+          const float G = spectral_G(kx, gyz, u2yz, g1, u2);
+          a[j] = cscale(cadd(c0(kx), cmul_iu(a[j], iu[kx])), G);
+        }
+      }
+      fft_r<L, +1>(a, t, c0, twr);  // P = unnormalised IFFT_x(chi~)
+      // Spectral sums of Eq. 4, by Parseval along x against the x-domain W~
+      // (its tile, or up to r = 128 its column straight from L2):
+      // sum_kx conj(W~(kx)) chi~(kx) = sum_x conj(W~_x(x)) P(x),
+      // sum_kx chi~(kx) = P(x = 0).
       if constexpr (NCH == 3) {
         auto c2 = colref(2);
 #pragma unroll
@@ -182,13 +184,12 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
           am += w.x * a[j].x + w.y * a[j].y;
         }
       }
-    }
-    if (t == 0) as = a[0].x;
-    const float wz = (kz == 0 || kz == P::H) ? 1.f : 2.f;
-    if (!valid) am = as = 0.f;
-    if (own) {
+      if (t == 0) as = a[0].x;
+      wz = (kz == 0 || kz == P::H) ? 1.f : 2.f;
+      if (own) {
 #pragma unroll
-      for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = a[j];
+        for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = a[j];
+      }
     }
     double dm = (double)am * wz, ds = (double)as * wz;
 #pragma unroll
