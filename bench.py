@@ -407,11 +407,11 @@ def bench_serving(args):
     out = {"rate_per_s": 200.0, "duration_s": args.serve_seconds, "requests": len(trace),
            "budget_bytes": 8 << 30}
     out["slots"] = args.serve_slots
+    ring = serve.OutputRing()  # pinned output buffers, shared by both servers
+    ring.prefill(keys, args.serve_slots + 2, 200000)
     for slots, label in ((args.serve_slots, "served"), (1, "loop")):
         srv = serve.Server(8 << 30, slots)
-        serve.warm(srv, pool)
-        ring = serve.OutputRing()
-        ring.prefill(keys, slots + 2, 200000)
+        serve.warm(srv, pool, slots=slots, n=200000)
         t0 = time.perf_counter()
         res = serve.replay(trace, srv, pool, realtime=True, ring=ring)
         wall = time.perf_counter() - t0

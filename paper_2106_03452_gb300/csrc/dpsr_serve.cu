@@ -51,8 +51,9 @@ struct PooledPlan {
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  int64_t ticket = -1;  // -1: free
-  int pooled = -1;      // index into the plan pool
+  int64_t ticket = -1;   // -1: free
+  int pooled = -1;       // index into the plan pool
+  bool claimed = false;  // admitted, its work being queued
 };
 
 }  // namespace
@@ -82,8 +83,8 @@ size_t request_bytes(int r, int64_t N, bool bwd) {
   return dpsr_plan_workspace_bytes(r, N, bwd) + 2 * grid + 4 * (size_t)N * 3 * sizeof(float);
 }
 
-// Find or create an idle plan of grid size r holding N points. Called with
-// the lock held, from the worker thread only.
+// Find or create an idle plan of grid size r holding N points. Called from
+// the worker thread only (the pool belongs to it).
 int get_plan(dpsr_server s, int r, int64_t N) {
   int best = -1;
   for (size_t i = 0; i < s->pool.size(); ++i) {
@@ -176,7 +177,10 @@ void worker_main(dpsr_server s) {
     if (progress) s->cv_done.notify_all();
     // admissions (FIFO): a request enters when a slot is free and its bytes
     // fit the budget next to the running ones; one too large for the whole
-    // budget is rejected.
+    // budget is rejected. The CUDA work of the admitted requests is queued
+    // with the lock released (submit, poll and wait only need the lock for
+    // the queue and the request table; slots and plans belong to this thread).
+    std::vector<std::pair<Slot*, Request*>> admit;
     while (!s->queue.empty()) {
       Request& q = s->reqs[s->queue.front()];
       if (q.bytes > s->budget) {
@@ -189,22 +193,35 @@ void worker_main(dpsr_server s) {
       if (s->used + q.bytes > s->budget) break;
       Slot* free_slot = nullptr;
       for (Slot& sl : s->slots)
-        if (sl.ticket < 0) {
+        if (sl.ticket < 0 && !sl.claimed) {
           free_slot = &sl;
           break;
         }
       if (!free_slot) break;
       s->queue.pop_front();
-      const int rc = launch(s, *free_slot, q);
-      if (rc != DPSR_OK) {
-        q.status = rc;
-        q.done = true;
-        s->cv_done.notify_all();
-        continue;
-      }
+      free_slot->claimed = true;
       s->used += q.bytes;
-      ++s->admitted;
-      ++active;
+      admit.emplace_back(free_slot, &q);  // the table never moves its entries
+    }
+    if (!admit.empty()) {
+      lk.unlock();
+      std::vector<int> rcs;
+      for (auto& a : admit) rcs.push_back(launch(s, *a.first, *a.second));
+      lk.lock();
+      for (size_t i = 0; i < admit.size(); ++i) {
+        Slot& sl = *admit[i].first;
+        Request& q = *admit[i].second;
+        sl.claimed = false;
+        if (rcs[i] != DPSR_OK) {
+          q.status = rcs[i];
+          q.done = true;
+          s->used -= q.bytes;
+          s->cv_done.notify_all();
+          continue;
+        }
+        ++s->admitted;
+        ++active;
+      }
       progress = true;
     }
     if (active > s->max_active) s->max_active = active;

@@ -163,14 +163,23 @@ def summarize(results, wall_s):
             "solves_per_s": len(results) / wall_s, "wall_s": wall_s}
 
 
-def warm(server: Server, pool: InputPool, rs=(64, 128, 256)):
-    """One fwd+bwd request per grid size: creates the pooled plans and runs
-    the autotuner outside the measured window."""
+def warm(server: Server, pool: InputPool, rs=(64, 128, 256), slots=1, n=20000):
+    """Fill the server's plan pool before a measurement: for every grid size,
+    `slots` concurrent fwd+bwd requests of n points, so that the pool holds a
+    plan per slot at full capacity (plans are created, and grown, only when
+    no pooled plan fits; creating or growing one allocates device memory,
+    which would otherwise stall the GPU in the middle of a measurement). The
+    first request per grid size also runs the autotuner, alone."""
     ring = OutputRing()
     for r in rs:
-        pts, nrm = pool.inputs(0, 20000)
-        chi, dp, dn = ring.get(r, 20000, True)
-        t = server.submit(r, pts, nrm, chi, pool.dchi[r], dp, dn)
-        st = server.wait(t, 120.0)
+        pts, nrm = pool.inputs(0, n)
+        chi, dp, dn = ring.get(r, n, True)
+        st = server.wait(server.submit(r, pts, nrm, chi, pool.dchi[r], dp, dn), 120.0)
         if st != 0:
             raise RuntimeError(f"warm-up request r={r} failed with status {st}")
+        bufs = [ring.get(r, n, True) for _ in range(slots)]
+        tickets = [server.submit(r, pts, nrm, c, pool.dchi[r], d, e) for (c, d, e) in bufs]
+        for t in tickets:
+            st = server.wait(t, 120.0)
+            if st != 0:
+                raise RuntimeError(f"warm-up request r={r} failed with status {st}")
