@@ -624,22 +624,30 @@ __global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : (L >= 256 ? 
 }
 
 // ===========================================================================
-// Backward z pass over tiles of YB rows: the sums S = sum dchi and
+// Backward z pass over tiles of ZB rows: the sums S = sum dchi and
 // sum dchi * chi (per-CTA partials, reduced by the last CTA into the adjoint
 // scalars) and the R2C along z of dchi -> kSpD. Persistent CTAs, each loading
 // the next tile's dchi and chi rows by bulk copies while it transforms the
-// current one.
+// current one. The pass reads no points, so its tile height is free: two
+// rows per FFT group, every group busy.
 // ===========================================================================
 template <int L>
+struct ZbGeo {
+  static constexpr int NT = 128, G = NT / Shape<L>::T;
+  static constexpr int ZB = 2 * G < L ? 2 * G : L;  // rows per tile
+};
+
+template <int L>
 constexpr size_t zbfwd_smem() {
-  return sizeof(float) * 2 * 2 * Pen<L>::YB * L + sizeof(float2) * L;
+  return sizeof(float) * 2 * 2 * ZbGeo<L>::ZB * L + sizeof(float2) * L;
 }
 
 template <int L>
-__global__ void __launch_bounds__(Pen<L>::ZNT, 3) k_zbfwd(const __grid_constant__ Solve s0,
+__global__ void __launch_bounds__(ZbGeo<L>::NT, 3) k_zbfwd(const __grid_constant__ Solve s0,
                                                           const Solve* __restrict__ tab) {
   using P = Pen<L>;
-  constexpr int YB = P::YB, H = P::H, NT = P::ZNT, STAGE = 2 * YB * L;  // floats: dchi, chi
+  constexpr int YB = ZbGeo<L>::ZB, H = P::H, NT = ZbGeo<L>::NT, ZG = ZbGeo<L>::G;
+  constexpr int STAGE = 2 * YB * L;  // floats: dchi, chi
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
   extern __shared__ float4 smem4[];
@@ -656,7 +664,7 @@ __global__ void __launch_bounds__(Pen<L>::ZNT, 3) k_zbfwd(const __grid_constant_
   }
   pdl_wait();
   __syncthreads();
-  constexpr int ntiles = L * P::NYB;
+  constexpr int ntiles = L * (L / YB);
   constexpr uint32_t kRowBytes = YB * L * sizeof(float);
   auto issue = [&](int tile, int st) {  // thread 0: dchi and chi rows of the tile
     const size_t row0 = (size_t)tile * YB * L;  // tiles are consecutive blocks of rows
@@ -697,14 +705,14 @@ __global__ void __launch_bounds__(Pen<L>::ZNT, 3) k_zbfwd(const __grid_constant_
     dS += accS;
     dD += accD;
     __syncthreads();  // the sums have read the rows before the R2C rewrites them
-    for (int p0 = 0; p0 < YB / 2; p0 += P::ZG) {
+    for (int p0 = 0; p0 < YB / 2; p0 += ZG) {
       const int pi = p0 + g;
       if (pi < YB / 2) r2c_pair_ip<L>(t, twr, rows + 2 * pi * L);  // whole groups
     }
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {  // packed rows out by bulk copies; waited for before the refill
-      const int X = tile / P::NYB, y0 = (tile % P::NYB) * YB;
+      const int X = tile / (L / YB), y0 = (tile % (L / YB)) * YB;
       for (int ly = 0; ly < YB; ++ly)
         bulk_store(S.spec[kSpD] + ((size_t)X * L + y0 + ly) * P::KP, rows + ly * L,
                    H * (uint32_t)sizeof(float2));
@@ -789,10 +797,10 @@ static cudaError_t launch_pencil_t(int kind, const Solve& s, const Solve* tab, i
         e = set_smem(k_zbfwd<L>, a);
         if (e == cudaSuccess) e = set_smem(k_yfwd<L, true>, b);
         if (e != cudaSuccess) return e;
-        nz = persistent_ctas(k_zbfwd<L>, P::ZNT, a, L * P::NYB, 1);
+        nz = persistent_ctas(k_zbfwd<L>, ZbGeo<L>::NT, a, L * (L / ZbGeo<L>::ZB), 1);
         attr_set[2] = true;
       }
-      e = launch_k(k_zbfwd<L>, dim3(nz, 1, count), dim3(P::ZNT), a, st, 0, s, tab);
+      e = launch_k(k_zbfwd<L>, dim3(nz, 1, count), dim3(ZbGeo<L>::NT), a, st, 0, s, tab);
       if (e == cudaSuccess) e = launch_k(k_yfwd<L, true>, gy, dim3(ynt<L>()), b, st, 0, s, tab);
       return e;
     }
