@@ -133,7 +133,8 @@ def _barrier(dist):
 
 
 # ----------------------------------------------------------------------------
-# byte model (per launch / per solve), see the design doc
+# algorithmic byte model (per launch / per solve): the bytes each plane kind
+# must move at least, whichever path (cluster or pencil) runs it
 # ----------------------------------------------------------------------------
 def kernel_bytes(r: int, N: int):
     U = 4 * r ** 3                      # one FP32 real grid
