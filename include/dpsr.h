@@ -240,6 +240,15 @@ DPSR_API int dpsr_server_stats(dpsr_server server, int64_t *out4);
 /* Static description of an error code. */
 DPSR_API const char *dpsr_strerror(int status);
 
+/* Failure-detection check of the device side: launches one kernel whose
+ * bounded wait (the same wait every TMA and DSMEM barrier of the library
+ * uses) is on a barrier that nothing ever completes; the wait must give up
+ * after limit_s seconds (0 < limit_s <= 10) and report it in a device status
+ * word, leaving the GPU and the context usable. Synchronous. Returns
+ * DPSR_ETIMEOUT when the wait ran out as designed, DPSR_OK if it did not
+ * (a defect), DPSR_EINVAL or DPSR_ECUDA on errors. */
+DPSR_API int dpsr_check_bounded_wait(double limit_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -346,6 +346,25 @@ const char* dpsr_strerror(int st) {
   }
 }
 
+int dpsr_check_bounded_wait(double limit_s) {
+  if (!(limit_s > 0.0 && limit_s <= 10.0)) return DPSR_EINVAL;
+  unsigned* d = nullptr;
+  cudaStream_t st = nullptr;
+  unsigned h = 0;
+  int rc = DPSR_ECUDA;
+  if (cudaMalloc(&d, sizeof(unsigned)) == cudaSuccess &&
+      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+      cudaMemsetAsync(d, 0, sizeof(unsigned), st) == cudaSuccess &&
+      dpsr::launch_wait_probe(d, limit_s, st) == cudaSuccess &&
+      cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+      cudaStreamSynchronize(st) == cudaSuccess)
+    rc = (h & dpsr::kStTimeout) ? DPSR_ETIMEOUT : DPSR_OK;
+  if (rc == DPSR_ECUDA) cudaGetLastError();
+  if (st) cudaStreamDestroy(st);
+  if (d) cudaFree(d);
+  return rc;
+}
+
 size_t dpsr_plan_workspace_bytes(int r, int64_t n_max, int with_bwd) {
   (void)with_bwd;  // the backward reuses the forward's buffers
   if (!valid_r(r) || n_max < 0) return 0;

@@ -5,6 +5,7 @@
 
 #include "dpsr_dev.cuh"
 #include "launch.h"
+#include "tma.cuh"
 
 namespace dpsr {
 
@@ -216,6 +217,24 @@ __global__ void __launch_bounds__(256) k_grid_splat(float* __restrict__ grid, in
       atomicAdd(&grid[j], w * v);
     }
   }
+}
+
+// A bounded wait on a barrier that nothing completes (see
+// dpsr_check_bounded_wait): it must give up after limit_ns and say so.
+__global__ void k_wait_probe(unsigned* status, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = __syncthreads_and(mbar_wait(&bar, 0, limit_ns));
+  if (!ok && threadIdx.x == 0) atomicOr(status, kStTimeout);
+}
+
+cudaError_t launch_wait_probe(unsigned* status, double limit_s, cudaStream_t st) {
+  k_wait_probe<<<1, 64, 0, st>>>(status, (unsigned long long)(limit_s * 1e9));
+  return cudaGetLastError();
 }
 
 cudaError_t launch_grid_sample(const float* grid, int r, const float* q, int64_t M, float* out,

@@ -88,5 +88,7 @@ cudaError_t launch_grid_sample(const float* grid, int r, const float* q, int64_t
                                cudaStream_t st);
 cudaError_t launch_grid_splat(float* grid, int r, const float* q, const float* vals, int64_t M,
                               cudaStream_t st);
+// One CTA waiting (bounded) on a barrier that nothing completes.
+cudaError_t launch_wait_probe(unsigned* status, double limit_s, cudaStream_t st);
 
 }  // namespace dpsr
