@@ -101,7 +101,7 @@ size_t grid_ws_bytes(int r) {
   size_t b = dpsr::kNSpec * align256(spec_bytes(r));
   b += align256(sizeof(float2) * r) + 3 * align256(sizeof(float) * r);
   b += align256(sizeof(dpsr::Scalars)) + align256(sizeof(unsigned));
-  b += align256(sizeof(double) * 2 * part_count(r));
+  b += align256(sizeof(float4) * part_count(r));
   b += align256(sizeof(int) * dpsr::bins_ints(r));
   return b;
 }
@@ -414,8 +414,8 @@ int dpsr_plan_create(int r, float sigma, dpsr_plan* out) {
   q += align256(sizeof(dpsr::Scalars));
   s.status = (unsigned*)q;
   q += align256(sizeof(unsigned));
-  s.part = (double*)q;
-  q += align256(sizeof(double) * 2 * part_count(r));
+  s.part = (float4*)q;
+  q += align256(sizeof(float4) * part_count(r));
   s.bins = (int*)q;
   s.tw = tw;
   s.g1 = g1;
@@ -573,7 +573,7 @@ int dpsr_forward(dpsr_plan p, const float* points, const float* normals, int64_t
   if (rc != DPSR_OK) return rc;
   PdlScope pdl(p->profile);
   Solve s = p->s;
-  s.N = (int)N;
+  dpsr::set_count(s, N);
   s.points = points;
   s.normals = normals;
   s.chi = chi_out;
@@ -598,6 +598,7 @@ int dpsr_forward(dpsr_plan p, const float* points, const float* normals, int64_t
   p->last_launches = 3 + dpsr::plane_launches(p->C[0]) + dpsr::plane_launches(p->C[1]);
   cudaEventRecord(p->done_ev, st);
   p->s.N = s.N;
+  p->s.inv_N = s.inv_N;
   p->s.points = points;
   p->s.normals = normals;
   p->s.chi = chi_out;

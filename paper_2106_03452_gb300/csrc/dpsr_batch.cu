@@ -200,7 +200,7 @@ int dpsr_batch_bind(dpsr_batch b, int i, const float* points, const float* norma
   Solve& s = b->host[i];
   s.points = points;
   s.normals = normals;
-  s.N = (int)N;
+  dpsr::set_count(s, N);
   s.chi = chi;
   s.dchi = dchi;
   s.dpoints = dpoints;

@@ -351,6 +351,7 @@ struct Solve {
   CUtensorMap tmy[kNSpec];
   int r;
   int N;
+  double inv_N;  // 1 / N (set with N by set_count)
   // per call (caller-owned)
   const float* points;
   const float* normals;
@@ -365,7 +366,7 @@ struct Solve {
   float2* spec[kNSpec];  // r * r * (r/2 + 2) complex each
   float4* gfwd;     // [2][N]: gradient of the lookup of y, per plane side
   float* slots;     // [2][N][6]: backward partials per plane side
-  double* part;     // per-block partial sums
+  float4* part;     // per-block partial sums, float-float pairs (a.hi, a.lo, b.hi, b.lo)
   Scalars* sc;
   unsigned* status;
   const float2* tw;  // r
@@ -375,6 +376,12 @@ struct Solve {
 };
 
 enum : unsigned { kStBadInput = 1u, kStDegenerate = 2u, kStTimeout = 4u };
+
+// The point count of a solve and its reciprocal (used by the scalar pass).
+inline void set_count(Solve& s, int64_t N) {
+  s.N = (int)N;
+  s.inv_N = 1.0 / (double)N;
+}
 
 // Row pitch (complex values) of the spectral buffers along kz: the r/2 + 1
 // valid slots padded so that, from r = 32 on, every row starts on a 128-byte

@@ -45,7 +45,7 @@ constexpr size_t kOffStatus = kOffSc + al(sizeof(dpsr::Scalars));
 constexpr size_t kParts = ((kMaxR / 2 + 1 + 15) / 16) * kMaxR > kMaxR * 8
                               ? ((kMaxR / 2 + 1 + 15) / 16) * kMaxR : kMaxR * 8;
 constexpr size_t kOffPart = kOffStatus + al(sizeof(unsigned));
-constexpr size_t kOffBins = kOffPart + al(sizeof(double) * 2 * kParts);
+constexpr size_t kOffBins = kOffPart + al(sizeof(float4) * kParts);
 constexpr size_t kOffSorted = kOffBins + al(sizeof(int) * dpsr::bins_ints(kMaxR));
 constexpr size_t kOffCell = kOffSorted + al(sizeof(float4) * 2 * kMaxN);
 constexpr size_t kOffGfwd = kOffCell + al(sizeof(int) * kMaxN);
@@ -107,7 +107,7 @@ extern "C" DPSR_API int dpsr_forward_static(int r, float sigma, const float* poi
   }
   dpsr::Solve s = {};
   s.r = r;
-  s.N = (int)N;
+  dpsr::set_count(s, N);
   s.points = points;
   s.normals = normals;
   s.chi = chi_out;
@@ -122,7 +122,7 @@ extern "C" DPSR_API int dpsr_forward_static(int r, float sigma, const float* poi
   s.iu = iu;
   s.sc = (dpsr::Scalars*)(base + kOffSc);
   s.status = (unsigned*)(base + kOffStatus);
-  s.part = (double*)(base + kOffPart);
+  s.part = (float4*)(base + kOffPart);
   s.bins = (int*)(base + kOffBins);
   s.sorted = (float4*)(base + kOffSorted);
   s.cellx = (int*)(base + kOffCell);

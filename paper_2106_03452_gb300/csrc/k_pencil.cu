@@ -654,7 +654,6 @@ __global__ void __launch_bounds__(ZbGeo<L>::NT, 3) k_zbfwd(const __grid_constant
   float* stg = reinterpret_cast<float*>(smem4);
   float2* twt = reinterpret_cast<float2*>(stg + 2 * STAGE);
   __shared__ uint64_t bar[2];
-  __shared__ double red[2][NT / 32];
   pdl_trigger();
   for (int i = tid; i < L; i += NT) twt[i] = S.tw[i];
   if (tid == 0) {
@@ -673,7 +672,7 @@ __global__ void __launch_bounds__(ZbGeo<L>::NT, 3) k_zbfwd(const __grid_constant
     bulk_load(stg + st * STAGE + YB * L, S.chi + row0, kRowBytes, &bar[st]);
   };
   TwTab<L> twr{twt, t};
-  double dS = 0.0, dD = 0.0;
+  FF dS = {0.f, 0.f}, dD = {0.f, 0.f};  // float-float over the CTA's tiles
   uint32_t ph = 0u;
   int tile = blockIdx.x;
   if (tid == 0 && tile < ntiles) issue(tile, 0);
@@ -702,8 +701,8 @@ __global__ void __launch_bounds__(ZbGeo<L>::NT, 3) k_zbfwd(const __grid_constant
       accS += (a.x + a.y) + (a.z + a.w);
       accD += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
     }
-    dS += accS;
-    dD += accD;
+    dS = ff_add(dS, accS);
+    dD = ff_add(dD, accD);
     __syncthreads();  // the sums have read the rows before the R2C rewrites them
     for (int p0 = 0; p0 < YB / 2; p0 += ZG) {
       const int pi = p0 + g;
@@ -720,27 +719,9 @@ __global__ void __launch_bounds__(ZbGeo<L>::NT, 3) k_zbfwd(const __grid_constant
     }
   }
   if (tid == 0) tma_store_wait_read();  // shared memory stays valid until read
-  // this CTA's partial sums in FP64, fixed order; the last CTA finalises
-#pragma unroll
-  for (int m = 16; m > 0; m >>= 1) {
-    dS += __shfl_xor_sync(0xffffffffu, dS, m);
-    dD += __shfl_xor_sync(0xffffffffu, dD, m);
-  }
-  if ((tid & 31) == 0) {
-    red[0][tid >> 5] = dS;
-    red[1][tid >> 5] = dD;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double a = 0, b = 0;
-    for (int w = 0; w < NT / 32; ++w) {
-      a += red[0][w];
-      b += red[1][w];
-    }
-    S.part[2 * blockIdx.x] = a;
-    S.part[2 * blockIdx.x + 1] = b;
-  }
-  if (tid < 32) last_block_finalize(S, 1, (int)gridDim.x, true);
+  // this CTA's partial sums, fixed order; the last CTA finalises
+  block_sum_ff<NT>(dS, dD);
+  last_block_finalize<NT>(S, 1, (int)gridDim.x, (int)blockIdx.x, dS, dD, true);
 }
 
 // ---------------------------------------------------------------------------

@@ -590,7 +590,6 @@ __global__ void __launch_bounds__(kNT, plane_minb<L, C>(2))
   pdl_trigger();
   for (int i = tid; i < L; i += kNT) twt[i] = S.tw[i];
   pdl_wait();
-  __shared__ double red[2][kNT / 32];
   uint32_t rb[C];  // shared::cluster address of each CTA's rows
 #pragma unroll
   for (int q = 0; q < C; ++q) rb[q] = dsmem_map(rows, q);
@@ -661,31 +660,11 @@ __global__ void __launch_bounds__(kNT, plane_minb<L, C>(2))
     }
     __syncthreads();
   }
-  // block partial sums in FP64, fixed order
-  {
-    double dS = accS, dD = accD;
-#pragma unroll
-    for (int m = 16; m > 0; m >>= 1) {
-      dS += __shfl_xor_sync(0xffffffffu, dS, m);
-      dD += __shfl_xor_sync(0xffffffffu, dD, m);
-    }
-    if ((tid & 31) == 0) {
-      red[0][tid >> 5] = dS;
-      red[1][tid >> 5] = dD;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double a = 0, b = 0;
-      for (int w = 0; w < kNT / 32; ++w) {
-        a += red[0][w];
-        b += red[1][w];
-      }
-      S.part[2 * blockIdx.x] = a;
-      S.part[2 * blockIdx.x + 1] = b;
-    }
-  }
-  // the last CTA of the solve turns the sums into the adjoint scalars
-  if (tid < 32) last_block_finalize(S, 1, (int)gridDim.x, true);
+  // block partial sums (float-float, fixed order); the last CTA of the solve
+  // turns them into the adjoint scalars
+  FF dS = {accS, 0.f}, dD = {accD, 0.f};
+  block_sum_ff<kNT>(dS, dD);
+  last_block_finalize<kNT>(S, 1, (int)gridDim.x, (int)blockIdx.x, dS, dD, true);
   cl.sync();
 }
 

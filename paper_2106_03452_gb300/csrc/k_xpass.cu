@@ -82,7 +82,6 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
   float* u2 = g1 + L;
   float* iu = u2 + L;
   __shared__ uint64_t bar;
-  __shared__ double red[2][P::NT / 32];
   // inputs: forward D, C, W~; backward FFT_zy(dchi), W~
   const int src0 = kSpD, src1 = BWD ? kSpW : kSpC;
   pdl_trigger();
@@ -191,32 +190,16 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
         for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = a[j];
       }
     }
-    double dm = (double)am * wz, ds = (double)as * wz;
-#pragma unroll
-    for (int m = 16; m > 0; m >>= 1) {
-      dm += __shfl_xor_sync(0xffffffffu, dm, m);
-      ds += __shfl_xor_sync(0xffffffffu, ds, m);
-    }
-    if ((tid & 31) == 0) {
-      red[0][tid >> 5] = dm;
-      red[1][tid >> 5] = ds;
-    }
+    FF fm = {am * wz, 0.f}, fs = {as * wz, 0.f};  // wz in {1, 2}: exact
     fence_async_smem();
-    __syncthreads();
+    block_sum_ff<P::NT>(fm, fs);  // synchronises the block: the tile is complete
     if (tid == 0) {
       tma_store_3d(&S.tmx[kSpChi], kz0, ky, 0, box);
       tma_store_commit();
-      double sm = 0, ss = 0;
-      for (int q = 0; q < P::NT / 32; ++q) {
-        sm += red[0][q];
-        ss += red[1][q];
-      }
-      const size_t bid = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-      S.part[2 * bid] = sm;
-      S.part[2 * bid + 1] = ss;
-      tma_store_wait_read();
     }
-    if (tid < 32) last_block_finalize(S, 0, (int)(gridDim.x * gridDim.y), false);
+    last_block_finalize<P::NT>(S, 0, (int)(gridDim.x * gridDim.y),
+                               (int)(blockIdx.y * gridDim.x + blockIdx.x), fm, fs, false);
+    if (tid == 0) tma_store_wait_read();
   } else {
     // FFT_x of (g_a FFT_zy(dchi) + g_w W~ + g_s delta_{x=0}): the three terms
     // of the adjoint spectrum combined before the transform (it is linear).
