@@ -42,6 +42,29 @@ struct Pen {
   static_assert(YB == ybin(L) && NYB == nybins(L), "one point bin per z-pass CTA");
 };
 
+// Row pairs of the pair transforms in shared memory: pair p (rows 2p and
+// 2p + 1, L floats each, contiguous) starts pair_off(p) floats in. The pitch
+// 2L + 16 and 8 more floats for p = 2, 3 (mod 4) put the pairs that the
+// groups of one warp transform on distinct banks (T = 8: offsets 0, 16, 8,
+// 24 mod 32 banks; T = 16: 0, 16) for the 32-bit row loads and the 64-bit
+// FFT exchange alike; with a plain 2L pitch every group of a warp hits the
+// same banks. Offsets are multiples of 8 floats (bulk copies need 16 bytes).
+// SP = false keeps the plain pitch: where a pass only makes 64-bit accesses
+// and a group fills a half-warp (T = 16), the spread buys nothing and its
+// shared memory would cost occupancy.
+template <int L, bool SP = true>
+__host__ __device__ constexpr int pair_off(int p) {
+  return SP ? p * (2 * L + 16) + ((p & 2) ? 8 : 0) : p * 2 * L;
+}
+template <int L, bool SP = true>
+__host__ __device__ constexpr int row_off(int q) {
+  return pair_off<L, SP>(q >> 1) + (q & 1) * L;
+}
+template <int L, bool SP = true>
+constexpr int pairs_floats(int np) {  // floats spanned by np pairs
+  return pair_off<L, SP>(np - 1) + 2 * L;
+}
+
 // 1D weight of the trilinear stencil (Eq. A1): corner d of the cell, offset t.
 __device__ __forceinline__ float tri_w(int d, float t) { return d ? t : 1.f - t; }
 
@@ -144,7 +167,7 @@ __device__ __forceinline__ void c2r_acc(int t, const Tw& tw, Acc x) {
 template <int L>
 constexpr size_t zfwd_smem() {
   using P = Pen<L>;
-  return sizeof(float) * (4 * P::YB * L + L) + sizeof(float2) * L;
+  return sizeof(float) * (pairs_floats<L>(2 * P::YB) + L) + sizeof(float2) * L;
 }
 
 template <int L>
@@ -156,15 +179,16 @@ __global__ void __launch_bounds__(Pen<L>::ZNT, L >= 256 ? 3 : 4) k_zfwd(const __
   const int X = blockIdx.x / P::NYB, y0 = (blockIdx.x % P::NYB) * YB;
   const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
   extern __shared__ float4 smem4[];
-  float* rows = reinterpret_cast<float*>(smem4);  // [4][YB][L]: v_y, v_z, v_x, w
-  float2* twt = reinterpret_cast<float2*>(rows + 4 * YB * L);
+  constexpr int RF = pairs_floats<L>(2 * YB);
+  float* rows = reinterpret_cast<float*>(smem4);  // rows ch * YB + ly (row_off): v_y, v_z, v_x, w
+  float2* twt = reinterpret_cast<float2*>(rows + RF);
   float* iu = reinterpret_cast<float*>(twt + L);
   pdl_trigger();
   for (int i = tid; i < L; i += P::ZNT) {
     twt[i] = S.tw[i];
     iu[i] = S.iu[i];
   }
-  for (int i = tid; i < YB * L; i += P::ZNT) smem4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = tid; i < RF / 4; i += P::ZNT) smem4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   pdl_wait();
   __syncthreads();
   // Rasterization (Eq. A2): points of x-cells X (dx = 0) and X - 1 (dx = 1)
@@ -209,7 +233,7 @@ __global__ void __launch_bounds__(Pen<L>::ZNT, L >= 256 ? 3 : 4) k_zfwd(const __
       const float f0 = f * (1.f - az.t), f1 = f * az.t;
 #pragma unroll
       for (int ch = 0; ch < 4; ++ch) {
-        float* row = rows + (ch * YB + ly) * L;
+        float* row = rows + row_off<L>(ch * YB + ly);
         atomicAdd(row + az.i0, f0 * val[ch]);
         atomicAdd(row + az.i1, f1 * val[ch]);
       }
@@ -220,21 +244,21 @@ __global__ void __launch_bounds__(Pen<L>::ZNT, L >= 256 ? 3 : 4) k_zfwd(const __
   constexpr int NP = 4 * YB / 2;
   for (int p0 = 0; p0 < NP; p0 += P::ZG) {
     const int pi = p0 + g;
-    if (pi < NP) r2c_pair_ip<L>(t, twr, rows + 2 * pi * L);  // whole groups
+    if (pi < NP) r2c_pair_ip<L>(t, twr, rows + pair_off<L>(pi));  // whole groups
   }
   __syncthreads();
   // The v_z channel takes i u_z (zero at DC and Nyquist), then the packed rows
   // go out by bulk copies, one row per thread.
-  float2* vz = reinterpret_cast<float2*>(rows + YB * L);
   for (int i = tid; i < YB * H; i += P::ZNT) {
     const int sl = i % H;
-    vz[i] = sl == 0 ? czero() : cmul_iu(vz[i], iu[sl]);
+    float2* vz = reinterpret_cast<float2*>(rows + row_off<L>(YB + i / H)) + sl;
+    *vz = sl == 0 ? czero() : cmul_iu(*vz, iu[sl]);
   }
   fence_async_smem();
   __syncthreads();
   if (tid < 4 * YB) {
     const int ch = tid / YB, ly = tid % YB;
-    bulk_store(S.spec[ch] + ((size_t)X * L + y0 + ly) * P::KP, rows + (ch * YB + ly) * L,
+    bulk_store(S.spec[ch] + ((size_t)X * L + y0 + ly) * P::KP, rows + row_off<L>(ch * YB + ly),
                H * (uint32_t)sizeof(float2));
     tma_store_commit();
     tma_store_wait_read();  // shared memory stays valid until read
@@ -463,7 +487,10 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
 template <int L, int NCH>
 struct ZiGeo {
   static constexpr int NR = Pen<L>::YB + 2;              // rows per tile
-  static constexpr int STAGE = NCH * NR * (L / 2);        // float2 per stage (row pitch H)
+  // float2 per stage: NCH * NR / 2 row pairs at pair_off (rows of H float2);
+  // the C2R makes 64-bit accesses only, spread needed below T = 16
+  static constexpr bool SP = Shape<L>::T < 16;
+  static constexpr int STAGE = pairs_floats<L, SP>(NCH * NR / 2) / 2;
   static constexpr int NT = 256;
 };
 
@@ -481,7 +508,7 @@ __global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : (L >= 256 ? 
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
   extern __shared__ float4 smem4[];
-  float2* stg = reinterpret_cast<float2*>(smem4);  // 2 stages of [NCH][NR][KP]
+  float2* stg = reinterpret_cast<float2*>(smem4);  // 2 stages, row (ch, ly) at row_off(ch NR + ly)
   float2* twt = stg + 2 * Z::STAGE;
   __shared__ uint64_t bar[2];
   pdl_trigger();
@@ -501,9 +528,9 @@ __global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : (L >= 256 ? 
     for (int ch = 0; ch < NCH; ++ch) {
       const int buf = NCH == 1 ? kSpYa : (ch == 0 ? kSpC : (ch == 1 ? kSpYa : kSpYb));
       const float2* base = S.spec[buf] + (size_t)X * L * KP;
-      float2* dst = stg + st * Z::STAGE + ch * NR * H;
+      float2* dst = stg + st * Z::STAGE;
       for (int ly = 0; ly < NR; ++ly)  // row y0 + ly, wrapping to rows 0, 1
-        bulk_load(dst + ly * H, base + (size_t)((y0 + ly) & (L - 1)) * KP, H * (uint32_t)sizeof(float2),
+        bulk_load(dst + row_off<L, Z::SP>(ch * NR + ly) / 2, base + (size_t)((y0 + ly) & (L - 1)) * KP, H * (uint32_t)sizeof(float2),
                   &bar[st]);
     }
   };
@@ -533,7 +560,7 @@ __global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : (L >= 256 ? 
     const int X = tile / P::NYB, y0 = (tile % P::NYB) * YB;
     // pair p of channel ch: rows 2p (A) and 2p + 1 (B) of the stage, L float2
     auto pair = [&](int ch, int p) {
-      float2* ra = sb + (ch * NR + 2 * p) * H;
+      float2* ra = sb + pair_off<L, Z::SP>(ch * (NR / 2) + p) / 2;
       return [ra](int i) -> float2& { return ra[i]; };
     };
     constexpr int NP = NCH * NR / 2;
@@ -639,7 +666,7 @@ struct ZbGeo {
 
 template <int L>
 constexpr size_t zbfwd_smem() {
-  return sizeof(float) * 2 * 2 * ZbGeo<L>::ZB * L + sizeof(float2) * L;
+  return sizeof(float) * 2 * (pairs_floats<L>(ZbGeo<L>::ZB / 2) + ZbGeo<L>::ZB * L) + sizeof(float2) * L;
 }
 
 template <int L>
@@ -647,7 +674,8 @@ __global__ void __launch_bounds__(ZbGeo<L>::NT, 3) k_zbfwd(const __grid_constant
                                                           const Solve* __restrict__ tab) {
   using P = Pen<L>;
   constexpr int YB = ZbGeo<L>::ZB, H = P::H, NT = ZbGeo<L>::NT, ZG = ZbGeo<L>::G;
-  constexpr int STAGE = 2 * YB * L;  // floats: dchi, chi
+  constexpr int DF = pairs_floats<L>(YB / 2);
+  constexpr int STAGE = DF + YB * L;  // floats: dchi (row pairs, pair_off), chi
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
   extern __shared__ float4 smem4[];
@@ -668,8 +696,10 @@ __global__ void __launch_bounds__(ZbGeo<L>::NT, 3) k_zbfwd(const __grid_constant
   auto issue = [&](int tile, int st) {  // thread 0: dchi and chi rows of the tile
     const size_t row0 = (size_t)tile * YB * L;  // tiles are consecutive blocks of rows
     mbar_expect_tx(&bar[st], 2 * kRowBytes);
-    bulk_load(stg + st * STAGE, S.dchi + row0, kRowBytes, &bar[st]);
-    bulk_load(stg + st * STAGE + YB * L, S.chi + row0, kRowBytes, &bar[st]);
+    for (int q = 0; q < YB / 2; ++q)
+      bulk_load(stg + st * STAGE + pair_off<L>(q), S.dchi + row0 + 2 * q * L,
+                2 * L * (uint32_t)sizeof(float), &bar[st]);
+    bulk_load(stg + st * STAGE + DF, S.chi + row0, kRowBytes, &bar[st]);
   };
   TwTab<L> twr{twt, t};
   FF dS = {0.f, 0.f}, dD = {0.f, 0.f};  // float-float over the CTA's tiles
@@ -692,12 +722,12 @@ __global__ void __launch_bounds__(ZbGeo<L>::NT, 3) k_zbfwd(const __grid_constant
       }
       break;
     }
-    float* rows = stg + st * STAGE;  // dchi rows, then chi rows
-    const float4* g4 = reinterpret_cast<const float4*>(rows);
-    const float4* c4 = reinterpret_cast<const float4*>(rows + YB * L);
+    float* rows = stg + st * STAGE;  // dchi row pairs, then chi rows
+    const float4* c4 = reinterpret_cast<const float4*>(rows + DF);
     float accS = 0.f, accD = 0.f;
     for (int i = tid; i < YB * L / 4; i += NT) {
-      const float4 a = g4[i], b = c4[i];
+      const int q = i / (L / 2), w = i % (L / 2);  // pair, float4 within the pair
+      const float4 a = *reinterpret_cast<const float4*>(rows + pair_off<L>(q) + 4 * w), b = c4[i];
       accS += (a.x + a.y) + (a.z + a.w);
       accD += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
     }
@@ -706,14 +736,14 @@ __global__ void __launch_bounds__(ZbGeo<L>::NT, 3) k_zbfwd(const __grid_constant
     __syncthreads();  // the sums have read the rows before the R2C rewrites them
     for (int p0 = 0; p0 < YB / 2; p0 += ZG) {
       const int pi = p0 + g;
-      if (pi < YB / 2) r2c_pair_ip<L>(t, twr, rows + 2 * pi * L);  // whole groups
+      if (pi < YB / 2) r2c_pair_ip<L>(t, twr, rows + pair_off<L>(pi));  // whole groups
     }
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {  // packed rows out by bulk copies; waited for before the refill
       const int X = tile / (L / YB), y0 = (tile % (L / YB)) * YB;
       for (int ly = 0; ly < YB; ++ly)
-        bulk_store(S.spec[kSpD] + ((size_t)X * L + y0 + ly) * P::KP, rows + ly * L,
+        bulk_store(S.spec[kSpD] + ((size_t)X * L + y0 + ly) * P::KP, rows + row_off<L>(ly),
                    H * (uint32_t)sizeof(float2));
       tma_store_commit();
     }
