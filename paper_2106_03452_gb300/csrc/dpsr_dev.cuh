@@ -119,9 +119,15 @@ struct Dft<1, DIR> {
 // Synchronise the T lanes of this thread's group (aligned groups of T lanes
 // within a warp); a one-thread group needs no synchronisation. Groups may
 // therefore call the FFT helpers independently of the rest of their warp.
-template <int T>
+//
+// Interleaved lanes (IL, used with T = 16 only): the two groups of a warp
+// share both half-warps, 8 lanes each (see Lanes), and synchronise on their
+// own 16 lanes.
+template <int T, bool IL = false>
 __device__ __forceinline__ void group_sync() {
-  if constexpr (T >= 32) {
+  if constexpr (IL && T == 16) {
+    __syncwarp(0x00FF00FFu << (threadIdx.x & 8u));
+  } else if constexpr (T >= 32) {
     __syncwarp();
   } else if constexpr (T > 1) {
     const unsigned lane = threadIdx.x & 31u;
@@ -139,6 +145,26 @@ __device__ __forceinline__ void group_sync() {
 // xch: L float2 of shared memory owned by the group. Every lane of the warp
 // must call this together (they synchronise through group_sync).
 // ---------------------------------------------------------------------------
+// Group and lane-in-group of thread tid. Contiguous: group g holds lanes
+// [g T, g T + T) of its warp. Interleaved (T = 16): group 2w + h of warp w
+// holds lanes 8h..8h+7 and 16+8h..16+8h+7, thread t = (lane & 7) | (lane >> 4) << 3.
+// A group that reads one column of a 128-byte-swizzled box (rows of 16
+// float2) reaches only 16 of the 32 banks, so a half-warp of one group needs
+// two wavefronts per access; with the lanes interleaved each half-warp holds
+// 8 rows of two adjacent columns (groups 2w, 2w + 1), all 32 banks.
+template <int T, bool IL>
+struct Lanes {
+  static constexpr bool kIL = IL && T == 16;
+  static __device__ __forceinline__ int group(int tid) {
+    if constexpr (kIL) return 2 * (tid >> 5) + ((tid >> 3) & 1);
+    else return tid / T;
+  }
+  static __device__ __forceinline__ int lane(int tid) {
+    if constexpr (kIL) return (tid & 7) | (((tid >> 4) & 1) << 3);
+    else return tid % T;
+  }
+};
+
 template <int L> struct Shape;
 template <> struct Shape<8>   { static constexpr int R1 = 8,  T = 1; };
 template <> struct Shape<16>  { static constexpr int R1 = 16, T = 1; };
@@ -207,7 +233,7 @@ struct TwTab {
 };
 
 // Group FFT with register twiddles (see fft_x).
-template <int L, int DIR, class XA, class TW>
+template <int L, int DIR, bool IL = false, class XA, class TW>
 __device__ __forceinline__ void fft_r(float2 (&v)[Shape<L>::R1], int t, XA xa, const TW& tw) {
   constexpr int R1 = Shape<L>::R1, T = Shape<L>::T;
   if constexpr (T == 1) {
@@ -222,7 +248,7 @@ __device__ __forceinline__ void fft_r(float2 (&v)[Shape<L>::R1], int t, XA xa, c
     }
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) xa(k1 * T + (t ^ (k1 % T))) = v[k1];
-    group_sync<T>();
+    group_sync<T, IL>();
     constexpr int M = R1 / T;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
@@ -234,7 +260,7 @@ __device__ __forceinline__ void fft_r(float2 (&v)[Shape<L>::R1], int t, XA xa, c
 #pragma unroll
       for (int k2 = 0; k2 < T; ++k2) v[m + M * k2] = u[k2];
     }
-    group_sync<T>();
+    group_sync<T, IL>();
   }
 }
 

@@ -71,7 +71,7 @@ __device__ __forceinline__ float tri_w(int d, float t) { return d ? t : 1.f - t;
 // Column 0 of a box holds P = X0 + i Xn, the transforms of the DC and Nyquist
 // columns packed together. Split them in place (column 0 <- X0) and hand Xn
 // to nyq(ky, value). Run by the T threads of one group.
-template <int L, class Nyq>
+template <int L, bool IL = false, class Nyq>
 __device__ __forceinline__ void split_dc_nyq(float2* b, int t, Nyq nyq) {
   constexpr int R1 = Shape<L>::R1, T = Shape<L>::T;
   float2 x0[R1];
@@ -82,7 +82,7 @@ __device__ __forceinline__ void split_dc_nyq(float2* b, int t, Nyq nyq) {
     unpack_dc_nyq(b[bx(ky, 0)], b[bx((L - ky) & (L - 1), 0)], x0[j], xn);
     nyq(ky, xn);  // never column 0
   }
-  group_sync<T>();
+  group_sync<T, IL>();
 #pragma unroll
   for (int j = 0; j < R1; ++j) b[bx(t + T * j, 0)] = x0[j];
 }
@@ -290,7 +290,9 @@ __global__ void __launch_bounds__(ynt<L>(), BWD ? 4 : (L >= 256 ? 3 : 5)) k_yfwd
   const int X = blockIdx.x / P::NKC, kz0 = (blockIdx.x % P::NKC) * P::NCOL;
   const int kind = BWD ? 3 : (int)blockIdx.y;
   const int buf = kind == 1 ? kSpC : (kind == 2 ? kSpW : kSpD);  // input and output
-  const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
+  constexpr bool IL = P::T == 16;  // interleaved groups: conflict-free column accesses
+  using LN = Lanes<P::T, IL>;
+  const int tid = threadIdx.x, g = LN::group(tid), t = LN::lane(tid);
   extern __shared__ unsigned char smem_raw[];
   const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
   float2* box = reinterpret_cast<float2*>(smem_raw + pad);  // 1 or 2 boxes
@@ -327,14 +329,14 @@ __global__ void __launch_bounds__(ynt<L>(), BWD ? 4 : (L >= 256 ? 3 : 5)) k_yfwd
     float2 a[P::R1];
 #pragma unroll
     for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
-    fft_r<L, -1>(a, t, c0, twr);
+    fft_r<L, -1, IL>(a, t, c0, twr);
     if (kind == 0) {
       float2* b1 = box + P::BOX;
       auto c1 = [b1, g](int e) -> float2& { return b1[bx(e, g)]; };
       float2 b[P::R1];
 #pragma unroll
       for (int j = 0; j < P::R1; ++j) b[j] = c1(t + P::T * j);
-      fft_r<L, -1>(b, t, c1, twr);
+      fft_r<L, -1, IL>(b, t, c1, twr);
 #pragma unroll
       for (int j = 0; j < P::R1; ++j) a[j] = cadd(b[j], cmul_iu(a[j], iu[t + P::T * j]));
     }
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(ynt<L>(), BWD ? 4 : (L >= 256 ? 3 : 5)) k_yfwd
   if (kz0 == 0 && g == 0) {
     // column 0 holds X0 + i Xn of the DC and Nyquist columns: split them
     float2* dst = S.spec[buf];
-    split_dc_nyq<L>(box, t, [&](int ky, float2 w) {
+    split_dc_nyq<L, IL>(box, t, [&](int ky, float2 w) {
       if (H < 16) box[bx(ky, H)] = w;
       else dst[((size_t)X * L + ky) * P::KP + H] = w;
     });
@@ -378,7 +380,9 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
   constexpr int H = P::H, NT = 16 * P::T >= 32 ? 16 * P::T : 32;
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   const int X = blockIdx.x / P::NKC, kz0 = (blockIdx.x % P::NKC) * P::NCOL;
-  const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
+  constexpr bool IL = P::T == 16;  // interleaved groups: conflict-free column accesses
+  using LN = Lanes<P::T, IL>;
+  const int tid = threadIdx.x, g = LN::group(tid), t = LN::lane(tid);
   extern __shared__ unsigned char smem_raw[];
   const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
   float2* box = reinterpret_cast<float2*>(smem_raw + pad);
@@ -433,7 +437,7 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
     auto c0 = cref(0);
 #pragma unroll
     for (int j = 0; j < P::R1; ++j) v[j] = c0(t + P::T * j);
-    fft_r<L, +1>(v, t, c0, twr);
+    fft_r<L, +1, IL>(v, t, c0, twr);
 #pragma unroll
     for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = v[j];
     if constexpr (NCH == 3) {
@@ -445,13 +449,13 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
         c2(t + P::T * j) = v[j];
         v[j] = cmul_iu(v[j], -iu[t + P::T * j]);
       }
-      fft_r<L, +1>(v, t, c1, twr);
+      fft_r<L, +1, IL>(v, t, c1, twr);
 #pragma unroll
       for (int j = 0; j < P::R1; ++j) c1(t + P::T * j) = v[j];
-      group_sync<P::T>();
+      group_sync<P::T, IL>();
 #pragma unroll
       for (int j = 0; j < P::R1; ++j) v[j] = c2(t + P::T * j);
-      fft_r<L, +1>(v, t, c2, twr);
+      fft_r<L, +1, IL>(v, t, c2, twr);
       const float ez = s == 0 ? 0.f : -iu[s];
 #pragma unroll
       for (int j = 0; j < P::R1; ++j) c2(t + P::T * j) = cmul_iu(v[j], ez);

@@ -73,7 +73,9 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
   constexpr int NCH = P::template nch<BWD>();
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   const int kz0 = blockIdx.x * P::KC, ky = blockIdx.y;
-  const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
+  constexpr bool IL = P::T == 16;  // interleaved groups: conflict-free column accesses
+  using LN = Lanes<P::T, IL>;
+  const int tid = threadIdx.x, g = LN::group(tid), t = LN::lane(tid);
   extern __shared__ unsigned char smem_raw[];
   const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
   float2* box = reinterpret_cast<float2*>(smem_raw + pad);  // NCH boxes, 1024-aligned
@@ -133,10 +135,10 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
         float2 b[P::R1];
 #pragma unroll
         for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
-        fft_r<L, -1>(a, t, c0, twr);
+        fft_r<L, -1, IL>(a, t, c0, twr);
 #pragma unroll
         for (int j = 0; j < P::R1; ++j) b[j] = c1(t + P::T * j);
-        fft_r<L, -1>(b, t, c1, twr);
+        fft_r<L, -1, IL>(b, t, c1, twr);
 #pragma unroll
         for (int j = 0; j < P::R1; ++j) {
           const int kx = t + P::T * j;
@@ -148,14 +150,14 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
         // FFT_x(D) goes back to its column, FFT_x(C) meets it there.
 #pragma unroll
         for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
-        fft_r<L, -1>(a, t, c0, twr);
+        fft_r<L, -1, IL>(a, t, c0, twr);
         if (own) {  // groups past the last column (tiny r) only shadow it
 #pragma unroll
           for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = a[j];
         }
 #pragma unroll
         for (int j = 0; j < P::R1; ++j) a[j] = c1(t + P::T * j);
-        fft_r<L, -1>(a, t, c1, twr);
+        fft_r<L, -1, IL>(a, t, c1, twr);
 #pragma unroll
         for (int j = 0; j < P::R1; ++j) {
           const int kx = t + P::T * j;  // this lane wrote c0(kx) above
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
           a[j] = cscale(cadd(c0(kx), cmul_iu(a[j], iu[kx])), G);
         }
       }
-      fft_r<L, +1>(a, t, c0, twr);  // P = unnormalised IFFT_x(chi~)
+      fft_r<L, +1, IL>(a, t, c0, twr);  // P = unnormalised IFFT_x(chi~)
       // Spectral sums of Eq. 4, by Parseval along x against the x-domain W~
       // (its tile, or up to r = 128 its column straight from L2):
       // sum_kx conj(W~(kx)) chi~(kx) = sum_x conj(W~_x(x)) P(x),
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
       a[j] = cadd(cscale(c0(x), ga), cscale(c1(x), gw));
       if (x == 0) a[j].x += gs;
     }
-    fft_r<L, -1>(a, t, c0, twr);
+    fft_r<L, -1, IL>(a, t, c0, twr);
     if constexpr (L >= 256) {
       float2 b[P::R1];
 #pragma unroll
@@ -221,8 +223,8 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
         a[j] = f;
         b[j] = cmul_iu(f, -iu[kx]);
       }
-      fft_r<L, +1>(a, t, c0, twr);
-      fft_r<L, +1>(b, t, c1, twr);
+      fft_r<L, +1, IL>(a, t, c0, twr);
+      fft_r<L, +1, IL>(b, t, c1, twr);
       if (own) {
 #pragma unroll
         for (int j = 0; j < P::R1; ++j) {
@@ -239,15 +241,15 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
         a[j] = cscale(a[j], spectral_G(kx, gyz, u2yz, g1, u2));
         if (own) c1(kx) = cmul_iu(a[j], -iu[kx]);
       }
-      fft_r<L, +1>(a, t, c0, twr);
+      fft_r<L, +1, IL>(a, t, c0, twr);
       if (own) {
 #pragma unroll
         for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = a[j];
       }
-      group_sync<P::T>();
+      group_sync<P::T, IL>();
 #pragma unroll
       for (int j = 0; j < P::R1; ++j) a[j] = c1(t + P::T * j);
-      fft_r<L, +1>(a, t, c1, twr);
+      fft_r<L, +1, IL>(a, t, c1, twr);
       if (own) {
 #pragma unroll
         for (int j = 0; j < P::R1; ++j) c1(t + P::T * j) = a[j];
