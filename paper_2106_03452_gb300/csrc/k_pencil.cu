@@ -551,6 +551,18 @@ __global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : (L >= 256 ? 
     const int st = it & 1;
     const int next = tile + gridDim.x;
     if (tid == 0 && next < ntiles) issue(next, st ^ 1);  // released at the end of the last iteration
+    const int X = tile / P::NYB, y0 = (tile % P::NYB) * YB;
+    // The tile's point bins (both plane sides, one sequence) and this
+    // thread's first point record, read before the stage wait and the C2R so
+    // that their dependent latencies overlap them.
+    const int2 r0 = bin_range(S, X, y0 / YB), r1 = bin_range(S, (X - 1) & (L - 1), y0 / YB);
+    const int n0 = r0.y - r0.x, nv = n0 + (r1.y - r1.x);
+    float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa;
+    if (tid < nv) {
+      const int i = tid < n0 ? r0.x + tid : r1.x + (tid - n0);
+      pa = S.sorted[2 * i];
+      if constexpr (NCH == 3) pb = S.sorted[2 * i + 1];
+    }
     const bool ok = __syncthreads_and(mbar_wait(&bar[st], (ph >> st) & 1u));
     ph ^= 1u << st;
     if (!ok) {
@@ -561,7 +573,6 @@ __global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : (L >= 256 ? 
       break;
     }
     float2* sb = stg + st * Z::STAGE;
-    const int X = tile / P::NYB, y0 = (tile % P::NYB) * YB;
     // pair p of channel ch: rows 2p (A) and 2p + 1 (B) of the stage, L float2
     auto pair = [&](int ch, int p) {
       float2* ra = sb + pair_off<L, Z::SP>(ch * (NR / 2) + p) / 2;
@@ -590,14 +601,11 @@ __global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : (L >= 256 ? 
         reinterpret_cast<float4*>(chi + ((size_t)X * L + y0 + ly) * L)[z4 / 4] = o;
       }
     }
-    // both plane sides' bins as one sequence (their loads overlap)
-    const int2 r0 = bin_range(S, X, y0 / YB), r1 = bin_range(S, (X - 1) & (L - 1), y0 / YB);
-    const int n0 = r0.y - r0.x, nv = n0 + (r1.y - r1.x);
     for (int v = tid; v < nv; v += NT) {
       const int side = v < n0 ? 0 : 1;
       const int i = side ? r1.x + (v - n0) : r0.x + v;
       {
-        const float4 a = S.sorted[2 * i];
+        const float4 a = v == tid ? pa : S.sorted[2 * i];
         const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);
         const int ly0 = ay.i0 - y0;  // in [0, YB); row i1 is ly0 + 1 (a halo row at most)
         const float fx = tri_w(side, ax.t), dfx = side ? (float)L : -(float)L;
@@ -618,7 +626,7 @@ __global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : (L >= 256 ? 
           }
           S.gfwd[(size_t)side * S.N + i] = make_float4(gx, gy, gz, 0.f);
         } else {
-          const float4 b = S.sorted[2 * i + 1];
+          const float4 b = v == tid ? pb : S.sorted[2 * i + 1];
           const float n0 = a.w, n1 = b.x, n2 = b.y;
           float nb0 = 0.f, nb1 = 0.f, nb2 = 0.f, cb0 = 0.f, cb1 = 0.f, cb2 = 0.f;
 #pragma unroll
