@@ -300,22 +300,23 @@ __global__ void __launch_bounds__(ynt<L>(), BWD ? 4 : (L >= 256 ? 3 : 5)) k_yfwd
   float* iu = reinterpret_cast<float*>(twt + L);
   __shared__ uint64_t bar;
   pdl_trigger();
-  for (int i = tid; i < L; i += NT) {
-    twt[i] = S.tw[i];
-    iu[i] = S.iu[i];
-  }
+  // thread 0 issues the tile loads first; the tables load while they fly
   if (tid == 0) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   pdl_wait();
-  __syncthreads();
   if (tid == 0) {
     const int nin = kind == 0 ? 2 : 1;
     mbar_expect_tx(&bar, nin * P::BOX * (uint32_t)sizeof(float2));
     tma_load_3d(box, &S.tmy[buf], kz0, 0, X, &bar);
     if (kind == 0) tma_load_3d(box + P::BOX, &S.tmy[1], kz0, 0, X, &bar);  // i u_z v_z
   }
+  for (int i = tid; i < L; i += NT) {
+    twt[i] = S.tw[i];
+    iu[i] = S.iu[i];
+  }
+  __syncthreads();
   const bool landed = __syncthreads_and(mbar_wait(&bar, 0));
   if (!landed) {
     if (tid == 0) atomicOr(S.status, kStTimeout);
@@ -390,16 +391,12 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
   float* iu = reinterpret_cast<float*>(twt + L);
   __shared__ uint64_t bar;
   pdl_trigger();
-  for (int i = tid; i < L; i += NT) {
-    twt[i] = S.tw[i];
-    iu[i] = S.iu[i];
-  }
+  // thread 0 issues the tile loads first; the tables load while they fly
   if (tid == 0) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   pdl_wait();
-  __syncthreads();
   // NCH = 1: box 0 <- chi~; NCH = 3: box 0 <- Q2, box 1 <- Q1
   constexpr int NIN = NCH == 1 ? 1 : 2;
   if (tid == 0) {
@@ -407,6 +404,11 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
     tma_load_3d(box, &S.tmy[kSpChi], kz0, 0, X, &bar);
     if constexpr (NCH == 3) tma_load_3d(box + P::BOX, &S.tmy[kSpD], kz0, 0, X, &bar);
   }
+  for (int i = tid; i < L; i += NT) {
+    twt[i] = S.tw[i];
+    iu[i] = S.iu[i];
+  }
+  __syncthreads();
   const bool landed = __syncthreads_and(mbar_wait(&bar, 0));
   if (!landed) {
     if (tid == 0) atomicOr(S.status, kStTimeout);
