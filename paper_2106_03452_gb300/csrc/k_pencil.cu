@@ -97,7 +97,14 @@ __device__ __forceinline__ int2 bin_range(const Solve& S, int xc, int yb) {
 
 // R2C of two real rows a = p[0..L), b = p[L..2L) in place: afterwards the
 // storage, seen as L float2, holds A's packed half spectrum in [0, H) and B's
-// in [H, L). The storage is also the FFT exchange area.
+// in [H, L). The storage is also the FFT exchange area. The group's lanes are
+// contiguous (see Lanes).
+//
+// Z = FFT(a + i b) leaves Z[t + T j] in v[j] of thread t; the separation
+// A[k] = (Z[k] + conj Z[L-k]) / 2, B[k] = -i (Z[k] - conj Z[L-k]) / 2 needs
+// Z[L - k], k = t + T j, which is v[R1 - 1 - j] of thread T - t (t > 0) or
+// v[R1 - j] of thread 0 itself (t = 0, j > 0): one shuffle per value instead
+// of a round trip through shared memory.
 template <int L, class Tw>
 __device__ __forceinline__ void r2c_pair_ip(int t, const Tw& tw, float* p) {
   constexpr int R1 = Shape<L>::R1, T = Shape<L>::T, H = L / 2;
@@ -106,26 +113,31 @@ __device__ __forceinline__ void r2c_pair_ip(int t, const Tw& tw, float* p) {
   for (int j = 0; j < R1; ++j) v[j] = make_float2(p[t + T * j], p[L + t + T * j]);
   group_sync<T>();
   float2* x = reinterpret_cast<float2*>(p);
-  fft_r<L, -1>(v, t, [x](int i) -> float2& { return x[i]; }, tw);
-#pragma unroll
-  for (int j = 0; j < R1; ++j) x[t + T * j] = v[j];
-  group_sync<T>();
+  fft_r<L, -1>(v, t, [x](int i) -> float2& { return x[i]; }, tw);  // ends with a group sync
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned gmask = T >= 32 ? 0xffffffffu : (((1u << (T & 31)) - 1u) << (lane & ~(unsigned)(T - 1)));
+  const int src = (int)(lane & ~(unsigned)(T - 1)) | ((T - t) & (T - 1));
   float2 A[R1 / 2], B[R1 / 2];
 #pragma unroll
   for (int j = 0; j < R1 / 2; ++j) {
-    const int k = t + T * j;
-    if (k == 0) {
-      const float2 z0 = x[0], zn = x[H];
-      A[j] = make_float2(z0.x, zn.x);
-      B[j] = make_float2(z0.y, zn.y);
+    float2 zm = v[(R1 - j) & (R1 - 1)];  // thread 0's own mirror (j > 0)
+    if constexpr (T > 1) {
+      const float2 s = v[R1 - 1 - j];
+      const float mx = __shfl_sync(gmask, s.x, src), my = __shfl_sync(gmask, s.y, src);
+      if (t != 0) zm = make_float2(mx, my);
+    }
+    const float2 zk = v[j];
+    if (t == 0 && j == 0) {  // k = 0: Z[0] and Z[H] (v[R1 / 2] of thread 0)
+      const float2 zn = v[R1 / 2];
+      A[j] = make_float2(zk.x, zn.x);
+      B[j] = make_float2(zk.y, zn.y);
     } else {
-      const float2 zk = x[k], zm = cconj(x[L - k]);
+      zm = cconj(zm);
       A[j] = cscale(cadd(zk, zm), 0.5f);
       const float2 d = csub(zk, zm);  // B = -i d / 2
       B[j] = make_float2(0.5f * d.y, -0.5f * d.x);
     }
   }
-  group_sync<T>();
 #pragma unroll
   for (int j = 0; j < R1 / 2; ++j) {
     x[t + T * j] = A[j];
