@@ -278,14 +278,22 @@ __global__ void __launch_bounds__(Pen<L>::ZNT, L >= 256 ? 3 : 4) k_zfwd(const __
 }
 
 // ===========================================================================
-// Forward y pass over 16 kz columns of plane X, one output per CTA
-// (blockIdx.y): 0: D = FFT(i u_z v_z) + i u_y FFT(v_y) from buffers 0 and 1
-// into kSpD; 1: C = FFT(v_x) in place in kSpC; 2: W~ = FFT(w) in place in
-// kSpW. BWD: FFT of the z-transformed dchi in place in kSpD.
+// Forward y pass over 16 kz columns of plane X, by CTA kind (blockIdx.y):
+// 0: D = FFT(i u_z v_z) + i u_y FFT(v_y) from buffers 0 and 1 into kSpD;
+// 1: C = FFT(v_x) in place in kSpC, and from r = 256 on (yfwd_merge) also
+// W~ = FFT(w) in place in kSpW; 2 (below r = 256): W~. BWD: FFT of the
+// z-transformed dchi in place in kSpD. Merging C and W~ halves the CTAs of
+// the bandwidth-bound r = 256 pass; below, where the pass is bound by the
+// latency of each CTA, more and shorter CTAs win.
 // ===========================================================================
 template <int L>
 constexpr int ynt() {
   return 16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32;  // one group per column
+}
+
+template <int L>
+constexpr bool yfwd_merge() {
+  return L >= 256;
 }
 
 template <int L, bool BWD>
@@ -301,7 +309,10 @@ __global__ void __launch_bounds__(ynt<L>(), BWD ? 4 : (L >= 256 ? 3 : 5)) k_yfwd
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   const int X = blockIdx.x / P::NKC, kz0 = (blockIdx.x % P::NKC) * P::NCOL;
   const int kind = BWD ? 3 : (int)blockIdx.y;
-  const int buf = kind == 1 ? kSpC : (kind == 2 ? kSpW : kSpD);  // input and output
+  // box 0: input and output buf0; box 1 (two: kinds 0 and merged 1): i u_z v_z
+  // (buffer 1, kind 0) or w (kind 1)
+  const int buf0 = kind == 1 ? kSpC : (kind == 2 ? kSpW : kSpD), buf1 = kind == 1 ? kSpW : 1;
+  const bool two = !BWD && (kind == 0 || (kind == 1 && yfwd_merge<L>()));
   constexpr bool IL = P::T == 16;  // interleaved groups: conflict-free column accesses
   using LN = Lanes<P::T, IL>;
   const int tid = threadIdx.x, g = LN::group(tid), t = LN::lane(tid);
@@ -319,10 +330,9 @@ __global__ void __launch_bounds__(ynt<L>(), BWD ? 4 : (L >= 256 ? 3 : 5)) k_yfwd
   }
   pdl_wait();
   if (tid == 0) {
-    const int nin = kind == 0 ? 2 : 1;
-    mbar_expect_tx(&bar, nin * P::BOX * (uint32_t)sizeof(float2));
-    tma_load_3d(box, &S.tmy[buf], kz0, 0, X, &bar);
-    if (kind == 0) tma_load_3d(box + P::BOX, &S.tmy[1], kz0, 0, X, &bar);  // i u_z v_z
+    mbar_expect_tx(&bar, (two ? 2 : 1) * P::BOX * (uint32_t)sizeof(float2));
+    tma_load_3d(box, &S.tmy[buf0], kz0, 0, X, &bar);
+    if (two) tma_load_3d(box + P::BOX, &S.tmy[buf1], kz0, 0, X, &bar);
   }
   for (int i = tid; i < L; i += NT) {
     twt[i] = S.tw[i];
@@ -336,39 +346,49 @@ __global__ void __launch_bounds__(ynt<L>(), BWD ? 4 : (L >= 256 ? 3 : 5)) k_yfwd
     return;
   }
   TwTab<L> twr{twt, t};
-  if (g < P::NCOL) {  // whole groups
+  if (g < P::NCOL) {  // whole groups; one column array live at a time
     float2* b0 = box;
     auto c0 = [b0, g](int e) -> float2& { return b0[bx(e, g)]; };
     float2 a[P::R1];
 #pragma unroll
     for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
     fft_r<L, -1, IL>(a, t, c0, twr);
-    if (kind == 0) {
-      float2* b1 = box + P::BOX;
-      auto c1 = [b1, g](int e) -> float2& { return b1[bx(e, g)]; };
-      float2 b[P::R1];
-#pragma unroll
-      for (int j = 0; j < P::R1; ++j) b[j] = c1(t + P::T * j);
-      fft_r<L, -1, IL>(b, t, c1, twr);
-#pragma unroll
-      for (int j = 0; j < P::R1; ++j) a[j] = cadd(b[j], cmul_iu(a[j], iu[t + P::T * j]));
-    }
 #pragma unroll
     for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = a[j];
+    if (two) {
+      float2* b1 = box + P::BOX;
+      auto c1 = [b1, g](int e) -> float2& { return b1[bx(e, g)]; };
+#pragma unroll
+      for (int j = 0; j < P::R1; ++j) a[j] = c1(t + P::T * j);
+      fft_r<L, -1, IL>(a, t, c1, twr);
+      if (kind == 0) {  // D = FFT(i u_z v_z) + i u_y FFT(v_y); this lane wrote c0 above
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) {
+          const int ky = t + P::T * j;
+          c0(ky) = cadd(a[j], cmul_iu(c0(ky), iu[ky]));
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < P::R1; ++j) c1(t + P::T * j) = a[j];
+      }
+    }
   }
   __syncthreads();
-  if (kz0 == 0 && g == 0) {
+  const int nsplit = kind == 1 && two ? 2 : 1;  // tiles whose column 0 packs DC and Nyquist
+  if (kz0 == 0 && g < nsplit) {
     // column 0 holds X0 + i Xn of the DC and Nyquist columns: split them
-    float2* dst = S.spec[buf];
-    split_dc_nyq<L, IL>(box, t, [&](int ky, float2 w) {
-      if (H < 16) box[bx(ky, H)] = w;
+    float2* bb = box + g * P::BOX;
+    float2* dst = S.spec[g == 0 ? buf0 : buf1];
+    split_dc_nyq<L, IL>(bb, t, [&](int ky, float2 w) {
+      if (H < 16) bb[bx(ky, H)] = w;
       else dst[((size_t)X * L + ky) * P::KP + H] = w;
     });
   }
   fence_async_smem();
   __syncthreads();
   if (tid == 0) {
-    tma_store_3d(&S.tmy[buf], kz0, 0, X, box);
+    tma_store_3d(&S.tmy[buf0], kz0, 0, X, box);
+    if (kind == 1 && two) tma_store_3d(&S.tmy[buf1], kz0, 0, X, box + P::BOX);
     tma_store_commit();
     tma_store_wait_read();
   }
@@ -808,7 +828,8 @@ static cudaError_t launch_pencil_t(int kind, const Solve& s, const Solve* tab, i
       }
       e = launch_k(k_zfwd<L>, gz, dim3(P::ZNT), a, st, 0, s, tab);
       if (e == cudaSuccess)
-        e = launch_k(k_yfwd<L, false>, dim3(L * P::NKC, 3, count), dim3(ynt<L>()), b, st, 0, s, tab);
+        e = launch_k(k_yfwd<L, false>, dim3(L * P::NKC, yfwd_merge<L>() ? 2 : 3, count), dim3(ynt<L>()),
+                     b, st, 0, s, tab);
       return e;
     }
     case 1: {
