@@ -83,18 +83,21 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
   float* g1 = reinterpret_cast<float*>(tw + L);
   float* u2 = g1 + L;
   float* iu = u2 + L;
-  __shared__ uint64_t bar;
+  // One barrier per box: the forward transforms D while C and W~ still land.
+  __shared__ uint64_t bar[NCH];
   // inputs: forward D, C, W~; backward FFT_zy(dchi), W~
   const int src0 = kSpD, src1 = BWD ? kSpW : kSpC;
   pdl_trigger();
   pdl_wait();
   if (tid == 0) {
-    mbar_init(&bar, 1);
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) mbar_init(&bar[c], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    mbar_expect_tx(&bar, NCH * P::BOX * (uint32_t)sizeof(float2));
-    tma_load_3d(box, &S.tmx[src0], kz0, ky, 0, &bar);
-    tma_load_3d(box + P::BOX, &S.tmx[src1], kz0, ky, 0, &bar);
-    if constexpr (NCH == 3) tma_load_3d(box + 2 * P::BOX, &S.tmx[kSpW], kz0, ky, 0, &bar);
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      mbar_expect_tx(&bar[c], P::BOX * (uint32_t)sizeof(float2));
+      tma_load_3d(box + c * P::BOX, &S.tmx[c == 0 ? src0 : (c == 1 ? src1 : kSpW)], kz0, ky, 0, &bar[c]);
+    }
   }
   for (int i = tid; i < L; i += P::NT) {
     tw[i] = S.tw[i];
@@ -103,12 +106,20 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
     iu[i] = S.iu[i];
   }
   __syncthreads();
-  const bool landed = __syncthreads_and(mbar_wait(&bar, 0));
-  if (!landed) {
-    if (tid == 0) atomicOr(S.status, kStTimeout);
-    mbar_wait(&bar, 0);  // give copies in flight a last bounded chance before leaving
-    return;
-  }
+  // Each thread records its own bounded waits; the block votes before any
+  // store, so that a timeout leaves uniformly (the transforms of a lane whose
+  // wait ran out compute on stale data, which is never stored).
+  bool ok = true;
+  auto box_wait = [&](int c) {
+    if (ok) ok = mbar_wait(&bar[c], 0);
+  };
+  auto leave = [&]() {  // after a failed vote
+    if (tid == 0) {
+      atomicOr(S.status, kStTimeout);
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) mbar_wait(&bar[c], 0);  // copies in flight: a last bounded chance
+    }
+  };
   const int gc = g < P::KC ? g : P::KC - 1;  // extra groups (tiny r) shadow the last column
   const bool own = g < P::KC;
   const int kz = min(kz0 + gc, P::H);
@@ -133,9 +144,11 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
       if constexpr (L >= 256) {
         // chi~ = G (FFT_x(D) + i u_x FFT_x(C))
         float2 b[P::R1];
+        box_wait(0);
 #pragma unroll
         for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
         fft_r<L, -1, IL>(a, t, c0, twr);
+        box_wait(1);
 #pragma unroll
         for (int j = 0; j < P::R1; ++j) b[j] = c1(t + P::T * j);
         fft_r<L, -1, IL>(b, t, c1, twr);
@@ -148,6 +161,7 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
       } else {
         // chi~ = G (FFT_x(D) + i u_x FFT_x(C)); one column array live at a time:
         // FFT_x(D) goes back to its column, FFT_x(C) meets it there.
+        box_wait(0);
 #pragma unroll
         for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
         fft_r<L, -1, IL>(a, t, c0, twr);
@@ -155,6 +169,7 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
 #pragma unroll
           for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = a[j];
         }
+        box_wait(1);
 #pragma unroll
         for (int j = 0; j < P::R1; ++j) a[j] = c1(t + P::T * j);
         fft_r<L, -1, IL>(a, t, c1, twr);
@@ -172,6 +187,7 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
       // sum_kx chi~(kx) = P(x = 0).
       if constexpr (NCH == 3) {
         auto c2 = colref(2);
+        box_wait(2);
 #pragma unroll
         for (int j = 0; j < P::R1; ++j) {
           const float2 w = c2(t + P::T * j);
@@ -193,6 +209,10 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
       }
     }
     FF fm = {am * wz, 0.f}, fs = {as * wz, 0.f};  // wz in {1, 2}: exact
+    if (!__syncthreads_and(ok)) {
+      leave();
+      return;
+    }
     fence_async_smem();
     block_sum_ff<P::NT>(fm, fs);  // synchronises the block: the tile is complete
     if (tid == 0) {
@@ -207,6 +227,12 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
     // of the adjoint spectrum combined before the transform (it is linear).
     const Scalars* sc = S.sc;
     const float ga = sc->g_a, gs = sc->g_s, gw = sc->g_w;
+    box_wait(0);
+    box_wait(1);
+    if (!__syncthreads_and(ok)) {  // both tiles are needed from the start
+      leave();
+      return;
+    }
 #pragma unroll
     for (int j = 0; j < P::R1; ++j) {
       const int x = t + P::T * j;
