@@ -290,7 +290,10 @@ def run_gpu(args):
                 "solves_per_s": ws * k3 / (ms3 / 1e3), "ms_per_step": t3 * 1e3,
                 "model_bytes_per_solve": bytes3,
                 "roofline_frac_of_model": bytes3 / t3 / 1e9 / hbm_peak,
-                "kernels": per3}
+                "kernels": per3,
+                # autotuned plane paths (0 pencil, else cluster size) of the four
+                # plane kinds; DPSR_PLANE_PATHS_256 pins them for a profiler run
+                "paths": L.dpsr_plan_clusters(plan3.handle)}
         plan3.close()
 
     # ---------------- batched: 32 clouds, r in {64, 128} ----------------
@@ -324,6 +327,7 @@ def run_gpu(args):
                          "peak_kind": peak_kind,
                          "bytes_per_launch": per[dom]["bytes"], "ms_per_launch": per[dom]["ms"]},
             "kernels": per,
+            "paths": L.dpsr_plan_clusters(plan.handle),  # see r256["paths"]
             "clocks": clk,
             "r256": r256,
             "batched": batched,

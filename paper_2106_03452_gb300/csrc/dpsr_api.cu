@@ -15,6 +15,7 @@
 //   binv   IFFT along y, C2R along z of V_bar_{x,y,z}, gather + weight
 //          derivatives at the points
 //   combine  the two plane sides of each point, in the caller's order
+#include <cstdio>
 #include <cstdlib>
 #include <math.h>
 #include <stdlib.h>
@@ -167,14 +168,25 @@ bool tuning_enabled() {
   return !(e && e[0] == '0');
 }
 
-// DPSR_PLANE_PATH in the environment fixes the plane path of every kind:
-// 0 = pencil passes, 1/2/4/8 = cluster size (for tests and measurements).
-// Returns -1 when unset.
-int forced_path() {
+// Plane paths fixed from the environment (tests and measurements):
+// DPSR_PLANE_PATHS_<r> = "a,b,c,d" fixes the four kinds at grid size r (for
+// instance the choices an autotuned run reported, to profile the same
+// kernels), else DPSR_PLANE_PATH fixes every kind at every r; 0 = pencil
+// passes, 1/2/4/8 = cluster size. Returns -1 when neither applies.
+int forced_path(int kind, int r) {
+  auto valid = [](int c) { return c == 0 || c == 1 || c == 2 || c == 4 || c == 8; };
+  char name[32];
+  snprintf(name, sizeof(name), "DPSR_PLANE_PATHS_%d", r);
+  if (const char* e = getenv(name)) {
+    int c[4];
+    if (sscanf(e, "%d,%d,%d,%d", &c[0], &c[1], &c[2], &c[3]) == 4 && kind >= 0 && kind < 4 &&
+        valid(c[kind]))
+      return c[kind];
+  }
   const char* e = getenv("DPSR_PLANE_PATH");
   if (!e || !*e) return -1;
   const int c = atoi(e);
-  return (c == 0 || c == 1 || c == 2 || c == 4 || c == 8) ? c : -1;
+  return valid(c) ? c : -1;
 }
 
 // Launch plane kernel `kind` for every candidate C, time each with events
@@ -227,7 +239,7 @@ cudaError_t tune_plane(dpsr_plan p, int kind, const Solve& s, cudaStream_t st) {
 // Launch plane kernel `kind`, tuning it first if it has not been tuned for
 // this r (and the stream is not being captured).
 cudaError_t run_plane(dpsr_plan p, int kind, const Solve& s, cudaStream_t st) {
-  const int forced = forced_path();
+  const int forced = forced_path(kind, p->r);
   if (forced >= 0) {
     p->C[kind] = forced;
     return dpsr::launch_plane(kind, p->r, forced, s, nullptr, 1, st);
@@ -519,7 +531,7 @@ int dpsr_grid_splat(float* grid, int r, const float* q, const float* vals, int64
 const void* dpsr_internal_solve(dpsr_plan p) { return p ? (const void*)&p->s : nullptr; }
 int dpsr_internal_cluster(dpsr_plan p, int kind) {
   if (!p || kind < 0 || kind > 3) return 1;
-  const int forced = forced_path();
+  const int forced = forced_path(kind, p->r);
   if (forced >= 0) return forced;
   if (tuning_enabled()) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
