@@ -55,6 +55,9 @@ struct dpsr_plan_s {
   // recorded after the work of every forward / backward call: destroy waits on
   // it, so it never touches a stream the caller may have destroyed since
   cudaEvent_t done_ev = nullptr;
+  // pinned host copy of the status word, filled on the plan's stream by
+  // dpsr_sync so that one stream synchronisation returns it
+  unsigned* status_host = nullptr;
   // optional per-kernel timing: an event before and after each launch
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -464,12 +467,19 @@ int dpsr_plan_create(int r, float sigma, dpsr_plan* out) {
   free(htw);
   free(hg);
   if (rc == DPSR_OK) rc = dpsr::make_tensor_maps(s, r);
+  if (rc == DPSR_OK && cudaHostAlloc((void**)&p->status_host, sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    p->status_host = nullptr;
+    rc = DPSR_ENOMEM;
+  }
   if (rc == DPSR_OK && cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming) != cudaSuccess)
     rc = DPSR_ECUDA;
   if (rc == DPSR_OK) rc = grow_points(p, 1024);
   if (rc != DPSR_OK) {
     cudaFree(p->grid_ws);
     if (p->pts_ws) cudaFree(p->pts_ws);
+    if (p->status_host) cudaFreeHost(p->status_host);
+    if (p->done_ev) cudaEventDestroy(p->done_ev);
     delete p;
     return rc;
   }
@@ -488,6 +498,7 @@ int dpsr_plan_destroy(dpsr_plan p) {
   cudaFree(p->grid_ws);
   if (p->pts_ws) cudaFree(p->pts_ws);
   if (p->host_io) cudaFree(p->host_io);
+  if (p->status_host) cudaFreeHost(p->status_host);
   delete p;
   return DPSR_OK;
 }
@@ -654,13 +665,15 @@ int dpsr_backward(dpsr_plan p, const float* dchi, float* dpoints, float* dnormal
 int dpsr_sync(dpsr_plan p) {
   if (!p) return DPSR_EINVAL;
   DeviceGuard dg(p->device);
-  if (cudaStreamSynchronize(p->stream) != cudaSuccess) {
+  // the status word comes back on the plan's stream, behind its work: one
+  // host round trip
+  if (cudaMemcpyAsync(p->status_host, p->s.status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                      p->stream) != cudaSuccess ||
+      cudaStreamSynchronize(p->stream) != cudaSuccess) {
     cudaGetLastError();
     return DPSR_ECUDA;
   }
-  unsigned st = 0;
-  if (cudaMemcpy(&st, p->s.status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
-    return DPSR_ECUDA;
+  const unsigned st = *p->status_host;
   if (st) {
     cudaMemset(p->s.status, 0, sizeof(unsigned));
     return DPSR_EDEGENERATE;
