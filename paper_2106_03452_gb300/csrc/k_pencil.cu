@@ -104,9 +104,11 @@ __device__ __forceinline__ int2 bin_range(const Solve& S, int xc, int yb) {
 // A[k] = (Z[k] + conj Z[L-k]) / 2, B[k] = -i (Z[k] - conj Z[L-k]) / 2 needs
 // Z[L - k], k = t + T j, which is v[R1 - 1 - j] of thread T - t (t > 0) or
 // v[R1 - j] of thread 0 itself (t = 0, j > 0): one shuffle per value instead
-// of a round trip through shared memory.
+// of a round trip through shared memory. With iu given, both spectra leave
+// multiplied by i u(k) (slot 0, DC and Nyquist, becomes 0): the spectral
+// derivative of the forward's v_z rows, folded into the stores.
 template <int L, class Tw>
-__device__ __forceinline__ void r2c_pair_ip(int t, const Tw& tw, float* p) {
+__device__ __forceinline__ void r2c_pair_ip(int t, const Tw& tw, float* p, const float* iu = nullptr) {
   constexpr int R1 = Shape<L>::R1, T = Shape<L>::T, H = L / 2;
   float2 v[R1];
 #pragma unroll
@@ -136,6 +138,15 @@ __device__ __forceinline__ void r2c_pair_ip(int t, const Tw& tw, float* p) {
       A[j] = cscale(cadd(zk, zm), 0.5f);
       const float2 d = csub(zk, zm);  // B = -i d / 2
       B[j] = make_float2(0.5f * d.y, -0.5f * d.x);
+    }
+  }
+  if (iu) {
+#pragma unroll
+    for (int j = 0; j < R1 / 2; ++j) {
+      const int k = t + T * j;
+      const float u = k == 0 ? 0.f : iu[k];
+      A[j] = cmul_iu(A[j], u);
+      B[j] = cmul_iu(B[j], u);
     }
   }
 #pragma unroll
@@ -256,16 +267,11 @@ __global__ void __launch_bounds__(Pen<L>::ZNT, L >= 256 ? 3 : 4) k_zfwd(const __
   constexpr int NP = 4 * YB / 2;
   for (int p0 = 0; p0 < NP; p0 += P::ZG) {
     const int pi = p0 + g;
-    if (pi < NP) r2c_pair_ip<L>(t, twr, rows + pair_off<L>(pi));  // whole groups
+    // the v_z rows (pairs YB/2 .. YB-1) take i u_z (zero at DC and Nyquist)
+    const bool vz = pi >= YB / 2 && pi < YB;
+    if (pi < NP) r2c_pair_ip<L>(t, twr, rows + pair_off<L>(pi), vz ? iu : nullptr);  // whole groups
   }
-  __syncthreads();
-  // The v_z channel takes i u_z (zero at DC and Nyquist), then the packed rows
-  // go out by bulk copies, one row per thread.
-  for (int i = tid; i < YB * H; i += P::ZNT) {
-    const int sl = i % H;
-    float2* vz = reinterpret_cast<float2*>(rows + row_off<L>(YB + i / H)) + sl;
-    *vz = sl == 0 ? czero() : cmul_iu(*vz, iu[sl]);
-  }
+  // the packed rows go out by bulk copies, one row per thread
   fence_async_smem();
   __syncthreads();
   if (tid < 4 * YB) {
