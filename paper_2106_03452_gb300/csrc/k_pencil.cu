@@ -405,15 +405,24 @@ __global__ void __launch_bounds__(ynt<L>(), BWD ? 4 : (L >= 256 ? 3 : 5)) k_yfwd
 // run again on the same inputs). NCH = 1: chi~ (kSpChi) -> kSpYa. NCH = 3:
 // the adjoint fields V_bar_x = IFFT_y(Q2) -> kSpC, V_bar_y = IFFT_y(-i u_y
 // Q1) -> kSpYa, V_bar_z = -i u_z IFFT_y(Q1) -> kSpYb, with Q1 in kSpD and
-// Q2 in kSpChi.
+// Q2 in kSpChi. Below r = 256 (yinv_split) the adjoint fields take two CTA
+// kinds (blockIdx.y): 0: V_bar_x from Q2; 1: V_bar_y and V_bar_z from Q1.
+// There the pass is bound by each CTA's latency and shorter CTAs win; at
+// r = 256, bound by bandwidth, one CTA does all three.
 // ===========================================================================
+template <int L, int NCH>
+constexpr bool yinv_split() {
+  return NCH == 3 && L < 256;
+}
+
 template <int L, int NCH>
 constexpr size_t yinv_smem() {
   return 1024 + sizeof(float2) * ((size_t)NCH * Pen<L>::BOX + L) + sizeof(float) * L;
 }
 
 template <int L, int NCH>
-__global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32, NCH == 1 ? 4 : 2)
+__global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32,
+                                  NCH == 1 || yinv_split<L, NCH>() ? 4 : 2)
     k_yinv(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = Pen<L>;
   constexpr int H = P::H, NT = 16 * P::T >= 32 ? 16 * P::T : 32;
@@ -435,12 +444,15 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   pdl_wait();
-  // NCH = 1: box 0 <- chi~; NCH = 3: box 0 <- Q2, box 1 <- Q1
+  // NCH = 1: box 0 <- chi~; NCH = 3: box 0 <- Q2, box 1 <- Q1 (split: only
+  // the kind's own input)
   constexpr int NIN = NCH == 1 ? 1 : 2;
+  const int part = yinv_split<L, NCH>() ? (int)blockIdx.y : -1;  // -1: all fields
+  const bool do0 = part != 1, do1 = NCH == 3 && part != 0;
   if (tid == 0) {
-    mbar_expect_tx(&bar, NIN * P::BOX * (uint32_t)sizeof(float2));
-    tma_load_3d(box, &S.tmy[kSpChi], kz0, 0, X, &bar);
-    if constexpr (NCH == 3) tma_load_3d(box + P::BOX, &S.tmy[kSpD], kz0, 0, X, &bar);
+    mbar_expect_tx(&bar, ((do0 ? 1 : 0) + (do1 ? 1 : 0)) * P::BOX * (uint32_t)sizeof(float2));
+    if (do0) tma_load_3d(box, &S.tmy[kSpChi], kz0, 0, X, &bar);
+    if (do1) tma_load_3d(box + P::BOX, &S.tmy[kSpD], kz0, 0, X, &bar);
   }
   for (int i = tid; i < L; i += NT) {
     twt[i] = S.tw[i];
@@ -454,7 +466,7 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
     return;
   }
   TwTab<L> twr{twt, t};
-  if (kz0 == 0 && g < NIN) {
+  if (kz0 == 0 && g < NIN && (g == 0 ? do0 : do1)) {
     // column 0 becomes X0 + i Xn (Xn: the Nyquist column); the same lanes
     // read these elements again below
     float2* b = box + g * P::BOX;
@@ -475,12 +487,14 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
     };
     float2 v[P::R1];
     auto c0 = cref(0);
+    if (do0) {
 #pragma unroll
-    for (int j = 0; j < P::R1; ++j) v[j] = c0(t + P::T * j);
-    fft_r<L, +1, IL>(v, t, c0, twr);
+      for (int j = 0; j < P::R1; ++j) v[j] = c0(t + P::T * j);
+      fft_r<L, +1, IL>(v, t, c0, twr);
 #pragma unroll
-    for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = v[j];
-    if constexpr (NCH == 3) {
+      for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = v[j];
+    }
+    if (do1) {
       auto c1 = cref(1);
       auto c2 = cref(2);
 #pragma unroll
@@ -507,9 +521,11 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
     if constexpr (NCH == 1) {
       tma_store_3d(&S.tmy[kSpYa], kz0, 0, X, box);
     } else {
-      tma_store_3d(&S.tmy[kSpC], kz0, 0, X, box);
-      tma_store_3d(&S.tmy[kSpYa], kz0, 0, X, box + P::BOX);
-      tma_store_3d(&S.tmy[kSpYb], kz0, 0, X, box + 2 * P::BOX);
+      if (do0) tma_store_3d(&S.tmy[kSpC], kz0, 0, X, box);
+      if (do1) {
+        tma_store_3d(&S.tmy[kSpYa], kz0, 0, X, box + P::BOX);
+        tma_store_3d(&S.tmy[kSpYb], kz0, 0, X, box + 2 * P::BOX);
+      }
     }
     tma_store_commit();
     tma_store_wait_read();
@@ -879,7 +895,8 @@ static cudaError_t launch_pencil_t(int kind, const Solve& s, const Solve* tab, i
         nz = persistent_ctas(k_zinv<L, 3>, ZiGeo<L, 3>::NT, b, L * P::NYB, 1);
         attr_set[3] = true;
       }
-      e = launch_k(k_yinv<L, 3>, gy, dim3(nt), a, st, 0, s, tab);
+      e = launch_k(k_yinv<L, 3>, dim3(L * P::NKC, yinv_split<L, 3>() ? 2 : 1, count), dim3(nt), a, st, 0,
+                   s, tab);
       if (e == cudaSuccess)
         e = launch_k(k_zinv<L, 3>, dim3(nz, 1, count), dim3(ZiGeo<L, 3>::NT), b, st, 0, s, tab);
       return e;
