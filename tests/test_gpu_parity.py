@@ -117,6 +117,20 @@ def test_ellipsoids_r128(oracle, monkeypatch, path):
     _check(oracle, w["r"], w["sigma"], w["points"], w["normals"], w["dchi"], key="ellipsoids_r128")
 
 
+def test_ellipsoids_r128_mixed_paths(oracle, monkeypatch):
+    # one path per plane kind, pinned for this grid size only: pencil forward,
+    # clusters of 2, 1 and 4 for the inverse, backward and adjoint
+    from paper_2106_03452_gb300 import libdpsr as L
+    from gpu_util import gpu_fwd_bwd, relmax
+    w = synth.workload_ellipsoids_r128()
+    monkeypatch.delenv("DPSR_PLANE_PATH", raising=False)
+    monkeypatch.setenv("DPSR_PLANE_PATHS_128", "0,2,1,4")
+    _check(oracle, w["r"], w["sigma"], w["points"], w["normals"], w["dchi"], key="ellipsoids_r128")
+    g = gpu_fwd_bwd(w["r"], w["sigma"], w["points"], w["normals"], w["dchi"])
+    assert g["status"] == 0 and g["bstatus"] == 0
+    assert L.dpsr_plan_clusters(g["plan"].handle) == [0, 2, 1, 4]
+
+
 @pytest.mark.parametrize("path", PATHS + ["tuned"])
 def test_torus_r256(oracle, monkeypatch, path):
     w = synth.workload_torus_r256()
