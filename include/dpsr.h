@@ -152,10 +152,13 @@ enum {
 };
 DPSR_API int dpsr_plan_profile(dpsr_plan plan, int enable);
 
-/* Cluster sizes (CTAs per x-plane) the plan currently uses for its four
- * plane kernels, in the order forward, forward inverse, backward, backward
- * inverse. An autotuner sets them on the first solve of each grid size in a
- * process (set DPSR_TUNE=0 to keep the static choice). */
+/* Plane paths the plan currently uses for its four plane kinds, in the
+ * order forward, forward inverse, backward, backward inverse: 0 = two pencil
+ * passes of independent CTAs, else the cluster size (CTAs per x-plane). An
+ * autotuner sets them on the first solve of each grid size in a process
+ * (DPSR_TUNE=0 keeps the static choice). The environment can fix them:
+ * DPSR_PLANE_PATHS_<r>="a,b,c,d" for grid size r, or DPSR_PLANE_PATH=c for
+ * every kind and size (c in 0, 1, 2, 4, 8). */
 DPSR_API int dpsr_plan_clusters(dpsr_plan plan, int *C4);
 DPSR_API int dpsr_plan_profile_read(dpsr_plan plan, double *ms, int *launches);
 
