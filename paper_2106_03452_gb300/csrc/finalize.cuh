@@ -126,7 +126,9 @@ __device__ inline void finalize_scalars(const Solve& S, double a, double b, bool
 // thread 0 (block_sum_ff). Thread 0 publishes them as the block's partial
 // S.part[bid]; the last of the `nblocks` blocks of the solve to arrive sums
 // all partials (each thread a strided subset, loads in flight together, then
-// the block tree: a fixed order) and writes the scalars.
+// the block tree: a fixed order) and writes the scalars. Only thread 0
+// fences, on both sides of its ticket; the block barrier orders the other
+// threads' accesses around it (the pattern of a cooperative grid barrier).
 template <int NT>
 __device__ inline void last_block_finalize(const Solve& S, int ticket, int nblocks, int bid, FF a,
                                            FF b, bool bwd) {
@@ -136,10 +138,10 @@ __device__ inline void last_block_finalize(const Solve& S, int ticket, int nbloc
     S.part[bid] = make_float4(a.hi, a.lo, b.hi, b.lo);
     __threadfence();  // this block's partials before its arrival
     last = atomicAdd(&S.sc->ticket[ticket], 1u) == (unsigned)nblocks - 1u ? 1u : 0u;
+    if (last) __threadfence();  // every arrival before the reads below
   }
   __syncthreads();
   if (!last) return;
-  __threadfence();
   FF x = {0.f, 0.f}, y = {0.f, 0.f};
 #pragma unroll 4
   for (int i = tid; i < nblocks; i += NT) {

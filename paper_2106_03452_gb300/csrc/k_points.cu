@@ -122,12 +122,16 @@ __global__ void __launch_bounds__(256) k_bin_count(const __grid_constant__ Solve
   __syncthreads();
   for (int i = threadIdx.x; i < nb; i += blockDim.x)
     if (h[i]) atomicAdd(&S.bins[i], h[i]);
-  __threadfence();  // this thread's counts before the block's arrival
+  // the block's counts before its arrival: a block barrier, then one fence
+  // and the ticket in thread 0 (the pattern of a cooperative grid barrier)
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&S.sc->ticket[2], 1u) == gridDim.x - 1u;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&S.sc->ticket[2], 1u) == gridDim.x - 1u;
+    if (last) __threadfence();  // every block's counts before the scan
+  }
   __syncthreads();
   if (!last) return;
-  __threadfence();
   scan_bins<256>(S);
 }
 
