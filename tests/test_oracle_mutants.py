@@ -24,6 +24,10 @@ MUTANTS = [
     ("bwd_dw_sign", "df[d] = del[d] ? (double)r : -(double)r;", "df[d] = del[d] ? -(double)r : (double)r;"),
     ("bwd_no_conj", "tmp[j] = conj(spectral_H(a, k, r, sigma)) * Ghat[j];", "tmp[j] = spectral_H(a, k, r, sigma) * Ghat[j];"),
     ("bwd_s_bar_sign", "const double s_bar = -kM * sgn", "const double s_bar = kM * sgn"),
+    ("bwd_mean_term_is_rest", "if (dpts_mean) dpts_mean[3 * i + d] = gm[d];",
+     "if (dpts_mean) dpts_mean[3 * i + d] = gc[d];"),
+    ("bwd_mean_term_no_mu_bar", "gm[d] += (mu_bar / (double)N) * st.dw[v][d]",
+     "gm[d] += (1.0 / (double)N) * st.dw[v][d]"),
 ]
 
 

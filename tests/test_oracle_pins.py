@@ -231,3 +231,48 @@ def test_splat_gather_adjoint(oracle):
     lhs = float(np.sum(oracle.splat(r, pts, v[:, None]) * G))
     rhs = float(np.dot(v, oracle.gather(G, pts)))
     assert math.isclose(lhs, rhs, rel_tol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# The part of dL/dpoints that flows through the mean of Eq. 4, on its own.
+# Hold chi' fixed at the unperturbed points and let only mu(c) = mean_i of the
+# trilinear lookup of chi' at c_i move (s = chi'(0) - mu moves with it):
+#   L_mu(c) = sum_j dchi_j m / |chi'(0) - mu(c)| (chi'_j - mu(c)).
+# Its central finite differences in c are the mean term the oracle returns
+# separately. The rest, dL/dpoints minus that term, is the finite difference of
+# L with chi' recomputed from the moved points while mu looks chi' up at the
+# unmoved points (the lookup weights frozen; the change of chi' itself still
+# reaches mu and s).
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("r,sigma,N", [(8, 1.0, 25), (16, 2.0, 3)])
+def test_backward_mean_term_finite_differences(oracle, r, sigma, N):
+    rng = synth.Rng(53 + r + N)
+    pts = 0.15 + 0.7 * rng.uniform(N, 3)
+    f = pts * r - np.floor(pts * r)
+    pts = (np.floor(pts * r) + np.clip(f, 0.01, 0.99)) / r   # off the cell faces
+    nrm = rng.normal(N, 3)
+    G = rng.normal(r, r, r)
+    dp, dn, dm = oracle.backward(r, sigma, pts, nrm, G, mean_term=True)
+    _, chip, _, _ = oracle.forward(r, sigma, pts, nrm, full=True)
+    m = 0.5
+
+    def L_mu(p):
+        mu = float(np.mean(oracle.gather(chip, p)))
+        return float(np.sum(G * (m / abs(chip[0, 0, 0] - mu)) * (chip - mu)))
+
+    def L_rest(p):  # the lookup weights of mu frozen at the unmoved points
+        _, cp, _, _ = oracle.forward(r, sigma, p, nrm, full=True)
+        mu = float(np.mean(oracle.gather(cp, pts)))
+        return float(np.sum(G * (m / abs(cp[0, 0, 0] - mu)) * (cp - mu)))
+
+    h = 1e-6
+    scale = max(np.max(np.abs(dm)), np.max(np.abs(dp - dm)))
+    for i in range(min(N, 6)):
+        for d in range(3):
+            pp, pm = pts.copy(), pts.copy()
+            pp[i, d] += h
+            pm[i, d] -= h
+            fd = (L_mu(pp) - L_mu(pm)) / (2 * h)
+            assert abs(fd - dm[i, d]) <= 1e-7 * scale, (i, d, fd, dm[i, d])
+            fd = (L_rest(pp) - L_rest(pm)) / (2 * h)
+            assert abs(fd - (dp[i, d] - dm[i, d])) <= 1e-7 * scale, (i, d, fd, dp[i, d] - dm[i, d])
