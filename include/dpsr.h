@@ -57,7 +57,7 @@ typedef struct dpsr_plan_s *dpsr_plan;
 
 enum {
     DPSR_OK = 0,
-    DPSR_EINVAL = -1,      /* bad argument: r not a power of two in [8, 256], N < 1, NULL, ... */
+    DPSR_EINVAL = -1,      /* bad argument: r not a power of two in range, N < 1, NULL, ... */
     DPSR_ENOMEM = -2,      /* device allocation failed */
     DPSR_ECUDA = -3,       /* a CUDA runtime call failed */
     DPSR_EDEGENERATE = -4, /* non-finite input or chi'(0) - mu == 0 (no finite scale) */
@@ -96,9 +96,15 @@ DPSR_API size_t dpsr_plan_workspace_bytes(int r, int64_t n_max, int with_bwd);
 DPSR_API int dpsr_forward(dpsr_plan plan, const float *points, const float *normals, int64_t N,
                  float *chi_out);
 
-/* Backward pass: given dchi = dL/dchi (r^3, device), overwrite dpoints and
- * dnormals (N x 3, device) with dL/dpoints and dL/dnormals of the last
- * forward pass on this plan. Returns DPSR_ESTATE if no forward pass ran. */
+/* Backward pass: the exact adjoint (reverse-mode derivative, what Eq. 5
+ * backpropagates through) of Eq. 4 (normalisation, including the mean mu and
+ * the scale s), Eq. 3 / A7 (spectral solve: conj(H_a) = -H_a) and Eq. A1-A2
+ * (the splat: its transpose is the trilinear gather, plus the derivative of
+ * the trilinear weights for dL/dpoints). Given dchi = dL/dchi (r^3, device,
+ * 16-byte aligned), overwrite dpoints and dnormals (N x 3, device) with
+ * dL/dpoints and dL/dnormals of the last forward pass on this plan. Returns
+ * DPSR_ESTATE if no forward pass ran, DPSR_EINVAL for a NULL or misaligned
+ * pointer. */
 DPSR_API int dpsr_backward(dpsr_plan plan, const float *dchi, float *dpoints, float *dnormals);
 
 /* Host-memory variants: the same computation with host input and output
@@ -109,10 +115,21 @@ DPSR_API int dpsr_forward_host(dpsr_plan plan, const float *points, const float 
 DPSR_API int dpsr_backward_host(dpsr_plan plan, const float *dchi, float *dpoints, float *dnormals);
 
 /* Wait for the plan's stream; return the device status of the work queued so
- * far (DPSR_OK, DPSR_EDEGENERATE, ...) and clear it. */
+ * far and clear it: DPSR_ETIMEOUT if a bounded device wait gave up (checked
+ * first: the outputs of that call are incomplete), else DPSR_EDEGENERATE for
+ * a non-finite input or a vanishing scale of Eq. 4, else DPSR_OK. DPSR_ECUDA
+ * if the stream itself failed. */
 DPSR_API int dpsr_sync(dpsr_plan plan);
 
-/* Synchronise, then read the scalars of the last forward pass:
+/* Failure-detection check through a plan: queue on the plan's stream one
+ * kernel whose bounded wait (the wait every TMA barrier of the library uses)
+ * is on a barrier that nothing completes. It gives up after limit_s seconds
+ * (0 < limit_s <= 10) and sets the plan's status word, so that the next
+ * dpsr_sync returns DPSR_ETIMEOUT; the context and the plan stay usable.
+ * Asynchronous; DPSR_EINVAL for a bad limit. The paper has no counterpart. */
+DPSR_API int dpsr_plan_check_bounded_wait(dpsr_plan plan, double limit_s);
+
+/* Synchronise, then read the scalars of Eq. 4 of the last forward pass:
  * out[0] = mu (mean of chi' at the points), out[1] = s = chi'(0) - mu,
  * out[2] = m/|s|. chi' is recovered from chi as chi/out[2] + mu. */
 DPSR_API int dpsr_get_scalars(dpsr_plan plan, double out[3]);
@@ -167,15 +184,22 @@ DPSR_API int dpsr_plan_profile_read(dpsr_plan plan, double *ms, int *launches);
  * driver-level plugins with a fixed memory budget, or real-time loops that
  * must not enter the allocator). The paper has no counterpart: this is a
  * deployment variant of dpsr_forward. points, normals and chi_out are device
- * pointers as in dpsr_forward; `stream` is a cudaStream_t (NULL = legacy).
+ * pointers as in dpsr_forward (chi_out 16-byte aligned, else DPSR_EINVAL);
+ * `stream` is a cudaStream_t (NULL = legacy).
  * All scratch memory is one static device array of about 14 MB that every
  * GPU loading the library holds until exit; the call allocates nothing.
  * Limits: r a power of two with 8 <= r <= 64, 1 <= N <= 65536; anything
  * larger returns DPSR_EINVAL. Every call shares the array and sees what the
  * previous call left there, so calls that overlap on the GPU race: the call
- * waits for its own work and returns the device status (DPSR_OK or
- * DPSR_EDEGENERATE). The first call on a device looks up the array's device
- * address; make that first call before any stream capture on that device. */
+ * waits for its own work and returns the device status (DPSR_OK,
+ * DPSR_ETIMEOUT or DPSR_EDEGENERATE, as dpsr_sync). Concurrent calls from
+ * several host threads are not supported: they overlap on the GPU and
+ * corrupt each other's results, whatever streams they use.
+ * The call synchronises its stream and reads the status word back, which a
+ * stream capture forbids: it returns DPSR_ESTATE, without launching
+ * anything, while its stream is capturing or a capture in global mode is
+ * active. The first call in a CUDA context of a device (and again after a
+ * device reset) looks up the array's device address. */
 DPSR_API int dpsr_forward_static(int r, float sigma, const float *points, const float *normals,
                                  int64_t N, float *chi_out, void *stream);
 

@@ -321,6 +321,12 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 namespace dpsr {
 static thread_local bool t_pdl_off = false;
 
+int status_code(unsigned st) {
+  if (st & kStTimeout) return DPSR_ETIMEOUT;  // a wait gave up: the outputs are incomplete
+  if (st) return DPSR_EDEGENERATE;
+  return DPSR_OK;
+}
+
 bool pdl_enabled() {
   static const bool on = [] {
     const char* v = std::getenv("DPSR_PDL");
@@ -683,10 +689,19 @@ int dpsr_sync(dpsr_plan p) {
     return DPSR_ECUDA;
   }
   const unsigned st = *p->status_host;
-  if (st) {
-    cudaMemset(p->s.status, 0, sizeof(unsigned));
-    return DPSR_EDEGENERATE;
+  if (st) cudaMemset(p->s.status, 0, sizeof(unsigned));
+  return dpsr::status_code(st);
+}
+
+int dpsr_plan_check_bounded_wait(dpsr_plan p, double limit_s) {
+  if (!p || !(limit_s > 0.0 && limit_s <= 10.0)) return DPSR_EINVAL;
+  DeviceGuard dg(p->device);
+  if (!dg.ok) return DPSR_ECUDA;
+  if (dpsr::launch_wait_probe(p->s.status, limit_s, p->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return DPSR_ECUDA;
   }
+  cudaEventRecord(p->done_ev, p->stream);
   return DPSR_OK;
 }
 

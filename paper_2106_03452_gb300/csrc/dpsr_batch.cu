@@ -278,10 +278,14 @@ int dpsr_batch_sync(dpsr_batch b) {
     cudaGetLastError();
     return DPSR_ECUDA;
   }
+  // worst first: a failed CUDA call, then a timed-out wait, then a degenerate input
+  auto rank = [](int st) {
+    return st == DPSR_ECUDA ? 3 : (st == DPSR_ETIMEOUT ? 2 : (st == DPSR_OK ? 0 : 1));
+  };
   int worst = DPSR_OK;
   for (dpsr_plan p : b->plans) {
     const int st = dpsr_sync(p);
-    if (st != DPSR_OK) worst = st;
+    if (rank(st) > rank(worst)) worst = st;
   }
   return worst;
 }

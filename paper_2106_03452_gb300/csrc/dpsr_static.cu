@@ -16,14 +16,21 @@
 // Sharing: every call, on every stream, uses the same array, and the array
 // keeps what the last call left in it. Calls that overlap on the GPU race on
 // it and corrupt each other's results; this entry point therefore waits for
-// its own work to finish before it returns. What must start at zero (the bin
-// counters and the status word) is cleared at the start of each call.
+// its own work to finish before it returns. Calls from several host threads
+// at once overlap on the GPU whatever streams they use, so they are not
+// supported. What must start at zero (the bin counters and the status word)
+// is cleared at the start of each call.
 //
-// Set-up: the first call on a device looks up the device address of the
-// array (cudaGetSymbolAddress, with that device current). That first call
-// should come before any stream capture on that device.
+// Set-up: the first call in a CUDA context of a device looks up the device
+// address of the array (cudaGetSymbolAddress, with that device current) and
+// keeps it with the context's unique id; a device reset makes a new context,
+// and the next call looks the address up again. The call synchronises its
+// stream and reads the status word back, so it refuses to run (DPSR_ESTATE)
+// while a stream capture is active.
 #include <math.h>
 #include <mutex>
+
+#include <cudaTypedefs.h>
 
 #include "dpsr.h"
 #include "dpsr_dev.cuh"
@@ -58,14 +65,42 @@ static __device__ __align__(256) unsigned char g_dpsr_static_scratch[kScratchByt
 namespace {
 
 std::mutex g_mu;
-void* g_addr[64] = {};  // device address of the array, per device ordinal
+void* g_addr[64] = {};                 // device address of the array, per device ordinal
+unsigned long long g_ctx_id[64] = {};  // unique id of the context it was looked up in
 
-// Look up (once per device, with that device current) the device address of
-// the static array. The array's name in host code is only a stand-in.
+// Unique id (never reused within the process) of the device's current
+// context, through the driver entry points the runtime hands out; 0 if it
+// cannot be read.
+unsigned long long current_context_id() {
+  static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_cur = (PFN_cuCtxGetCurrent_v4000)p;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = (PFN_cuCtxGetId_v12000)p;
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_cur || !get_id || get_cur(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Look up (once per device and context, with that device current) the device
+// address of the static array. The array's name in host code is only a
+// stand-in: a kernel given it would fault or, where the GPU can reach host
+// memory, silently use the wrong memory.
 int scratch_address(int dev, unsigned char** out) {
   if (dev < 0 || dev >= 64) return DPSR_EINVAL;
+  const unsigned long long id = current_context_id();  // 0: unknown, look up again
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  if (!g_addr[dev] || id == 0 || id != g_ctx_id[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_dpsr_static_scratch);
     if (e != cudaSuccess || !p) {
@@ -73,9 +108,23 @@ int scratch_address(int dev, unsigned char** out) {
       return DPSR_ECUDA;
     }
     g_addr[dev] = p;
+    g_ctx_id[dev] = id;
   }
   *out = (unsigned char*)g_addr[dev];
   return DPSR_OK;
+}
+
+// Whether work queued on `st` now would be captured: its own capture, or a
+// global-mode capture on another stream (which makes the query on the legacy
+// stream fail). Either way this entry point must not run.
+bool capture_active(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return cs != cudaStreamCaptureStatusNone;
 }
 
 }  // namespace
@@ -86,12 +135,14 @@ extern "C" DPSR_API int dpsr_forward_static(int r, float sigma, const float* poi
   if (r < 8 || r > kMaxR || (r & (r - 1)) != 0) return DPSR_EINVAL;
   if (N < 1 || N > kMaxN) return DPSR_EINVAL;
   if (!points || !normals || !chi_out || !(sigma >= 0.f) || !isfinite(sigma)) return DPSR_EINVAL;
+  if (((uintptr_t)chi_out & 15) != 0) return DPSR_EINVAL;  // written by bulk and vector stores
+  cudaStream_t st = (cudaStream_t)stream;
+  if (capture_active(st)) return DPSR_ESTATE;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return DPSR_ECUDA;
   unsigned char* base = nullptr;
   int rc = scratch_address(dev, &base);
   if (rc != DPSR_OK) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
 
   // Per-call tables: twiddles, per-axis Gaussian factor, u^2, derivative u.
   float2 htw[kMaxR];
@@ -148,5 +199,5 @@ extern "C" DPSR_API int dpsr_forward_static(int r, float sigma, const float* poi
   unsigned status = 0;
   if (cudaMemcpy(&status, s.status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
     return DPSR_ECUDA;
-  return status ? DPSR_EDEGENERATE : DPSR_OK;
+  return dpsr::status_code(status);
 }

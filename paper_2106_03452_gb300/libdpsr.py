@@ -41,6 +41,7 @@ _PROTOS = {
     "dpsr_plan_last_launches": (_c_int, [_vp]),
     "dpsr_strerror": (ctypes.c_char_p, [_c_int]),
     "dpsr_check_bounded_wait": (_c_int, [ctypes.c_double]),
+    "dpsr_plan_check_bounded_wait": (_c_int, [_vp, ctypes.c_double]),
     "dpsr_forward_static": (_c_int, [_c_int, ctypes.c_float, _vp, _vp, _c_i64, _vp, _vp]),
     "dpsr_grid_sample": (_c_int, [_vp, _c_int, _vp, _c_i64, _vp, _vp]),
     "dpsr_grid_splat": (_c_int, [_vp, _c_int, _vp, _vp, _c_i64, _c_int, _vp]),
@@ -160,6 +161,12 @@ def dpsr_strerror(code: int) -> str:
 
 def dpsr_check_bounded_wait(limit_s: float) -> int:
     return int(load().dpsr_check_bounded_wait(float(limit_s)))
+
+
+def dpsr_plan_check_bounded_wait(plan: int, limit_s: float) -> int:
+    """Queues the never-completed bounded wait on the plan's stream; the next
+    dpsr_sync(plan) reports DPSR_ETIMEOUT. Returns the call's status."""
+    return int(load().dpsr_plan_check_bounded_wait(plan, float(limit_s)))
 
 
 def dpsr_plan_profile(plan: int, enable: bool) -> None:

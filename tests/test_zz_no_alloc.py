@@ -24,8 +24,11 @@ def test_static_forward_matches_plan_forward():
     from paper_2106_03452_gb300 import synth
     from paper_2106_03452_gb300.dpsr import Plan
 
-    cases = [synth.workload_sphere_r32(), synth.workload_sphere_r32(seed=7, N=5000)]
+    cases = [synth.workload_sphere_r32(), synth.workload_sphere_r32(seed=7, N=5000),
+             synth.workload_sphere_r32(seed=8, N=300), synth.workload_sphere_r32(seed=9, N=900)]
     cases[1]["r"] = 64
+    cases[2]["r"] = 8
+    cases[3]["r"] = 16
     stream = torch.cuda.current_stream().cuda_stream
     for w in cases:
         r, sigma = w["r"], w["sigma"]
@@ -53,3 +56,31 @@ def test_static_forward_rejects_sizes_above_its_limit():
     assert L.dpsr_forward_static(128, 2.0, P.data_ptr(), P.data_ptr(), 100, out.data_ptr(), 0) == L.DPSR_EINVAL
     assert L.dpsr_forward_static(32, 2.0, P.data_ptr(), P.data_ptr(), 70000, out.data_ptr(), 0) == L.DPSR_EINVAL
     assert L.dpsr_forward_static(12, 2.0, P.data_ptr(), P.data_ptr(), 100, out.data_ptr(), 0) == L.DPSR_EINVAL
+
+
+def test_static_forward_rejects_misaligned_output_and_capture():
+    """chi_out is written by bulk and vector stores: a pointer off a 16-byte
+    boundary is rejected before anything is launched. The call synchronises
+    and reads its status back, so it refuses to run inside a stream capture."""
+    import torch
+    from paper_2106_03452_gb300 import libdpsr as L
+    from paper_2106_03452_gb300 import synth
+    w = synth.workload_sphere_r32()
+    P = torch.from_numpy(w["points"]).cuda()
+    Nn = torch.from_numpy(w["normals"]).cuda()
+    out = torch.zeros(32 ** 3 + 4, device="cuda")
+    torch.cuda.synchronize()
+    assert L.dpsr_forward_static(32, 2.0, P.data_ptr(), Nn.data_ptr(), P.shape[0], out.data_ptr() + 4, 0) \
+        == L.DPSR_EINVAL
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(out).item() == 0  # nothing ran
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        try:
+            rc = L.dpsr_forward_static(32, 2.0, P.data_ptr(), Nn.data_ptr(), P.shape[0], out.data_ptr(),
+                                       s.cuda_stream)
+        finally:
+            g.capture_end()
+    assert rc == L.DPSR_ESTATE
