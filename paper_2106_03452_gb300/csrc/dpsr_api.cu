@@ -630,9 +630,11 @@ int dpsr_forward(dpsr_plan p, const float* points, const float* normals, int64_t
   if (e != cudaSuccess) {
     cudaGetLastError();
     p->have_fwd = false;
+    // the x-pass may not have cleared the bin counters: the next forward needs them at zero
+    cudaMemsetAsync(s.bins, 0, sizeof(int) * dpsr::bins_ints(r), st);
     return cuda_err(e);
   }
-  // bin: count (+ scan) and scatter, plane pass(es), x-pass (+ scalars), inverse plane pass(es)
+  // bin: count and scatter (+ scan), plane pass(es), x-pass (+ scalars), inverse plane pass(es)
   p->last_launches = 3 + dpsr::plane_launches(p->C[0]) + dpsr::plane_launches(p->C[1]);
   cudaEventRecord(p->done_ev, st);
   p->s.N = s.N;

@@ -426,6 +426,20 @@ __host__ __device__ constexpr int nybins(int r) { return r / ybin(r); }
 __host__ __device__ constexpr int nbins(int r) { return r * nybins(r); }
 __host__ __device__ constexpr size_t bins_ints(int r) { return 3 * (size_t)nbins(r) + 1; }
 
+// Clear the bin counts and scatter cursors of a solve for its next forward
+// pass, spread over the calling grid (block bid of nblocks). Run by a kernel
+// that follows the scatter in stream order and reads neither array: the
+// forward x-pass.
+__device__ __forceinline__ void clear_bin_counters(const Solve& S, int bid, int nblocks) {
+  const int nb = nbins(S.r);
+  int* count = S.bins;
+  int* cur = S.bins + 2 * nb + 1;
+  for (int i = bid * (int)blockDim.x + (int)threadIdx.x; i < nb; i += nblocks * (int)blockDim.x) {
+    count[i] = 0;
+    cur[i] = 0;
+  }
+}
+
 struct Axis {
   int i0, i1;
   float t;

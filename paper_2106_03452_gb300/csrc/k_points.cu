@@ -18,85 +18,15 @@ __device__ __forceinline__ int bin_key(float x, float y, int r) {
   return axis_of(x, r).i0 * nybins(r) + axis_of(y, r).i0 / ybin(r);
 }
 
-// Exclusive scan of the nbins counts into off[0..nbins] and the scatter
-// cursors, by one block of NT threads; resets the counts and the last-block
-// arrival counters for the next call. Warp w owns a contiguous run of bins
-// and walks it 32 bins per round (lane = bin: coalesced loads and stores),
-// carrying its running total; a scan of the warp totals then offsets the
-// warps. (Contiguous 16-bin segments per thread made every access 64-byte
-// strided: ~9 us of one SM at r = 256.)
-template <int NT>
-__device__ void scan_bins(const Solve& S) {
-  static_assert(NT % 32 == 0 && NT <= 1024, "block of whole warps");
-  constexpr int W = NT / 32;
-  constexpr int MAXR = (4096 + NT - 1) / NT;  // rounds per warp at r = 256
-  __shared__ int wsum[W];
-  const int r = S.r, nb = nbins(r);
-  int* count = S.bins;
-  int* off = S.bins + nb;
-  int* cur = off + nb + 1;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int ch = (nb + 32 * W - 1) / (32 * W) * 32;  // bins per warp, a multiple of 32
-  const int base = w * ch, rounds = ch / 32;
-  int c[MAXR];
-#pragma unroll
-  for (int k = 0; k < MAXR; ++k) {
-    const int idx = base + 32 * k + lane;
-    c[k] = (k < rounds && idx < nb) ? __ldcg(count + idx) : 0;
-  }
-  int run = 0;  // warp total so far (uniform over the warp)
-#pragma unroll
-  for (int k = 0; k < MAXR; ++k) {
-    int incl = c[k];
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += v;
-    }
-    const int e = run + incl - c[k];
-    run += __shfl_sync(0xffffffffu, incl, 31);
-    c[k] = e;  // exclusive prefix within the warp's run
-  }
-  if (lane == 0) wsum[w] = run;
-  __syncthreads();
-  if (w == 0) {
-    const int v0 = lane < W ? wsum[lane] : 0;
-    int v = v0;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int u = __shfl_up_sync(0xffffffffu, v, d);
-      if (lane >= d) v += u;
-    }
-    if (lane < W) wsum[lane] = v - v0;  // exclusive over warps
-    if (lane == W - 1) off[nb] = v;     // total
-  }
-  __syncthreads();
-  const int wo = wsum[w];
-#pragma unroll
-  for (int k = 0; k < MAXR; ++k) {
-    const int idx = base + 32 * k + lane;
-    if (k < rounds && idx < nb) {
-      off[idx] = wo + c[k];
-      cur[idx] = wo + c[k];
-      count[idx] = 0;  // ready for the next call
-    }
-  }
-  if (threadIdx.x == 0) {  // arrival counters of this solve's last-block reductions
-    S.sc->ticket[0] = 0;
-    S.sc->ticket[1] = 0;
-    S.sc->ticket[2] = 0;
-  }
-}
-
 // count[key]++ per point (see nbins for the key); validates the inputs
 // (non-finite or huge values raise kStBadInput and are replaced by 0 so that
 // indexing stays in range). Per-block histogram in shared memory, then one
-// global add per touched bin; the last block to finish scans the counts.
+// global add per touched bin. The counts must be zero on entry: the forward
+// x-pass clears them (and the scatter cursors) once the scatter is done.
 __global__ void __launch_bounds__(256) k_bin_count(const __grid_constant__ Solve s0,
                                                    const Solve* __restrict__ tab) {
   static_assert(nbins(256) == 4096, "histogram size");
   __shared__ int h[4096];
-  __shared__ bool last;
   pdl_trigger();
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   const int r = S.r, nb = nbins(r);
@@ -122,27 +52,73 @@ __global__ void __launch_bounds__(256) k_bin_count(const __grid_constant__ Solve
   __syncthreads();
   for (int i = threadIdx.x; i < nb; i += blockDim.x)
     if (h[i]) atomicAdd(&S.bins[i], h[i]);
-  // the block's counts before its arrival: a block barrier, then one fence
-  // and the ticket in thread 0 (the pattern of a cooperative grid barrier)
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(&S.sc->ticket[2], 1u) == gridDim.x - 1u;
-    if (last) __threadfence();  // every block's counts before the scan
-  }
-  __syncthreads();
-  if (!last) return;
-  scan_bins<256>(S);
 }
 
+// Shared-memory slot of bin i in the scatter's scan: one pad word per 32
+// bins, so that threads scanning 16 consecutive bins each hit distinct banks.
+__device__ __forceinline__ int scan_slot(int i) { return i + (i >> 5); }
+
+// Counting-sort scatter. Every block first turns the (L2-resident) bin counts
+// into exclusive prefix sums in its own shared memory: each thread sums a
+// run of consecutive bins, a block scan offsets the runs. No block waits for
+// another, so there is no serial last-block step. Block 0 also publishes the
+// offsets off[0..nbins] (read by the plane passes) and resets the arrival
+// counters of the solve's last-block reductions. A point's slot is its bin's
+// offset plus a ticket from that bin's cursor (zero on entry; cleared again
+// by the forward x-pass).
 __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Solve s0,
                                                      const Solve* __restrict__ tab) {
+  constexpr int NT = 256, MAXNB = 4096;
+  __shared__ int h[MAXNB + MAXNB / 32];
+  __shared__ int wsum[NT / 32];
   pdl_trigger();
   pdl_wait();
   const Solve& S = tab ? tab[blockIdx.z] : s0;
-  const int r = S.r;
-  int* cur = S.bins + 2 * nbins(r) + 1;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < S.N; p += gridDim.x * blockDim.x) {
+  const int r = S.r, nb = nbins(r), tid = threadIdx.x;
+  int* off = S.bins + nb;
+  int* cur = off + nb + 1;
+  for (int i = tid; i < nb; i += NT) h[scan_slot(i)] = __ldcg(S.bins + i);
+  __syncthreads();
+  const int C = (nb + NT - 1) / NT;  // consecutive bins per thread
+  const int b0 = tid * C;
+  int run = 0;
+  for (int j = 0; j < C; ++j)
+    if (b0 + j < nb) run += h[scan_slot(b0 + j)];
+  // block-wide exclusive scan of the runs: lanes, then warps in order
+  const int lane = tid & 31, w = tid >> 5;
+  int incl = run;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += v;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  int wbase = 0, total = 0;
+#pragma unroll
+  for (int k = 0; k < NT / 32; ++k) {
+    wbase += k < w ? wsum[k] : 0;
+    total += wsum[k];
+  }
+  int acc = wbase + incl - run;
+  for (int j = 0; j < C; ++j) {
+    if (b0 + j < nb) {
+      const int c = h[scan_slot(b0 + j)];
+      h[scan_slot(b0 + j)] = acc;
+      acc += c;
+    }
+  }
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    for (int i = tid; i < nb; i += NT) off[i] = h[scan_slot(i)];
+    if (tid == 0) {
+      off[nb] = total;
+      S.sc->ticket[0] = 0;
+      S.sc->ticket[1] = 0;
+      S.sc->ticket[2] = 0;
+    }
+  }
+  for (int p = blockIdx.x * NT + tid; p < S.N; p += gridDim.x * NT) {
     float x = S.points[3 * p], y = S.points[3 * p + 1], z = S.points[3 * p + 2];
     float nx = S.normals[3 * p], ny = S.normals[3 * p + 1], nz = S.normals[3 * p + 2];
     if (!coord_ok(x, r)) x = 0.f;
@@ -151,7 +127,8 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Sol
     if (!isfinite(nx)) nx = 0.f;
     if (!isfinite(ny)) ny = 0.f;
     if (!isfinite(nz)) nz = 0.f;
-    const int pos = atomicAdd(&cur[S.cellx[p]], 1);  // key of k_bin_count
+    const int key = S.cellx[p];  // key of k_bin_count
+    const int pos = h[scan_slot(key)] + atomicAdd(&cur[key], 1);
     S.sorted[2 * pos] = make_float4(x, y, z, nx);
     S.sorted[2 * pos + 1] = make_float4(ny, nz, __int_as_float(p), 0.f);
   }

@@ -89,6 +89,8 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
   const int src0 = kSpD, src1 = BWD ? kSpW : kSpC;
   pdl_trigger();
   pdl_wait();
+  // the binning of this forward pass is done: its counters start the next one at zero
+  if constexpr (!BWD) clear_bin_counters(S, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
   if (tid == 0) {
 #pragma unroll
     for (int c = 0; c < NCH; ++c) mbar_init(&bar[c], 1);
