@@ -390,7 +390,8 @@ def bench_batched(args, dev, dist, ws, timed):
            "solves_per_s": ws * 32 * k / (ms_b / 1e3), "ms_per_batch": ms_b / k,
            "loop_solves_per_s": ws * 32 * k / (ms_l / 1e3), "loop_ms_per_batch": ms_l / k,
            "speedup_vs_loop": ms_l / ms_b, "launches_per_batch": batch.launches(True),
-           "loop_launches_per_batch": 32 * loop_launches}
+           "loop_launches_per_batch": 32 * loop_launches,
+           "paths": {str(r): batch.paths(r) for r in sorted({w["r"] for w in inst})}}
     batch.close()
     for p in plans:
         p.close()

@@ -234,6 +234,14 @@ DPSR_API int dpsr_batch_graph_launch(dpsr_batch batch, int with_bwd);
 DPSR_API int dpsr_batch_sync(dpsr_batch batch);
 /* Kernel launches in one forward (+ backward) of the batch. */
 DPSR_API int dpsr_batch_launches(dpsr_batch batch, int with_bwd);
+/* Plane paths of the batch's instances of grid size r, in the order of
+ * dpsr_plan_clusters (0 = pencil passes, else the cluster size). A batch
+ * tunes them on its first eager run (dpsr_batch_forward / _backward, or the
+ * first dpsr_batch_graph_launch, which runs the sequence once before it
+ * captures it): each plane kind of each grid size is timed over every path on
+ * the batch's own instances and the fastest kept. DPSR_EINVAL if the batch
+ * has no instance of size r. */
+DPSR_API int dpsr_batch_paths(dpsr_batch batch, int r, int *C4);
 
 /* ------------------------------------------------------------------------
  * Serving. A server runs submitted solves concurrently on `slots` CUDA

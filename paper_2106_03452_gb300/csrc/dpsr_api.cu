@@ -567,6 +567,14 @@ int dpsr_internal_cluster(dpsr_plan p, int kind) {
   return p->C[kind];
 }
 
+// The path of plane kind `kind` at grid size r fixed by the environment, or
+// -1 (tune), or -2 (tuning switched off: keep the plan's choice).
+int dpsr_internal_forced(int kind, int r) {
+  const int forced = forced_path(kind, r);
+  if (forced >= 0) return forced;
+  return tuning_enabled() ? -1 : -2;
+}
+
 int dpsr_plan_clusters(dpsr_plan p, int* C4) {
   if (!p || !C4) return DPSR_EINVAL;
   for (int k = 0; k < 4; ++k) C4[k] = p->C[k];

@@ -19,6 +19,7 @@ using dpsr::Solve;
 // Internal hooks of dpsr_api.cu (same library).
 extern "C" const void* dpsr_internal_solve(dpsr_plan p);
 extern "C" int dpsr_internal_cluster(dpsr_plan p, int kind);
+extern "C" int dpsr_internal_forced(int kind, int r);
 
 struct BatchClass {
   int r = 0;
@@ -26,6 +27,7 @@ struct BatchClass {
   Solve* dtab = nullptr;     // device table, one descriptor per member
   int nmax = 0;
   int C[4] = {1, 1, 1, 1};
+  bool tuned[4] = {false, false, false, false};
   // Classes run side by side: each on its own stream, forked from and
   // joined back into the batch stream (also inside a captured graph).
   cudaStream_t st = nullptr;
@@ -99,6 +101,96 @@ cudaError_t launch_bwd(dpsr_batch b) {
     if (e == cudaSuccess) e = dpsr::launch_combine(dummy, c.dtab, n, c.nmax, st);
     return e;
   });
+}
+
+// Batch autotuner. A class launch covers all of its instances, so it is
+// bound by throughput where a solo solve is bound by latency, and the best
+// plane path can differ from the solo choice. On the first eager run of a
+// batch, each plane kind of each class is timed over every path that fits
+// (the pencil passes and each cluster size; fastest of three timed runs after
+// an untimed one) on the class's own instances, in the order of the solve, so
+// that every kind runs on its real inputs; the last run leaves the chosen
+// path's results. The environment's fixed paths (DPSR_PLANE_PATH[S_<r>]) and
+// DPSR_TUNE=0 take precedence.
+cudaError_t tune_kind(BatchClass& c, int kind, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+  const Solve dummy = {};
+  const int n = (int)c.members.size();
+  const int forced = dpsr_internal_forced(kind, c.r);
+  if (forced != -1) {
+    if (forced >= 0) c.C[kind] = forced;
+    c.tuned[kind] = true;
+    return dpsr::launch_plane(kind, c.r, c.C[kind], dummy, c.dtab, n, st);
+  }
+  const int cands[5] = {0, 1, 2, 4, 8};
+  float best = 1e30f;
+  int bestC = c.C[kind];
+  for (int C : cands) {
+    const size_t sm = dpsr::plane_smem_bytes(kind, c.r, C);
+    if (sm == 0 || sm > 227 * 1024 - 1024) continue;
+    cudaError_t e = dpsr::launch_plane(kind, c.r, C, dummy, c.dtab, n, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    float ms = 1e30f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      float m = 0.f;
+      e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess) e = dpsr::launch_plane(kind, c.r, C, dummy, c.dtab, n, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&m, e0, e1);
+      if (e == cudaSuccess && m < ms) ms = m;
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (ms < best) {
+      best = ms;
+      bestC = C;
+    }
+  }
+  c.C[kind] = bestC;
+  c.tuned[kind] = true;
+  return dpsr::launch_plane(kind, c.r, bestC, dummy, c.dtab, n, st);
+}
+
+// One eager forward (and backward) of every class on the batch stream, tuning
+// the plane kinds not tuned yet. Not capturable (it synchronises on events).
+cudaError_t tune_batch(dpsr_batch b, bool with_bwd) {
+  const Solve dummy = {};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  cudaStream_t st = b->stream;
+  for (auto& c : b->classes) {
+    const int n = (int)c.members.size();
+    auto plane = [&](int kind) {
+      return c.tuned[kind] ? dpsr::launch_plane(kind, c.r, c.C[kind], dummy, c.dtab, n, st)
+                           : tune_kind(c, kind, st, e0, e1);
+    };
+    if (e == cudaSuccess) e = dpsr::launch_bin(dummy, c.dtab, n, c.nmax, st);
+    if (e == cudaSuccess) e = plane(0);
+    if (e == cudaSuccess) e = dpsr::launch_xpass(false, c.r, dummy, c.dtab, n, st);
+    if (e == cudaSuccess) e = plane(1);
+    if (with_bwd) {
+      if (e == cudaSuccess) e = plane(2);
+      if (e == cudaSuccess) e = dpsr::launch_xpass(true, c.r, dummy, c.dtab, n, st);
+      if (e == cudaSuccess) e = plane(3);
+      if (e == cudaSuccess) e = dpsr::launch_combine(dummy, c.dtab, n, c.nmax, st);
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return e;
+}
+
+bool needs_tuning(dpsr_batch b, bool with_bwd) {
+  for (auto& c : b->classes)
+    for (int k = 0; k < (with_bwd ? 4 : 2); ++k)
+      if (!c.tuned[k]) return true;
+  return false;
 }
 
 void drop_graph(dpsr_batch b) {
@@ -212,7 +304,8 @@ int dpsr_batch_forward(dpsr_batch b) {
   if (!b) return DPSR_EINVAL;
   int rc = upload(b);
   if (rc != DPSR_OK) return rc;
-  if (launch_fwd(b) != cudaSuccess) {
+  const bool tune = needs_tuning(b, false);
+  if ((tune ? tune_batch(b, false) : launch_fwd(b)) != cudaSuccess) {
     cudaGetLastError();
     return DPSR_ECUDA;
   }
@@ -227,7 +320,9 @@ int dpsr_batch_backward(dpsr_batch b) {
     if (!b->host[i].dchi || !b->host[i].dpoints || !b->host[i].dnormals) return DPSR_EINVAL;
   int rc = upload(b);
   if (rc != DPSR_OK) return rc;
-  if (launch_bwd(b) != cudaSuccess) {
+  // tuning the backward kinds runs the forward again first (it is idempotent)
+  const bool tune = needs_tuning(b, true);
+  if ((tune ? tune_batch(b, true) : launch_bwd(b)) != cudaSuccess) {
     cudaGetLastError();
     return DPSR_ECUDA;
   }
@@ -244,6 +339,12 @@ int dpsr_batch_graph_launch(dpsr_batch b, int with_bwd) {
   if (!b->graph || b->graph_bwd != (with_bwd ? 1 : 0)) {
     drop_graph(b);
     if (b->stream == nullptr) return DPSR_EINVAL;  // capture needs a non-default stream
+    if (needs_tuning(b, with_bwd != 0)) {  // picks the paths the graph will hold
+      if (tune_batch(b, with_bwd != 0) != cudaSuccess) {
+        cudaGetLastError();
+        return DPSR_ECUDA;
+      }
+    }
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return DPSR_ECUDA;
@@ -288,6 +389,16 @@ int dpsr_batch_sync(dpsr_batch b) {
     if (rank(st) > rank(worst)) worst = st;
   }
   return worst;
+}
+
+int dpsr_batch_paths(dpsr_batch b, int r, int* C4) {
+  if (!b || !C4) return DPSR_EINVAL;
+  for (const auto& c : b->classes)
+    if (c.r == r) {
+      for (int k = 0; k < 4; ++k) C4[k] = c.C[k];
+      return DPSR_OK;
+    }
+  return DPSR_EINVAL;
 }
 
 int dpsr_batch_launches(dpsr_batch b, int with_bwd) {

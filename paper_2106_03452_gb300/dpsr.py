@@ -157,6 +157,10 @@ class Batch:
     def sync(self) -> int:
         return L.dpsr_batch_sync(self.handle)
 
+    def paths(self, r: int):
+        """Plane paths (tuned on the first run) of the instances of size r."""
+        return L.dpsr_batch_paths(self.handle, r)
+
     def launches(self, with_bwd=True) -> int:
         return L.dpsr_batch_launches(self.handle, with_bwd)
 

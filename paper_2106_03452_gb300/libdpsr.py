@@ -47,6 +47,7 @@ _PROTOS = {
     "dpsr_grid_splat": (_c_int, [_vp, _c_int, _vp, _vp, _c_i64, _c_int, _vp]),
     "dpsr_plan_profile": (_c_int, [_vp, _c_int]),
     "dpsr_plan_clusters": (_c_int, [_vp, ctypes.POINTER(_c_int)]),
+    "dpsr_batch_paths": (_c_int, [_vp, _c_int, ctypes.POINTER(_c_int)]),
     "dpsr_batch_create": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(_c_i64), ctypes.POINTER(_vp)]),
     "dpsr_batch_destroy": (_c_int, [_vp]),
@@ -240,6 +241,13 @@ def dpsr_batch_sync(batch: int) -> int:
 
 def dpsr_batch_launches(batch: int, with_bwd: bool = True) -> int:
     return int(load().dpsr_batch_launches(batch, 1 if with_bwd else 0))
+
+
+def dpsr_batch_paths(batch: int, r: int):
+    """The four plane paths of the batch's instances of grid size r."""
+    out = (_c_int * 4)()
+    check(load().dpsr_batch_paths(batch, int(r), out), "dpsr_batch_paths")
+    return [int(v) for v in out]
 
 
 def dpsr_server_create(hbm_budget_bytes: int, slots: int = 8, sigma: float = 2.0) -> int:

@@ -69,3 +69,37 @@ def test_batch_equals_solo_and_oracle(oracle, monkeypatch, path):
     n = batch.launches(True)
     assert 2 * 9 <= n <= 2 * 13 and (path != "pencil" or n == 2 * 13)
     batch.close()
+
+
+def test_batch_mixed_sigma_and_sizes(oracle):
+    """One batch whose instances differ in sigma (0 = no smoothing, up to 5
+    grid units: the coarse-to-fine schedule of the optimisation setting varies
+    sigma per level) and in r (32 / 64): every instance matches the FP64
+    oracle at its own sigma, so the per-instance Gaussian tables are not
+    shared across the class."""
+    import torch
+    from paper_2106_03452_gb300 import synth
+    from paper_2106_03452_gb300.dpsr import Batch
+    sigmas = [0.0, 1.0, 2.0, 3.0, 5.0, 2.5]
+    rs = [32, 64, 32, 64, 32, 64]
+    inst = [synth.workload_sphere_r32(seed=200 + i, N=1500 + 300 * i) for i in range(len(rs))]
+    batch = Batch(rs, sigmas, [w["points"].shape[0] for w in inst])
+    T = []
+    for i, w in enumerate(inst):
+        r = rs[i]
+        P = torch.from_numpy(w["points"]).cuda()
+        Nn = torch.from_numpy(w["normals"]).cuda()
+        G = torch.from_numpy(synth.upstream_grad(synth.Rng(300 + i), r)).cuda()
+        chi = torch.empty((r, r, r), device="cuda")
+        dp, dn = torch.empty_like(P), torch.empty_like(P)
+        batch.bind(i, P, Nn, chi, G, dp, dn)
+        T.append((G, chi, dp, dn))
+    batch.run(with_bwd=True, graph=True)
+    assert batch.sync() == 0
+    for i, w in enumerate(inst):
+        G, chi, dp, dn = T[i]
+        ref = oracle.forward(rs[i], sigmas[i], w["points"], w["normals"])
+        assert _rel(chi.cpu(), ref) <= 1e-5, (i, sigmas[i])
+        rdp, rdn = oracle.backward(rs[i], sigmas[i], w["points"], w["normals"], G.cpu().numpy())
+        assert _rel(dp.cpu(), rdp) <= 1e-4 and _rel(dn.cpu(), rdn) <= 1e-4, (i, sigmas[i])
+    batch.close()
