@@ -294,12 +294,29 @@ def run_gpu(args):
                 # autotuned plane paths (0 pencil, else cluster size) of the four
                 # plane kinds; DPSR_PLANE_PATHS_256 pins them for a profiler run
                 "paths": L.dpsr_plan_clusters(plan3.handle)}
+        # the differentiable loop of this workload: 50 Adam steps of
+        # L = mean chi(q)^2 over its 200 000 clean targets through the adjoint
+        from paper_2106_03452_gb300.loop import optimize
+        Q3 = torch.from_numpy(w3["targets"]).to(dev)
+        hist, _, _, s_step = optimize(P3, N3t, Q3, r=r3, sigma=w3["sigma"], steps=50, plan=plan3)
+        r256["loop"] = {"workload": "50 Adam steps of mean chi(q)^2 over 200000 targets, lr 2e-3 * 0.7^3",
+                        "s_per_step": s_step, "loss_first": hist[0], "loss_last": hist[-1]}
         plan3.close()
 
     # ---------------- batched: 32 clouds, r in {64, 128} ----------------
     batched = None
     if not args.no_batch:
         batched = bench_batched(args, dev, dist, ws, timed)
+
+    # ---------------- L_DPSR training step (Eq. 9) at 128^3 ----------------
+    train = None
+    if not args.no_train:
+        train = bench_train(args, dev, dist, ws, timed)
+
+    # ---------------- L2 read bandwidth (the ceiling of the L2-resident r = 128 solve) ----
+    l2 = measure_l2_read(dev)
+    l2_ach = per[dom]["bytes"] / (per[dom]["ms"] / 1e3) / 1e9
+    solve_gbs = solve_bytes_model(r, N) / (ms_max / args.steps / 1e3) / 1e9
 
     # ---------------- serving: Poisson arrivals at 200 req/s ----------------
     serving = None
@@ -325,12 +342,21 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                          "frac": ach / hbm_peak, "traffic": None, "kernel": dom,
                          "peak_kind": peak_kind,
-                         "bytes_per_launch": per[dom]["bytes"], "ms_per_launch": per[dom]["ms"]},
+                         "bytes_per_launch": per[dom]["bytes"], "ms_per_launch": per[dom]["ms"],
+                         # the r = 128 working set stays in L2: the same bytes against the
+                         # L2 copy bandwidth measured here, and the whole solve's byte model
+                         "l2": {"achieved": l2_ach, "peak": l2, "unit": "GB/s",
+                                "frac": l2_ach / l2 if l2 else None,
+                                "peak_kind": "measured in this run: L2 read bandwidth, 64 reads of a 24 MiB buffer in one kernel"},
+                         "solve": {"model_bytes": solve_bytes_model(r, N), "achieved": solve_gbs,
+                                   "frac_hbm": solve_gbs / hbm_peak,
+                                   "frac_l2": solve_gbs / l2 if l2 else None}},
             "kernels": per,
             "paths": L.dpsr_plan_clusters(plan.handle),  # see r256["paths"]
             "clocks": clk,
             "r256": r256,
             "batched": batched,
+            "train": train,
             "serving": serving,
             "cpu_baseline": cpu,
         }
@@ -339,6 +365,96 @@ def run_gpu(args):
     plan_h.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def measure_l2_read(dev) -> float | None:
+    """L2 read bandwidth: one reduction kernel reads a 24 MiB buffer 64 times
+    over (a stride-0 expanded view, 1.5 GiB of reads in one launch), so every
+    read after the first pass hits L2; best of 10 after warm-up."""
+    import torch
+    try:
+        a = torch.ones(24 * 2 ** 20 // 4, device=dev)
+        K = 64
+        v = a.expand(K, a.numel())
+        for _ in range(3):
+            v.sum(1)
+        best = 1e30
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            v.sum(1)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return K * a.numel() * 4 / (best / 1e3) / 1e9
+    except Exception:
+        return None
+
+
+def bench_train(args, dev, dist, ws, timed):
+    """The L_DPSR training step of the learning setting (Sec. 3.3, Eq. 9;
+    supplementary Sec. B) at 128^3: 8 instances (the paper trains with batch
+    32 on two GPUs), each a predicted cloud of 3000 x 7 = 21 000 points
+    against a ground-truth grid solved once from a 100 000-point sampling.
+    One step = forward, fused loss and gradient, backward of every instance,
+    as one CUDA graph launch; against a per-solve loop (forward, loss,
+    backward per instance) of the same kernels."""
+    import torch
+
+    from paper_2106_03452_gb300 import synth
+    from paper_2106_03452_gb300.dpsr import Batch, Plan
+    r, sigma, count = 128, 2.0, 8
+    gtb = Batch([r] * count, [sigma] * count, [100000] * count, device=dev)
+    data, gts = [], []
+    for i in range(count):
+        rng = synth.Rng(2000 + i)
+        gp, gn = synth.ellipsoid_cloud(rng, 100000, 1 + i % 4, jitter=0.0)
+        pp, pn = synth.ellipsoid_cloud(rng, 21000, 1 + (i + 1) % 4, jitter=0.005)
+        g = torch.empty((r, r, r), device=dev)
+        gtb.bind(i, torch.from_numpy(gp).to(dev), torch.from_numpy(gn).to(dev), g)
+        gts.append(g)
+        data.append((torch.from_numpy(pp).to(dev), torch.from_numpy(pn).to(dev)))
+    gtb.run(with_bwd=False, graph=False)
+    if gtb.sync() != 0:
+        raise RuntimeError("ground-truth batch device status")
+    b = Batch([r] * count, [sigma] * count, [21000] * count, device=dev)
+    T = []
+    for i, (P, Nn) in enumerate(data):
+        chi, dchi = torch.empty((r, r, r), device=dev), torch.empty((r, r, r), device=dev)
+        dp, dn = torch.empty_like(P), torch.empty_like(P)
+        b.bind(i, P, Nn, chi, dchi, dp, dn)
+        b.bind_target(i, gts[i])
+        T.append((P, Nn, chi, dchi, dp, dn))
+    plans = [Plan(r, sigma, device=dev, n_max=21000) for _ in range(count)]
+
+    def step_batch():
+        b.train_step()
+
+    def step_loop():
+        for p, (P, Nn, chi, dchi, dp, dn), g in zip(plans, T, gts):
+            p.forward(P, Nn, chi)
+            p.mse_grad(g, dchi)
+            p.backward(dchi, dp, dn)
+
+    step_batch()
+    if b.sync() != 0:
+        raise RuntimeError("train batch device status")
+    k = max(5, args.steps)
+    ms_b, _ = timed(step_batch, k, args.warmup, flush_l2=False)
+    ms_l, _ = timed(step_loop, k, args.warmup, flush_l2=False)
+    ms_b, ms_l = _max_over_ranks(dist, ms_b), _max_over_ranks(dist, ms_l)
+    losses = b.losses()
+    out = {"workload": "L_DPSR training step, r=128, sigma=2: 8 predicted clouds of 21000 points (unions of "
+                       "1-4 ellipsoids) against ground-truth grids solved from 100000-point samplings",
+           "steps_per_s": ws * k / (ms_b / 1e3), "ms_per_step": ms_b / k,
+           "solves_per_s": ws * count * k / (ms_b / 1e3),
+           "loop_ms_per_step": ms_l / k, "speedup_vs_loop": ms_l / ms_b,
+           "loss_mean": sum(losses) / len(losses), "paths": b.paths(r)}
+    b.close()
+    gtb.close()
+    for p in plans:
+        p.close()
+    return out
 
 
 def bench_batched(args, dev, dist, ws, timed):
@@ -507,6 +623,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--cpu-budget", type=float, default=12.0)

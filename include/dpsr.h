@@ -134,6 +134,21 @@ DPSR_API int dpsr_plan_check_bounded_wait(dpsr_plan plan, double limit_s);
  * out[2] = m/|s|. chi' is recovered from chi as chi/out[2] + mu. */
 DPSR_API int dpsr_get_scalars(dpsr_plan plan, double out[3]);
 
+/* L_DPSR of Eq. 9, the training loss of the learning setting (Sec. 3.3;
+ * supplementary Sec. B): the mean squared error between the chi of the last
+ * forward pass on this plan and a target grid (for instance the solve of a
+ * dense ground-truth sampling: 100 000 points at 128^3 in the paper),
+ * loss = (1/n) sum_j (chi_j - target_j)^2, n = r^3 (the paper prints the
+ * squared norm; the mean differs by the constant 1/n), and its gradient
+ * dchi = (2/n) (chi - target), in one fused pass. target and dchi: r^3
+ * float32 device arrays in chi's layout, 16-byte aligned, owned by the
+ * caller; dchi is overwritten and can be passed to dpsr_backward as is.
+ * Asynchronous on the plan's stream; dpsr_get_loss synchronises and reads
+ * the loss (FP64 from deterministic float-float sums). DPSR_ESTATE without a
+ * forward pass, DPSR_EINVAL for NULL or misaligned pointers. */
+DPSR_API int dpsr_mse_grad(dpsr_plan plan, const float *target, float *dchi);
+DPSR_API int dpsr_get_loss(dpsr_plan plan, double *loss);
+
 /* Number of kernel launches the last dpsr_forward / dpsr_backward queued. */
 DPSR_API int dpsr_plan_last_launches(dpsr_plan plan);
 
@@ -230,6 +245,18 @@ DPSR_API int dpsr_batch_forward(dpsr_batch batch);
 DPSR_API int dpsr_batch_backward(dpsr_batch batch);
 /* Forward, and the backward if with_bwd != 0, as one CUDA graph launch. */
 DPSR_API int dpsr_batch_graph_launch(dpsr_batch batch, int with_bwd);
+/* Training step of the learning setting (Sec. 3.3, Eq. 9) over the whole
+ * batch as one CUDA graph launch: the forward pass of every instance, the
+ * L_DPSR loss and gradient of each against its target (as dpsr_mse_grad,
+ * written into the instance's bound dchi buffer, which must be writable), and
+ * the backward pass into its dpoints / dnormals. Targets are bound per
+ * instance with dpsr_batch_bind_target (r^3 float32 device array, 16-byte
+ * aligned, caller-owned); dpsr_batch_losses synchronises and writes the
+ * `count` losses to out. DPSR_EINVAL if an instance lacks a target or a
+ * gradient buffer. */
+DPSR_API int dpsr_batch_bind_target(dpsr_batch batch, int i, const float *target);
+DPSR_API int dpsr_batch_train_step(dpsr_batch batch);
+DPSR_API int dpsr_batch_losses(dpsr_batch batch, double *out);
 /* Wait; return the worst device status over the instances (and clear them). */
 DPSR_API int dpsr_batch_sync(dpsr_batch batch);
 /* Kernel launches in one forward (+ backward) of the batch. */

@@ -715,6 +715,33 @@ int dpsr_plan_check_bounded_wait(dpsr_plan p, double limit_s) {
   return DPSR_OK;
 }
 
+int dpsr_mse_grad(dpsr_plan p, const float* target, float* dchi) {
+  if (!p || !target || !dchi) return DPSR_EINVAL;
+  if ((((uintptr_t)target) | ((uintptr_t)dchi)) & 15) return DPSR_EINVAL;  // float4 accesses
+  if (!p->have_fwd) return DPSR_ESTATE;
+  DeviceGuard dg(p->device);
+  if (!dg.ok) return DPSR_ECUDA;
+  PdlScope pdl(p->profile);
+  Solve s = p->s;
+  s.target = target;
+  s.dchi_rw = dchi;
+  if (dpsr::launch_mse_grad(s, nullptr, 1, p->r, p->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return DPSR_ECUDA;
+  }
+  cudaEventRecord(p->done_ev, p->stream);
+  return DPSR_OK;
+}
+
+int dpsr_get_loss(dpsr_plan p, double* loss) {
+  if (!p || !loss) return DPSR_EINVAL;
+  DeviceGuard dg(p->device);
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return DPSR_ECUDA;
+  if (cudaMemcpy(loss, &p->s.sc->loss, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DPSR_ECUDA;
+  return DPSR_OK;
+}
+
 int dpsr_get_scalars(dpsr_plan p, double out[3]) {
   if (!p || !out) return DPSR_EINVAL;
   if (!p->have_fwd) return DPSR_ESTATE;

@@ -45,7 +45,7 @@ struct dpsr_batch_s {
   Solve* hstage = nullptr;  // pinned staging of the tables
   cudaEvent_t fork = nullptr;
   cudaGraphExec_t graph = nullptr;
-  int graph_bwd = -1;
+  int graph_bwd = -1;  // what the graph holds: 0 forward, 1 forward + backward, 2 training step
   bool have_fwd = false;
 };
 
@@ -88,6 +88,15 @@ cudaError_t launch_fwd(dpsr_batch b) {
     if (e == cudaSuccess) e = dpsr::launch_xpass(false, c.r, dummy, c.dtab, n, st);
     if (e == cudaSuccess) e = dpsr::launch_plane(1, c.r, c.C[1], dummy, c.dtab, n, st);
     return e;
+  });
+}
+
+// L_DPSR of every instance against its bound target (Eq. 9), gradient into
+// the instance's dchi buffer.
+cudaError_t launch_mse(dpsr_batch b) {
+  const Solve dummy = {};
+  return per_class(b, [&](BatchClass& c, cudaStream_t st) {
+    return dpsr::launch_mse_grad(dummy, c.dtab, (int)c.members.size(), c.r, st);
   });
 }
 
@@ -295,6 +304,7 @@ int dpsr_batch_bind(dpsr_batch b, int i, const float* points, const float* norma
   dpsr::set_count(s, N);
   s.chi = chi;
   s.dchi = dchi;
+  s.dchi_rw = const_cast<float*>(dchi);  // written by the training step's loss pass
   s.dpoints = dpoints;
   s.dnormals = dnormals;
   return DPSR_OK;
@@ -329,18 +339,24 @@ int dpsr_batch_backward(dpsr_batch b) {
   return DPSR_OK;
 }
 
-int dpsr_batch_graph_launch(dpsr_batch b, int with_bwd) {
+// mode: 0 forward, 1 forward + backward, 2 training step (forward, L_DPSR
+// against the bound targets, backward).
+static int graph_launch(dpsr_batch b, int mode) {
   if (!b) return DPSR_EINVAL;
+  const bool with_bwd = mode != 0;
   if (with_bwd)
     for (int i = 0; i < b->count; ++i)
       if (!b->host[i].dchi || !b->host[i].dpoints || !b->host[i].dnormals) return DPSR_EINVAL;
+  if (mode == 2)
+    for (int i = 0; i < b->count; ++i)
+      if (!b->host[i].target) return DPSR_EINVAL;
   int rc = upload(b);
   if (rc != DPSR_OK) return rc;
-  if (!b->graph || b->graph_bwd != (with_bwd ? 1 : 0)) {
+  if (!b->graph || b->graph_bwd != mode) {
     drop_graph(b);
     if (b->stream == nullptr) return DPSR_EINVAL;  // capture needs a non-default stream
-    if (needs_tuning(b, with_bwd != 0)) {  // picks the paths the graph will hold
-      if (tune_batch(b, with_bwd != 0) != cudaSuccess) {
+    if (needs_tuning(b, with_bwd)) {  // picks the paths the graph will hold
+      if (tune_batch(b, with_bwd) != cudaSuccess) {
         cudaGetLastError();
         return DPSR_ECUDA;
       }
@@ -349,6 +365,7 @@ int dpsr_batch_graph_launch(dpsr_batch b, int with_bwd) {
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return DPSR_ECUDA;
     cudaError_t e = launch_fwd(b);
+    if (e == cudaSuccess && mode == 2) e = launch_mse(b);
     if (e == cudaSuccess && with_bwd) e = launch_bwd(b);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess || !g) {
@@ -363,13 +380,41 @@ int dpsr_batch_graph_launch(dpsr_batch b, int with_bwd) {
       b->graph = nullptr;
       return DPSR_ECUDA;
     }
-    b->graph_bwd = with_bwd ? 1 : 0;
+    b->graph_bwd = mode;
   }
   if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) {
     cudaGetLastError();
     return DPSR_ECUDA;
   }
   b->have_fwd = true;
+  return DPSR_OK;
+}
+
+int dpsr_batch_graph_launch(dpsr_batch b, int with_bwd) { return graph_launch(b, with_bwd ? 1 : 0); }
+
+int dpsr_batch_bind_target(dpsr_batch b, int i, const float* target) {
+  if (!b || i < 0 || i >= b->count || !target) return DPSR_EINVAL;
+  if (((uintptr_t)target) & 15) return DPSR_EINVAL;
+  b->host[i].target = target;
+  return DPSR_OK;
+}
+
+int dpsr_batch_train_step(dpsr_batch b) {
+  if (!b) return DPSR_EINVAL;
+  for (int i = 0; i < b->count; ++i)
+    if (((uintptr_t)b->host[i].dchi_rw) & 15) return DPSR_EINVAL;
+  return graph_launch(b, 2);
+}
+
+int dpsr_batch_losses(dpsr_batch b, double* out) {
+  if (!b || !out) return DPSR_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return DPSR_ECUDA;
+  }
+  for (int i = 0; i < b->count; ++i)
+    if (cudaMemcpy(&out[i], &b->host[i].sc->loss, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return DPSR_ECUDA;
   return DPSR_OK;
 }
 

@@ -350,9 +350,10 @@ struct Scalars {
   float a_chi, b_chi;     // chi = a_chi * y + b_chi, y = unnormalised inverse FFT
   float g_a, g_s, g_w;    // backward: G^ = g_a * FFT(dchi) + g_s + g_w * W^
   float c_mu;             // backward: weight of the stored lookup gradient
+  double loss;            // L_DPSR of Eq. 9 (mean squared error against a target grid)
   // arrival counters of the last-block reductions: [0] forward x-pass,
-  // [1] backward plane pass (both reset by the binning of every forward),
-  // [2] the binning's count pass (reset by its last block)
+  // [1] backward plane pass, [2] the L_DPSR loss (all reset by the binning's
+  // scatter of every forward, and each by its own last block)
   unsigned ticket[3];
 };
 
@@ -385,6 +386,8 @@ struct Solve {
   const float* dchi;
   float* dpoints;
   float* dnormals;
+  const float* target;  // L_DPSR target grid (r^3), and where its gradient goes
+  float* dchi_rw;
   // plan workspace
   float4* sorted;   // 2 records per point: (x, y, z, nx), (ny, nz, orig, 0)
   int* cellx;       // N

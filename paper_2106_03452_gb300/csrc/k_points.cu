@@ -4,6 +4,7 @@
 #include <algorithm>
 
 #include "dpsr_dev.cuh"
+#include "finalize.cuh"
 #include "launch.h"
 #include "tma.cuh"
 
@@ -210,6 +211,71 @@ __global__ void __launch_bounds__(256) k_grid_splat(float* __restrict__ grid, in
       atomicAdd(&grid[j], w * v);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// L_DPSR of Eq. 9, the training loss of the learning setting (Sec. 3.3): the
+// mean squared error between the solved indicator grid chi and a target grid
+// (the solve of a dense ground-truth sampling), and its gradient, in one pass:
+//   loss = (1/n) sum_j (chi_j - target_j)^2,   dchi_j = (2/n) (chi_j - target_j).
+// Per-thread FP32 sums, float-float block and grid sums (the last block to
+// arrive writes sc->loss), deterministic. n = r^3 is a power of two, so 2/n
+// and 1/n are exact.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_mse_grad(const __grid_constant__ Solve s0,
+                                                  const Solve* __restrict__ tab) {
+  constexpr int NT = 256;
+  pdl_trigger();
+  pdl_wait();
+  const Solve& S = tab ? tab[blockIdx.z] : s0;
+  const int64_t n4 = (int64_t)S.r * S.r * S.r / 4;
+  const float two_n = 2.f / ((float)S.r * (float)S.r * (float)S.r);
+  const float4* chi = reinterpret_cast<const float4*>(S.chi);
+  const float4* tg = reinterpret_cast<const float4*>(S.target);
+  float4* g = reinterpret_cast<float4*>(S.dchi_rw);
+  // this instance's blocks (a batch launch sizes the grid for its largest r)
+  const int nblk = (int)min((int64_t)gridDim.x, max(n4 / (2 * NT), (int64_t)1));
+  if ((int)blockIdx.x >= nblk) return;
+  float acc = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n4; i += (int64_t)nblk * NT) {
+    const float4 a = __ldcs(chi + i), b = __ldcs(tg + i);
+    const float4 d = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+    __stcs(g + i, make_float4(two_n * d.x, two_n * d.y, two_n * d.z, two_n * d.w));
+    acc += (d.x * d.x + d.y * d.y) + (d.z * d.z + d.w * d.w);
+  }
+  FF a = {acc, 0.f}, z = {0.f, 0.f};
+  block_sum_ff<NT>(a, z);
+  __shared__ unsigned last;
+  if (threadIdx.x == 0) {
+    S.part[blockIdx.x] = make_float4(a.hi, a.lo, 0.f, 0.f);
+    __threadfence();
+    last = atomicAdd(&S.sc->ticket[2], 1u) == (unsigned)nblk - 1u ? 1u : 0u;
+    if (last) __threadfence();
+  }
+  __syncthreads();
+  if (!last) return;
+  FF x = {0.f, 0.f}, y = {0.f, 0.f};
+  for (int i = threadIdx.x; i < nblk; i += NT) {
+    const float4 p = __ldcg(S.part + i);
+    x = ff_add(x, FF{p.x, p.y});
+  }
+  block_sum_ff<NT>(x, y);
+  if (threadIdx.x == 0) {
+    S.sc->loss = ff_to_double(x) / ((double)S.r * S.r * S.r);
+    S.sc->ticket[2] = 0;
+  }
+}
+
+// Blocks of the loss pass for grid size r: two float4 per thread, at most
+// the r * 16 block partials the workspace holds.
+int mse_blocks(int r) {
+  const int64_t n4 = (int64_t)r * r * r / 4;
+  const int64_t b = n4 / (2 * 256);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)r * 16));
+}
+
+cudaError_t launch_mse_grad(const Solve& s, const Solve* tab, int count, int r, cudaStream_t st) {
+  return launch_k(k_mse_grad, dim3(mse_blocks(r), 1, count), dim3(256), 0, st, 0, s, tab);
 }
 
 // A bounded wait on a barrier that nothing completes (see

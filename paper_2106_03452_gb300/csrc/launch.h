@@ -88,6 +88,9 @@ cudaError_t launch_grid_sample(const float* grid, int r, const float* q, int64_t
                                cudaStream_t st);
 cudaError_t launch_grid_splat(float* grid, int r, const float* q, const float* vals, int64_t M,
                               cudaStream_t st);
+// L_DPSR (Eq. 9) against S.target: loss into S.sc->loss, gradient into
+// S.dchi_rw. r: the grid size of every instance of the launch.
+cudaError_t launch_mse_grad(const Solve& s, const Solve* tab, int count, int r, cudaStream_t st);
 // Public status of a device status word: DPSR_ETIMEOUT when a bounded wait
 // gave up (ahead of everything else), DPSR_EDEGENERATE for any other bit.
 int status_code(unsigned st);

@@ -81,6 +81,21 @@ class Plan:
             L.dpsr_backward(self.handle, dchi.data_ptr(), dpoints.data_ptr(), dnormals.data_ptr())
         return dpoints, dnormals
 
+    def mse_grad(self, target: torch.Tensor, dchi=None) -> torch.Tensor:
+        """L_DPSR (Eq. 9) of the last forward's chi against `target`: returns
+        dL/dchi = (2/n)(chi - target); the loss is read by loss()."""
+        target = _dev_f32(target, "target", (self.r,) * 3)
+        if dchi is None:
+            dchi = torch.empty_like(target)
+        with torch.cuda.device(self.device):
+            self._bind_stream()
+            L.dpsr_mse_grad(self.handle, target.data_ptr(), dchi.data_ptr())
+        self._target = target
+        return dchi
+
+    def loss(self) -> float:
+        return L.dpsr_get_loss(self.handle)
+
     def sync(self) -> int:
         return L.dpsr_sync(self.handle)
 
@@ -156,6 +171,24 @@ class Batch:
 
     def sync(self) -> int:
         return L.dpsr_batch_sync(self.handle)
+
+    def bind_target(self, i, target):
+        """Target grid of instance i for train_step (L_DPSR, Eq. 9)."""
+        target = _dev_f32(target, "target", (self.rs[i],) * 3)
+        L.dpsr_batch_bind_target(self.handle, i, target.data_ptr())
+        self._targets = getattr(self, "_targets", {})
+        self._targets[i] = target
+
+    def train_step(self):
+        """One CUDA graph: forward, L_DPSR against the bound targets (gradient
+        into each bound dchi), backward."""
+        cur = torch.cuda.current_stream(self.device)
+        self.stream.wait_stream(cur)
+        L.dpsr_batch_train_step(self.handle)
+        cur.wait_stream(self.stream)
+
+    def losses(self):
+        return L.dpsr_batch_losses(self.handle, len(self.rs))
 
     def paths(self, r: int):
         """Plane paths (tuned on the first run) of the instances of size r."""

@@ -48,6 +48,11 @@ _PROTOS = {
     "dpsr_plan_profile": (_c_int, [_vp, _c_int]),
     "dpsr_plan_clusters": (_c_int, [_vp, ctypes.POINTER(_c_int)]),
     "dpsr_batch_paths": (_c_int, [_vp, _c_int, ctypes.POINTER(_c_int)]),
+    "dpsr_mse_grad": (_c_int, [_vp, _vp, _vp]),
+    "dpsr_get_loss": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
+    "dpsr_batch_bind_target": (_c_int, [_vp, _c_int, _vp]),
+    "dpsr_batch_train_step": (_c_int, [_vp]),
+    "dpsr_batch_losses": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "dpsr_batch_create": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(_c_i64), ctypes.POINTER(_vp)]),
     "dpsr_batch_destroy": (_c_int, [_vp]),
@@ -241,6 +246,30 @@ def dpsr_batch_sync(batch: int) -> int:
 
 def dpsr_batch_launches(batch: int, with_bwd: bool = True) -> int:
     return int(load().dpsr_batch_launches(batch, 1 if with_bwd else 0))
+
+
+def dpsr_mse_grad(plan: int, target: int, dchi: int) -> None:
+    check(load().dpsr_mse_grad(plan, target, dchi), "dpsr_mse_grad")
+
+
+def dpsr_get_loss(plan: int) -> float:
+    out = ctypes.c_double()
+    check(load().dpsr_get_loss(plan, ctypes.byref(out)), "dpsr_get_loss")
+    return float(out.value)
+
+
+def dpsr_batch_bind_target(batch: int, i: int, target: int) -> None:
+    check(load().dpsr_batch_bind_target(batch, int(i), target), "dpsr_batch_bind_target")
+
+
+def dpsr_batch_train_step(batch: int) -> None:
+    check(load().dpsr_batch_train_step(batch), "dpsr_batch_train_step")
+
+
+def dpsr_batch_losses(batch: int, count: int):
+    out = (ctypes.c_double * count)()
+    check(load().dpsr_batch_losses(batch, out), "dpsr_batch_losses")
+    return [float(v) for v in out]
 
 
 def dpsr_batch_paths(batch: int, r: int):

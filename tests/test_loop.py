@@ -42,6 +42,35 @@ def test_loss_chain_finite_differences(oracle):
             assert abs(fd - g[i, d]) <= 1e-6 * np.max(np.abs(g)) + 1e-12, (i, d, fd, g[i, d])
 
 
+@pytest.mark.slow
+def test_r256_workload_finite_differences(oracle):
+    """Step 0 of the r = 256 workload itself (N = 100 000 sources, M = 200 000
+    targets, sigma = 2): central finite differences of the FP64 oracle loss
+    chain against its adjoint, on the entries with the largest gradients among
+    points at least 2 % of a voxel away from every cell face."""
+    w = synth.workload_torus_r256()
+    r, sigma = w["r"], w["sigma"]
+    pts, nrm, q = (w[k].astype(np.float64) for k in ("points", "normals", "targets"))
+    L0, dp, dn = _oracle_loss_grad(oracle, r, sigma, pts, nrm, q)
+    f = pts * r - np.floor(pts * r)
+    off_faces = np.all((f > 0.02) & (f < 0.98), axis=1)
+    picks = []
+    for g in (dp, dn):
+        mag = np.where(off_faces[:, None], np.abs(g), 0.0)
+        flat = np.argsort(mag.ravel())[::-1][:3]
+        picks.append([divmod(int(k), 3) for k in flat])
+    h = 1e-6
+    for (arr, g, sel) in ((pts, dp, picks[0]), (nrm, dn, picks[1])):
+        for (i, d) in sel:
+            a, b = arr.copy(), arr.copy()
+            a[i, d] += h
+            b[i, d] -= h
+            la = _oracle_loss_grad(oracle, r, sigma, a if arr is pts else pts, a if arr is nrm else nrm, q)[0]
+            lb = _oracle_loss_grad(oracle, r, sigma, b if arr is pts else pts, b if arr is nrm else nrm, q)[0]
+            fd = (la - lb) / (2 * h)
+            assert abs(fd - g[i, d]) <= 1e-5 * abs(g[i, d]) + 1e-9 * np.max(np.abs(g)), (i, d, fd, g[i, d])
+
+
 @pytest.mark.gpu
 def test_r256_loop_gradient_and_descent(oracle):
     torch = pytest.importorskip("torch")
