@@ -193,27 +193,14 @@ constexpr size_t zfwd_smem() {
   return sizeof(float) * (pairs_floats<L>(2 * P::YB) + L) + sizeof(float2) * L;
 }
 
+// One z-pass tile (plane X, rows y0 .. y0 + YB - 1) on zeroed `rows`:
+// splat, R2C, bulk stores of the packed rows.
 template <int L>
-__global__ void __launch_bounds__(Pen<L>::ZNT, L >= 256 ? 3 : 4) k_zfwd(const __grid_constant__ Solve s0,
-                                                      const Solve* __restrict__ tab) {
+__device__ __forceinline__ void zfwd_tile(const Solve& S, int X, int y0, float* rows,
+                                          const float2* twt, const float* iu) {
   using P = Pen<L>;
   constexpr int YB = P::YB, H = P::H;
-  const Solve& S = tab ? tab[blockIdx.z] : s0;
-  const int X = blockIdx.x / P::NYB, y0 = (blockIdx.x % P::NYB) * YB;
   const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
-  extern __shared__ float4 smem4[];
-  constexpr int RF = pairs_floats<L>(2 * YB);
-  float* rows = reinterpret_cast<float*>(smem4);  // rows ch * YB + ly (row_off): v_y, v_z, v_x, w
-  float2* twt = reinterpret_cast<float2*>(rows + RF);
-  float* iu = reinterpret_cast<float*>(twt + L);
-  pdl_trigger();
-  for (int i = tid; i < L; i += P::ZNT) {
-    twt[i] = S.tw[i];
-    iu[i] = S.iu[i];
-  }
-  for (int i = tid; i < RF / 4; i += P::ZNT) smem4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  pdl_wait();
-  __syncthreads();
   // Rasterization (Eq. A2): points of x-cells X (dx = 0) and X - 1 (dx = 1)
   // whose stencil rows i0 or i1 fall in [y0, y0 + YB), i.e. i0 in
   // [y0 - 1, y0 + YB - 1] (mod L): per side the CTA's own bin and the
@@ -283,6 +270,30 @@ __global__ void __launch_bounds__(Pen<L>::ZNT, L >= 256 ? 3 : 4) k_zfwd(const __
   }
 }
 
+template <int L>
+__global__ void __launch_bounds__(Pen<L>::ZNT, L >= 256 ? 3 : 4) k_zfwd(const __grid_constant__ Solve s0,
+                                                      const Solve* __restrict__ tab) {
+  using P = Pen<L>;
+  constexpr int YB = P::YB;
+  const Solve& S = tab ? tab[blockIdx.z] : s0;
+  const int X = blockIdx.x / P::NYB, y0 = (blockIdx.x % P::NYB) * YB;
+  const int tid = threadIdx.x;
+  extern __shared__ float4 smem4[];
+  constexpr int RF = pairs_floats<L>(2 * YB);
+  float* rows = reinterpret_cast<float*>(smem4);  // rows ch * YB + ly (row_off): v_y, v_z, v_x, w
+  float2* twt = reinterpret_cast<float2*>(rows + RF);
+  float* iu = reinterpret_cast<float*>(twt + L);
+  pdl_trigger();
+  for (int i = tid; i < L; i += P::ZNT) {
+    twt[i] = S.tw[i];
+    iu[i] = S.iu[i];
+  }
+  for (int i = tid; i < RF / 4; i += P::ZNT) smem4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  pdl_wait();
+  __syncthreads();
+  zfwd_tile<L>(S, X, y0, rows, twt, iu);
+}
+
 // ===========================================================================
 // Forward y pass over 16 kz columns of plane X, by CTA kind (blockIdx.y):
 // 0: D = FFT(i u_z v_z) + i u_y FFT(v_y) from buffers 0 and 1 into kSpD;
@@ -307,49 +318,52 @@ constexpr size_t yfwd_smem() {
   return 1024 + sizeof(float2) * ((size_t)(BWD ? 1 : 2) * Pen<L>::BOX + L) + sizeof(float) * L;
 }
 
+// Input buffers of a y-pass tile of kind `kind` (see k_yfwd): box 0 holds
+// buf0 (input and output), box 1 (kinds 0 and merged 1) buf1.
+struct YfwdBufs {
+  int buf0, buf1;
+  bool two;
+};
 template <int L, bool BWD>
-__global__ void __launch_bounds__(ynt<L>(), BWD ? 4 : (L >= 256 ? 3 : 5)) k_yfwd(const __grid_constant__ Solve s0,
-                                                   const Solve* __restrict__ tab) {
+__device__ __forceinline__ YfwdBufs yfwd_bufs(int kind) {
+  YfwdBufs b;
+  b.buf0 = kind == 1 ? kSpC : (kind == 2 ? kSpW : kSpD);
+  b.buf1 = kind == 1 ? kSpW : 1;
+  b.two = !BWD && (kind == 0 || (kind == 1 && yfwd_merge<L>()));
+  return b;
+}
+
+// Thread 0: the TMA tile loads of a y-pass tile, completion on `bar`.
+template <int L, bool BWD>
+__device__ __forceinline__ void yfwd_issue(const Solve& S, int X, int kz0, int kind, float2* box,
+                                           uint64_t* bar) {
   using P = Pen<L>;
-  constexpr int H = P::H, NT = ynt<L>();
-  const Solve& S = tab ? tab[blockIdx.z] : s0;
-  const int X = blockIdx.x / P::NKC, kz0 = (blockIdx.x % P::NKC) * P::NCOL;
-  const int kind = BWD ? 3 : (int)blockIdx.y;
-  // box 0: input and output buf0; box 1 (two: kinds 0 and merged 1): i u_z v_z
-  // (buffer 1, kind 0) or w (kind 1)
-  const int buf0 = kind == 1 ? kSpC : (kind == 2 ? kSpW : kSpD), buf1 = kind == 1 ? kSpW : 1;
-  const bool two = !BWD && (kind == 0 || (kind == 1 && yfwd_merge<L>()));
+  const YfwdBufs b = yfwd_bufs<L, BWD>(kind);
+  mbar_expect_tx(bar, (b.two ? 2 : 1) * P::BOX * (uint32_t)sizeof(float2));
+  tma_load_3d(box, &S.tmy[b.buf0], kz0, 0, X, bar);
+  if (b.two) tma_load_3d(box + P::BOX, &S.tmy[b.buf1], kz0, 0, X, bar);
+}
+
+// All threads: wait for the tile (phase `phase` of `bar`), transform, store
+// (thread 0 waits until the stores have read shared memory). False if the
+// bounded wait gave up (status set; the caller leaves).
+template <int L, bool BWD>
+__device__ __forceinline__ bool yfwd_tile(const Solve& S, int X, int kz0, int kind, float2* box,
+                                          const float2* twt, const float* iu, uint64_t* bar,
+                                          uint32_t phase) {
+  using P = Pen<L>;
+  constexpr int H = P::H;
+  const YfwdBufs bb = yfwd_bufs<L, BWD>(kind);
+  const int buf0 = bb.buf0, buf1 = bb.buf1;
+  const bool two = bb.two;
   constexpr bool IL = P::T == 16;  // interleaved groups: conflict-free column accesses
   using LN = Lanes<P::T, IL>;
   const int tid = threadIdx.x, g = LN::group(tid), t = LN::lane(tid);
-  extern __shared__ unsigned char smem_raw[];
-  const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
-  float2* box = reinterpret_cast<float2*>(smem_raw + pad);  // 1 or 2 boxes
-  float2* twt = box + (BWD ? 1 : 2) * P::BOX;
-  float* iu = reinterpret_cast<float*>(twt + L);
-  __shared__ uint64_t bar;
-  pdl_trigger();
-  // thread 0 issues the tile loads first; the tables load while they fly
-  if (tid == 0) {
-    mbar_init(&bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  pdl_wait();
-  if (tid == 0) {
-    mbar_expect_tx(&bar, (two ? 2 : 1) * P::BOX * (uint32_t)sizeof(float2));
-    tma_load_3d(box, &S.tmy[buf0], kz0, 0, X, &bar);
-    if (two) tma_load_3d(box + P::BOX, &S.tmy[buf1], kz0, 0, X, &bar);
-  }
-  for (int i = tid; i < L; i += NT) {
-    twt[i] = S.tw[i];
-    iu[i] = S.iu[i];
-  }
-  __syncthreads();
-  const bool landed = __syncthreads_and(mbar_wait(&bar, 0));
+  const bool landed = __syncthreads_and(mbar_wait(bar, phase));
   if (!landed) {
     if (tid == 0) atomicOr(S.status, kStTimeout);
-    mbar_wait(&bar, 0);  // a last bounded chance for copies in flight
-    return;
+    mbar_wait(bar, phase);  // a last bounded chance for copies in flight
+    return false;
   }
   TwTab<L> twr{twt, t};
   if (g < P::NCOL) {  // whole groups; one column array live at a time
@@ -383,10 +397,10 @@ __global__ void __launch_bounds__(ynt<L>(), BWD ? 4 : (L >= 256 ? 3 : 5)) k_yfwd
   const int nsplit = kind == 1 && two ? 2 : 1;  // tiles whose column 0 packs DC and Nyquist
   if (kz0 == 0 && g < nsplit) {
     // column 0 holds X0 + i Xn of the DC and Nyquist columns: split them
-    float2* bb = box + g * P::BOX;
+    float2* bq = box + g * P::BOX;
     float2* dst = S.spec[g == 0 ? buf0 : buf1];
-    split_dc_nyq<L, IL>(bb, t, [&](int ky, float2 w) {
-      if (H < 16) bb[bx(ky, H)] = w;
+    split_dc_nyq<L, IL>(bq, t, [&](int ky, float2 w) {
+      if (H < 16) bq[bx(ky, H)] = w;
       else dst[((size_t)X * L + ky) * P::KP + H] = w;
     });
   }
@@ -398,6 +412,38 @@ __global__ void __launch_bounds__(ynt<L>(), BWD ? 4 : (L >= 256 ? 3 : 5)) k_yfwd
     tma_store_commit();
     tma_store_wait_read();
   }
+  return true;
+}
+
+template <int L, bool BWD>
+__global__ void __launch_bounds__(ynt<L>(), BWD ? 4 : (L >= 256 ? 3 : 5)) k_yfwd(const __grid_constant__ Solve s0,
+                                                   const Solve* __restrict__ tab) {
+  using P = Pen<L>;
+  constexpr int NT = ynt<L>();
+  const Solve& S = tab ? tab[blockIdx.z] : s0;
+  const int X = blockIdx.x / P::NKC, kz0 = (blockIdx.x % P::NKC) * P::NCOL;
+  const int kind = BWD ? 3 : (int)blockIdx.y;
+  const int tid = threadIdx.x;
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+  float2* box = reinterpret_cast<float2*>(smem_raw + pad);  // 1 or 2 boxes
+  float2* twt = box + (BWD ? 1 : 2) * P::BOX;
+  float* iu = reinterpret_cast<float*>(twt + L);
+  __shared__ uint64_t bar;
+  pdl_trigger();
+  // thread 0 issues the tile loads first; the tables load while they fly
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  pdl_wait();
+  if (tid == 0) yfwd_issue<L, BWD>(S, X, kz0, kind, box, &bar);
+  for (int i = tid; i < L; i += NT) {
+    twt[i] = S.tw[i];
+    iu[i] = S.iu[i];
+  }
+  __syncthreads();
+  yfwd_tile<L, BWD>(S, X, kz0, kind, box, twt, iu, &bar, 0);
 }
 
 // ===========================================================================
@@ -420,50 +466,38 @@ constexpr size_t yinv_smem() {
   return 1024 + sizeof(float2) * ((size_t)NCH * Pen<L>::BOX + L) + sizeof(float) * L;
 }
 
+// Thread 0: the TMA tile loads of an inverse y-pass tile (part: -1 all
+// fields, else the CTA kind of yinv_split), completion on `bar`.
 template <int L, int NCH>
-__global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32,
-                                  NCH == 1 || yinv_split<L, NCH>() ? 4 : 2)
-    k_yinv(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
+__device__ __forceinline__ void yinv_issue(const Solve& S, int X, int kz0, int part, float2* box,
+                                           uint64_t* bar) {
   using P = Pen<L>;
-  constexpr int H = P::H, NT = 16 * P::T >= 32 ? 16 * P::T : 32;
-  const Solve& S = tab ? tab[blockIdx.z] : s0;
-  const int X = blockIdx.x / P::NKC, kz0 = (blockIdx.x % P::NKC) * P::NCOL;
+  // NCH = 1: box 0 <- chi~; NCH = 3: box 0 <- Q2, box 1 <- Q1 (split: only
+  // the kind's own input)
+  const bool do0 = part != 1, do1 = NCH == 3 && part != 0;
+  mbar_expect_tx(bar, ((do0 ? 1 : 0) + (do1 ? 1 : 0)) * P::BOX * (uint32_t)sizeof(float2));
+  if (do0) tma_load_3d(box, &S.tmy[kSpChi], kz0, 0, X, bar);
+  if (do1) tma_load_3d(box + P::BOX, &S.tmy[kSpD], kz0, 0, X, bar);
+}
+
+// All threads: wait, transform, TMA stores (thread 0 waits until they have
+// read shared memory). False if the bounded wait gave up.
+template <int L, int NCH>
+__device__ __forceinline__ bool yinv_tile(const Solve& S, int X, int kz0, int part, float2* box,
+                                          const float2* twt, const float* iu, uint64_t* bar,
+                                          uint32_t phase) {
+  using P = Pen<L>;
+  constexpr int H = P::H;
   constexpr bool IL = P::T == 16;  // interleaved groups: conflict-free column accesses
   using LN = Lanes<P::T, IL>;
   const int tid = threadIdx.x, g = LN::group(tid), t = LN::lane(tid);
-  extern __shared__ unsigned char smem_raw[];
-  const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
-  float2* box = reinterpret_cast<float2*>(smem_raw + pad);
-  float2* twt = box + NCH * P::BOX;
-  float* iu = reinterpret_cast<float*>(twt + L);
-  __shared__ uint64_t bar;
-  pdl_trigger();
-  // thread 0 issues the tile loads first; the tables load while they fly
-  if (tid == 0) {
-    mbar_init(&bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  pdl_wait();
-  // NCH = 1: box 0 <- chi~; NCH = 3: box 0 <- Q2, box 1 <- Q1 (split: only
-  // the kind's own input)
   constexpr int NIN = NCH == 1 ? 1 : 2;
-  const int part = yinv_split<L, NCH>() ? (int)blockIdx.y : -1;  // -1: all fields
   const bool do0 = part != 1, do1 = NCH == 3 && part != 0;
-  if (tid == 0) {
-    mbar_expect_tx(&bar, ((do0 ? 1 : 0) + (do1 ? 1 : 0)) * P::BOX * (uint32_t)sizeof(float2));
-    if (do0) tma_load_3d(box, &S.tmy[kSpChi], kz0, 0, X, &bar);
-    if (do1) tma_load_3d(box + P::BOX, &S.tmy[kSpD], kz0, 0, X, &bar);
-  }
-  for (int i = tid; i < L; i += NT) {
-    twt[i] = S.tw[i];
-    iu[i] = S.iu[i];
-  }
-  __syncthreads();
-  const bool landed = __syncthreads_and(mbar_wait(&bar, 0));
+  const bool landed = __syncthreads_and(mbar_wait(bar, phase));
   if (!landed) {
     if (tid == 0) atomicOr(S.status, kStTimeout);
-    mbar_wait(&bar, 0);
-    return;
+    mbar_wait(bar, phase);
+    return false;
   }
   TwTab<L> twr{twt, t};
   if (kz0 == 0 && g < NIN && (g == 0 ? do0 : do1)) {
@@ -480,7 +514,7 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
   }
   __syncthreads();
   if (g < P::NCOL) {
-    const int s = kz0 + g;
+    const int sz = kz0 + g;
     auto cref = [&](int k) {
       float2* b = box + k * P::BOX;
       return [b, g](int e) -> float2& { return b[bx(e, g)]; };
@@ -510,7 +544,7 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
 #pragma unroll
       for (int j = 0; j < P::R1; ++j) v[j] = c2(t + P::T * j);
       fft_r<L, +1, IL>(v, t, c2, twr);
-      const float ez = s == 0 ? 0.f : -iu[s];
+      const float ez = sz == 0 ? 0.f : -iu[sz];
 #pragma unroll
       for (int j = 0; j < P::R1; ++j) c2(t + P::T * j) = cmul_iu(v[j], ez);
     }
@@ -530,6 +564,39 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
     tma_store_commit();
     tma_store_wait_read();
   }
+  return true;
+}
+
+template <int L, int NCH>
+__global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32,
+                                  NCH == 1 || yinv_split<L, NCH>() ? 4 : 2)
+    k_yinv(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
+  using P = Pen<L>;
+  constexpr int NT = 16 * P::T >= 32 ? 16 * P::T : 32;
+  const Solve& S = tab ? tab[blockIdx.z] : s0;
+  const int X = blockIdx.x / P::NKC, kz0 = (blockIdx.x % P::NKC) * P::NCOL;
+  const int tid = threadIdx.x;
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+  float2* box = reinterpret_cast<float2*>(smem_raw + pad);
+  float2* twt = box + NCH * P::BOX;
+  float* iu = reinterpret_cast<float*>(twt + L);
+  __shared__ uint64_t bar;
+  pdl_trigger();
+  // thread 0 issues the tile loads first; the tables load while they fly
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  pdl_wait();
+  const int part = yinv_split<L, NCH>() ? (int)blockIdx.y : -1;  // -1: all fields
+  if (tid == 0) yinv_issue<L, NCH>(S, X, kz0, part, box, &bar);
+  for (int i = tid; i < L; i += NT) {
+    twt[i] = S.tw[i];
+    iu[i] = S.iu[i];
+  }
+  __syncthreads();
+  yinv_tile<L, NCH>(S, X, kz0, part, box, twt, iu, &bar, 0);
 }
 
 // ===========================================================================
@@ -559,14 +626,148 @@ constexpr size_t zinv_smem() {
   return sizeof(float2) * ((size_t)2 * ZiGeo<L, NCH>::STAGE + L);
 }
 
+// Thread 0: bulk loads of a z-pass tile's rows (H slots each, YB + 2 rows
+// per field) into the stage at `sb`, completion on `bar`.
+template <int L, int NCH>
+__device__ __forceinline__ void zinv_issue(const Solve& S, int tile, float2* sb, uint64_t* bar) {
+  using P = Pen<L>;
+  using Z = ZiGeo<L, NCH>;
+  constexpr int YB = P::YB, H = P::H, NR = Z::NR, KP = P::KP;
+  const int X = tile / P::NYB, y0 = (tile % P::NYB) * YB;
+  mbar_expect_tx(bar, NCH * NR * H * (uint32_t)sizeof(float2));
+#pragma unroll
+  for (int ch = 0; ch < NCH; ++ch) {
+    const int buf = NCH == 1 ? kSpYa : (ch == 0 ? kSpC : (ch == 1 ? kSpYa : kSpYb));
+    const float2* base = S.spec[buf] + (size_t)X * L * KP;
+    for (int ly = 0; ly < NR; ++ly)  // row y0 + ly, wrapping to rows 0, 1
+      bulk_load(sb + row_off<L, Z::SP>(ch * NR + ly) / 2, base + (size_t)((y0 + ly) & (L - 1)) * KP,
+                H * (uint32_t)sizeof(float2), bar);
+  }
+}
+
+// All threads: one z-pass tile whose rows land in the stage at `sb`. The
+// tile's point bins and this thread's first point record are read before
+// wait_stage() (which waits for the rows, block-uniformly, and returns false
+// on a timeout), so that their latencies overlap it; then C2R of the row
+// pairs in place and the per-point outputs.
+template <int L, int NCH, class Wait>
+__device__ __forceinline__ bool zinv_tile(const Solve& S, int tile, float2* sb, const float2* twt,
+                                          float a_chi, float b_chi, Wait wait_stage) {
+  using P = Pen<L>;
+  using Z = ZiGeo<L, NCH>;
+  constexpr int YB = P::YB, NR = Z::NR, NT = Z::NT, G = NT / P::T;
+  const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
+  const int X = tile / P::NYB, y0 = (tile % P::NYB) * YB;
+  // The tile's point bins (both plane sides, one sequence) and this
+  // thread's first point record, read before the stage wait and the C2R so
+  // that their dependent latencies overlap them.
+  const int2 r0 = bin_range(S, X, y0 / YB), r1 = bin_range(S, (X - 1) & (L - 1), y0 / YB);
+  const int n0 = r0.y - r0.x, nv = n0 + (r1.y - r1.x);
+  float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa;
+  if (tid < nv) {
+    const int i = tid < n0 ? r0.x + tid : r1.x + (tid - n0);
+    pa = S.sorted[2 * i];
+    if constexpr (NCH == 3) pb = S.sorted[2 * i + 1];
+  }
+  if (!wait_stage()) return false;
+  TwTab<L> twr{twt, t};
+  // pair p of channel ch: rows 2p (A) and 2p + 1 (B) of the stage, L float2
+  auto pair = [&](int ch, int p) {
+    float2* ra = sb + pair_off<L, Z::SP>(ch * (NR / 2) + p) / 2;
+    return [ra](int i) -> float2& { return ra[i]; };
+  };
+  constexpr int NP = NCH * NR / 2;
+  for (int p0 = 0; p0 < NP; p0 += G) {
+    const int pi = p0 + g;
+    if (pi < NP) c2r_acc<L>(t, twr, pair(pi / (NR / 2), pi % (NR / 2)));  // whole groups
+  }
+  __syncthreads();
+  // value of channel ch, tile row ly, column z
+  auto val = [&](int ch, int ly, int z) {
+    const float2 f = pair(ch, ly >> 1)(z);
+    return (ly & 1) ? f.y : f.x;
+  };
+  if constexpr (NCH == 1) {
+    float* chi = S.chi;
+    for (int i = tid; i < YB * L / 4; i += NT) {
+      const int ly = i / (L / 4), z4 = (i % (L / 4)) * 4;
+      float4 o;
+      o.x = fmaf(a_chi, val(0, ly, z4), b_chi);
+      o.y = fmaf(a_chi, val(0, ly, z4 + 1), b_chi);
+      o.z = fmaf(a_chi, val(0, ly, z4 + 2), b_chi);
+      o.w = fmaf(a_chi, val(0, ly, z4 + 3), b_chi);
+      reinterpret_cast<float4*>(chi + ((size_t)X * L + y0 + ly) * L)[z4 / 4] = o;
+    }
+  }
+  for (int v = tid; v < nv; v += NT) {
+    const int side = v < n0 ? 0 : 1;
+    const int i = side ? r1.x + (v - n0) : r0.x + v;
+    {
+      const float4 a = v == tid ? pa : S.sorted[2 * i];
+      const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);
+      const int ly0 = ay.i0 - y0;  // in [0, YB); row i1 is ly0 + 1 (a halo row at most)
+      const float fx = tri_w(side, ax.t), dfx = side ? (float)L : -(float)L;
+      if constexpr (NCH == 1) {
+        float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+          const float fy = tri_w(dy, ay.t), dfy = dy ? (float)L : -(float)L;
+#pragma unroll
+          for (int dz = 0; dz < 2; ++dz) {
+            const int z = dz ? az.i1 : az.i0;
+            const float fz = tri_w(dz, az.t), dfz = dz ? (float)L : -(float)L;
+            const float vv = val(0, ly0 + dy, z);
+            gx += dfx * fy * fz * vv;
+            gy += fx * dfy * fz * vv;
+            gz += fx * fy * dfz * vv;
+          }
+        }
+        S.gfwd[(size_t)side * S.N + i] = make_float4(gx, gy, gz, 0.f);
+      } else {
+        const float4 b = v == tid ? pb : S.sorted[2 * i + 1];
+        const float n0_ = a.w, n1 = b.x, n2 = b.y;
+        float nb0 = 0.f, nb1 = 0.f, nb2 = 0.f, cb0 = 0.f, cb1 = 0.f, cb2 = 0.f;
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+          const float fy = tri_w(dy, ay.t), dfy = dy ? (float)L : -(float)L;
+#pragma unroll
+          for (int dz = 0; dz < 2; ++dz) {
+            const int z = dz ? az.i1 : az.i0;
+            const float fz = tri_w(dz, az.t), dfz = dz ? (float)L : -(float)L;
+            const float vx = val(0, ly0 + dy, z), vy = val(1, ly0 + dy, z), vz = val(2, ly0 + dy, z);
+            const float w = fx * fy * fz;
+            nb0 += w * vx;
+            nb1 += w * vy;
+            nb2 += w * vz;
+            const float sdot = n0_ * vx + n1 * vy + n2 * vz;
+            cb0 += dfx * fy * fz * sdot;
+            cb1 += fx * dfy * fz * sdot;
+            cb2 += fx * fy * dfz * sdot;
+          }
+        }
+        float* o = S.slots + ((size_t)side * S.N + i) * 6;
+        o[0] = nb0;
+        o[1] = nb1;
+        o[2] = nb2;
+        o[3] = cb0;
+        o[4] = cb1;
+        o[5] = cb2;
+      }
+    }
+  }
+  fence_async_smem();  // this stage is refilled by a bulk copy later
+  __syncthreads();
+  return true;
+}
+
 template <int L, int NCH>
 __global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : (L >= 256 ? 2 : 3))
     k_zinv(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = Pen<L>;
   using Z = ZiGeo<L, NCH>;
-  constexpr int YB = P::YB, H = P::H, NR = Z::NR, KP = P::KP, NT = Z::NT, G = NT / P::T;
+  constexpr int NT = Z::NT;
   const Solve& S = tab ? tab[blockIdx.z] : s0;
-  const int tid = threadIdx.x, g = tid / P::T, t = tid % P::T;
+  const int tid = threadIdx.x;
   extern __shared__ float4 smem4[];
   float2* stg = reinterpret_cast<float2*>(smem4);  // 2 stages, row (ch, ly) at row_off(ch NR + ly)
   float2* twt = stg + 2 * Z::STAGE;
@@ -581,46 +782,24 @@ __global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : (L >= 256 ? 
   pdl_wait();
   __syncthreads();
   constexpr int ntiles = L * P::NYB;
-  auto issue = [&](int tile, int st) {  // thread 0: the tile's rows (H slots each) into stage st
-    const int X = tile / P::NYB, y0 = (tile % P::NYB) * YB;
-    mbar_expect_tx(&bar[st], NCH * NR * H * (uint32_t)sizeof(float2));
-#pragma unroll
-    for (int ch = 0; ch < NCH; ++ch) {
-      const int buf = NCH == 1 ? kSpYa : (ch == 0 ? kSpC : (ch == 1 ? kSpYa : kSpYb));
-      const float2* base = S.spec[buf] + (size_t)X * L * KP;
-      float2* dst = stg + st * Z::STAGE;
-      for (int ly = 0; ly < NR; ++ly)  // row y0 + ly, wrapping to rows 0, 1
-        bulk_load(dst + row_off<L, Z::SP>(ch * NR + ly) / 2, base + (size_t)((y0 + ly) & (L - 1)) * KP, H * (uint32_t)sizeof(float2),
-                  &bar[st]);
-    }
-  };
   float a_chi = 0.f, b_chi = 0.f;
   if constexpr (NCH == 1) {
     a_chi = S.sc->a_chi;
     b_chi = S.sc->b_chi;
   }
-  TwTab<L> twr{twt, t};
   uint32_t ph = 0u;  // bit st: parity of stage st's next completion
   int tile = blockIdx.x;
-  if (tid == 0 && tile < ntiles) issue(tile, 0);
+  if (tid == 0 && tile < ntiles) zinv_issue<L, NCH>(S, tile, stg, &bar[0]);
   for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
     const int st = it & 1;
     const int next = tile + gridDim.x;
-    if (tid == 0 && next < ntiles) issue(next, st ^ 1);  // released at the end of the last iteration
-    const int X = tile / P::NYB, y0 = (tile % P::NYB) * YB;
-    // The tile's point bins (both plane sides, one sequence) and this
-    // thread's first point record, read before the stage wait and the C2R so
-    // that their dependent latencies overlap them.
-    const int2 r0 = bin_range(S, X, y0 / YB), r1 = bin_range(S, (X - 1) & (L - 1), y0 / YB);
-    const int n0 = r0.y - r0.x, nv = n0 + (r1.y - r1.x);
-    float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa;
-    if (tid < nv) {
-      const int i = tid < n0 ? r0.x + tid : r1.x + (tid - n0);
-      pa = S.sorted[2 * i];
-      if constexpr (NCH == 3) pb = S.sorted[2 * i + 1];
-    }
-    const bool ok = __syncthreads_and(mbar_wait(&bar[st], (ph >> st) & 1u));
-    ph ^= 1u << st;
+    // released at the end of the last iteration
+    if (tid == 0 && next < ntiles) zinv_issue<L, NCH>(S, next, stg + (st ^ 1) * Z::STAGE, &bar[st ^ 1]);
+    bool ok = zinv_tile<L, NCH>(S, tile, stg + st * Z::STAGE, twt, a_chi, b_chi, [&]() {
+      const bool landed = __syncthreads_and(mbar_wait(&bar[st], (ph >> st) & 1u));
+      ph ^= 1u << st;
+      return landed;
+    });
     if (!ok) {
       if (tid == 0) {
         atomicOr(S.status, kStTimeout);
@@ -628,93 +807,6 @@ __global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : (L >= 256 ? 
       }
       break;
     }
-    float2* sb = stg + st * Z::STAGE;
-    // pair p of channel ch: rows 2p (A) and 2p + 1 (B) of the stage, L float2
-    auto pair = [&](int ch, int p) {
-      float2* ra = sb + pair_off<L, Z::SP>(ch * (NR / 2) + p) / 2;
-      return [ra](int i) -> float2& { return ra[i]; };
-    };
-    constexpr int NP = NCH * NR / 2;
-    for (int p0 = 0; p0 < NP; p0 += G) {
-      const int pi = p0 + g;
-      if (pi < NP) c2r_acc<L>(t, twr, pair(pi / (NR / 2), pi % (NR / 2)));  // whole groups
-    }
-    __syncthreads();
-    // value of channel ch, tile row ly, column z
-    auto val = [&](int ch, int ly, int z) {
-      const float2 f = pair(ch, ly >> 1)(z);
-      return (ly & 1) ? f.y : f.x;
-    };
-    if constexpr (NCH == 1) {
-      float* chi = S.chi;
-      for (int i = tid; i < YB * L / 4; i += NT) {
-        const int ly = i / (L / 4), z4 = (i % (L / 4)) * 4;
-        float4 o;
-        o.x = fmaf(a_chi, val(0, ly, z4), b_chi);
-        o.y = fmaf(a_chi, val(0, ly, z4 + 1), b_chi);
-        o.z = fmaf(a_chi, val(0, ly, z4 + 2), b_chi);
-        o.w = fmaf(a_chi, val(0, ly, z4 + 3), b_chi);
-        reinterpret_cast<float4*>(chi + ((size_t)X * L + y0 + ly) * L)[z4 / 4] = o;
-      }
-    }
-    for (int v = tid; v < nv; v += NT) {
-      const int side = v < n0 ? 0 : 1;
-      const int i = side ? r1.x + (v - n0) : r0.x + v;
-      {
-        const float4 a = v == tid ? pa : S.sorted[2 * i];
-        const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);
-        const int ly0 = ay.i0 - y0;  // in [0, YB); row i1 is ly0 + 1 (a halo row at most)
-        const float fx = tri_w(side, ax.t), dfx = side ? (float)L : -(float)L;
-        if constexpr (NCH == 1) {
-          float gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-          for (int dy = 0; dy < 2; ++dy) {
-            const float fy = tri_w(dy, ay.t), dfy = dy ? (float)L : -(float)L;
-#pragma unroll
-            for (int dz = 0; dz < 2; ++dz) {
-              const int z = dz ? az.i1 : az.i0;
-              const float fz = tri_w(dz, az.t), dfz = dz ? (float)L : -(float)L;
-              const float v = val(0, ly0 + dy, z);
-              gx += dfx * fy * fz * v;
-              gy += fx * dfy * fz * v;
-              gz += fx * fy * dfz * v;
-            }
-          }
-          S.gfwd[(size_t)side * S.N + i] = make_float4(gx, gy, gz, 0.f);
-        } else {
-          const float4 b = v == tid ? pb : S.sorted[2 * i + 1];
-          const float n0 = a.w, n1 = b.x, n2 = b.y;
-          float nb0 = 0.f, nb1 = 0.f, nb2 = 0.f, cb0 = 0.f, cb1 = 0.f, cb2 = 0.f;
-#pragma unroll
-          for (int dy = 0; dy < 2; ++dy) {
-            const float fy = tri_w(dy, ay.t), dfy = dy ? (float)L : -(float)L;
-#pragma unroll
-            for (int dz = 0; dz < 2; ++dz) {
-              const int z = dz ? az.i1 : az.i0;
-              const float fz = tri_w(dz, az.t), dfz = dz ? (float)L : -(float)L;
-              const float vx = val(0, ly0 + dy, z), vy = val(1, ly0 + dy, z), vz = val(2, ly0 + dy, z);
-              const float w = fx * fy * fz;
-              nb0 += w * vx;
-              nb1 += w * vy;
-              nb2 += w * vz;
-              const float sdot = n0 * vx + n1 * vy + n2 * vz;
-              cb0 += dfx * fy * fz * sdot;
-              cb1 += fx * dfy * fz * sdot;
-              cb2 += fx * fy * dfz * sdot;
-            }
-          }
-          float* o = S.slots + ((size_t)side * S.N + i) * 6;
-          o[0] = nb0;
-          o[1] = nb1;
-          o[2] = nb2;
-          o[3] = cb0;
-          o[4] = cb1;
-          o[5] = cb2;
-        }
-      }
-    }
-    fence_async_smem();  // this stage is refilled by a bulk copy two tiles on
-    __syncthreads();
   }
 }
 

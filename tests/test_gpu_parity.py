@@ -55,14 +55,24 @@ def _check(oracle, r, sigma, pts, nrm, dchi, tol_chi=TOL_CHI, tol_grad=TOL_GRAD,
             _ORACLE_CACHE[key] = ref
     chi, chip, mu, s = ref[0]
     e = relmax(g["chi"], chi)
-    assert e <= tol_chi, f"chi parity {e:.3e}"
+    # chi = m / |s| (chi' - mu) with s = chi'(0) - mu: an FP32 evaluation of
+    # s carries a rounding of order 2^-24 max|chi'|, which the scale amplifies
+    # by max|chi'| / |s|. That ratio is about 2 for surfaces (the bound stays
+    # within 1 % of tol_chi) but reaches thousands for a lone point, whose
+    # dipole field vanishes at the point and is tiny at the grid origin.
+    cond = np.max(np.abs(chip)) / abs(s)
+    tol = tol_chi + 2.0 ** -24 * cond
+    assert e <= tol, f"chi parity {e:.3e} (bound {tol:.3e}, scale condition {cond:.1f})"
     gmu, gs, galpha = g["scalars"]
     assert abs(gmu - mu) <= 1e-5 * np.max(np.abs(chip)) and abs(gs - s) <= 1e-5 * abs(s) + 1e-6 * np.max(np.abs(chip))
     if dchi is not None:
         assert g["bstatus"] == 0
         dp, dn, dm = ref[1]
+        # the gradient carries the same factors 1/|s| (alpha) and 1/s^2 (s_bar),
+        # so the rounding of s enters it with the same relative weight
+        tol_g = tol_grad + 2.0 ** -24 * cond
         en = relmax(g["dnormals"], dn)
-        assert en <= tol_grad, f"dnormals parity {en:.3e}"
+        assert en <= tol_g, f"dnormals parity {en:.3e} (bound {tol_g:.3e})"
         # dpoints is the sum of the part through the mean of Eq. 4 (dm) and the
         # rest (dp - dm). With a handful of points the two nearly cancel, so an
         # FP32 sum is only accurate to ~1e-6 of the larger part: the bound is
@@ -70,7 +80,7 @@ def _check(oracle, r, sigma, pts, nrm, dchi, tol_chi=TOL_CHI, tol_grad=TOL_GRAD,
         # only when the cancellation exceeds 50x, i.e. for N of order 1).
         scale = max(np.max(np.abs(dm)), np.max(np.abs(dp - dm)))
         err = np.max(np.abs(g["dpoints"] - dp))
-        bound = tol_grad * np.max(np.abs(dp)) + 2e-6 * scale
+        bound = tol_g * np.max(np.abs(dp)) + 2e-6 * scale
         assert err <= bound, f"dpoints parity {err / np.max(np.abs(dp)):.3e} (bound {bound:.3e})"
     return g
 
@@ -137,6 +147,19 @@ def test_torus_r256(oracle, monkeypatch, path):
     _set_path(monkeypatch, path, w["r"])
     dchi = synth.upstream_grad(synth.Rng(77), 256)
     _check(oracle, w["r"], w["sigma"], w["points"], w["normals"], dchi, key="torus_r256")
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("N,sigma", [(1, 2.0), (2049, 0.0)])
+def test_random_clouds_r256(oracle, monkeypatch, path, N, sigma):
+    """r = 256 on a lone point (nearly every plane empty) and on a sparse
+    cloud with no smoothing, wrapping around the cube."""
+    _set_path(monkeypatch, path, 256)
+    rng = synth.Rng(256000 + N)
+    pts = (rng.uniform(N, 3) * 1.4 - 0.2).astype(np.float32)
+    nrm = rng.normal(N, 3).astype(np.float32)
+    dchi = rng.normal(256, 256, 256).astype(np.float32)
+    _check(oracle, 256, sigma, pts, nrm, dchi)
 
 
 def test_degenerate_and_errors():
