@@ -519,40 +519,48 @@ def bench_serving(args):
     with N log-uniform in [1000, 200000], r in {64, 128, 256} (0.5 / 0.35 /
     0.15), 30% forward + backward, admitted by an 8 GB device budget. The
     continuous-batching server (--serve-slots stream slots) against a per-solve loop (the
-    same server with one slot), saturated (the first 400 requests submitted
-    at once) for throughput, then replayed in real time (latency =
-    completion - arrival)."""
+    same server with one slot and no coalescing), saturated (the first 400
+    requests submitted at once) for throughput, then replayed in real time
+    (latency = completion - arrival): the served configuration over the whole
+    trace (60 s, about 12 000 requests), the loop over its first 15 s."""
     from paper_2106_03452_gb300 import serve, synth
     trace = synth.serving_trace(duration_s=args.serve_seconds)
+    loop_trace = [q for q in trace if q["t"] < args.serve_loop_seconds]
     pool = serve.InputPool(n_clouds=6, n_max=200000)
     keys = [(r, b) for r in (64, 128, 256) for b in (False, True)]
     out = {"rate_per_s": 200.0, "duration_s": args.serve_seconds, "requests": len(trace),
            "budget_bytes": 8 << 30}
     out["slots"] = args.serve_slots
     ring = serve.OutputRing()  # pinned output buffers, shared by both servers
-    ring.prefill(keys, args.serve_slots + 2, 200000)
-    configs = ((args.serve_slots, "served"), (1, "loop"))
+    ring.prefill(keys, args.serve_slots * 8 + 2, 200000)
+    # the served configuration coalesces same-size requests (grid <= 128) into
+    # batched launches of up to 8; the loop is one slot, one solve at a time
+    configs = ((args.serve_slots, "served", 8), (1, "loop", 1))
     servers = {}
-    for slots, label in configs:
-        servers[label] = serve.Server(8 << 30, slots)
+    for slots, label, group in configs:
+        servers[label] = serve.Server(8 << 30, slots, max_group=group)
         serve.warm(servers[label], pool, slots=slots, n=200000)
     # both saturation runs before either real-time replay: the replay's
     # scattered buffer traffic measurably slows a burst that follows it in
     # the same process
     sat = trace[:400]
     sat_rate = {}
-    for slots, label in configs:
+    for slots, label, _ in configs:
         t0 = time.perf_counter()
         serve.replay(sat, servers[label], pool, realtime=False, ring=ring)
         sat_rate[label] = len(sat) / (time.perf_counter() - t0)
-    for slots, label in configs:
+    for slots, label, group in configs:
         srv = servers[label]
+        g0 = srv.stats()
         t0 = time.perf_counter()
-        res = serve.replay(trace, srv, pool, realtime=True, ring=ring)
+        res = serve.replay(trace if label == "served" else loop_trace, srv, pool, realtime=True, ring=ring)
         wall = time.perf_counter() - t0
+        st = srv.stats()
         out[label] = serve.summarize(res, wall)
         out[label]["saturated_solves_per_s"] = sat_rate[label]
-        out[label]["max_in_flight"] = srv.stats()["max_in_flight"]
+        out[label]["max_in_flight"] = st["max_in_flight"]
+        out[label]["max_group"] = group
+        out[label]["coalesced_requests"] = st["grouped_requests"] - g0["grouped_requests"]
         srv.close()
     out["saturated_speedup_vs_loop"] = out["served"]["saturated_solves_per_s"] / out["loop"]["saturated_solves_per_s"]
     return out
@@ -624,7 +632,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-train", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-loop-seconds", type=float, default=15.0)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     args = ap.parse_args()

@@ -296,7 +296,17 @@ DPSR_API int dpsr_server_submit(dpsr_server server, int r, const float *points,
 DPSR_API int dpsr_server_poll(dpsr_server server, int64_t ticket, int *done);
 /* Block until the ticket completes (or timeout_s passes: DPSR_ETIMEOUT). */
 DPSR_API int dpsr_server_wait(dpsr_server server, int64_t ticket, double timeout_s);
-/* out4 = {admitted, completed, most requests in flight at once, bytes in use}. */
+/* Coalescing: requests of grid size up to 128 that wait in the queue with
+ * the same grid size and mode (forward only / forward + backward) are
+ * admitted together, up to max_group of them (1..8, default 8), and run as
+ * one batched launch per kernel on one slot, each result equal to its solo
+ * solve up to floating-point rounding. Grid size 256 always runs solo.
+ * max_group = 1 turns coalescing off (a server of one slot is then the
+ * per-solve loop). */
+DPSR_API int dpsr_server_set_max_group(dpsr_server server, int max_group);
+/* out2 = {coalesced launches so far, requests they ran}. */
+DPSR_API int dpsr_server_group_stats(dpsr_server server, int64_t *out2);
+/* out4 = {admitted, completed, most slots busy at once, bytes in use}. */
 DPSR_API int dpsr_server_stats(dpsr_server server, int64_t *out4);
 
 /* Static description of an error code. */

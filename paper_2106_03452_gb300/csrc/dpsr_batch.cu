@@ -436,6 +436,48 @@ int dpsr_batch_sync(dpsr_batch b) {
   return worst;
 }
 
+// Internal hooks for the server (same library, not exported): the plan of
+// instance i (its staging buffers hold a request's inputs and outputs), and a
+// run of the forward (and backward) of the first k instances only. The first
+// k instances of a batch of one grid size are the first k members of its
+// class, so a launch with k instances instead of all of them runs exactly
+// those (the paths were tuned on the whole class).
+dpsr_plan dpsr_internal_batch_plan(dpsr_batch b, int i) {
+  return (b && i >= 0 && i < b->count) ? b->plans[i] : nullptr;
+}
+
+int dpsr_internal_batch_run(dpsr_batch b, int k, int with_bwd) {
+  if (!b || b->classes.size() != 1 || k < 1 || k > b->count) return DPSR_EINVAL;
+  BatchClass& c = b->classes[0];
+  const Solve dummy = {};
+  int rc = upload(b);
+  if (rc != DPSR_OK) return rc;
+  if (needs_tuning(b, with_bwd != 0)) {  // once, on the whole class (all bound)
+    if (tune_batch(b, with_bwd != 0) != cudaSuccess) {
+      cudaGetLastError();
+      return DPSR_ECUDA;
+    }
+    return DPSR_OK;
+  }
+  cudaStream_t st = b->stream;
+  cudaError_t e = dpsr::launch_bin(dummy, c.dtab, k, c.nmax, st);
+  if (e == cudaSuccess) e = dpsr::launch_plane(0, c.r, c.C[0], dummy, c.dtab, k, st);
+  if (e == cudaSuccess) e = dpsr::launch_xpass(false, c.r, dummy, c.dtab, k, st);
+  if (e == cudaSuccess) e = dpsr::launch_plane(1, c.r, c.C[1], dummy, c.dtab, k, st);
+  if (with_bwd) {
+    if (e == cudaSuccess) e = dpsr::launch_plane(2, c.r, c.C[2], dummy, c.dtab, k, st);
+    if (e == cudaSuccess) e = dpsr::launch_xpass(true, c.r, dummy, c.dtab, k, st);
+    if (e == cudaSuccess) e = dpsr::launch_plane(3, c.r, c.C[3], dummy, c.dtab, k, st);
+    if (e == cudaSuccess) e = dpsr::launch_combine(dummy, c.dtab, k, c.nmax, st);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return DPSR_ECUDA;
+  }
+  b->have_fwd = true;
+  return DPSR_OK;
+}
+
 int dpsr_batch_paths(dpsr_batch b, int r, int* C4) {
   if (!b || !C4) return DPSR_EINVAL;
   for (const auto& c : b->classes)

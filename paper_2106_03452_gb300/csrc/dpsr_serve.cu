@@ -1,11 +1,17 @@
 // Serving: a request loop that admits DPSR solves by device-memory budget and
-// runs them concurrently (continuous batching). Each admitted request takes a
-// slot (its own CUDA stream) and a pooled plan of its grid size; its host-to-
-// device copies, kernels and device-to-host copies are queued on the slot's
-// stream, so requests that arrive while others are running start as soon as
-// a slot and enough budget are free, and their work overlaps on the GPU.
+// runs them concurrently (continuous batching). An admitted request takes a
+// slot (its own CUDA stream); its host-to-device copies, kernels and
+// device-to-host copies are queued on the slot's stream, so requests that
+// arrive while others are running start as soon as a slot and enough budget
+// are free, and their work overlaps on the GPU. Requests of grid size up to
+// kCoalesceMaxR that wait in the queue with the same grid size and mode
+// (forward only, or forward + backward) are admitted together, up to
+// max_group of them, and run as one batched launch per kernel (a pooled
+// dpsr_batch of that grid size) on one slot; larger grids, which fill the GPU
+// on their own, run as solo solves on pooled plans.
 // A worker thread owns every CUDA call of the server; callers only enqueue
 // requests and wait for tickets.
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -22,8 +28,14 @@
 
 extern "C" int dpsr_internal_io(dpsr_plan p, int64_t N, float** pts, float** nrm, float** chi,
                                 float** dchi, float** dpts, float** dnrm);
+extern "C" dpsr_plan dpsr_internal_batch_plan(dpsr_batch b, int i);
+extern "C" int dpsr_internal_batch_run(dpsr_batch b, int k, int with_bwd);
 
 namespace {
+
+constexpr int kCoalesceMaxR = 128;  // grid sizes whose solves are coalesced
+constexpr int kMaxGroup = 8;        // instances of a pooled batch
+constexpr int64_t kPoolN = 200000;  // point capacity of pooled plans and batches
 
 struct Request {
   int64_t ticket = 0;
@@ -48,12 +60,20 @@ struct PooledPlan {
   size_t bytes = 0;
 };
 
+struct PooledBatch {
+  dpsr_batch batch = nullptr;
+  int r = 0;
+  bool busy = false;
+};
+
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  int64_t ticket = -1;   // -1: free
-  int pooled = -1;       // index into the plan pool
-  bool claimed = false;  // admitted, its work being queued
+  int64_t ticket = -1;         // -1: free; else the (first) request running here
+  std::vector<int64_t> group;  // a coalesced group: its tickets, instance order
+  int pooled = -1;             // index into the plan pool (solo request)
+  int pbatch = -1;             // index into the batch pool (coalesced group)
+  bool claimed = false;        // admitted, its work being queued
 };
 
 }  // namespace
@@ -68,12 +88,15 @@ struct dpsr_server_s {
   std::map<int64_t, Request> reqs;
   std::vector<Slot> slots;
   std::vector<PooledPlan> pool;
+  std::vector<PooledBatch> bpool;
+  int max_group = kMaxGroup;
   size_t used = 0;  // bytes held by admitted requests
   int64_t next_ticket = 1;
   bool stop = false;
   std::thread worker;
   // statistics
   int64_t completed = 0, admitted = 0, max_active = 0;
+  int64_t groups = 0, grouped = 0;  // coalesced launches and the requests they ran
 };
 
 namespace {
@@ -111,6 +134,109 @@ int get_plan(dpsr_server s, int r, int64_t N) {
   p.cap = N;
   s->pool.push_back(p);
   return (int)s->pool.size() - 1;
+}
+
+// Find or create an idle pooled batch of grid size r (kMaxGroup instances of
+// kPoolN points). A new batch is warmed once on `st`: every instance bound to
+// a small valid cloud (256 points on a sphere, zero dchi) in its plan's
+// staging, one forward and backward of all instances (which tunes the
+// batch's plane paths on them), and a sync that clears their status words.
+// Worker thread only.
+int get_batch(dpsr_server s, int r, cudaStream_t st) {
+  for (size_t i = 0; i < s->bpool.size(); ++i)
+    if (!s->bpool[i].busy && s->bpool[i].r == r) return (int)i;
+  int rs[kMaxGroup];
+  float sig[kMaxGroup];
+  int64_t nm[kMaxGroup];
+  for (int i = 0; i < kMaxGroup; ++i) {
+    rs[i] = r;
+    sig[i] = s->sigma;
+    nm[i] = kPoolN;
+  }
+  PooledBatch pb;
+  pb.r = r;
+  if (dpsr_batch_create(kMaxGroup, rs, sig, nm, &pb.batch) != DPSR_OK) return -1;
+  constexpr int n0 = 256;
+  std::vector<float> hp(3 * n0), hn(3 * n0);
+  for (int j = 0; j < n0; ++j) {  // a spiral of directions over the sphere
+    const double z = 1.0 - (2.0 * j + 1.0) / n0, rho = sqrt(1.0 - z * z), phi = 2.399963229728653 * j;
+    const double d[3] = {rho * cos(phi), rho * sin(phi), z};
+    for (int a = 0; a < 3; ++a) {
+      hp[3 * j + a] = (float)(0.5 + 0.3 * d[a]);
+      hn[3 * j + a] = (float)d[a];
+    }
+  }
+  int rc = dpsr_batch_set_stream(pb.batch, st);
+  for (int i = 0; i < kMaxGroup && rc == DPSR_OK; ++i) {
+    float *pts, *nrm, *chi, *dchi, *dpts, *dnrm;
+    dpsr_plan p = dpsr_internal_batch_plan(pb.batch, i);
+    rc = dpsr_internal_io(p, kPoolN, &pts, &nrm, &chi, &dchi, &dpts, &dnrm);
+    if (rc != DPSR_OK) break;
+    rc = dpsr_internal_io(p, n0, &pts, &nrm, &chi, &dchi, &dpts, &dnrm);
+    if (rc != DPSR_OK) break;
+    if (cudaMemcpyAsync(pts, hp.data(), sizeof(float) * 3 * n0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(nrm, hn.data(), sizeof(float) * 3 * n0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(dchi, 0, sizeof(float) * r * r * r, st) != cudaSuccess) {
+      rc = DPSR_ECUDA;
+      break;
+    }
+    rc = dpsr_batch_bind(pb.batch, i, pts, nrm, n0, chi, dchi, dpts, dnrm);
+  }
+  if (rc == DPSR_OK) rc = dpsr_internal_batch_run(pb.batch, kMaxGroup, 1);
+  if (rc == DPSR_OK) rc = dpsr_batch_sync(pb.batch);
+  if (rc != DPSR_OK) {
+    cudaGetLastError();
+    dpsr_batch_destroy(pb.batch);
+    return -1;
+  }
+  s->bpool.push_back(pb);
+  return (int)s->bpool.size() - 1;
+}
+
+// Queue a coalesced group (same r and mode, 2..kMaxGroup requests) on a
+// slot's stream as one batched launch of its first g.size() instances.
+int launch_group(dpsr_server s, Slot& sl, std::vector<Request*>& g) {
+  const int r = g[0]->r;
+  const bool bwd = g[0]->dchi != nullptr;
+  const int bi = get_batch(s, r, sl.stream);
+  if (bi < 0) return DPSR_ENOMEM;
+  dpsr_batch b = s->bpool[bi].batch;
+  if (dpsr_batch_set_stream(b, sl.stream) != DPSR_OK) return DPSR_ECUDA;
+  const size_t gb = sizeof(float) * r * r * r;
+  std::vector<float*> out(3 * g.size());
+  for (size_t i = 0; i < g.size(); ++i) {
+    Request& q = *g[i];
+    float *pts, *nrm, *chi, *dchi, *dpts, *dnrm;
+    int rc = dpsr_internal_io(dpsr_internal_batch_plan(b, (int)i), q.N, &pts, &nrm, &chi, &dchi, &dpts, &dnrm);
+    if (rc != DPSR_OK) return rc;
+    const size_t nb = sizeof(float) * 3 * q.N;
+    if (cudaMemcpyAsync(pts, q.points, nb, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess ||
+        cudaMemcpyAsync(nrm, q.normals, nb, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess ||
+        (bwd && cudaMemcpyAsync(dchi, q.dchi, gb, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess))
+      return DPSR_ECUDA;
+    rc = dpsr_batch_bind(b, (int)i, pts, nrm, q.N, chi, bwd ? dchi : nullptr, dpts, dnrm);
+    if (rc != DPSR_OK) return rc;
+    out[3 * i] = chi;
+    out[3 * i + 1] = dpts;
+    out[3 * i + 2] = dnrm;
+  }
+  int rc = dpsr_internal_batch_run(b, (int)g.size(), bwd ? 1 : 0);
+  if (rc != DPSR_OK) return rc;
+  for (size_t i = 0; i < g.size(); ++i) {
+    Request& q = *g[i];
+    const size_t nb = sizeof(float) * 3 * q.N;
+    if (cudaMemcpyAsync(q.chi, out[3 * i], gb, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
+        (bwd && (cudaMemcpyAsync(q.dpoints, out[3 * i + 1], nb, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
+                 cudaMemcpyAsync(q.dnormals, out[3 * i + 2], nb, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)))
+      return DPSR_ECUDA;
+  }
+  if (cudaEventRecord(sl.done, sl.stream) != cudaSuccess) return DPSR_ECUDA;
+  s->bpool[bi].busy = true;
+  sl.pbatch = bi;
+  sl.ticket = g[0]->ticket;
+  sl.group.clear();
+  for (Request* q : g) sl.group.push_back(q->ticket);
+  return DPSR_OK;
 }
 
 // Queue one request on a slot's stream.
@@ -161,17 +287,32 @@ void worker_main(dpsr_server s) {
         ++active;
         continue;
       }
-      Request& rq = s->reqs[sl.ticket];
-      PooledPlan& pp = s->pool[sl.pooled];
-      rq.status = q == cudaSuccess ? dpsr_sync(pp.plan) : DPSR_ECUDA;
       if (q != cudaSuccess) cudaGetLastError();
-      rq.done = true;
-      pp.busy = false;
-      dpsr_plan_set_stream(pp.plan, nullptr);
-      s->used -= rq.bytes;
+      if (sl.pbatch >= 0) {  // a coalesced group: instance i is request group[i]
+        PooledBatch& pb = s->bpool[sl.pbatch];
+        for (size_t i = 0; i < sl.group.size(); ++i) {
+          Request& rq = s->reqs[sl.group[i]];
+          rq.status = q == cudaSuccess ? dpsr_sync(dpsr_internal_batch_plan(pb.batch, (int)i)) : DPSR_ECUDA;
+          rq.done = true;
+          s->used -= rq.bytes;
+          ++s->completed;
+        }
+        pb.busy = false;
+        dpsr_batch_set_stream(pb.batch, nullptr);
+        sl.group.clear();
+        sl.pbatch = -1;
+      } else {
+        Request& rq = s->reqs[sl.ticket];
+        PooledPlan& pp = s->pool[sl.pooled];
+        rq.status = q == cudaSuccess ? dpsr_sync(pp.plan) : DPSR_ECUDA;
+        rq.done = true;
+        pp.busy = false;
+        dpsr_plan_set_stream(pp.plan, nullptr);
+        s->used -= rq.bytes;
+        ++s->completed;
+      }
       sl.ticket = -1;
       sl.pooled = -1;
-      ++s->completed;
       progress = true;
     }
     if (progress) s->cv_done.notify_all();
@@ -180,7 +321,10 @@ void worker_main(dpsr_server s) {
     // budget is rejected. The CUDA work of the admitted requests is queued
     // with the lock released (submit, poll and wait only need the lock for
     // the queue and the request table; slots and plans belong to this thread).
-    std::vector<std::pair<Slot*, Request*>> admit;
+    // Each admission takes the head of the queue and, for a coalescible grid
+    // size, the queued requests behind it with the same grid size and mode
+    // that fit the budget (up to max_group, in queue order).
+    std::vector<std::pair<Slot*, std::vector<Request*>>> admit;
     while (!s->queue.empty()) {
       Request& q = s->reqs[s->queue.front()];
       if (q.bytes > s->budget) {
@@ -199,27 +343,49 @@ void worker_main(dpsr_server s) {
         }
       if (!free_slot) break;
       s->queue.pop_front();
+      std::vector<Request*> grp{&q};  // the table never moves its entries
+      size_t bytes = q.bytes;
+      if (q.r <= kCoalesceMaxR && s->max_group > 1) {
+        for (auto it = s->queue.begin(); it != s->queue.end() && (int)grp.size() < s->max_group;) {
+          Request& o = s->reqs[*it];
+          if (o.r == q.r && (o.dchi != nullptr) == (q.dchi != nullptr) && o.bytes <= s->budget &&
+              s->used + bytes + o.bytes <= s->budget) {
+            grp.push_back(&o);
+            bytes += o.bytes;
+            it = s->queue.erase(it);
+          } else {
+            ++it;
+          }
+        }
+      }
       free_slot->claimed = true;
-      s->used += q.bytes;
-      admit.emplace_back(free_slot, &q);  // the table never moves its entries
+      s->used += bytes;
+      admit.emplace_back(free_slot, std::move(grp));
     }
     if (!admit.empty()) {
       lk.unlock();
       std::vector<int> rcs;
-      for (auto& a : admit) rcs.push_back(launch(s, *a.first, *a.second));
+      for (auto& a : admit)
+        rcs.push_back(a.second.size() > 1 ? launch_group(s, *a.first, a.second)
+                                          : launch(s, *a.first, *a.second[0]));
       lk.lock();
       for (size_t i = 0; i < admit.size(); ++i) {
         Slot& sl = *admit[i].first;
-        Request& q = *admit[i].second;
         sl.claimed = false;
         if (rcs[i] != DPSR_OK) {
-          q.status = rcs[i];
-          q.done = true;
-          s->used -= q.bytes;
+          for (Request* q : admit[i].second) {
+            q->status = rcs[i];
+            q->done = true;
+            s->used -= q->bytes;
+          }
           s->cv_done.notify_all();
           continue;
         }
-        ++s->admitted;
+        s->admitted += (int64_t)admit[i].second.size();
+        if (admit[i].second.size() > 1) {
+          ++s->groups;
+          s->grouped += (int64_t)admit[i].second.size();
+        }
         ++active;
       }
       progress = true;
@@ -271,11 +437,15 @@ int dpsr_server_destroy(dpsr_server s) {
   if (s->worker.joinable()) s->worker.join();
   for (Slot& sl : s->slots)
     if (sl.stream) cudaStreamSynchronize(sl.stream);
-  // Plans first: a pooled plan still refers to the stream of the last slot
-  // that ran it, and destroying a plan synchronises that stream.
+  // Plans and batches first: a pooled plan still refers to the stream of the
+  // last slot that ran it, and destroying a plan synchronises that stream.
   for (PooledPlan& p : s->pool) {
     dpsr_plan_set_stream(p.plan, nullptr);
     dpsr_plan_destroy(p.plan);
+  }
+  for (PooledBatch& b : s->bpool) {
+    dpsr_batch_set_stream(b.batch, nullptr);
+    dpsr_batch_destroy(b.batch);
   }
   for (Slot& sl : s->slots) {
     if (sl.done) cudaEventDestroy(sl.done);
@@ -336,6 +506,21 @@ int dpsr_server_wait(dpsr_server s, int64_t ticket, double timeout_s) {
   const int st = s->reqs[ticket].status;
   s->reqs.erase(ticket);
   return st;
+}
+
+int dpsr_server_set_max_group(dpsr_server s, int max_group) {
+  if (!s || max_group < 1 || max_group > kMaxGroup) return DPSR_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->max_group = max_group;
+  return DPSR_OK;
+}
+
+int dpsr_server_group_stats(dpsr_server s, int64_t* out2) {
+  if (!s || !out2) return DPSR_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  out2[0] = s->groups;
+  out2[1] = s->grouped;
+  return DPSR_OK;
 }
 
 int dpsr_server_stats(dpsr_server s, int64_t* out4) {

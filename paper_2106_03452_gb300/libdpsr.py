@@ -53,6 +53,8 @@ _PROTOS = {
     "dpsr_batch_bind_target": (_c_int, [_vp, _c_int, _vp]),
     "dpsr_batch_train_step": (_c_int, [_vp]),
     "dpsr_batch_losses": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
+    "dpsr_server_set_max_group": (_c_int, [_vp, _c_int]),
+    "dpsr_server_group_stats": (_c_int, [_vp, ctypes.POINTER(_c_i64)]),
     "dpsr_batch_create": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(_c_i64), ctypes.POINTER(_vp)]),
     "dpsr_batch_destroy": (_c_int, [_vp]),
@@ -272,6 +274,10 @@ def dpsr_batch_losses(batch: int, count: int):
     return [float(v) for v in out]
 
 
+def dpsr_server_set_max_group(server: int, max_group: int) -> None:
+    check(load().dpsr_server_set_max_group(server, int(max_group)), "dpsr_server_set_max_group")
+
+
 def dpsr_batch_paths(batch: int, r: int):
     """The four plane paths of the batch's instances of grid size r."""
     out = (_c_int * 4)()
@@ -308,6 +314,12 @@ def dpsr_server_poll(server: int, ticket: int):
 
 def dpsr_server_wait(server: int, ticket: int, timeout_s: float = 0.0) -> int:
     return int(load().dpsr_server_wait(server, int(ticket), float(timeout_s)))
+
+
+def dpsr_server_group_stats(server: int):
+    out = (_c_i64 * 2)()
+    check(load().dpsr_server_group_stats(server, out), "dpsr_server_group_stats")
+    return dict(groups=out[0], grouped_requests=out[1])
 
 
 def dpsr_server_stats(server: int):

@@ -23,8 +23,14 @@ from . import synth
 
 
 class Server:
-    def __init__(self, hbm_budget_bytes: int = 8 << 30, slots: int = 8, sigma: float = 2.0):
+    """max_group: requests of grid size <= 128 coalesced per batched launch
+    (1 = every request solo; with one slot that is the per-solve loop)."""
+
+    def __init__(self, hbm_budget_bytes: int = 8 << 30, slots: int = 8, sigma: float = 2.0,
+                 max_group: int = 8):
         self.handle = L.dpsr_server_create(hbm_budget_bytes, slots, sigma)
+        self.slots, self.max_group = slots, max_group
+        L.dpsr_server_set_max_group(self.handle, max_group)
 
     def submit(self, r, points, normals, chi_out, dchi=None, dpoints=None, dnormals=None) -> int:
         p = lambda t: t.data_ptr() if t is not None else 0
@@ -38,7 +44,9 @@ class Server:
         return L.dpsr_server_wait(self.handle, ticket, timeout_s)
 
     def stats(self):
-        return L.dpsr_server_stats(self.handle)
+        d = L.dpsr_server_stats(self.handle)
+        d.update(L.dpsr_server_group_stats(self.handle))
+        return d
 
     def close(self):
         if getattr(self, "handle", None):
@@ -164,12 +172,14 @@ def summarize(results, wall_s):
 
 
 def warm(server: Server, pool: InputPool, rs=(64, 128, 256), slots=1, n=20000):
-    """Fill the server's plan pool before a measurement: for every grid size,
-    `slots` concurrent fwd+bwd requests of n points, so that the pool holds a
-    plan per slot at full capacity (plans are created, and grown, only when
-    no pooled plan fits; creating or growing one allocates device memory,
-    which would otherwise stall the GPU in the middle of a measurement). The
-    first request per grid size also runs the autotuner, alone."""
+    """Fill the server's plan and batch pools before a measurement: for every
+    grid size, `slots` concurrent groups of fwd+bwd requests of n points
+    (max_group requests per group where the server coalesces that size), so
+    that the pools hold a plan or a batch per slot at full capacity (plans and
+    batches are created, and grown, only when none in the pool fits; that
+    allocates device memory and tunes, which would otherwise stall the GPU in
+    the middle of a measurement). The first request per grid size also runs
+    the plan autotuner, alone."""
     ring = OutputRing()
     for r in rs:
         pts, nrm = pool.inputs(0, n)
@@ -177,7 +187,8 @@ def warm(server: Server, pool: InputPool, rs=(64, 128, 256), slots=1, n=20000):
         st = server.wait(server.submit(r, pts, nrm, chi, pool.dchi[r], dp, dn), 120.0)
         if st != 0:
             raise RuntimeError(f"warm-up request r={r} failed with status {st}")
-        bufs = [ring.get(r, n, True) for _ in range(slots)]
+        per = getattr(server, "max_group", 1) if r <= 128 else 1
+        bufs = [ring.get(r, n, True) for _ in range(slots * per)]
         tickets = [server.submit(r, pts, nrm, c, pool.dchi[r], d, e) for (c, d, e) in bufs]
         for t in tickets:
             st = server.wait(t, 120.0)

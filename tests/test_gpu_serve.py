@@ -52,9 +52,11 @@ def test_mix_equals_alone():
         return [(chi.clone(), None if dp is None else dp.clone(), None if dn is None else dn.clone())
                 for _, chi, dp, dn in res], st
 
-    alone, _ = run(1)
+    alone, st1 = run(1)
     mixed, st = run(8)
+    assert st1["groups"] == 0                # one at a time: nothing to coalesce
     assert st["max_in_flight"] >= 2          # requests overlapped on the GPU
+    assert st["groups"] >= 1 and st["grouped_requests"] >= 2  # and same-size ones ran batched
     for q, a, m in zip(trace, alone, mixed):
         assert _rel(m[0], a[0]) <= 1e-5
         if q["backward"]:
@@ -76,3 +78,58 @@ def test_budget_admission():
     t = small.submit(64, pts, nrm, chi64)
     assert small.wait(t, 60.0) == 0
     small.close()
+
+
+def test_coalesced_groups_equal_alone_at_each_size(oracle):
+    """Eight forward + backward requests of one grid size submitted at once to
+    a one-slot server with coalescing on run as a single batched launch; each
+    result equals the same request run alone, and two of them match the FP64
+    oracle."""
+    import torch
+    from paper_2106_03452_gb300 import serve, synth
+    for r in (64, 128):
+        rng = synth.Rng(4100 + r)
+        reqs = []
+        for i in range(8):
+            N = 1000 + 2500 * i
+            pts, nrm = synth.ellipsoid_cloud(rng, N, 1 + i % 4)
+            reqs.append((torch.from_numpy(pts).pin_memory(), torch.from_numpy(nrm).pin_memory(),
+                         torch.from_numpy(synth.upstream_grad(rng, r)).pin_memory()))
+
+        def outs(N):
+            return (torch.empty((r, r, r)).pin_memory(), torch.empty((N, 3)).pin_memory(),
+                    torch.empty((N, 3)).pin_memory())
+
+        res = {}
+        for mode, groups in (("alone", 1), ("group", 8)):
+            srv = serve.Server(8 << 30, 1, max_group=groups)
+            o = [outs(p.shape[0]) for (p, _, _) in reqs]
+            if mode == "alone":
+                for (p, n, g), (c, d, e) in zip(reqs, o):
+                    assert srv.wait(srv.submit(r, p, n, c, g, d, e), 120.0) == 0
+            else:
+                # hold the slot with an r = 256 request (solo, several milliseconds)
+                # so that the eight queue up behind it
+                hp, hn = synth.ellipsoid_cloud(synth.Rng(4099), 200000, 3)
+                hp, hn = torch.from_numpy(hp).pin_memory(), torch.from_numpy(hn).pin_memory()
+                hg = torch.from_numpy(synth.upstream_grad(synth.Rng(4098), 256)).pin_memory()
+                h_out = (torch.empty((256,) * 3).pin_memory(), torch.empty((200000, 3)).pin_memory(),
+                         torch.empty((200000, 3)).pin_memory())
+                t0 = srv.submit(256, hp, hn, h_out[0], hg, h_out[1], h_out[2])
+                ts = [srv.submit(r, p, n, c, g, d, e) for (p, n, g), (c, d, e) in zip(reqs, o)]
+                assert srv.wait(t0, 120.0) == 0
+                assert all(srv.wait(t, 120.0) == 0 for t in ts)
+                st = srv.stats()
+                assert st["groups"] >= 1 and st["grouped_requests"] >= 7, st
+            res[mode] = o
+            srv.close()
+        for i in range(8):
+            a, g = res["alone"][i], res["group"][i]
+            assert _rel(g[0], a[0]) <= 1e-5
+            assert _rel(g[1], a[1]) <= 1e-4 and _rel(g[2], a[2]) <= 1e-4
+        for i in (0, 7):
+            p, n, G = reqs[i]
+            ref = oracle.forward(r, 2.0, p.numpy(), n.numpy())
+            assert _rel(res["group"][i][0], ref) <= 1e-5
+            rdp, rdn = oracle.backward(r, 2.0, p.numpy(), n.numpy(), G.numpy())
+            assert _rel(res["group"][i][1], rdp) <= 1e-4 and _rel(res["group"][i][2], rdn) <= 1e-4
