@@ -27,11 +27,14 @@ struct XGeo {
   static constexpr int NCHUNK = (H + 1 + KC - 1) / KC;
   static constexpr int BOX = L * KC;                        // float2 per box
   static constexpr int KP = kpitch(L);                      // row pitch of the spectral buffers
-  // Up to r = 128 the forward reads W~ straight from L2 (the spectra stay
-  // resident there): two tiles per CTA instead of three, more CTAs per SM.
+  // Two tiles per CTA in both directions. The forward needs W~ only for its
+  // spectral sums, after the transforms of C: up to r = 128 it reads W~'s
+  // column straight from L2 (the spectra stay resident there); at r = 256 a
+  // TMA load brings W~'s tile into C's box once every group is done with C,
+  // overlapping the inverse transform.
   static constexpr bool WL2 = L <= 128;
   template <bool BWD>
-  static constexpr int nch() { return BWD ? 2 : (WL2 ? 2 : 3); }
+  static constexpr int nch() { return 2; }
 };
 
 // G(k) = g(k) / (-2 pi |u|^2) with g separable: g1[kx] * (g1[ky] g1[kz]);
@@ -67,7 +70,7 @@ constexpr size_t xpass_smem() {
 // one kz column along x in registers (the box column doubles as its exchange
 // buffer), and TMA stores the results.
 template <int L, bool BWD>
-__global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
+__global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? (BWD ? 2 : 3) : 5)
     k_xpass(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = XGeo<L>;
   constexpr int NCH = P::template nch<BWD>();
@@ -112,23 +115,25 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
   // store, so that a timeout leaves uniformly (the transforms of a lane whose
   // wait ran out compute on stale data, which is never stored).
   bool ok = true;
-  auto box_wait = [&](int c) {
-    if (ok) ok = mbar_wait(&bar[c], 0);
+  auto box_wait = [&](int c, uint32_t phase = 0u) {
+    if (ok) ok = mbar_wait(&bar[c], phase);
   };
+  bool w_reload = false;  // r = 256 forward: W~ went into box 1 (its second phase)
   auto leave = [&]() {  // after a failed vote
     if (tid == 0) {
       atomicOr(S.status, kStTimeout);
 #pragma unroll
       for (int c = 0; c < NCH; ++c) mbar_wait(&bar[c], 0);  // copies in flight: a last bounded chance
+      if (w_reload) mbar_wait(&bar[1], 1);
     }
   };
   const int gc = g < P::KC ? g : P::KC - 1;  // extra groups (tiny r) shadow the last column
   const bool own = g < P::KC;
   const int kz = min(kz0 + gc, P::H);
   const bool valid = own && kz0 + g <= P::H;
-  // r = 256: register twiddles and both column arrays live (two CTAs per
-  // SM); below, shared-memory twiddles and one array (more CTAs per SM)
-  using Tw = typename std::conditional<(L >= 256), Twid<L>, TwTab<L>>::type;
+  // shared-memory twiddles and one live column array: at r = 256 three CTAs
+  // per SM forward (two backward, where three would spill), five below
+  using Tw = TwTab<L>;
   Tw twr = make_tw<L, Tw>(tw, t);
   const float gyz = g1[ky] * g1[kz], u2yz = u2[ky] + u2[kz];
   auto colref = [&](int ch) {
@@ -143,56 +148,49 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
     // their groups skip the transforms.
     float am = 0.f, as = 0.f, wz = 0.f;
     if (valid) {
-      if constexpr (L >= 256) {
-        // chi~ = G (FFT_x(D) + i u_x FFT_x(C))
-        float2 b[P::R1];
-        box_wait(0);
+      // chi~ = G (FFT_x(D) + i u_x FFT_x(C)); one column array live at a time:
+      // FFT_x(D) goes back to its column, FFT_x(C) meets it there.
+      box_wait(0);
 #pragma unroll
-        for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
-        fft_r<L, -1, IL>(a, t, c0, twr);
-        box_wait(1);
+      for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
+      fft_r<L, -1, IL>(a, t, c0, twr);
+      if (own) {  // groups past the last column (tiny r) only shadow it
 #pragma unroll
-        for (int j = 0; j < P::R1; ++j) b[j] = c1(t + P::T * j);
-        fft_r<L, -1, IL>(b, t, c1, twr);
-#pragma unroll
-        for (int j = 0; j < P::R1; ++j) {
-          const int kx = t + P::T * j;
-          const float G = spectral_G(kx, gyz, u2yz, g1, u2);
-          a[j] = cscale(cadd(a[j], cmul_iu(b[j], iu[kx])), G);
-        }
-      } else {
-        // chi~ = G (FFT_x(D) + i u_x FFT_x(C)); one column array live at a time:
-        // FFT_x(D) goes back to its column, FFT_x(C) meets it there.
-        box_wait(0);
-#pragma unroll
-        for (int j = 0; j < P::R1; ++j) a[j] = c0(t + P::T * j);
-        fft_r<L, -1, IL>(a, t, c0, twr);
-        if (own) {  // groups past the last column (tiny r) only shadow it
-#pragma unroll
-          for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = a[j];
-        }
-        box_wait(1);
-#pragma unroll
-        for (int j = 0; j < P::R1; ++j) a[j] = c1(t + P::T * j);
-        fft_r<L, -1, IL>(a, t, c1, twr);
-#pragma unroll
-        for (int j = 0; j < P::R1; ++j) {
-          const int kx = t + P::T * j;  // this lane wrote c0(kx) above
-          const float G = spectral_G(kx, gyz, u2yz, g1, u2);
-          a[j] = cscale(cadd(c0(kx), cmul_iu(a[j], iu[kx])), G);
-        }
+        for (int j = 0; j < P::R1; ++j) c0(t + P::T * j) = a[j];
       }
+      box_wait(1);
+#pragma unroll
+      for (int j = 0; j < P::R1; ++j) a[j] = c1(t + P::T * j);
+      fft_r<L, -1, IL>(a, t, c1, twr);
+#pragma unroll
+      for (int j = 0; j < P::R1; ++j) {
+        const int kx = t + P::T * j;  // this lane wrote c0(kx) above
+        const float G = spectral_G(kx, gyz, u2yz, g1, u2);
+        a[j] = cscale(cadd(c0(kx), cmul_iu(a[j], iu[kx])), G);
+      }
+    }
+    if constexpr (!P::WL2) {
+      // every group is done with box 1 (C and its exchange): W~'s tile goes
+      // there (the fence orders this thread's writes to it before the copy's)
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0 && ok) {
+        mbar_expect_tx(&bar[1], P::BOX * (uint32_t)sizeof(float2));
+        tma_load_3d(box + P::BOX, &S.tmx[kSpW], kz0, ky, 0, &bar[1]);
+      }
+      w_reload = true;
+    }
+    if (valid) {
       fft_r<L, +1, IL>(a, t, c0, twr);  // P = unnormalised IFFT_x(chi~)
       // Spectral sums of Eq. 4, by Parseval along x against the x-domain W~
       // (its tile, or up to r = 128 its column straight from L2):
       // sum_kx conj(W~(kx)) chi~(kx) = sum_x conj(W~_x(x)) P(x),
       // sum_kx chi~(kx) = P(x = 0).
-      if constexpr (NCH == 3) {
-        auto c2 = colref(2);
-        box_wait(2);
+      if constexpr (!P::WL2) {
+        box_wait(1, 1u);
 #pragma unroll
         for (int j = 0; j < P::R1; ++j) {
-          const float2 w = c2(t + P::T * j);
+          const float2 w = c1(t + P::T * j);
           am += w.x * a[j].x + w.y * a[j].y;
         }
       } else {
@@ -242,25 +240,7 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? 2 : 5)
       if (x == 0) a[j].x += gs;
     }
     fft_r<L, -1, IL>(a, t, c0, twr);
-    if constexpr (L >= 256) {
-      float2 b[P::R1];
-#pragma unroll
-      for (int j = 0; j < P::R1; ++j) {
-        const int kx = t + P::T * j;
-        const float2 f = cscale(a[j], spectral_G(kx, gyz, u2yz, g1, u2));
-        a[j] = f;
-        b[j] = cmul_iu(f, -iu[kx]);
-      }
-      fft_r<L, +1, IL>(a, t, c0, twr);
-      fft_r<L, +1, IL>(b, t, c1, twr);
-      if (own) {
-#pragma unroll
-        for (int j = 0; j < P::R1; ++j) {
-          c0(t + P::T * j) = a[j];
-          c1(t + P::T * j) = b[j];
-        }
-      }
-    } else {
+    {
       // F = G (.); Q2's input -i u_x F goes to the column of W~ (read above by
       // this group), Q1 = IFFT_x(F) is transformed from registers first
 #pragma unroll
