@@ -66,7 +66,7 @@ enum {
     DPSR_EBUSY = -7        /* resource busy (serving admission) */
 };
 
-/* Create a plan for grid size r (a power of two, 8 <= r <= 256) and Gaussian
+/* Create a plan for grid size r (a power of two, 8 <= r <= 512) and Gaussian
  * bandwidth sigma >= 0 in grid units of Eq. 3 (sigma = 0: no smoothing).
  * Allocates the plan's device workspace on the current device; the plan
  * stays bound to that device. On success *out receives the plan. */
@@ -190,7 +190,8 @@ DPSR_API int dpsr_plan_profile(dpsr_plan plan, int enable);
  * autotuner sets them on the first solve of each grid size in a process
  * (DPSR_TUNE=0 keeps the static choice). The environment can fix them:
  * DPSR_PLANE_PATHS_<r>="a,b,c,d" for grid size r, or DPSR_PLANE_PATH=c for
- * every kind and size (c in 0, 1, 2, 4, 8). */
+ * every kind and size (c in 0, 1, 2, 4, 8). At r = 512 only the pencil
+ * passes exist (a plane no longer fits a cluster's shared memory). */
 DPSR_API int dpsr_plan_clusters(dpsr_plan plan, int *C4);
 DPSR_API int dpsr_plan_profile_read(dpsr_plan plan, double *ms, int *launches);
 

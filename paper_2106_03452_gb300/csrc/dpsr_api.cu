@@ -90,7 +90,7 @@ struct DeviceGuard {
   }
 };
 
-bool valid_r(int r) { return r >= 8 && r <= 256 && (r & (r - 1)) == 0; }
+bool valid_r(int r) { return r >= 8 && r <= 512 && (r & (r - 1)) == 0; }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -119,7 +119,8 @@ size_t pts_ws_bytes(int64_t n) {
 }
 
 // Cluster size of a plane kernel: the smallest whose CTAs fit two per SM
-// (<= 113 KB of shared memory), else the smallest that fits at all.
+// (<= 113 KB of shared memory), else the smallest that fits at all, else 0:
+// the pencil passes (r = 512, where no cluster kernel is built).
 int pick_cluster(int kind, int r) {
   const int cands[4] = {1, 2, 4, 8};
   for (int C : cands) {
@@ -158,7 +159,7 @@ int cuda_err(cudaError_t e) { return e == cudaErrorMemoryAllocation ? DPSR_ENOME
 // tuner off (the static choice of pick_cluster is used).
 // ---------------------------------------------------------------------------
 std::mutex g_tune_mu;
-int g_tuned[4][9] = {};  // [kind][log2 r]: 1 + chosen C (0 = pencil path), 0 = not tuned yet
+int g_tuned[4][10] = {};  // [kind][log2 r]: 1 + chosen C (0 = pencil path), 0 = not tuned yet
 
 int log2i(int r) {
   int l = 0;
@@ -345,7 +346,7 @@ int make_tensor_maps(Solve& s, int r) {
   if (!enc) return DPSR_ECUDA;
   const cuuint64_t dims[3] = {(cuuint64_t)(r / 2 + 1), (cuuint64_t)r, (cuuint64_t)r};
   const cuuint64_t strides[2] = {(cuuint64_t)kpitch(r) * 8, (cuuint64_t)r * kpitch(r) * 8};
-  const cuuint32_t boxx[3] = {16, 1, (cuuint32_t)r}, boxy[3] = {16, (cuuint32_t)r, 1};
+  const cuuint32_t boxx[3] = {16, 1, (cuuint32_t)tma_rows(r)}, boxy[3] = {16, (cuuint32_t)tma_rows(r), 1};
   const cuuint32_t es[3] = {1, 1, 1};
   for (int k = 0; k < kNSpec; ++k) {
     for (int w = 0; w < 2; ++w) {
@@ -412,13 +413,7 @@ int dpsr_plan_create(int r, float sigma, dpsr_plan* out) {
     delete p;
     return DPSR_ECUDA;
   }
-  for (int k = 0; k < 4; ++k) {
-    p->C[k] = pick_cluster(k, r);
-    if (!p->C[k]) {
-      delete p;
-      return DPSR_EINVAL;
-    }
-  }
+  for (int k = 0; k < 4; ++k) p->C[k] = pick_cluster(k, r);
   p->grid_bytes = grid_ws_bytes(r);
   if (cudaMalloc(&p->grid_ws, p->grid_bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -631,7 +626,7 @@ int dpsr_forward(dpsr_plan p, const float* points, const float* normals, int64_t
     if (e == cudaSuccess) e = fn();
     if (e == cudaSuccess) e = prof_mark(p, kind, false);
   };
-  run(DPSR_K_BIN, [&] { return dpsr::launch_bin(s, nullptr, 1, (int)N, st); });
+  run(DPSR_K_BIN, [&] { return dpsr::launch_bin(s, nullptr, 1, (int)N, r, st); });
   run(DPSR_K_PLANE_FWD, [&] { return run_plane(p, 0, s, st); });
   run(DPSR_K_XPASS_FWD, [&] { return dpsr::launch_xpass(false, r, s, nullptr, 1, st); });
   run(DPSR_K_PLANE_INV, [&] { return run_plane(p, 1, s, st); });

@@ -83,7 +83,7 @@ cudaError_t launch_fwd(dpsr_batch b) {
   const Solve dummy = {};
   return per_class(b, [&](BatchClass& c, cudaStream_t st) {
     const int n = (int)c.members.size();
-    cudaError_t e = dpsr::launch_bin(dummy, c.dtab, n, c.nmax, st);
+    cudaError_t e = dpsr::launch_bin(dummy, c.dtab, n, c.nmax, c.r, st);
     if (e == cudaSuccess) e = dpsr::launch_plane(0, c.r, c.C[0], dummy, c.dtab, n, st);
     if (e == cudaSuccess) e = dpsr::launch_xpass(false, c.r, dummy, c.dtab, n, st);
     if (e == cudaSuccess) e = dpsr::launch_plane(1, c.r, c.C[1], dummy, c.dtab, n, st);
@@ -179,7 +179,7 @@ cudaError_t tune_batch(dpsr_batch b, bool with_bwd) {
       return c.tuned[kind] ? dpsr::launch_plane(kind, c.r, c.C[kind], dummy, c.dtab, n, st)
                            : tune_kind(c, kind, st, e0, e1);
     };
-    if (e == cudaSuccess) e = dpsr::launch_bin(dummy, c.dtab, n, c.nmax, st);
+    if (e == cudaSuccess) e = dpsr::launch_bin(dummy, c.dtab, n, c.nmax, c.r, st);
     if (e == cudaSuccess) e = plane(0);
     if (e == cudaSuccess) e = dpsr::launch_xpass(false, c.r, dummy, c.dtab, n, st);
     if (e == cudaSuccess) e = plane(1);
@@ -460,7 +460,7 @@ int dpsr_internal_batch_run(dpsr_batch b, int k, int with_bwd) {
     return DPSR_OK;
   }
   cudaStream_t st = b->stream;
-  cudaError_t e = dpsr::launch_bin(dummy, c.dtab, k, c.nmax, st);
+  cudaError_t e = dpsr::launch_bin(dummy, c.dtab, k, c.nmax, c.r, st);
   if (e == cudaSuccess) e = dpsr::launch_plane(0, c.r, c.C[0], dummy, c.dtab, k, st);
   if (e == cudaSuccess) e = dpsr::launch_xpass(false, c.r, dummy, c.dtab, k, st);
   if (e == cudaSuccess) e = dpsr::launch_plane(1, c.r, c.C[1], dummy, c.dtab, k, st);

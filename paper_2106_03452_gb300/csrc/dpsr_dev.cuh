@@ -90,8 +90,34 @@ __device__ __forceinline__ float2 twc(float2 a) {
   }
 }
 
-// In-register DFT of E points (E = 1, 2, 4, 8, 16), natural order in and out,
-// exponent sign DIR (-1 forward, +1 inverse), unnormalised. Radix-2
+// cos / sin of 2*pi*q/32 for odd q: cos(k pi / 16), k = 1, 3, 5, 7 and
+// their reflections (the even q are the sixteenth roots above).
+__host__ __device__ constexpr float cos32_odd(int q) {
+  constexpr float c1 = 0.98078528040323044913f, c3 = 0.83146961230254523708f,
+                  c5 = 0.55557023301960222474f, c7 = 0.19509032201612826785f;
+  switch (q & 31) {
+    case 1: return c1;   case 3: return c3;   case 5: return c5;   case 7: return c7;
+    case 9: return -c7;  case 11: return -c5; case 13: return -c3; case 15: return -c1;
+    case 17: return -c1; case 19: return -c3; case 21: return -c5; case 23: return -c7;
+    case 25: return c7;  case 27: return c5;  case 29: return c3;  default: return c1;  // 31
+  }
+}
+__host__ __device__ constexpr float sin32_odd(int q) { return cos32_odd((q - 8) & 31); }
+
+// a * exp(DIR * 2 pi i q / 32).
+template <int Q, int DIR>
+__device__ __forceinline__ float2 twc32(float2 a) {
+  constexpr int q = ((Q % 32) + 32) % 32;
+  if constexpr ((q & 1) == 0) {
+    return twc<q / 2, DIR>(a);
+  } else {
+    constexpr float c = cos32_odd(q), s = DIR * sin32_odd(q);
+    return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+  }
+}
+
+// In-register DFT of E points (E = 1, 2, 4, 8, 16, 32), natural order in and
+// out, exponent sign DIR (-1 forward, +1 inverse), unnormalised. Radix-2
 // decimation in time, fully unrolled.
 template <int E, int DIR>
 struct Dft {
@@ -104,8 +130,8 @@ struct Dft {
     Dft<E / 2, DIR>::run(ev);
     Dft<E / 2, DIR>::run(od);
     sfor<0, E / 2>([&](auto k) {
-      constexpr int q = decltype(k)::value * (16 / E);
-      const float2 t = twc<q, DIR>(od[k]);
+      constexpr int q = decltype(k)::value * (32 / E);
+      const float2 t = twc32<q, DIR>(od[k]);
       v[k] = cadd(ev[k], t);
       v[k + E / 2] = csub(ev[k], t);
     });
@@ -172,6 +198,13 @@ template <> struct Shape<32>  { static constexpr int R1 = 8,  T = 4; };
 template <> struct Shape<64>  { static constexpr int R1 = 8,  T = 8; };
 template <> struct Shape<128> { static constexpr int R1 = 16, T = 8; };
 template <> struct Shape<256> { static constexpr int R1 = 16, T = 16; };
+template <> struct Shape<512> { static constexpr int R1 = 32, T = 16; };
+
+// Rows of a TMA box along a transform axis: the whole axis up to r = 256;
+// at r = 512 (above the 256-element limit of a box dimension) two boxes of
+// 256 rows, placed one after the other in shared memory (both start on a
+// 1024-byte boundary, so the 128-byte swizzle runs on unchanged).
+__host__ __device__ constexpr int tma_rows(int r) { return r < 256 ? r : 256; }
 
 template <int L, int DIR, class XA>
 __device__ __forceinline__ void fft_x(float2 (&v)[Shape<L>::R1], int t, XA xa, const float2* tw) {

@@ -187,7 +187,7 @@ extern "C" DPSR_API int dpsr_forward_static(int r, float sigma, const float* poi
   // the bin counters and the status word must start at zero
   if (e == cudaSuccess) e = cudaMemsetAsync(s.bins, 0, sizeof(int) * dpsr::bins_ints(r), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s.status, 0, sizeof(unsigned), st);
-  if (e == cudaSuccess) e = dpsr::launch_bin(s, nullptr, 1, (int)N, st);
+  if (e == cudaSuccess) e = dpsr::launch_bin(s, nullptr, 1, (int)N, r, st);
   if (e == cudaSuccess) e = dpsr::launch_plane(0, r, 1, s, nullptr, 1, st);
   if (e == cudaSuccess) e = dpsr::launch_xpass(false, r, s, nullptr, 1, st);
   if (e == cudaSuccess) e = dpsr::launch_plane(1, r, 1, s, nullptr, 1, st);

@@ -271,7 +271,7 @@ __device__ __forceinline__ void zfwd_tile(const Solve& S, int X, int y0, float* 
 }
 
 template <int L>
-__global__ void __launch_bounds__(Pen<L>::ZNT, L >= 256 ? 3 : 4) k_zfwd(const __grid_constant__ Solve s0,
+__global__ void __launch_bounds__(Pen<L>::ZNT, L >= 512 ? 1 : (L >= 256 ? 3 : 4)) k_zfwd(const __grid_constant__ Solve s0,
                                                       const Solve* __restrict__ tab) {
   using P = Pen<L>;
   constexpr int YB = P::YB;
@@ -340,8 +340,10 @@ __device__ __forceinline__ void yfwd_issue(const Solve& S, int X, int kz0, int k
   using P = Pen<L>;
   const YfwdBufs b = yfwd_bufs<L, BWD>(kind);
   mbar_expect_tx(bar, (b.two ? 2 : 1) * P::BOX * (uint32_t)sizeof(float2));
-  tma_load_3d(box, &S.tmy[b.buf0], kz0, 0, X, bar);
-  if (b.two) tma_load_3d(box + P::BOX, &S.tmy[b.buf1], kz0, 0, X, bar);
+  for (int y = 0; y < L; y += tma_rows(L)) {
+    tma_load_3d(box + y * 16, &S.tmy[b.buf0], kz0, y, X, bar);
+    if (b.two) tma_load_3d(box + P::BOX + y * 16, &S.tmy[b.buf1], kz0, y, X, bar);
+  }
 }
 
 // All threads: wait for the tile (phase `phase` of `bar`), transform, store
@@ -407,8 +409,10 @@ __device__ __forceinline__ bool yfwd_tile(const Solve& S, int X, int kz0, int ki
   fence_async_smem();
   __syncthreads();
   if (tid == 0) {
-    tma_store_3d(&S.tmy[buf0], kz0, 0, X, box);
-    if (kind == 1 && two) tma_store_3d(&S.tmy[buf1], kz0, 0, X, box + P::BOX);
+    for (int y = 0; y < L; y += tma_rows(L)) {
+      tma_store_3d(&S.tmy[buf0], kz0, y, X, box + y * 16);
+      if (kind == 1 && two) tma_store_3d(&S.tmy[buf1], kz0, y, X, box + P::BOX + y * 16);
+    }
     tma_store_commit();
     tma_store_wait_read();
   }
@@ -416,7 +420,7 @@ __device__ __forceinline__ bool yfwd_tile(const Solve& S, int X, int kz0, int ki
 }
 
 template <int L, bool BWD>
-__global__ void __launch_bounds__(ynt<L>(), BWD ? 4 : (L >= 256 ? 3 : 5)) k_yfwd(const __grid_constant__ Solve s0,
+__global__ void __launch_bounds__(ynt<L>(), L >= 512 ? 1 : (BWD ? 4 : (L >= 256 ? 3 : 5))) k_yfwd(const __grid_constant__ Solve s0,
                                                    const Solve* __restrict__ tab) {
   using P = Pen<L>;
   constexpr int NT = ynt<L>();
@@ -476,8 +480,10 @@ __device__ __forceinline__ void yinv_issue(const Solve& S, int X, int kz0, int p
   // the kind's own input)
   const bool do0 = part != 1, do1 = NCH == 3 && part != 0;
   mbar_expect_tx(bar, ((do0 ? 1 : 0) + (do1 ? 1 : 0)) * P::BOX * (uint32_t)sizeof(float2));
-  if (do0) tma_load_3d(box, &S.tmy[kSpChi], kz0, 0, X, bar);
-  if (do1) tma_load_3d(box + P::BOX, &S.tmy[kSpD], kz0, 0, X, bar);
+  for (int y = 0; y < L; y += tma_rows(L)) {
+    if (do0) tma_load_3d(box + y * 16, &S.tmy[kSpChi], kz0, y, X, bar);
+    if (do1) tma_load_3d(box + P::BOX + y * 16, &S.tmy[kSpD], kz0, y, X, bar);
+  }
 }
 
 // All threads: wait, transform, TMA stores (thread 0 waits until they have
@@ -552,13 +558,15 @@ __device__ __forceinline__ bool yinv_tile(const Solve& S, int X, int kz0, int pa
   fence_async_smem();
   __syncthreads();
   if (tid == 0) {
-    if constexpr (NCH == 1) {
-      tma_store_3d(&S.tmy[kSpYa], kz0, 0, X, box);
-    } else {
-      if (do0) tma_store_3d(&S.tmy[kSpC], kz0, 0, X, box);
-      if (do1) {
-        tma_store_3d(&S.tmy[kSpYa], kz0, 0, X, box + P::BOX);
-        tma_store_3d(&S.tmy[kSpYb], kz0, 0, X, box + 2 * P::BOX);
+    for (int y = 0; y < L; y += tma_rows(L)) {
+      if constexpr (NCH == 1) {
+        tma_store_3d(&S.tmy[kSpYa], kz0, y, X, box + y * 16);
+      } else {
+        if (do0) tma_store_3d(&S.tmy[kSpC], kz0, y, X, box + y * 16);
+        if (do1) {
+          tma_store_3d(&S.tmy[kSpYa], kz0, y, X, box + P::BOX + y * 16);
+          tma_store_3d(&S.tmy[kSpYb], kz0, y, X, box + 2 * P::BOX + y * 16);
+        }
       }
     }
     tma_store_commit();
@@ -569,7 +577,7 @@ __device__ __forceinline__ bool yinv_tile(const Solve& S, int X, int kz0, int pa
 
 template <int L, int NCH>
 __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32,
-                                  NCH == 1 || yinv_split<L, NCH>() ? 4 : 2)
+                                  L >= 512 ? 1 : (NCH == 1 || yinv_split<L, NCH>() ? 4 : 2))
     k_yinv(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = Pen<L>;
   constexpr int NT = 16 * P::T >= 32 ? 16 * P::T : 32;
@@ -761,7 +769,7 @@ __device__ __forceinline__ bool zinv_tile(const Solve& S, int tile, float2* sb, 
 }
 
 template <int L, int NCH>
-__global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, NCH == 1 ? 4 : (L >= 256 ? 2 : 3))
+__global__ void __launch_bounds__(ZiGeo<L, NCH>::NT, L >= 512 ? 1 : (NCH == 1 ? 4 : (L >= 256 ? 2 : 3)))
     k_zinv(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = Pen<L>;
   using Z = ZiGeo<L, NCH>;
@@ -830,7 +838,7 @@ constexpr size_t zbfwd_smem() {
 }
 
 template <int L>
-__global__ void __launch_bounds__(ZbGeo<L>::NT, 3) k_zbfwd(const __grid_constant__ Solve s0,
+__global__ void __launch_bounds__(ZbGeo<L>::NT, L >= 512 ? 1 : 3) k_zbfwd(const __grid_constant__ Solve s0,
                                                           const Solve* __restrict__ tab) {
   using P = Pen<L>;
   constexpr int YB = ZbGeo<L>::ZB, H = P::H, NT = ZbGeo<L>::NT, ZG = ZbGeo<L>::G;
@@ -1005,6 +1013,7 @@ cudaError_t launch_pencil(int kind, int r, const Solve& s, const Solve* tab, int
     case 64: return launch_pencil_t<64>(kind, s, tab, count, st);
     case 128: return launch_pencil_t<128>(kind, s, tab, count, st);
     case 256: return launch_pencil_t<256>(kind, s, tab, count, st);
+    case 512: return launch_pencil_t<512>(kind, s, tab, count, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1029,6 +1038,7 @@ size_t pencil_smem_bytes(int kind, int r) {
     case 64: return pick(std::integral_constant<int, 64>{});
     case 128: return pick(std::integral_constant<int, 128>{});
     case 256: return pick(std::integral_constant<int, 256>{});
+    case 512: return pick(std::integral_constant<int, 512>{});
     default: return 0;
   }
 }

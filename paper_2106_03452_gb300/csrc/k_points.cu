@@ -24,10 +24,10 @@ __device__ __forceinline__ int bin_key(float x, float y, int r) {
 // indexing stays in range). Per-block histogram in shared memory, then one
 // global add per touched bin. The counts must be zero on entry: the forward
 // x-pass clears them (and the scatter cursors) once the scatter is done.
+// Dynamic shared memory: the histogram, nbins(r) ints.
 __global__ void __launch_bounds__(256) k_bin_count(const __grid_constant__ Solve s0,
                                                    const Solve* __restrict__ tab) {
-  static_assert(nbins(256) == 4096, "histogram size");
-  __shared__ int h[4096];
+  extern __shared__ int h[];
   pdl_trigger();
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   const int r = S.r, nb = nbins(r);
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) k_bin_count(const __grid_constant__ Solve
 
 // Shared-memory slot of bin i in the scatter's scan: one pad word per 32
 // bins, so that threads scanning 16 consecutive bins each hit distinct banks.
-__device__ __forceinline__ int scan_slot(int i) { return i + (i >> 5); }
+__host__ __device__ constexpr int scan_slot(int i) { return i + (i >> 5); }
 
 // Counting-sort scatter. Every block first turns the (L2-resident) bin counts
 // into exclusive prefix sums in its own shared memory: each thread sums a
@@ -66,11 +66,11 @@ __device__ __forceinline__ int scan_slot(int i) { return i + (i >> 5); }
 // offsets off[0..nbins] (read by the plane passes) and resets the arrival
 // counters of the solve's last-block reductions. A point's slot is its bin's
 // offset plus a ticket from that bin's cursor (zero on entry; cleared again
-// by the forward x-pass).
+// by the forward x-pass). Dynamic shared memory: scan_slot(nbins(r)) ints.
 __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Solve s0,
                                                      const Solve* __restrict__ tab) {
-  constexpr int NT = 256, MAXNB = 4096;
-  __shared__ int h[MAXNB + MAXNB / 32];
+  constexpr int NT = 256;
+  extern __shared__ int h[];
   __shared__ int wsum[NT / 32];
   pdl_trigger();
   pdl_wait();
@@ -135,10 +135,21 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Sol
   }
 }
 
-cudaError_t launch_bin(const Solve& s, const Solve* tab, int count, int nmax, cudaStream_t st) {
+cudaError_t launch_bin(const Solve& s, const Solve* tab, int count, int nmax, int r, cudaStream_t st) {
   const int blocks = min(max((nmax + 255) / 256, 1), 1184);
-  cudaError_t e = launch_k(k_bin_count, dim3(blocks, 1, count), dim3(256), 0, st, 0, s, tab);
-  if (e == cudaSuccess) e = launch_k(k_bin_scatter, dim3(blocks, 1, count), dim3(256), 0, st, 0, s, tab);
+  const size_t hc = sizeof(int) * nbins(r), hs = sizeof(int) * scan_slot(nbins(r));
+  static bool attr_set = false;  // 16384 bins at r = 512 need more than the default 48 KB
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(int) * nbins(512)));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(sizeof(int) * scan_slot(nbins(512))));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  cudaError_t e = launch_k(k_bin_count, dim3(blocks, 1, count), dim3(256), hc, st, 0, s, tab);
+  if (e == cudaSuccess) e = launch_k(k_bin_scatter, dim3(blocks, 1, count), dim3(256), hs, st, 0, s, tab);
   return e;
 }
 

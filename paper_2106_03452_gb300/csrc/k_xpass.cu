@@ -70,7 +70,7 @@ constexpr size_t xpass_smem() {
 // one kz column along x in registers (the box column doubles as its exchange
 // buffer), and TMA stores the results.
 template <int L, bool BWD>
-__global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? (BWD ? 2 : 3) : 5)
+__global__ void __launch_bounds__(XGeo<L>::NT, L >= 512 ? 1 : (L >= 256 ? (BWD ? 2 : 3) : 5))
     k_xpass(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using P = XGeo<L>;
   constexpr int NCH = P::template nch<BWD>();
@@ -101,7 +101,9 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? (BWD ? 2 : 3) : 5)
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
       mbar_expect_tx(&bar[c], P::BOX * (uint32_t)sizeof(float2));
-      tma_load_3d(box + c * P::BOX, &S.tmx[c == 0 ? src0 : (c == 1 ? src1 : kSpW)], kz0, ky, 0, &bar[c]);
+      for (int x = 0; x < L; x += tma_rows(L))
+        tma_load_3d(box + c * P::BOX + x * P::KC, &S.tmx[c == 0 ? src0 : (c == 1 ? src1 : kSpW)], kz0, ky,
+                    x, &bar[c]);
     }
   }
   for (int i = tid; i < L; i += P::NT) {
@@ -176,7 +178,8 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? (BWD ? 2 : 3) : 5)
       __syncthreads();
       if (tid == 0 && ok) {
         mbar_expect_tx(&bar[1], P::BOX * (uint32_t)sizeof(float2));
-        tma_load_3d(box + P::BOX, &S.tmx[kSpW], kz0, ky, 0, &bar[1]);
+        for (int x = 0; x < L; x += tma_rows(L))
+          tma_load_3d(box + P::BOX + x * P::KC, &S.tmx[kSpW], kz0, ky, x, &bar[1]);
       }
       w_reload = true;
     }
@@ -216,7 +219,7 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? (BWD ? 2 : 3) : 5)
     fence_async_smem();
     block_sum_ff<P::NT>(fm, fs);  // synchronises the block: the tile is complete
     if (tid == 0) {
-      tma_store_3d(&S.tmx[kSpChi], kz0, ky, 0, box);
+      for (int x = 0; x < L; x += tma_rows(L)) tma_store_3d(&S.tmx[kSpChi], kz0, ky, x, box + x * P::KC);
       tma_store_commit();
     }
     last_block_finalize<P::NT>(S, 0, (int)(gridDim.x * gridDim.y),
@@ -266,8 +269,10 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 256 ? (BWD ? 2 : 3) : 5)
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
-      tma_store_3d(&S.tmx[kSpD], kz0, ky, 0, box);          // Q1
-      tma_store_3d(&S.tmx[kSpChi], kz0, ky, 0, box + P::BOX);  // Q2
+      for (int x = 0; x < L; x += tma_rows(L)) {
+        tma_store_3d(&S.tmx[kSpD], kz0, ky, x, box + x * P::KC);             // Q1
+        tma_store_3d(&S.tmx[kSpChi], kz0, ky, x, box + P::BOX + x * P::KC);  // Q2
+      }
       tma_store_commit();
       tma_store_wait_read();
     }
@@ -297,6 +302,7 @@ cudaError_t launch_xpass(bool bwd, int r, const Solve& s, const Solve* tab, int 
     case 64: return bwd ? launch_xpass_t<64, true>(s, tab, count, st) : launch_xpass_t<64, false>(s, tab, count, st);
     case 128: return bwd ? launch_xpass_t<128, true>(s, tab, count, st) : launch_xpass_t<128, false>(s, tab, count, st);
     case 256: return bwd ? launch_xpass_t<256, true>(s, tab, count, st) : launch_xpass_t<256, false>(s, tab, count, st);
+    case 512: return bwd ? launch_xpass_t<512, true>(s, tab, count, st) : launch_xpass_t<512, false>(s, tab, count, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -309,6 +315,7 @@ int xpass_blocks(int r) {
     case 64: return XGeo<64>::NCHUNK * 64;
     case 128: return XGeo<128>::NCHUNK * 128;
     case 256: return XGeo<256>::NCHUNK * 256;
+    case 512: return XGeo<512>::NCHUNK * 512;
     default: return 0;
   }
 }

@@ -79,7 +79,7 @@ int xpass_blocks(int r);
 // Returns 0 on success.
 int make_tensor_maps(Solve& s, int r);
 // Points: x-plane bucketing (count, scan, scatter) and the backward combine.
-cudaError_t launch_bin(const Solve& s, const Solve* tab, int count, int nmax, cudaStream_t st);
+cudaError_t launch_bin(const Solve& s, const Solve* tab, int count, int nmax, int r, cudaStream_t st);
 cudaError_t launch_combine(const Solve& s, const Solve* tab, int count, int nmax,
                            cudaStream_t st);
 

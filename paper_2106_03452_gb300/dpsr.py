@@ -22,7 +22,7 @@ def _dev_f32(t: torch.Tensor, name: str, shape=None) -> torch.Tensor:
 
 
 class Plan:
-    """A libdpsr plan: grid size r (power of two in [8, 256]) and Gaussian
+    """A libdpsr plan: grid size r (power of two in [8, 512]) and Gaussian
     bandwidth sigma (Eq. 3). Owns its device workspace; keeps the context of
     its last forward pass for the backward pass."""
 

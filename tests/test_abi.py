@@ -49,7 +49,8 @@ def test_host_only_calls(lib):
     assert L.dpsr_strerror(L.DPSR_EDEGENERATE).startswith("degenerate")
     assert L.dpsr_strerror(12345) == "unknown status"
     assert L.dpsr_plan_workspace_bytes(12, 100) == 0          # r not a power of two
-    assert L.dpsr_plan_workspace_bytes(512, 100) == 0         # above the maximum size
+    assert L.dpsr_plan_workspace_bytes(1024, 100) == 0        # above the maximum size
+    assert L.dpsr_plan_workspace_bytes(512, 100) > 6 * 8 * 512 * 512 * 257   # six half spectra
     b128 = L.dpsr_plan_workspace_bytes(128, 20000)
     b256 = L.dpsr_plan_workspace_bytes(256, 100000)
     assert 4 * 128 * 128 * 66 * 8 < b128 < 2 * 4 * 128 * 128 * 66 * 8
@@ -59,7 +60,7 @@ def test_host_only_calls(lib):
 def test_create_rejects_bad_arguments(lib):
     from paper_2106_03452_gb300 import libdpsr as L
     h = ctypes.c_void_p()
-    for r, sigma in ((12, 2.0), (4, 2.0), (512, 2.0), (64, -1.0), (64, float("nan"))):
+    for r, sigma in ((12, 2.0), (4, 2.0), (1024, 2.0), (64, -1.0), (64, float("nan"))):
         assert L.load().dpsr_plan_create(r, sigma, ctypes.byref(h)) == L.DPSR_EINVAL
     assert L.load().dpsr_forward(None, None, None, 10, None) == L.DPSR_EINVAL
     assert L.load().dpsr_backward(None, None, None, None) == L.DPSR_EINVAL

@@ -162,6 +162,20 @@ def test_random_clouds_r256(oracle, monkeypatch, path, N, sigma):
     _check(oracle, 256, sigma, pts, nrm, dchi)
 
 
+@pytest.mark.parametrize("path", ["tuned"])
+def test_sphere_r512(oracle, monkeypatch, path):
+    """The largest grid size, r = 512 (pencil passes only; TMA boxes split in
+    two along each 512-long axis; 16384 point bins): a sphere of 20000
+    points and a random upstream gradient against the FP64 oracle."""
+    _set_path(monkeypatch, path, 512)
+    rng = synth.Rng(5120)
+    pts, nrm = synth.sphere_cloud(rng, 20000)
+    dchi = rng.normal(512, 512, 512).astype(np.float32)
+    g = _check(oracle, 512, 2.0, pts, nrm, dchi)
+    from paper_2106_03452_gb300 import libdpsr as L
+    assert L.dpsr_plan_clusters(g["plan"].handle) == [0, 0, 0, 0]
+
+
 def test_degenerate_and_errors():
     import torch
     from paper_2106_03452_gb300 import libdpsr as L
