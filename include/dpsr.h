@@ -163,6 +163,33 @@ DPSR_API int dpsr_grid_sample(const float *grid, int r, const float *q, int64_t 
 DPSR_API int dpsr_grid_splat(float *grid, int r, const float *q, const float *vals, int64_t M,
                              int accumulate, void *stream);
 
+/* Mesh extraction for the optimisation setting (Sec. 3.2: the indicator grid
+ * becomes a mesh at level 0, where the paper runs Marching Cubes). chi: r^3
+ * float32 device grid (layout as dpsr_forward's chi_out, periodic), r a
+ * power of two, 2 <= r <= 512. Each cube is split into Kuhn's six
+ * tetrahedra (a marching-cubes variant without case tables; neighbouring
+ * cubes agree on every shared vertex, so the surface is closed away from
+ * the periodic wrap-around) and the level set chi = level is cut from each.
+ * Writes up to max_tris triangles: tris[t][3][3] float32 corner coordinates
+ * in the unit cube (unwrapped: cube r - 1 reaches 1.0), counter-clockwise
+ * about normals[t][3], the unit normal pointing towards increasing chi. The
+ * total number of triangles goes to *count (a device uint64, written on
+ * `stream`); more than max_tris means the buffers were too small (the
+ * triangles beyond max_tris are dropped). Triangle order varies between
+ * calls; the set does not. Asynchronous; DPSR_EINVAL for bad arguments. */
+DPSR_API int dpsr_mesh_extract(const float *chi, int r, float level, float *tris, float *normals,
+                               int64_t max_tris, unsigned long long *count, void *stream);
+
+/* The surrogate gradient of Eq. 6 (d p_mesh / d chi = -n_mesh) for M points
+ * on the mesh, p (M x 3, unit cube) with unit normals n (M x 3) and the
+ * loss gradient dldp = dL/dp (M x 3), all device float32: each point
+ * contributes dL/dp . (-n) to dL/dchi through the adjoint of the trilinear
+ * lookup at p (the rasterization of Eq. A2, periodic). dchi: r^3 device
+ * grid, zeroed first unless accumulate != 0; float atomics (summation order
+ * varies). The result goes to dpsr_backward as its dchi. */
+DPSR_API int dpsr_mesh_surrogate_splat(float *dchi, int r, const float *points, const float *normals,
+                                       const float *dldp, int64_t M, int accumulate, void *stream);
+
 /* Per-kernel timing. With profiling on, every kernel launch of the plan is
  * bracketed by CUDA events on the plan's stream (a small overhead per launch).
  * dpsr_plan_profile_read synchronises, then returns, per kernel kind (the

@@ -55,6 +55,8 @@ _PROTOS = {
     "dpsr_batch_losses": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "dpsr_server_set_max_group": (_c_int, [_vp, _c_int]),
     "dpsr_server_group_stats": (_c_int, [_vp, ctypes.POINTER(_c_i64)]),
+    "dpsr_mesh_extract": (_c_int, [_vp, _c_int, ctypes.c_float, _vp, _vp, _c_i64, _vp, _vp]),
+    "dpsr_mesh_surrogate_splat": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _c_i64, _c_int, _vp]),
     "dpsr_batch_create": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(_c_i64), ctypes.POINTER(_vp)]),
     "dpsr_batch_destroy": (_c_int, [_vp]),
@@ -276,6 +278,18 @@ def dpsr_batch_losses(batch: int, count: int):
 
 def dpsr_server_set_max_group(server: int, max_group: int) -> None:
     check(load().dpsr_server_set_max_group(server, int(max_group)), "dpsr_server_set_max_group")
+
+
+def dpsr_mesh_extract(chi: int, r: int, level: float, tris: int, normals: int, max_tris: int, count: int,
+                      stream: int = 0) -> None:
+    check(load().dpsr_mesh_extract(chi, int(r), float(level), tris, normals, int(max_tris), count, stream),
+          "dpsr_mesh_extract")
+
+
+def dpsr_mesh_surrogate_splat(dchi: int, r: int, points: int, normals: int, dldp: int, M: int,
+                              accumulate: bool = False, stream: int = 0) -> None:
+    check(load().dpsr_mesh_surrogate_splat(dchi, int(r), points, normals, dldp, int(M), 1 if accumulate else 0,
+                                           stream), "dpsr_mesh_surrogate_splat")
 
 
 def dpsr_batch_paths(batch: int, r: int):
