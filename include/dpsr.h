@@ -190,6 +190,45 @@ DPSR_API int dpsr_mesh_extract(const float *chi, int r, float level, float *tris
 DPSR_API int dpsr_mesh_surrogate_splat(float *dchi, int r, const float *points, const float *normals,
                                        const float *dldp, int64_t M, int accumulate, void *stream);
 
+/* The optimisation setting's other kernels (Sec. 3.2; supplementary Sec. B).
+ * All pointers are device pointers, all work is queued on `stream`.
+ *
+ * Bi-directional L2 Chamfer distance between points a (na x 3) sampled on the
+ * mesh and the input cloud b (nb x 3):
+ *   loss = mean_a min_b |a - b|^2 + mean_b min_a |a - b|^2
+ * (nearest neighbours by brute force, ties to the lowest index), written to
+ * *loss (one double), and its gradient with respect to a into grad_a
+ * (na x 3, overwritten; float atomics). ws_idx: na + nb ints, ws_d2: na + nb
+ * floats of caller-owned scratch. */
+DPSR_API int dpsr_chamfer(const float *a, int64_t na, const float *b, int64_t nb, int *ws_idx, float *ws_d2,
+                          float *grad_a, double *loss, void *stream);
+
+/* The largest component of the inside region {chi < level} of the periodic
+ * grid (voxels joined along the edges of the extraction's tetrahedra: x, y, z
+ * and the monotone diagonals), for the resampling step: the surface of that
+ * component is the mesh's largest component, without small detached pieces.
+ * labels: r^3 ints (out), the component's representative voxel for inside
+ * voxels, -1 outside; ws: r^3 ints of scratch; *best (one uint64, out):
+ * (voxel count << 32) | (0xffffffff - representative) of the largest
+ * component (0: no inside voxel); *err (one unsigned, out) nonzero if a
+ * bounded union-find loop ran out (not expected). */
+DPSR_API int dpsr_largest_region(const float *chi, int r, float level, int *labels, int *ws,
+                                 unsigned long long *best, unsigned *err, void *stream);
+
+/* dpsr_mesh_extract restricted to the component `keep` of labels (the
+ * tetrahedra whose inside corners belong to it). */
+DPSR_API int dpsr_mesh_extract_region(const float *chi, int r, float level, const int *labels, int keep,
+                                      float *tris, float *normals, int64_t max_tris,
+                                      unsigned long long *count, void *stream);
+
+/* M points drawn uniformly by area on a triangle soup (tris T x 3 x 3 with
+ * normals T x 3, as from dpsr_mesh_extract), each with its triangle's
+ * normal: points, pnormals (M x 3, out). The draws come from a counter-based
+ * generator (SplitMix64's finaliser of seed and index), so the same seed
+ * gives the same points. ws: T + ceil(T / 1024) + 1 doubles of scratch. */
+DPSR_API int dpsr_mesh_sample(const float *tris, const float *normals, int64_t T, int64_t M,
+                              uint64_t seed, double *ws, float *points, float *pnormals, void *stream);
+
 /* Per-kernel timing. With profiling on, every kernel launch of the plan is
  * bracketed by CUDA events on the plan's stream (a small overhead per launch).
  * dpsr_plan_profile_read synchronises, then returns, per kernel kind (the

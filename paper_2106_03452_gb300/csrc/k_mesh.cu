@@ -82,10 +82,14 @@ __device__ __forceinline__ void emit(float* tris, float* nrm, unsigned long long
   nrm[3 * k + 2] = n.z * s;
 }
 
+// labels (optional): a component label per voxel (dpsr_largest_region);
+// then only the tetrahedra whose negative corners carry label `keep` emit
+// (their negative corners are always in one component).
 __global__ void __launch_bounds__(256) k_mesh_extract(const float* __restrict__ chi, int r, float level,
                                                       float* __restrict__ tris, float* __restrict__ nrm,
                                                       unsigned long long* __restrict__ count,
-                                                      unsigned long long cap) {
+                                                      unsigned long long cap, const int* __restrict__ labels,
+                                                      int keep) {
   const int64_t n = (int64_t)r * r * r;
   const float inv_r = 1.f / (float)r;  // r is a power of two: exact
   for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < n;
@@ -100,15 +104,35 @@ __global__ void __launch_bounds__(256) k_mesh_extract(const float* __restrict__ 
       neg |= (c.f[q] < 0.f ? 1u : 0u) << q;
     }
     if (neg == 0u || neg == 255u) continue;
+    if (labels) {  // keep the negative corners of component `keep` only
+      unsigned kept = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (!((neg >> q) & 1u)) continue;
+        const int ii = (i + (q & 1)) & (r - 1), jj = (j + ((q >> 1) & 1)) & (r - 1), kk = (k + ((q >> 2) & 1)) & (r - 1);
+        if (__ldg(labels + ((int64_t)ii * r + jj) * r + kk) == keep) kept |= 1u << q;
+      }
+      if (!kept) continue;
+      // a tetrahedron emits when its negative corners are kept ones
+      neg |= (~kept & neg) << 8;  // bits 8..15: negative corners of other components
+    }
     c.o = make_float3((float)i, (float)j, (float)k);
     // count first, reserve once per cube, then write
+    const unsigned other = neg >> 8;
+    neg &= 255u;
+    auto skip = [&](int t) {  // a tetrahedron whose negative corners lie in another component
+      unsigned o = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) o |= (other >> kTet[t][a]) & 1u;
+      return o != 0u;
+    };
     int nt = 0;
 #pragma unroll
     for (int t = 0; t < 6; ++t) {
       unsigned m = 0;
 #pragma unroll
       for (int a = 0; a < 4; ++a) m |= ((neg >> kTet[t][a]) & 1u) << a;
-      nt += tet_tris(m);
+      if (!skip(t)) nt += tet_tris(m);
     }
     unsigned long long base = atomicAdd(count, (unsigned long long)nt);
 #pragma unroll
@@ -121,7 +145,7 @@ __global__ void __launch_bounds__(256) k_mesh_extract(const float* __restrict__ 
         m |= ((neg >> q[a]) & 1u) << a;
       }
       const int cnt = __popc(m);
-      if (cnt == 0 || cnt == 4) continue;
+      if (cnt == 0 || cnt == 4 || skip(t)) continue;
       // up: from the centroid of the negative corners to that of the positive ones
       float3 pn = make_float3(0.f, 0.f, 0.f), pp = pn;
 #pragma unroll
@@ -194,7 +218,21 @@ int dpsr_mesh_extract(const float* chi, int r, float level, float* tris, float* 
   const int64_t n = (int64_t)r * r * r;
   const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 64);
   dpsr::k_mesh_extract<<<blocks, 256, 0, st>>>(chi, r, level, tris, normals, count,
-                                                (unsigned long long)max_tris);
+                                                (unsigned long long)max_tris, nullptr, 0);
+  return cudaGetLastError() == cudaSuccess ? DPSR_OK : DPSR_ECUDA;
+}
+
+int dpsr_mesh_extract_region(const float* chi, int r, float level, const int* labels, int keep, float* tris,
+                             float* normals, int64_t max_tris, unsigned long long* count, void* stream) {
+  if (!chi || !labels || !count || r < 2 || r > 512 || (r & (r - 1)) || max_tris < 0 || !isfinite(level))
+    return DPSR_EINVAL;
+  if (max_tris > 0 && (!tris || !normals)) return DPSR_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(count, 0, sizeof(unsigned long long), st) != cudaSuccess) return DPSR_ECUDA;
+  const int64_t n = (int64_t)r * r * r;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 64);
+  dpsr::k_mesh_extract<<<blocks, 256, 0, st>>>(chi, r, level, tris, normals, count,
+                                                (unsigned long long)max_tris, labels, keep);
   return cudaGetLastError() == cudaSuccess ? DPSR_OK : DPSR_ECUDA;
 }
 

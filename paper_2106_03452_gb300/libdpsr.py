@@ -57,6 +57,10 @@ _PROTOS = {
     "dpsr_server_group_stats": (_c_int, [_vp, ctypes.POINTER(_c_i64)]),
     "dpsr_mesh_extract": (_c_int, [_vp, _c_int, ctypes.c_float, _vp, _vp, _c_i64, _vp, _vp]),
     "dpsr_mesh_surrogate_splat": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _c_i64, _c_int, _vp]),
+    "dpsr_chamfer": (_c_int, [_vp, _c_i64, _vp, _c_i64, _vp, _vp, _vp, _vp, _vp]),
+    "dpsr_largest_region": (_c_int, [_vp, _c_int, ctypes.c_float, _vp, _vp, _vp, _vp, _vp]),
+    "dpsr_mesh_extract_region": (_c_int, [_vp, _c_int, ctypes.c_float, _vp, _c_int, _vp, _vp, _c_i64, _vp, _vp]),
+    "dpsr_mesh_sample": (_c_int, [_vp, _vp, _c_i64, _c_i64, ctypes.c_uint64, _vp, _vp, _vp, _vp]),
     "dpsr_batch_create": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(_c_i64), ctypes.POINTER(_vp)]),
     "dpsr_batch_destroy": (_c_int, [_vp]),
@@ -290,6 +294,29 @@ def dpsr_mesh_surrogate_splat(dchi: int, r: int, points: int, normals: int, dldp
                               accumulate: bool = False, stream: int = 0) -> None:
     check(load().dpsr_mesh_surrogate_splat(dchi, int(r), points, normals, dldp, int(M), 1 if accumulate else 0,
                                            stream), "dpsr_mesh_surrogate_splat")
+
+
+def dpsr_chamfer(a: int, na: int, b: int, nb: int, ws_idx: int, ws_d2: int, grad_a: int, loss: int,
+                 stream: int = 0) -> None:
+    check(load().dpsr_chamfer(a, int(na), b, int(nb), ws_idx, ws_d2, grad_a, loss, stream), "dpsr_chamfer")
+
+
+def dpsr_largest_region(chi: int, r: int, level: float, labels: int, ws: int, best: int, err: int,
+                        stream: int = 0) -> None:
+    check(load().dpsr_largest_region(chi, int(r), float(level), labels, ws, best, err, stream),
+          "dpsr_largest_region")
+
+
+def dpsr_mesh_extract_region(chi: int, r: int, level: float, labels: int, keep: int, tris: int, normals: int,
+                             max_tris: int, count: int, stream: int = 0) -> None:
+    check(load().dpsr_mesh_extract_region(chi, int(r), float(level), labels, int(keep), tris, normals,
+                                          int(max_tris), count, stream), "dpsr_mesh_extract_region")
+
+
+def dpsr_mesh_sample(tris: int, normals: int, T: int, M: int, seed: int, ws: int, points: int, pnormals: int,
+                     stream: int = 0) -> None:
+    check(load().dpsr_mesh_sample(tris, normals, int(T), int(M), int(seed) & (2 ** 64 - 1), ws, points,
+                                  pnormals, stream), "dpsr_mesh_sample")
 
 
 def dpsr_batch_paths(batch: int, r: int):

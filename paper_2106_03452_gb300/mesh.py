@@ -4,7 +4,7 @@ optimisation setting (Sec. 3.2, Eq. 6), over libdpsr's kernels
 
 MeshPoints is a torch.autograd.Function: its forward cuts the level set
 chi = level into triangles and returns points on them with their normals
-(the triangle centroids, or `samples` area-weighted random points); its
+(the triangle centroids, or `samples` points drawn by area); its
 backward sends dL/dp to dL/dchi through the inverse surface normal of Eq. 6,
 so that a loss on mesh points reaches the oriented point cloud through the
 DPSR layer's adjoint.
@@ -36,27 +36,59 @@ def extract(chi: torch.Tensor, level: float = 0.0):
     raise RuntimeError("mesh extraction did not converge")
 
 
-def sample(tris: torch.Tensor, normals: torch.Tensor, M: int, generator=None):
-    """M area-weighted uniform points on a triangle soup, with the normal of
-    the triangle each falls in."""
-    a = torch.linalg.cross(tris[:, 1] - tris[:, 0], tris[:, 2] - tris[:, 0]).norm(dim=1)
-    idx = torch.multinomial(a, M, replacement=True, generator=generator)
-    u = torch.rand((M, 2), device=tris.device, generator=generator)
-    flip = u.sum(1) > 1
-    u[flip] = 1 - u[flip]
-    t = tris[idx]
-    p = t[:, 0] + u[:, :1] * (t[:, 1] - t[:, 0]) + u[:, 1:] * (t[:, 2] - t[:, 0])
-    return p, normals[idx]
+def sample(tris: torch.Tensor, normals: torch.Tensor, M: int, seed: int = 0):
+    """M points drawn uniformly by area on a triangle soup (dpsr_mesh_sample),
+    with the normal of the triangle each falls in."""
+    T = tris.shape[0]
+    ws = torch.empty(T + (T + 1023) // 1024 + 1, dtype=torch.float64, device=tris.device)
+    p = torch.empty((M, 3), device=tris.device)
+    n = torch.empty((M, 3), device=tris.device)
+    st = torch.cuda.current_stream(tris.device).cuda_stream
+    L.dpsr_mesh_sample(tris.contiguous().data_ptr(), normals.contiguous().data_ptr(), T, M, seed, ws.data_ptr(),
+                       p.data_ptr(), n.data_ptr(), st)
+    return p, n
+
+
+def largest_component(chi: torch.Tensor, level: float = 0.0):
+    """(tris, normals) of the mesh's largest component: the surface of the
+    largest connected part of {chi < level} (dpsr_largest_region)."""
+    r = chi.shape[0]
+    chi = chi.contiguous().float()
+    st = torch.cuda.current_stream(chi.device).cuda_stream
+    labels = torch.empty((r, r, r), dtype=torch.int32, device=chi.device)
+    ws = torch.empty((r, r, r), dtype=torch.int32, device=chi.device)
+    best = torch.zeros(1, dtype=torch.int64, device=chi.device)
+    err = torch.zeros(1, dtype=torch.int32, device=chi.device)
+    L.dpsr_largest_region(chi.data_ptr(), r, level, labels.data_ptr(), ws.data_ptr(), best.data_ptr(),
+                          err.data_ptr(), st)
+    b, e = int(best.item()), int(err.item())
+    if e:
+        raise RuntimeError("component labelling ran out of its iteration bound")
+    if b == 0:
+        return extract(chi, level)  # nothing inside: the plain extraction (empty)
+    keep = 0xFFFFFFFF - (b & 0xFFFFFFFF)
+    count = torch.zeros(1, dtype=torch.int64, device=chi.device)
+    cap = max(1024, 24 * r * r)
+    for _ in range(2):
+        tris = torch.empty((cap, 3, 3), device=chi.device)
+        nrm = torch.empty((cap, 3), device=chi.device)
+        L.dpsr_mesh_extract_region(chi.data_ptr(), r, level, labels.data_ptr(), keep, tris.data_ptr(),
+                                   nrm.data_ptr(), cap, count.data_ptr(), st)
+        n = int(count.item())
+        if n <= cap:
+            return tris[:n], nrm[:n]
+        cap = n
+    raise RuntimeError("mesh extraction did not converge")
 
 
 class MeshPoints(torch.autograd.Function):
     """(points, normals) on the level set of chi; backward: Eq. 6."""
 
     @staticmethod
-    def forward(ctx, chi, level=0.0, samples=0, generator=None):
+    def forward(ctx, chi, level=0.0, samples=0, seed=0):
         tris, nrm = extract(chi.detach(), level)
         if samples:
-            p, n = sample(tris, nrm, samples, generator)
+            p, n = sample(tris, nrm, samples, seed)
         else:
             p, n = tris.mean(1), nrm
         ctx.save_for_backward(p, n)
