@@ -499,12 +499,18 @@ int dpsr_server_wait(dpsr_server s, int64_t ticket, double timeout_s) {
   std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->reqs.find(ticket);
   if (it == s->reqs.end()) return DPSR_EINVAL;
-  const bool ok = s->cv_done.wait_for(
-      lk, std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 1e9),
-      [&] { return s->reqs[ticket].done; });
+  // find, never operator[]: another thread may retire the ticket meanwhile
+  // (poll), and operator[] would insert a fresh request that never completes
+  auto done = [&] {
+    auto f = s->reqs.find(ticket);
+    return f == s->reqs.end() || f->second.done;
+  };
+  const bool ok = s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 1e9), done);
   if (!ok) return DPSR_ETIMEOUT;
-  const int st = s->reqs[ticket].status;
-  s->reqs.erase(ticket);
+  auto f = s->reqs.find(ticket);
+  if (f == s->reqs.end()) return DPSR_EINVAL;  // retired by another caller
+  const int st = f->second.status;
+  s->reqs.erase(f);
   return st;
 }
 
