@@ -114,6 +114,18 @@ DPSR_API int dpsr_forward_host(dpsr_plan plan, const float *points, const float 
                       float *chi_out);
 DPSR_API int dpsr_backward_host(dpsr_plan plan, const float *dchi, float *dpoints, float *dnormals);
 
+/* Forward and backward of one solve with HOST buffers in one call (the
+ * layer of Sec. 3.1 and its adjoint, as dpsr_forward_host followed by
+ * dpsr_backward_host with the upstream gradient dchi given up front). The
+ * copies that do not feed the next kernel overlap the kernels on a second
+ * stream of the plan: dchi goes up during the forward pass and chi comes down
+ * during the backward pass; one synchronisation at the end returns the
+ * device status. Page-locked host buffers let the copies overlap (pageable
+ * ones serialise them). chi_out, dpoints, dnormals are overwritten; the plan
+ * keeps the forward context, as after dpsr_forward_host. */
+DPSR_API int dpsr_solve_host(dpsr_plan plan, const float *points, const float *normals, int64_t N,
+                             const float *dchi, float *chi_out, float *dpoints, float *dnormals);
+
 /* Wait for the plan's stream; return the device status of the work queued so
  * far and clear it: DPSR_ETIMEOUT if a bounded device wait gave up (checked
  * first: the outputs of that call are incomplete), else DPSR_EDEGENERATE for

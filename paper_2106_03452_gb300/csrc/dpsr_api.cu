@@ -58,6 +58,10 @@ struct dpsr_plan_s {
   // pinned host copy of the status word, filled on the plan's stream by
   // dpsr_sync so that one stream synchronisation returns it
   unsigned* status_host = nullptr;
+  // dpsr_solve_host: a second stream for the copies that overlap the
+  // kernels, and the events that order the two streams (created on first use)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_dchi = nullptr, ev_fwd = nullptr, ev_chi = nullptr;
   // optional per-kernel timing: an event before and after each launch
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -505,6 +509,12 @@ int dpsr_plan_destroy(dpsr_plan p) {
     cudaEventDestroy(p->done_ev);
   }
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  if (p->copy_stream) {
+    cudaStreamSynchronize(p->copy_stream);
+    cudaStreamDestroy(p->copy_stream);
+  }
+  for (cudaEvent_t e : {p->ev_dchi, p->ev_fwd, p->ev_chi})
+    if (e) cudaEventDestroy(e);
   cudaFree(p->grid_ws);
   if (p->pts_ws) cudaFree(p->pts_ws);
   if (p->host_io) cudaFree(p->host_io);
@@ -820,6 +830,52 @@ int dpsr_forward_host(dpsr_plan p, const float* points, const float* normals, in
   if (cudaMemcpyAsync(chi_out, v.chi, gb, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess)
     return DPSR_ECUDA;
   p->host_n = N;
+  return dpsr_sync(p);
+}
+
+int dpsr_solve_host(dpsr_plan p, const float* points, const float* normals, int64_t N, const float* dchi,
+                    float* chi_out, float* dpoints, float* dnormals) {
+  if (!p || !points || !normals || !dchi || !chi_out || !dpoints || !dnormals || N < 1 || N > INT32_MAX / 2)
+    return DPSR_EINVAL;
+  DeviceGuard dg(p->device);
+  if (!dg.ok) return DPSR_ECUDA;
+  int rc = host_io_reserve(p, N);
+  if (rc != DPSR_OK) return rc;
+  if (!p->copy_stream) {
+    if (cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_dchi, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_fwd, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_chi, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return DPSR_ECUDA;
+    }
+  }
+  HostIo v = host_io_view(p, N);
+  const size_t nb = sizeof(float) * 3 * N, gb = sizeof(float) * p->r * p->r * p->r;
+  cudaStream_t st = p->stream, cs = p->copy_stream;
+  // copy stream: the upstream gradient goes up while the forward pass runs;
+  // the plan's stream (and the staging it reuses) is free of earlier work first
+  if (cudaEventRecord(p->ev_fwd, st) != cudaSuccess || cudaStreamWaitEvent(cs, p->ev_fwd, 0) != cudaSuccess ||
+      cudaMemcpyAsync(v.dchi, dchi, gb, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+      cudaEventRecord(p->ev_dchi, cs) != cudaSuccess)
+    return DPSR_ECUDA;
+  if (cudaMemcpyAsync(v.pts, points, nb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(v.nrm, normals, nb, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return DPSR_ECUDA;
+  rc = dpsr_forward(p, v.pts, v.nrm, N, v.chi);
+  if (rc != DPSR_OK) return rc;
+  // chi comes down while the backward pass runs (it reads chi, never writes it)
+  if (cudaEventRecord(p->ev_fwd, st) != cudaSuccess || cudaStreamWaitEvent(cs, p->ev_fwd, 0) != cudaSuccess ||
+      cudaMemcpyAsync(chi_out, v.chi, gb, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+      cudaEventRecord(p->ev_chi, cs) != cudaSuccess || cudaStreamWaitEvent(st, p->ev_dchi, 0) != cudaSuccess)
+    return DPSR_ECUDA;
+  p->host_n = N;
+  rc = dpsr_backward(p, v.dchi, v.dpts, v.dnrm);
+  if (rc != DPSR_OK) return rc;
+  if (cudaMemcpyAsync(dpoints, v.dpts, nb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(dnormals, v.dnrm, nb, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamWaitEvent(st, p->ev_chi, 0) != cudaSuccess)
+    return DPSR_ECUDA;
   return dpsr_sync(p);
 }
 

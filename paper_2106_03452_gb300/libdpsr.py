@@ -36,6 +36,7 @@ _PROTOS = {
     "dpsr_backward": (_c_int, [_vp, _vp, _vp, _vp]),
     "dpsr_forward_host": (_c_int, [_vp, _vp, _vp, _c_i64, _vp]),
     "dpsr_backward_host": (_c_int, [_vp, _vp, _vp, _vp]),
+    "dpsr_solve_host": (_c_int, [_vp, _vp, _vp, _c_i64, _vp, _vp, _vp, _vp]),
     "dpsr_sync": (_c_int, [_vp]),
     "dpsr_get_scalars": (_c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "dpsr_plan_last_launches": (_c_int, [_vp]),
@@ -152,6 +153,11 @@ def dpsr_forward_host(plan: int, points: int, normals: int, N: int, chi_out: int
 
 def dpsr_backward_host(plan: int, dchi: int, dpoints: int, dnormals: int) -> None:
     check(load().dpsr_backward_host(plan, dchi, dpoints, dnormals), "dpsr_backward_host")
+
+
+def dpsr_solve_host(plan: int, points: int, normals: int, N: int, dchi: int, chi_out: int, dpoints: int,
+                    dnormals: int) -> None:
+    check(load().dpsr_solve_host(plan, points, normals, int(N), dchi, chi_out, dpoints, dnormals), "dpsr_solve_host")
 
 
 def dpsr_sync(plan: int) -> int:

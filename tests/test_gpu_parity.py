@@ -222,3 +222,17 @@ def test_autograd_function_and_host_api(oracle):
     hdn = np.zeros_like(hn)
     L.dpsr_backward_host(plan.handle, hg.ctypes.data, hdp.ctypes.data, hdn.ctypes.data)
     assert relmax(hdp, P.grad.cpu().numpy()) <= 1e-5 and relmax(hdn, Nn.grad.cpu().numpy()) <= 1e-5
+    # the one-call host solve (copies overlapped on a second stream), with
+    # pageable and with page-locked buffers, twice in a row
+    for pinned in (False, True):
+        for _ in range(2):
+            bufs = [torch.from_numpy(x.copy()) for x in (hp, hn, hg)] + \
+                   [torch.zeros((r, r, r)), torch.zeros(hp.shape), torch.zeros(hn.shape)]
+            if pinned:
+                bufs = [b.pin_memory() for b in bufs]
+            tp, tn, tg, tchi, tdp, tdn = bufs
+            L.dpsr_solve_host(plan.handle, tp.data_ptr(), tn.data_ptr(), hp.shape[0], tg.data_ptr(),
+                              tchi.data_ptr(), tdp.data_ptr(), tdn.data_ptr())
+            assert relmax(tchi.numpy(), chi.detach().cpu().numpy()) <= 1e-6
+            assert relmax(tdp.numpy(), P.grad.cpu().numpy()) <= 1e-5
+            assert relmax(tdn.numpy(), Nn.grad.cpu().numpy()) <= 1e-5
