@@ -152,6 +152,15 @@ def kernel_bytes(r: int, N: int):
     }
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# plane kind's kernel at (grid size, plane path), from one ncu capture of the
+# current build on the same workload (profiles/sections_r128_plane_binv_xpass.md);
+# a kind, size or path not listed reports traffic as null.
+MEASURED_TRAFFIC = {
+    ("plane_binv", 128, 1): 21764352,   # k_plane_binv<128, 1>, r = 128 ellipsoids, N = 20000
+}
+
+
 def solve_bytes_model(r: int, N: int) -> float:
     """Whole fwd+bwd solve: 23 one-grid units plus ~200 B per point."""
     return 23 * 4 * r ** 3 + 200 * N
@@ -233,6 +242,11 @@ def run_gpu(args):
     per = {k: {"ms": v[0] / max(v[1], 1), "launches": v[1], "bytes": kb.get(k)} for k, v in prof.items() if v[1]}
     dom = max((k for k in per if per[k]["bytes"]), key=lambda k: per[k]["ms"] * per[k]["launches"])
     ach = per[dom]["bytes"] / (per[dom]["ms"] / 1e3) / 1e9
+    kind_index = {"plane_fwd": 0, "plane_inv": 1, "plane_bfwd": 2, "plane_binv": 3}
+    paths = L.dpsr_plan_clusters(plan.handle)
+    traffic = None
+    if dom in kind_index:
+        traffic = MEASURED_TRAFFIC.get((dom, r, paths[kind_index[dom]]))
 
     # ---------------- e2e through the host-buffer entry points ----------------
     hp = torch.from_numpy(w["points"]).pin_memory()
@@ -298,11 +312,12 @@ def run_gpu(args):
                 "paths": L.dpsr_plan_clusters(plan3.handle)}
         # the differentiable loop of this workload: 50 Adam steps of
         # L = mean chi(q)^2 over its 200 000 clean targets through the adjoint
-        from paper_2106_03452_gb300.loop import optimize
-        Q3 = torch.from_numpy(w3["targets"]).to(dev)
-        hist, _, _, s_step = optimize(P3, N3t, Q3, r=r3, sigma=w3["sigma"], steps=50, plan=plan3)
-        r256["loop"] = {"workload": "50 Adam steps of mean chi(q)^2 over 200000 targets, lr 2e-3 * 0.7^3",
-                        "s_per_step": s_step, "loss_first": hist[0], "loss_last": hist[-1]}
+        if not args.no_loop:
+            from paper_2106_03452_gb300.loop import optimize
+            Q3 = torch.from_numpy(w3["targets"]).to(dev)
+            hist, _, _, s_step = optimize(P3, N3t, Q3, r=r3, sigma=w3["sigma"], steps=50, plan=plan3)
+            r256["loop"] = {"workload": "50 Adam steps of mean chi(q)^2 over 200000 targets, lr 2e-3 * 0.7^3",
+                            "s_per_step": s_step, "loss_first": hist[0], "loss_last": hist[-1]}
         plan3.close()
 
     # ---------------- batched: 32 clouds, r in {64, 128} ----------------
@@ -347,7 +362,7 @@ def run_gpu(args):
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": ach / hbm_peak, "traffic": None, "kernel": dom,
+                         "frac": ach / hbm_peak, "traffic": traffic, "kernel": dom,
                          "peak_kind": peak_kind,
                          "bytes_per_launch": per[dom]["bytes"], "ms_per_launch": per[dom]["ms"],
                          # the r = 128 working set stays in L2: the same bytes against the
@@ -669,6 +684,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-optimize", action="store_true")
+    ap.add_argument("--no-loop", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-loop-seconds", type=float, default=15.0)
     ap.add_argument("--serve-slots", type=int, default=8)
