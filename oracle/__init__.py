@@ -64,7 +64,11 @@ def _load():
                                                  dp, dp, dp]
             lib.oracle_dpsr_backward_terms.argtypes = [ctypes.c_int, ctypes.c_double, i64, dp, dp,
                                                        dp, dp, dp, dp]
-            for f in ("oracle_dpsr_backward_terms", "oracle_fft3", "oracle_splat", "oracle_gather", "oracle_dpsr_forward",
+            lib.oracle_dpsr_forward_box.argtypes = [ctypes.c_int, ctypes.c_double, i64, dp, dp, dp,
+                                                    dp, dp, dp]
+            lib.oracle_dpsr_backward_box.argtypes = [ctypes.c_int, ctypes.c_double, i64, dp, dp, dp,
+                                                     dp, dp, dp]
+            for f in ("oracle_dpsr_forward_box", "oracle_dpsr_backward_box", "oracle_dpsr_backward_terms", "oracle_fft3", "oracle_splat", "oracle_gather", "oracle_dpsr_forward",
                       "oracle_dpsr_backward", "oracle_threads"):
                 getattr(lib, f).restype = ctypes.c_int
             lib.oracle_threads.argtypes = []
@@ -130,30 +134,43 @@ def gather(grid, points) -> np.ndarray:
     return out
 
 
-def forward(r: int, sigma: float, points, normals, full: bool = False):
+def forward(r: int, sigma: float, points, normals, full: bool = False, box=None):
     """DPSR forward (Eq. 3, Eq. 4). Returns chi (r^3), or with full=True the
-    tuple (chi, chi_prime, mu, s)."""
+    tuple (chi, chi_prime, mu, s). box: side lengths (L0, L1, L2) of the
+    periodic domain (default the unit cube); points in box coordinates."""
     pts = _f64(points, (-1, 3))
     nrm = _f64(normals, (-1, 3))
     chi = np.zeros((r, r, r), np.float64)
     chip = np.zeros((r, r, r), np.float64) if full else None
     mus = np.zeros(2, np.float64)
-    _check(_load().oracle_dpsr_forward(r, float(sigma), pts.shape[0], _p(pts), _p(nrm), _p(chi),
-                                       _p(chip), _p(mus)), "oracle_dpsr_forward")
+    if box is None:
+        _check(_load().oracle_dpsr_forward(r, float(sigma), pts.shape[0], _p(pts), _p(nrm), _p(chi),
+                                           _p(chip), _p(mus)), "oracle_dpsr_forward")
+    else:
+        b = _f64(box, (3,))
+        _check(_load().oracle_dpsr_forward_box(r, float(sigma), pts.shape[0], _p(pts), _p(nrm), _p(b),
+                                               _p(chi), _p(chip), _p(mus)), "oracle_dpsr_forward_box")
     if full:
         return chi, chip, float(mus[0]), float(mus[1])
     return chi
 
 
-def backward(r: int, sigma: float, points, normals, dchi, mean_term: bool = False):
+def backward(r: int, sigma: float, points, normals, dchi, mean_term: bool = False, box=None):
     """DPSR backward: (dL/dpoints, dL/dnormals), each N x 3. With
     mean_term=True also the part of dL/dpoints that flows through the mean of
-    Eq. 4, as a third array."""
+    Eq. 4, as a third array. box: as for forward (not with mean_term)."""
     pts = _f64(points, (-1, 3))
     nrm = _f64(normals, (-1, 3))
     g = _f64(dchi, (r, r, r))
     dp = np.zeros_like(pts)
     dn = np.zeros_like(nrm)
+    if box is not None:
+        if mean_term:
+            raise ValueError("mean_term is for the unit cube")
+        b = _f64(box, (3,))
+        _check(_load().oracle_dpsr_backward_box(r, float(sigma), pts.shape[0], _p(pts), _p(nrm), _p(b),
+                                                _p(g), _p(dp), _p(dn)), "oracle_dpsr_backward_box")
+        return dp, dn
     if mean_term:
         dm = np.zeros_like(pts)
         _check(_load().oracle_dpsr_backward_terms(r, float(sigma), pts.shape[0], _p(pts), _p(nrm),

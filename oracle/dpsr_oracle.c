@@ -39,6 +39,9 @@
  *   R11 when c*r is an integer the floor cell is used; the weight derivative
  *      is the one-sided (right) derivative of that cell.
  *   R12 the backward pass differentiates through the mean and the scale.
+ *   R13 a box of side lengths L (voxel size L_d / r, Eq. A1's anisotropic
+ *      s): coordinates enter as c_d / L_d, u_d = f_d / L_d, the Gaussian's
+ *      sigma stays in grid units along every axis, dL/dc_d = dL/dx_d / L_d.
  *
  * Conventions: points and normals are N x 3 row-major; grids are r^3 in C
  * order g[ix][iy][iz] (iz fastest), axis 0 is the x coordinate. The forward
@@ -257,20 +260,28 @@ int oracle_gather(int r, int64_t N, const double *pts, const double *grid, doubl
 /* Spectral solve (Eq. 3 / Eq. A5-A7).                                       */
 /* H_a(k) = g(k) * i u_a / (-2 pi |u|^2), g(k) = exp(-2 sigma^2 |u|^2 / r^2), */
 /* with the DC term zero (R5) and the a-th term zero at k_a = r/2 (R6).      */
+/* In a box of side lengths L (R13: voxel size L_d / r along axis d, Eq. A1  */
+/* with an anisotropic s), u_d = f_d / L_d cycles per unit length for the    */
+/* integer frequency f_d, and the Gaussian keeps sigma in grid units along   */
+/* every axis: g = exp(-2 sigma^2 sum_d f_d^2 / r^2). The unit cube (L = 1)  */
+/* gives the formula above.                                                  */
 /* ------------------------------------------------------------------------ */
 static double freq(int k, int r) { return k < r / 2 ? (double)k : (double)(k - r); }
 
-static cplx spectral_H(int a, const int k[3], int r, double sigma)
+static const double kUnitBox[3] = {1.0, 1.0, 1.0};
+
+static cplx spectral_H(int a, const int k[3], int r, double sigma, const double *box)
 {
     if (k[0] == 0 && k[1] == 0 && k[2] == 0) return 0.0;
     if (k[a] == r / 2) return 0.0;
-    double u2 = 0.0;
+    double f2 = 0.0, u2 = 0.0;
     for (int d = 0; d < 3; d++) {
-        double u = k[d] == r / 2 ? (double)(r / 2) : freq(k[d], r);
-        u2 += u * u;
+        double f = k[d] == r / 2 ? (double)(r / 2) : freq(k[d], r);
+        f2 += f * f;
+        u2 += (f / box[d]) * (f / box[d]);
     }
-    double g = exp(-2.0 * sigma * sigma * u2 / ((double)r * (double)r));
-    return g * (I * freq(k[a], r)) / (-2.0 * kPi * u2);
+    double g = exp(-2.0 * sigma * sigma * f2 / ((double)r * (double)r));
+    return g * (I * (freq(k[a], r) / box[a])) / (-2.0 * kPi * u2);
 }
 
 /* The state the backward pass needs from the forward pass. */
@@ -289,8 +300,9 @@ static void free_state(fwd_state *S)
     free(S->chip);
 }
 
+/* pts are unit-cube coordinates (c_d / L_d); box holds the lengths L. */
 static int forward_core(int r, double sigma, int64_t N, const double *pts,
-                        const double *nrm, fwd_state *S)
+                        const double *nrm, const double *box, fwd_state *S)
 {
     const int64_t n = (int64_t)r * r * r;
     memset(S, 0, sizeof(*S));
@@ -320,7 +332,7 @@ static int forward_core(int r, double sigma, int64_t N, const double *pts,
     for (int64_t j = 0; j < n; j++) {
         int k[3] = {(int)(j / ((int64_t)r * r)), (int)((j / r) % r), (int)(j % r)};
         cplx acc = 0.0;
-        for (int a = 0; a < 3; a++) acc += spectral_H(a, k, r, sigma) * S->vhat[a][j];
+        for (int a = 0; a < 3; a++) acc += spectral_H(a, k, r, sigma, box) * S->vhat[a][j];
         chihat[j] = acc;
     }
     /* chi' = Re IFFT(chi~) (Eq. A8, reading R6). */
@@ -355,14 +367,34 @@ out:
  * chi (r^3, required), chi_prime (r^3, optional), mu_s (2 doubles: mu, s;
  * optional).
  */
-int oracle_dpsr_forward(int r, double sigma, int64_t N, const double *pts,
-                        const double *nrm, double *chi, double *chi_prime,
-                        double *mu_s)
+/* Coordinates in a box of side lengths L as unit-cube coordinates c_d / L_d
+ * (reading R13; NULL or the unit box: a copy is not needed). */
+static double *to_unit(int64_t N, const double *pts, const double *box)
 {
-    if (!is_pow2(r) || N < 1 || !pts || !nrm || !chi || !(sigma >= 0.0))
+    double *u = malloc(sizeof(double) * (size_t)(3 * (N > 0 ? N : 1)));
+    if (!u) return NULL;
+    for (int64_t i = 0; i < N; i++)
+        for (int d = 0; d < 3; d++) u[3 * i + d] = pts[3 * i + d] / box[d];
+    return u;
+}
+
+static int valid_box(const double *box)
+{
+    for (int d = 0; d < 3; d++)
+        if (!(box[d] > 0.0) || !isfinite(box[d])) return 0;
+    return 1;
+}
+
+static int forward_box(int r, double sigma, int64_t N, const double *pts, const double *nrm,
+                       const double *box, double *chi, double *chi_prime, double *mu_s)
+{
+    if (!is_pow2(r) || N < 1 || !pts || !nrm || !chi || !(sigma >= 0.0) || !valid_box(box))
         return ORACLE_EINVAL;
+    double *upts = to_unit(N, pts, box);
+    if (!upts) return ORACLE_ENOMEM;
     fwd_state S;
-    int e = forward_core(r, sigma, N, pts, nrm, &S);
+    int e = forward_core(r, sigma, N, upts, nrm, box, &S);
+    free(upts);
     if (e) return e;
     const int64_t n = (int64_t)r * r * r;
     const double alpha = kM / fabs(S.s);
@@ -374,6 +406,23 @@ int oracle_dpsr_forward(int r, double sigma, int64_t N, const double *pts,
     }
     free_state(&S);
     return ORACLE_OK;
+}
+
+int oracle_dpsr_forward(int r, double sigma, int64_t N, const double *pts,
+                        const double *nrm, double *chi, double *chi_prime,
+                        double *mu_s)
+{
+    return forward_box(r, sigma, N, pts, nrm, kUnitBox, chi, chi_prime, mu_s);
+}
+
+/* The same in a periodic box [0, L_0) x [0, L_1) x [0, L_2) (reading R13):
+ * pts in box coordinates, the grid's voxel size L_d / r along axis d. */
+int oracle_dpsr_forward_box(int r, double sigma, int64_t N, const double *pts,
+                            const double *nrm, const double *box, double *chi,
+                            double *chi_prime, double *mu_s)
+{
+    if (!box) return ORACLE_EINVAL;
+    return forward_box(r, sigma, N, pts, nrm, box, chi, chi_prime, mu_s);
 }
 
 /*
@@ -389,15 +438,17 @@ int oracle_dpsr_forward(int r, double sigma, int64_t N, const double *pts,
  *   dpoints_i = sum_a n_ia d/dc (sum_j w_ij V_bar_a[j])
  *               + (mu_bar / N) d/dc (sum_j w_ij chi'_j)
  */
+/* pts in unit-cube coordinates; dpts are derivatives with respect to them
+ * (backward_box turns them into derivatives in box coordinates). */
 static int backward_impl(int r, double sigma, int64_t N, const double *pts,
-                         const double *nrm, const double *dchi, double *dpts,
-                         double *dnrm, double *dpts_mean)
+                         const double *nrm, const double *box, const double *dchi,
+                         double *dpts, double *dnrm, double *dpts_mean)
 {
     if (!is_pow2(r) || N < 1 || !pts || !nrm || !dchi || !dpts || !dnrm ||
         !(sigma >= 0.0))
         return ORACLE_EINVAL;
     fwd_state S;
-    int e = forward_core(r, sigma, N, pts, nrm, &S);
+    int e = forward_core(r, sigma, N, pts, nrm, box, &S);
     if (e) return e;
     const int64_t n = (int64_t)r * r * r;
     const double alpha = kM / fabs(S.s);
@@ -428,7 +479,7 @@ static int backward_impl(int r, double sigma, int64_t N, const double *pts,
 #pragma omp parallel for schedule(static)
         for (int64_t j = 0; j < n; j++) {
             int k[3] = {(int)(j / ((int64_t)r * r)), (int)((j / r) % r), (int)(j % r)};
-            tmp[j] = conj(spectral_H(a, k, r, sigma)) * Ghat[j];
+            tmp[j] = conj(spectral_H(a, k, r, sigma, box)) * Ghat[j];
         }
         e = fft3(tmp, r, 1);
         if (e) goto out;
@@ -463,11 +514,38 @@ out:
     return e;
 }
 
+/* The backward pass in a box (reading R13): with x_d = c_d / L_d the unit
+ * coordinates the layer works in, dL/dc_d = (1 / L_d) dL/dx_d. */
+static int backward_box(int r, double sigma, int64_t N, const double *pts, const double *nrm,
+                        const double *box, const double *dchi, double *dpts, double *dnrm,
+                        double *dpts_mean)
+{
+    if (!box || !valid_box(box) || N < 1 || !pts) return ORACLE_EINVAL;
+    double *upts = to_unit(N, pts, box);
+    if (!upts) return ORACLE_ENOMEM;
+    int e = backward_impl(r, sigma, N, upts, nrm, box, dchi, dpts, dnrm, dpts_mean);
+    free(upts);
+    if (e) return e;
+    for (int64_t i = 0; i < N; i++)
+        for (int d = 0; d < 3; d++) {
+            dpts[3 * i + d] /= box[d];
+            if (dpts_mean) dpts_mean[3 * i + d] /= box[d];
+        }
+    return ORACLE_OK;
+}
+
 int oracle_dpsr_backward(int r, double sigma, int64_t N, const double *pts,
                          const double *nrm, const double *dchi, double *dpts,
                          double *dnrm)
 {
-    return backward_impl(r, sigma, N, pts, nrm, dchi, dpts, dnrm, NULL);
+    return backward_box(r, sigma, N, pts, nrm, kUnitBox, dchi, dpts, dnrm, NULL);
+}
+
+int oracle_dpsr_backward_box(int r, double sigma, int64_t N, const double *pts,
+                             const double *nrm, const double *box, const double *dchi,
+                             double *dpts, double *dnrm)
+{
+    return backward_box(r, sigma, N, pts, nrm, box, dchi, dpts, dnrm, NULL);
 }
 
 /* The same backward pass, also returning the part of dL/dpoints that flows
@@ -480,5 +558,5 @@ int oracle_dpsr_backward_terms(int r, double sigma, int64_t N, const double *pts
                                double *dnrm, double *dpts_mean)
 {
     if (!dpts_mean) return ORACLE_EINVAL;
-    return backward_impl(r, sigma, N, pts, nrm, dchi, dpts, dnrm, dpts_mean);
+    return backward_box(r, sigma, N, pts, nrm, kUnitBox, dchi, dpts, dnrm, dpts_mean);
 }

@@ -38,16 +38,22 @@ def freqs_plus_nyquist(r):
     return np.where(k <= r // 2, k, k - r).astype(np.float64)
 
 
-def forward(points, normals, r, sigma, m=0.5):
-    """chi, chi', mu, s by direct sums (Eq. 3, Eq. 4)."""
-    W = dense_weights(points, r)                                 # N x n
+def forward(points, normals, r, sigma, m=0.5, box=(1.0, 1.0, 1.0)):
+    """chi, chi', mu, s by direct sums (Eq. 3, Eq. 4). box: side lengths of
+    the periodic domain; the grid vertex j sits at j_d L_d / r, the tent
+    weight of Eq. A1 has half-width L_d / r along axis d, frequencies are
+    f_d / L_d cycles per unit length and the Gaussian's sigma is in grid
+    units (f_d / r)."""
+    box = np.asarray(box, np.float64)
+    W = dense_weights(np.asarray(points, np.float64).reshape(-1, 3) / box, r)   # tent in grid units
     V = W.T @ np.asarray(normals, np.float64).reshape(-1, 3)     # n x 3 (Eq. A2)
     E = dft_matrix(r, -1)
     Vh = E @ V                                                   # n x 3 (Eq. A3)
     u1 = freqs_plus_nyquist(r)
-    U = np.stack(np.meshgrid(u1, u1, u1, indexing="ij"), -1).reshape(-1, 3)
+    F = np.stack(np.meshgrid(u1, u1, u1, indexing="ij"), -1).reshape(-1, 3)
+    U = F / box
     u2 = (U ** 2).sum(1)
-    g = np.exp(-2.0 * sigma ** 2 * u2 / r ** 2)
+    g = np.exp(-2.0 * sigma ** 2 * (F ** 2).sum(1) / r ** 2)
     with np.errstate(divide="ignore", invalid="ignore"):
         chih = g * (1j * (U * Vh).sum(1)) / (-2.0 * np.pi * u2)
     chih[0] = 0.0

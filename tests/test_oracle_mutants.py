@@ -13,17 +13,21 @@ SRC = os.path.join(os.path.dirname(HERE), "oracle", "dpsr_oracle.c")
 # (name, exact text in the oracle, replacement)
 MUTANTS = [
     ("dft_sign", "double ang = sign * 2.0 * kPi", "double ang = -sign * 2.0 * kPi"),
-    ("no_gaussian", "double g = exp(-2.0 * sigma * sigma * u2", "double g = 1.0 + 0.0 * exp(-2.0 * sigma * sigma * u2"),
-    ("gaussian_no_r2", "u2 / ((double)r * (double)r))", "u2 / ((double)r))"),
+    ("no_gaussian", "double g = exp(-2.0 * sigma * sigma * f2", "double g = 1.0 + 0.0 * exp(-2.0 * sigma * sigma * f2"),
+    ("gaussian_no_r2", "f2 / ((double)r * (double)r))", "f2 / ((double)r))"),
     ("laplacian_factor", "(-2.0 * kPi * u2)", "(-kPi * u2)"),
-    ("transposed_u", "(I * freq(k[a], r))", "(I * freq(k[(a + 1) % 3], r))"),
+    ("transposed_u", "(I * (freq(k[a], r) / box[a]))", "(I * (freq(k[(a + 1) % 3], r) / box[a]))"),
     ("nyquist_norm", "k[d] == r / 2 ? (double)(r / 2)", "k[d] == r / 2 ? 0.0"),
     ("unshifted_scale", "S->s = S->chip[0] - S->mu;", "S->s = S->chip[0];"),
     ("weights_swapped", "f[d] = del[d] ? t[d] : 1.0 - t[d];", "f[d] = del[d] ? 1.0 - t[d] : t[d];"),
     ("bwd_drop_W", "Ghat[j] = alpha * dchi[j] + (mu_bar / (double)N) * W[j];", "Ghat[j] = alpha * dchi[j];"),
     ("bwd_dw_sign", "df[d] = del[d] ? (double)r : -(double)r;", "df[d] = del[d] ? -(double)r : (double)r;"),
-    ("bwd_no_conj", "tmp[j] = conj(spectral_H(a, k, r, sigma)) * Ghat[j];", "tmp[j] = spectral_H(a, k, r, sigma) * Ghat[j];"),
+    ("bwd_no_conj", "tmp[j] = conj(spectral_H(a, k, r, sigma, box)) * Ghat[j];", "tmp[j] = spectral_H(a, k, r, sigma, box) * Ghat[j];"),
     ("bwd_s_bar_sign", "const double s_bar = -kM * sgn", "const double s_bar = kM * sgn"),
+    ("box_u_not_scaled", "u2 += (f / box[d]) * (f / box[d]);", "u2 += f * f;"),
+    ("box_grad_not_scaled", "dpts[3 * i + d] /= box[d];", "dpts[3 * i + d] /= 1.0;"),
+    ("box_gaussian_in_u", "sigma * sigma * f2 /", "sigma * sigma * u2 /"),
+    ("box_coords_axis0", "u[3 * i + d] = pts[3 * i + d] / box[d];", "u[3 * i + d] = pts[3 * i + d] / box[0];"),
     ("bwd_mean_term_is_rest", "if (dpts_mean) dpts_mean[3 * i + d] = gm[d];",
      "if (dpts_mean) dpts_mean[3 * i + d] = gc[d];"),
     ("bwd_mean_term_no_mu_bar", "gm[d] += (mu_bar / (double)N) * st.dw[v][d]",

@@ -276,3 +276,129 @@ def test_backward_mean_term_finite_differences(oracle, r, sigma, N):
             assert abs(fd - dm[i, d]) <= 1e-7 * scale, (i, d, fd, dm[i, d])
             fd = (L_rest(pp) - L_rest(pm)) / (2 * h)
             assert abs(fd - (dp[i, d] - dm[i, d])) <= 1e-7 * scale, (i, d, fd, dp[i, d] - dm[i, d])
+
+
+# --------------------------------------------------------------------------
+# A periodic box of side lengths L (voxel size L_d / r along axis d, Eq. A1
+# with an anisotropic s). Reading: coordinates in the box, frequencies u_d =
+# f_d / L_d cycles per unit length, sigma in grid units along every axis.
+# --------------------------------------------------------------------------
+BOX = np.array([1.0, 0.75, 1.5])
+
+
+def _box_lattice(r, box):
+    return _lattice(r) * box
+
+
+@pytest.mark.parametrize("m,along", [((1, 2, 0), "k"), ((0, 1, 1), "k"), ((2, 0, 3), "k"),
+                                     ((1, 1, 2), "perp"), ((3, 1, 0), "perp")])
+def test_box_plane_wave_closed_form(oracle, m, along):
+    """V = nhat cos(2 pi (k.x - phi)) on the vertices of the box lattice with
+    k_d = m_d / L_d. Its divergence is -2 pi (k.nhat) sin(...), so the
+    periodic solution of Eq. 1 smoothed by Eq. 3 is
+    chi' = g (k.nhat) sin(2 pi (k.x - phi)) / (2 pi |k|^2), with
+    g = exp(-2 sigma^2 |m|^2 / r^2). nhat = k/|k| gives the amplitude
+    g / (2 pi |k|); nhat orthogonal to k gives chi' = 0 although nhat is
+    not orthogonal to m."""
+    r, sigma, phi = 8, 1.25, 0.15
+    m = np.array(m, float)
+    k = m / BOX
+    if along == "k":
+        nhat = k / np.linalg.norm(k)
+    else:
+        nhat = np.cross(k, [0.3, -0.2, 1.0])
+        nhat /= np.linalg.norm(nhat)
+        assert abs(nhat @ m) > 0.05
+    x = _box_lattice(r, BOX)
+    theta = 2 * np.pi * (x @ k - phi)
+    nrm = nhat[None, :] * np.cos(theta)[:, None]
+    g = math.exp(-2 * sigma ** 2 * float(m @ m) / r ** 2)
+    expect = g * float(k @ nhat) * np.sin(theta) / (2 * np.pi * float(k @ k))
+    ref = np.array([1.0, 0, 0])[None, :] * np.cos(2 * np.pi * (x[:, 0] - 0.125))[:, None]
+    _, chip_ref, _, _ = oracle.forward(r, sigma, x, ref, full=True, box=BOX)
+    _, chip, _, _ = oracle.forward(r, sigma, x, nrm + ref, full=True, box=BOX)
+    assert np.max(np.abs(chip.ravel() - chip_ref.ravel() - expect)) <= 1e-13
+    if along == "k":
+        _, cw, mu, s = oracle.forward(r, sigma, x, nrm, full=True, box=BOX)
+        assert np.max(np.abs(cw.ravel() - expect)) <= 1e-13
+        assert math.isclose(s, expect[0] - mu, rel_tol=1e-10, abs_tol=1e-15)
+
+
+@pytest.mark.parametrize("r,sigma,N", [(4, 0.0, 9), (8, 1.5, 20)])
+def test_box_forward_bruteforce(oracle, r, sigma, N):
+    pts, nrm = _cloud(900 + r + N, N, -0.2, 1.2)
+    pts = pts * BOX
+    chi, chip, mu, s = oracle.forward(r, sigma, pts, nrm, full=True, box=BOX)
+    bchi, bchip, bmu, bs = bf.forward(pts, nrm, r, sigma, box=BOX)
+    sc = np.max(np.abs(bchip))
+    assert np.max(np.abs(chip - bchip)) <= 1e-12 * sc
+    assert abs(mu - bmu) <= 1e-12 * sc and abs(s - bs) <= 1e-12 * sc
+    assert np.max(np.abs(chi - bchi)) <= 1e-11
+
+
+def test_box_cubic_scaling(oracle):
+    """A cube of side L is the unit cube stretched by L: chi' and s grow by L
+    (u = f / L), chi is unchanged, dL/dpoints shrinks by 1/L and dL/dnormals
+    is unchanged."""
+    r, sigma, L = 16, 2.0, 2.5
+    rng = synth.Rng(41)
+    pts = 0.2 + 0.6 * rng.uniform(60, 3)
+    nrm = rng.normal(60, 3)
+    G = rng.normal(r, r, r)
+    chi, chip, mu, s = oracle.forward(r, sigma, pts, nrm, full=True)
+    chiL, chipL, muL, sL = oracle.forward(r, sigma, L * pts, nrm, full=True, box=(L, L, L))
+    assert np.max(np.abs(chiL - chi)) <= 1e-12
+    assert np.max(np.abs(chipL - L * chip)) <= 1e-12 * L * np.max(np.abs(chip))
+    assert math.isclose(sL, L * s, rel_tol=1e-10)
+    dp, dn = oracle.backward(r, sigma, pts, nrm, G)
+    dpL, dnL = oracle.backward(r, sigma, L * pts, nrm, G, box=(L, L, L))
+    assert np.max(np.abs(dpL - dp / L)) <= 1e-10 * np.max(np.abs(dp))
+    assert np.max(np.abs(dnL - dn)) <= 1e-10 * np.max(np.abs(dn))
+
+
+def test_box_axis_permutation_and_wrap(oracle):
+    """Permuting the axes of points, normals and box permutes the axes of
+    chi; shifting a point by a whole box length along an axis changes
+    nothing (the domain is periodic with period L_d)."""
+    r, sigma = 16, 1.5
+    rng = synth.Rng(43)
+    pts = (0.2 + 0.6 * rng.uniform(80, 3)) * BOX
+    nrm = rng.normal(80, 3)
+    chi = oracle.forward(r, sigma, pts, nrm, box=BOX)
+    perm = [2, 0, 1]
+    chp = oracle.forward(r, sigma, pts[:, perm], nrm[:, perm], box=BOX[perm])
+    assert np.max(np.abs(chp - np.transpose(chi, perm))) <= 1e-12
+    sh = pts.copy()
+    sh[::3] += BOX * np.array([1, -2, 3])
+    assert np.max(np.abs(oracle.forward(r, sigma, sh, nrm, box=BOX) - chi)) <= 1e-12
+    for bad in ([1.0, 0.0, 1.0], [1.0, -1.0, 1.0], [1.0, np.inf, 1.0], [np.nan, 1.0, 1.0]):
+        with pytest.raises(oracle.OracleError) as e:
+            oracle.forward(r, sigma, pts, nrm, box=bad)
+        assert e.value.code == oracle.ORACLE_EINVAL
+
+
+def test_box_backward_finite_differences(oracle):
+    """Central differences of L = <dchi, chi> in box coordinates."""
+    r, sigma, N = 8, 1.0, 20
+    rng = synth.Rng(47)
+    u = 0.15 + 0.7 * rng.uniform(N, 3)
+    f = u * r - np.floor(u * r)
+    u = (np.floor(u * r) + np.clip(f, 0.01, 0.99)) / r      # off the cell faces
+    pts = u * BOX
+    nrm = rng.normal(N, 3)
+    G = rng.normal(r, r, r)
+    dp, dn = oracle.backward(r, sigma, pts, nrm, G, box=BOX)
+    L = lambda p, n: float(np.sum(G * oracle.forward(r, sigma, p, n, box=BOX)))
+    h = 1e-6
+    scale_p, scale_n = np.max(np.abs(dp)), np.max(np.abs(dn))
+    for (i, d) in [(0, 0), (3, 1), (7, 2), (11, 1), (19, 2)]:
+        pp, pm = pts.copy(), pts.copy()
+        pp[i, d] += h
+        pm[i, d] -= h
+        fd = (L(pp, nrm) - L(pm, nrm)) / (2 * h)
+        assert abs(fd - dp[i, d]) <= 1e-6 * scale_p, (i, d, fd, dp[i, d])
+        npl, nmi = nrm.copy(), nrm.copy()
+        npl[i, d] += h
+        nmi[i, d] -= h
+        fd = (L(pts, npl) - L(pts, nmi)) / (2 * h)
+        assert abs(fd - dn[i, d]) <= 1e-6 * scale_n, (i, d, fd, dn[i, d])
