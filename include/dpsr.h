@@ -72,6 +72,19 @@ enum {
  * stays bound to that device. On success *out receives the plan. */
 DPSR_API int dpsr_plan_create(int r, float sigma, dpsr_plan *out);
 
+/* The same over a periodic box [0, L0) x [0, L1) x [0, L2) instead of the
+ * unit cube: the r^3 grid's voxel size is L_d / r along axis d (Eq. A1 with
+ * a per-axis voxel size s, Sec. 3.1). box: 3 side lengths, each finite and
+ * > 0, read during the call (NULL: the unit cube). Points are then given in
+ * box coordinates (wrapped with period L_d); the spectral operator of Eq. 3
+ * uses the physical frequency u_d = f_d / L_d of the integer frequency f_d,
+ * and the Gaussian keeps sigma in grid units on every axis,
+ * g = exp(-2 sigma^2 sum_d f_d^2 / r^2). dL/dpoints come back in box
+ * coordinates. The normalisation of Eq. 4 is unchanged. Errors: DPSR_EINVAL
+ * for a bad box, else as dpsr_plan_create. The batched, serving, static and
+ * mesh entry points work on the unit cube. */
+DPSR_API int dpsr_plan_create_box(int r, float sigma, const float *box, dpsr_plan *out);
+
 /* Free the plan and its workspace (synchronises its stream first). */
 DPSR_API int dpsr_plan_destroy(dpsr_plan plan);
 

@@ -36,6 +36,7 @@ using dpsr::Solve;
 struct dpsr_plan_s {
   int r = 0;
   float sigma = 0.f;
+  float box[3] = {1.f, 1.f, 1.f};  // side lengths of the periodic domain
   int device = 0;
   cudaStream_t stream = nullptr;
   int C[4] = {1, 1, 1, 1};
@@ -107,7 +108,7 @@ int part_count(int r) {
 
 size_t grid_ws_bytes(int r) {
   size_t b = dpsr::kNSpec * align256(spec_bytes(r));
-  b += align256(sizeof(float2) * r) + 3 * align256(sizeof(float) * r);
+  b += align256(sizeof(float2) * r) + align256(sizeof(float) * 7 * r);
   b += align256(sizeof(dpsr::Scalars)) + align256(sizeof(unsigned));
   b += align256(sizeof(float4) * part_count(r));
   b += align256(sizeof(int) * dpsr::bins_ints(r));
@@ -406,8 +407,17 @@ size_t dpsr_plan_workspace_bytes(int r, int64_t n_max, int with_bwd) {
   return grid_ws_bytes(r) + pts_ws_bytes(n_max > 0 ? n_max : 1);
 }
 
-int dpsr_plan_create(int r, float sigma, dpsr_plan* out) {
-  if (!out || !valid_r(r) || !(sigma >= 0.f) || !isfinite(sigma)) return DPSR_EINVAL;
+static bool valid_box(const float* box) {
+  if (!box) return true;
+  for (int d = 0; d < 3; ++d)
+    if (!(box[d] > 0.f) || !isfinite(box[d])) return false;
+  return true;
+}
+
+int dpsr_plan_create(int r, float sigma, dpsr_plan* out) { return dpsr_plan_create_box(r, sigma, nullptr, out); }
+
+int dpsr_plan_create_box(int r, float sigma, const float* box, dpsr_plan* out) {
+  if (!out || !valid_r(r) || !(sigma >= 0.f) || !isfinite(sigma) || !valid_box(box)) return DPSR_EINVAL;
   *out = nullptr;
   dpsr_plan p = new (std::nothrow) dpsr_plan_s();
   if (!p) return DPSR_ENOMEM;
@@ -426,6 +436,10 @@ int dpsr_plan_create(int r, float sigma, dpsr_plan* out) {
   }
   Solve& s = p->s;
   s.r = r;
+  for (int d = 0; d < 3; ++d) {
+    p->box[d] = box ? box[d] : 1.f;
+    s.inv_box[d] = box ? (float)(1.0 / (double)box[d]) : 1.f;
+  }
   char* q = (char*)p->grid_ws;
   for (int k = 0; k < dpsr::kNSpec; ++k) {
     s.spec[k] = (float2*)q;
@@ -433,12 +447,8 @@ int dpsr_plan_create(int r, float sigma, dpsr_plan* out) {
   }
   float2* tw = (float2*)q;
   q += align256(sizeof(float2) * r);
-  float* g1 = (float*)q;
-  q += align256(sizeof(float) * r);
-  float* u2 = (float*)q;
-  q += align256(sizeof(float) * r);
-  float* iu = (float*)q;
-  q += align256(sizeof(float) * r);
+  float* tab = (float*)q;
+  q += align256(sizeof(float) * 7 * r);
   s.sc = (dpsr::Scalars*)q;
   q += align256(sizeof(dpsr::Scalars));
   s.status = (unsigned*)q;
@@ -447,39 +457,25 @@ int dpsr_plan_create(int r, float sigma, dpsr_plan* out) {
   q += align256(sizeof(float4) * part_count(r));
   s.bins = (int*)q;
   s.tw = tw;
-  s.g1 = g1;
-  s.u2 = u2;
-  s.iu = iu;
-  // Tables in FP64, rounded to FP32: twiddles exp(-2 pi i m / r); per-axis
-  // frequency u (integer cycles per unit length, |u| = r/2 at Nyquist), the
-  // per-axis factor of the Gaussian of Eq. 3, and the derivative factor u
-  // (zero at Nyquist).
+  s.g1 = tab;
+  s.u2 = tab + r;
+  s.iu = tab + 4 * r;
   float2* htw = (float2*)malloc(sizeof(float2) * r);
-  float* hg = (float*)malloc(sizeof(float) * 3 * r);
+  float* htab = (float*)malloc(sizeof(float) * 7 * r);
   int rc = DPSR_OK;
-  if (!htw || !hg) {
+  if (!htw || !htab) {
     rc = DPSR_ENOMEM;
   } else {
-    const double pi = 3.14159265358979323846264338327950288;
-    for (int m = 0; m < r; ++m) {
-      const double ang = -2.0 * pi * (double)m / (double)r;
-      htw[m] = make_float2((float)cos(ang), (float)sin(ang));
-      const double u = m < r / 2 ? (double)m : (m == r / 2 ? (double)(r / 2) : (double)(m - r));
-      hg[m] = (float)exp(-2.0 * (double)sigma * (double)sigma * u * u / ((double)r * r));
-      hg[r + m] = (float)(u * u);
-      hg[2 * r + m] = m == r / 2 ? 0.f : (float)u;
-    }
+    dpsr::spectral_tables(r, (double)sigma, box, htw, htab);
     if (cudaMemcpy(tw, htw, sizeof(float2) * r, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(g1, hg, sizeof(float) * r, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(u2, hg + r, sizeof(float) * r, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(iu, hg + 2 * r, sizeof(float) * r, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(tab, htab, sizeof(float) * 7 * r, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(s.bins, 0, sizeof(int) * dpsr::bins_ints(r)) != cudaSuccess ||
         cudaMemset(s.status, 0, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(s.sc, 0, sizeof(dpsr::Scalars)) != cudaSuccess)
       rc = DPSR_ECUDA;
   }
   free(htw);
-  free(hg);
+  free(htab);
   if (rc == DPSR_OK) rc = dpsr::make_tensor_maps(s, r);
   if (rc == DPSR_OK && cudaHostAlloc((void**)&p->status_host, sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess) {
     cudaGetLastError();

@@ -412,6 +412,10 @@ struct Solve {
   int r;
   int N;
   double inv_N;  // 1 / N (set with N by set_count)
+  // 1 / L_d for a periodic box of side lengths L (voxel size L_d / r along
+  // axis d, Eq. A1 with a per-axis s): the binning turns box coordinates
+  // into unit-cube ones and the combine turns unit-cube gradients back.
+  float inv_box[3] = {1.f, 1.f, 1.f};
   // per call (caller-owned)
   const float* points;
   const float* normals;
@@ -432,10 +436,30 @@ struct Solve {
   Scalars* sc;
   unsigned* status;
   const float2* tw;  // r
-  const float* g1;   // r: exp(-2 sigma^2 u^2 / r^2)
-  const float* u2;   // r: u^2 (|u| = r/2 at Nyquist)
-  const float* iu;   // r: u, 0 at Nyquist (factor of the spectral derivative)
+  // Spectral tables, indexed by the integer frequency index k of an axis
+  // (f = k below r/2, k - r above, |f| = r/2 at Nyquist):
+  const float* g1;   // r: exp(-2 sigma^2 f^2 / r^2), the same on every axis
+  const float* u2;   // 3 x r, axis-major: (f / L_d)^2
+  const float* iu;   // 3 x r, axis-major: f / L_d, 0 at Nyquist (spectral derivative)
 };
+
+// Host side: the spectral tables of one plan, computed in FP64 and rounded
+// to FP32. tw[r]: twiddles exp(-2 pi i m / r); tab[7r]: g1 (r), u2 (3r) and
+// iu (3r) as laid out in Solve. box: side lengths L_d (nullptr: unit cube).
+inline void spectral_tables(int r, double sigma, const float* box, float2* tw, float* tab) {
+  const double pi = 3.14159265358979323846264338327950288;
+  for (int m = 0; m < r; ++m) {
+    const double ang = -2.0 * pi * (double)m / (double)r;
+    tw[m] = make_float2((float)cos(ang), (float)sin(ang));
+    const double f = m < r / 2 ? (double)m : (m == r / 2 ? (double)(r / 2) : (double)(m - r));
+    tab[m] = (float)exp(-2.0 * sigma * sigma * f * f / ((double)r * r));
+    for (int d = 0; d < 3; ++d) {
+      const double u = f / (box ? (double)box[d] : 1.0);
+      tab[(1 + d) * r + m] = (float)(u * u);
+      tab[(4 + d) * r + m] = m == r / 2 ? 0.f : (float)u;
+    }
+  }
+}
 
 enum : unsigned { kStBadInput = 1u, kStDegenerate = 2u, kStTimeout = 4u };
 

@@ -47,7 +47,7 @@ constexpr size_t kSpec = al((size_t)kMaxR * kMaxR * dpsr::kpitch(kMaxR) * sizeof
 constexpr size_t kOffSpec = 0;
 constexpr size_t kOffTw = kOffSpec + dpsr::kNSpec * kSpec;
 constexpr size_t kOffTab = kOffTw + al(sizeof(float2) * kMaxR);
-constexpr size_t kOffSc = kOffTab + 3 * al(sizeof(float) * kMaxR);
+constexpr size_t kOffSc = kOffTab + al(sizeof(float) * 7 * kMaxR);
 constexpr size_t kOffStatus = kOffSc + al(sizeof(dpsr::Scalars));
 constexpr size_t kParts = ((kMaxR / 2 + 1 + 15) / 16) * kMaxR > kMaxR * 8
                               ? ((kMaxR / 2 + 1 + 15) / 16) * kMaxR : kMaxR * 8;
@@ -144,18 +144,10 @@ extern "C" DPSR_API int dpsr_forward_static(int r, float sigma, const float* poi
   int rc = scratch_address(dev, &base);
   if (rc != DPSR_OK) return rc;
 
-  // Per-call tables: twiddles, per-axis Gaussian factor, u^2, derivative u.
+  // Per-call tables (unit cube): twiddles, Gaussian factor, u^2, derivative u.
   float2 htw[kMaxR];
-  float htab[3 * kMaxR];
-  const double pi = 3.14159265358979323846264338327950288;
-  for (int m = 0; m < r; ++m) {
-    const double ang = -2.0 * pi * (double)m / (double)r;
-    htw[m] = make_float2((float)cos(ang), (float)sin(ang));
-    const double u = m < r / 2 ? (double)m : (m == r / 2 ? (double)(r / 2) : (double)(m - r));
-    htab[m] = (float)exp(-2.0 * (double)sigma * (double)sigma * u * u / ((double)r * r));
-    htab[r + m] = (float)(u * u);
-    htab[2 * r + m] = m == r / 2 ? 0.f : (float)u;
-  }
+  float htab[7 * kMaxR];
+  dpsr::spectral_tables(r, (double)sigma, nullptr, htw, htab);
   dpsr::Solve s = {};
   s.r = r;
   dpsr::set_count(s, N);
@@ -164,13 +156,11 @@ extern "C" DPSR_API int dpsr_forward_static(int r, float sigma, const float* poi
   s.chi = chi_out;
   for (int k = 0; k < dpsr::kNSpec; ++k) s.spec[k] = (float2*)(base + kOffSpec + k * kSpec);
   float2* tw = (float2*)(base + kOffTw);
-  float* g1 = (float*)(base + kOffTab);
-  float* u2 = (float*)(base + kOffTab + al(sizeof(float) * kMaxR));
-  float* iu = (float*)(base + kOffTab + 2 * al(sizeof(float) * kMaxR));
+  float* tab = (float*)(base + kOffTab);
   s.tw = tw;
-  s.g1 = g1;
-  s.u2 = u2;
-  s.iu = iu;
+  s.g1 = tab;
+  s.u2 = tab + r;
+  s.iu = tab + 4 * r;
   s.sc = (dpsr::Scalars*)(base + kOffSc);
   s.status = (unsigned*)(base + kOffStatus);
   s.part = (float4*)(base + kOffPart);
@@ -181,9 +171,7 @@ extern "C" DPSR_API int dpsr_forward_static(int r, float sigma, const float* poi
   if (dpsr::make_tensor_maps(s, r) != DPSR_OK) return DPSR_ECUDA;
 
   cudaError_t e = cudaMemcpyAsync(tw, htw, sizeof(float2) * r, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(g1, htab, sizeof(float) * r, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(u2, htab + r, sizeof(float) * r, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(iu, htab + 2 * r, sizeof(float) * r, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tab, htab, sizeof(float) * 7 * r, cudaMemcpyHostToDevice, st);
   // the bin counters and the status word must start at zero
   if (e == cudaSuccess) e = cudaMemsetAsync(s.bins, 0, sizeof(int) * dpsr::bins_ints(r), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s.status, 0, sizeof(unsigned), st);

@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(Pen<L>::ZNT, L >= 512 ? 1 : (L >= 256 ? 3 : 4)
   pdl_trigger();
   for (int i = tid; i < L; i += P::ZNT) {
     twt[i] = S.tw[i];
-    iu[i] = S.iu[i];
+    iu[i] = S.iu[2 * L + i];  // z axis
   }
   for (int i = tid; i < RF / 4; i += P::ZNT) smem4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   pdl_wait();
@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(ynt<L>(), L >= 512 ? 1 : (BWD ? 4 : (L >= 256 
   if (tid == 0) yfwd_issue<L, BWD>(S, X, kz0, kind, box, &bar);
   for (int i = tid; i < L; i += NT) {
     twt[i] = S.tw[i];
-    iu[i] = S.iu[i];
+    iu[i] = S.iu[L + i];  // y axis
   }
   __syncthreads();
   yfwd_tile<L, BWD>(S, X, kz0, kind, box, twt, iu, &bar, 0);
@@ -550,7 +550,7 @@ __device__ __forceinline__ bool yinv_tile(const Solve& S, int X, int kz0, int pa
 #pragma unroll
       for (int j = 0; j < P::R1; ++j) v[j] = c2(t + P::T * j);
       fft_r<L, +1, IL>(v, t, c2, twr);
-      const float ez = sz == 0 ? 0.f : -iu[sz];
+      const float ez = sz == 0 ? 0.f : -__ldg(S.iu + 2 * L + sz);  // z axis
 #pragma unroll
       for (int j = 0; j < P::R1; ++j) c2(t + P::T * j) = cmul_iu(v[j], ez);
     }
@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(16 * Shape<L>::T >= 32 ? 16 * Shape<L>::T : 32
   if (tid == 0) yinv_issue<L, NCH>(S, X, kz0, part, box, &bar);
   for (int i = tid; i < L; i += NT) {
     twt[i] = S.tw[i];
-    iu[i] = S.iu[i];
+    iu[i] = S.iu[L + i];  // y axis
   }
   __syncthreads();
   yinv_tile<L, NCH>(S, X, kz0, part, box, twt, iu, &bar, 0);

@@ -319,9 +319,10 @@ __global__ void __launch_bounds__(fwd_threads<L, C>(), 512 / fwd_threads<L, C>()
   __shared__ int list_n;
   pdl_trigger();
   for (int i = tid; i < L; i += F::NT) {
-    iu[i] = S.iu[i];
+    iu[i] = S.iu[L + i];  // y axis; the z axis is read from global memory
     twt[i] = S.tw[i];
   }
+  const float* __restrict__ iuz = S.iu + 2 * L;
   if (tid == 0) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -373,7 +374,7 @@ __global__ void __launch_bounds__(fwd_threads<L, C>(), 512 / fwd_threads<L, C>()
         const int ya = y_lo + 2 * pr;
         auto put = [&](int row, int yy, int s, float2 v) {
           if (!ok) return;
-          if (ch == 2) v = s == 0 ? czero() : cmul_iu(v, iu[s]);
+          if (ch == 2) v = s == 0 ? czero() : cmul_iu(v, __ldg(iuz + s));
           rows[row * H + rsw<H>(yy, s)] = v;
         };
         r2c_pair<L>(
@@ -761,7 +762,7 @@ __global__ void __launch_bounds__(kNT, binv_smem<L, C>() <= 113 * 1024 ? 2 : 1)
   __shared__ int list_n;
   pdl_trigger();
   for (int i = tid; i < L; i += kNT) {
-    iu[i] = S.iu[i];
+    iu[i] = S.iu[L + i];  // y axis; the z axis is read from global memory
     twt[i] = S.tw[i];
   }
   pdl_wait();
@@ -831,7 +832,7 @@ __global__ void __launch_bounds__(kNT, binv_smem<L, C>() <= 113 * 1024 ? 2 : 1)
 #pragma unroll
               for (int j = 0; j < R1; ++j) v[j] = col(buf0, sl, t + T * j);
               fft_r<L, +1>(v, t, [&](int e) -> float2& { return col(buf0, sl, e); }, twr);
-              const float ez = s == 0 ? 0.f : -iu[s];
+              const float ez = s == 0 ? 0.f : -__ldg(S.iu + 2 * L + s);  // z axis
 #pragma unroll
               for (int j = 0; j < R1; ++j) col(buf0, sl, t + T * j) = cmul_iu(v[j], ez);
             }

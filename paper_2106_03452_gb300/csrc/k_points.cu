@@ -36,8 +36,8 @@ __global__ void __launch_bounds__(256) k_bin_count(const __grid_constant__ Solve
   __syncthreads();
   bool bad = false;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < S.N; p += gridDim.x * blockDim.x) {
-    float x = S.points[3 * p], y = S.points[3 * p + 1];
-    const float z = S.points[3 * p + 2];
+    float x = S.points[3 * p] * S.inv_box[0], y = S.points[3 * p + 1] * S.inv_box[1];
+    const float z = S.points[3 * p + 2] * S.inv_box[2];
     const float nx = S.normals[3 * p], ny = S.normals[3 * p + 1], nz = S.normals[3 * p + 2];
     if (!(coord_ok(x, r) && coord_ok(y, r) && coord_ok(z, r) && isfinite(nx) && isfinite(ny) &&
           isfinite(nz))) {
@@ -120,7 +120,9 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Sol
     }
   }
   for (int p = blockIdx.x * NT + tid; p < S.N; p += gridDim.x * NT) {
-    float x = S.points[3 * p], y = S.points[3 * p + 1], z = S.points[3 * p + 2];
+    // unit-cube coordinates from here on (exact for the unit cube)
+    float x = S.points[3 * p] * S.inv_box[0], y = S.points[3 * p + 1] * S.inv_box[1],
+          z = S.points[3 * p + 2] * S.inv_box[2];
     float nx = S.normals[3 * p], ny = S.normals[3 * p + 1], nz = S.normals[3 * p + 2];
     if (!coord_ok(x, r)) x = 0.f;
     if (!coord_ok(y, r)) y = 0.f;
@@ -153,8 +155,8 @@ cudaError_t launch_bin(const Solve& s, const Solve* tab, int count, int nmax, in
   return e;
 }
 
-// dpoints = sum of the two plane sides of the weight-derivative terms
-//           + (mu_bar / (N n)) * gradient of the lookup of y (Eq. 4 adjoint);
+// dpoints = (sum of the two plane sides of the weight-derivative terms
+//            + (mu_bar / (N n)) * gradient of the lookup of y (Eq. 4 adjoint)) / L_d;
 // dnormals = sum of the two plane sides of the gather. Written in the
 // caller's point order.
 __global__ void __launch_bounds__(256) k_combine(const __grid_constant__ Solve s0,
@@ -172,9 +174,10 @@ __global__ void __launch_bounds__(256) k_combine(const __grid_constant__ Solve s
     S.dnormals[3 * orig] = a[0] + b[0];
     S.dnormals[3 * orig + 1] = a[1] + b[1];
     S.dnormals[3 * orig + 2] = a[2] + b[2];
-    S.dpoints[3 * orig] = (a[3] + b[3]) + c_mu * (ga.x + gb.x);
-    S.dpoints[3 * orig + 1] = (a[4] + b[4]) + c_mu * (ga.y + gb.y);
-    S.dpoints[3 * orig + 2] = (a[5] + b[5]) + c_mu * (ga.z + gb.z);
+    // derivatives in unit-cube coordinates, times dx_d / dc_d = 1 / L_d
+    S.dpoints[3 * orig] = ((a[3] + b[3]) + c_mu * (ga.x + gb.x)) * S.inv_box[0];
+    S.dpoints[3 * orig + 1] = ((a[4] + b[4]) + c_mu * (ga.y + gb.y)) * S.inv_box[1];
+    S.dpoints[3 * orig + 2] = ((a[5] + b[5]) + c_mu * (ga.z + gb.z)) * S.inv_box[2];
   }
 }
 

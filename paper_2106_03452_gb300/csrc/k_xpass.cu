@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 512 ? 1 : (L >= 256 ? (BWD ?
   for (int i = tid; i < L; i += P::NT) {
     tw[i] = S.tw[i];
     g1[i] = S.g1[i];
-    u2[i] = S.u2[i];
+    u2[i] = S.u2[i];  // x axis
     iu[i] = S.iu[i];
   }
   __syncthreads();
@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(XGeo<L>::NT, L >= 512 ? 1 : (L >= 256 ? (BWD ?
   // per SM forward (two backward, where three would spill), five below
   using Tw = TwTab<L>;
   Tw twr = make_tw<L, Tw>(tw, t);
-  const float gyz = g1[ky] * g1[kz], u2yz = u2[ky] + u2[kz];
+  // u2 in shared memory is the x axis' table; the y and z axes' come from global memory
+  const float gyz = g1[ky] * g1[kz], u2yz = __ldg(S.u2 + L + ky) + __ldg(S.u2 + 2 * L + kz);
   auto colref = [&](int ch) {
     float2* b = box + ch * P::BOX;
     return [b, gc](int e) -> float2& { return b[bx(e, gc)]; };

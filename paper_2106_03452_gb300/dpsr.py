@@ -24,13 +24,19 @@ def _dev_f32(t: torch.Tensor, name: str, shape=None) -> torch.Tensor:
 class Plan:
     """A libdpsr plan: grid size r (power of two in [8, 512]) and Gaussian
     bandwidth sigma (Eq. 3). Owns its device workspace; keeps the context of
-    its last forward pass for the backward pass."""
+    its last forward pass for the backward pass. box: side lengths of a
+    periodic box (voxel size L_d / r per axis; points in box coordinates),
+    None for the unit cube."""
 
-    def __init__(self, r: int, sigma: float = 2.0, device=None, n_max: int | None = None):
+    def __init__(self, r: int, sigma: float = 2.0, device=None, n_max: int | None = None, box=None):
         self.r, self.sigma = int(r), float(sigma)
+        self.box = None if box is None else tuple(float(v) for v in box)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
-            self.handle = L.dpsr_plan_create(self.r, self.sigma)
+            if self.box is None:
+                self.handle = L.dpsr_plan_create(self.r, self.sigma)
+            else:
+                self.handle = L.dpsr_plan_create_box(self.r, self.sigma, self.box)
             if n_max:
                 L.dpsr_plan_reserve(self.handle, int(n_max))
         self._saved = None

@@ -28,6 +28,7 @@ DPSR_EBUSY = -7
 _c_int, _c_i64, _c_sz, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p
 _PROTOS = {
     "dpsr_plan_create": (_c_int, [_c_int, ctypes.c_float, ctypes.POINTER(_vp)]),
+    "dpsr_plan_create_box": (_c_int, [_c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_vp)]),
     "dpsr_plan_destroy": (_c_int, [_vp]),
     "dpsr_plan_set_stream": (_c_int, [_vp, _vp]),
     "dpsr_plan_reserve": (_c_int, [_vp, _c_i64]),
@@ -120,6 +121,13 @@ def check(code: int, what: str) -> None:
 def dpsr_plan_create(r: int, sigma: float) -> int:
     h = _vp()
     check(load().dpsr_plan_create(int(r), float(sigma), ctypes.byref(h)), "dpsr_plan_create")
+    return h.value
+
+
+def dpsr_plan_create_box(r: int, sigma: float, box) -> int:
+    h = _vp()
+    b = None if box is None else (ctypes.c_float * 3)(*[float(v) for v in box])
+    check(load().dpsr_plan_create_box(int(r), float(sigma), b, ctypes.byref(h)), "dpsr_plan_create_box")
     return h.value
 
 
