@@ -571,7 +571,7 @@ def bench_serving(args):
     0.15), 30% forward + backward, admitted by an 8 GB device budget. The
     continuous-batching server (--serve-slots stream slots) against a per-solve loop (the
     same server with one slot and no coalescing), saturated (the first 400
-    requests submitted at once) for throughput, then replayed in real time
+    requests submitted at once, best of three bursts) for throughput, then replayed in real time
     (latency = completion - arrival): the served configuration over the whole
     trace (60 s, about 12 000 requests), the loop over its first 15 s."""
     from paper_2106_03452_gb300 import serve, synth
@@ -594,12 +594,17 @@ def bench_serving(args):
     # both saturation runs before either real-time replay: the replay's
     # scattered buffer traffic measurably slows a burst that follows it in
     # the same process
+    # three bursts per configuration, alternating, best of three: the
+    # serving path runs on the host cores (submission, completion polling,
+    # the server thread), which other jobs on a shared machine disturb
     sat = trace[:400]
-    sat_rate = {}
-    for slots, label, _ in configs:
-        t0 = time.perf_counter()
-        serve.replay(sat, servers[label], pool, realtime=False, ring=ring)
-        sat_rate[label] = len(sat) / (time.perf_counter() - t0)
+    sat_runs = {label: [] for _, label, _ in configs}
+    for _rep in range(3):
+        for slots, label, _ in configs:
+            t0 = time.perf_counter()
+            serve.replay(sat, servers[label], pool, realtime=False, ring=ring)
+            sat_runs[label].append(len(sat) / (time.perf_counter() - t0))
+    sat_rate = {label: max(v) for label, v in sat_runs.items()}
     for slots, label, group in configs:
         srv = servers[label]
         g0 = srv.stats()
@@ -609,6 +614,7 @@ def bench_serving(args):
         st = srv.stats()
         out[label] = serve.summarize(res, wall)
         out[label]["saturated_solves_per_s"] = sat_rate[label]
+        out[label]["saturated_runs"] = sat_runs[label]
         out[label]["max_in_flight"] = st["max_in_flight"]
         out[label]["max_group"] = group
         out[label]["coalesced_requests"] = st["grouped_requests"] - g0["grouped_requests"]

@@ -160,11 +160,18 @@ int cuda_err(cudaError_t e) { return e == cudaErrorMemoryAllocation ? DPSR_ENOME
 // in this process. The plane kernels are idempotent (they rewrite the same
 // outputs from the same inputs), so the candidates run in place, one after
 // the other; the last run leaves the correct results. Results are cached per
-// (kernel, r) for the process. DPSR_TUNE=0 in the environment switches the
-// tuner off (the static choice of pick_cluster is used).
+// (kernel, r) for the process, and with DPSR_TUNE_CACHE=<file> persisted
+// across processes (tune_cache.cu): a choice found there is used without
+// timing. DPSR_TUNE=0 in the environment switches the tuner off (the static
+// choice of pick_cluster is used).
 // ---------------------------------------------------------------------------
 std::mutex g_tune_mu;
 int g_tuned[4][10] = {};  // [kind][log2 r]: 1 + chosen C (0 = pencil path), 0 = not tuned yet
+
+}  // namespace
+extern "C" int dpsr_internal_tc_lookup(int kind, int r, int batch);
+extern "C" void dpsr_internal_tc_store(int kind, int r, int batch, int path, float ms);
+namespace {
 
 int log2i(int r) {
   int l = 0;
@@ -247,9 +254,12 @@ cudaError_t tune_plane(dpsr_plan p, int kind, const Solve& s, cudaStream_t st) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (e == cudaSuccess) {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tuned[kind][log2i(r)] = bestC + 1;
-    p->C[kind] = bestC;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tuned[kind][log2i(r)] = bestC + 1;
+      p->C[kind] = bestC;
+    }
+    dpsr_internal_tc_store(kind, r, 0, bestC, best);
   }
   return e;
 }
@@ -267,6 +277,15 @@ cudaError_t run_plane(dpsr_plan p, int kind, const Solve& s, cudaStream_t st) {
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       tuned = g_tuned[kind][log2i(p->r)];
+    }
+    if (!tuned) {  // a choice persisted by an earlier process (DPSR_TUNE_CACHE)
+      const int c = dpsr_internal_tc_lookup(kind, p->r, 0);
+      const size_t sm = c >= 0 ? dpsr::plane_smem_bytes(kind, p->r, c) : 0;
+      if (sm != 0 && sm <= 227 * 1024 - 1024) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[kind][log2i(p->r)] = c + 1;
+        tuned = c + 1;
+      }
     }
     if (tuned) {
       p->C[kind] = tuned - 1;

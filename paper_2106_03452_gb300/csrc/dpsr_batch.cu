@@ -20,6 +20,8 @@ using dpsr::Solve;
 extern "C" const void* dpsr_internal_solve(dpsr_plan p);
 extern "C" int dpsr_internal_cluster(dpsr_plan p, int kind);
 extern "C" int dpsr_internal_forced(int kind, int r);
+extern "C" int dpsr_internal_tc_lookup(int kind, int r, int batch);
+extern "C" void dpsr_internal_tc_store(int kind, int r, int batch, int path, float ms);
 
 struct BatchClass {
   int r = 0;
@@ -120,7 +122,8 @@ cudaError_t launch_bwd(dpsr_batch b) {
 // an untimed one) on the class's own instances, in the order of the solve, so
 // that every kind runs on its real inputs; the last run leaves the chosen
 // path's results. The environment's fixed paths (DPSR_PLANE_PATH[S_<r>]) and
-// DPSR_TUNE=0 take precedence.
+// DPSR_TUNE=0 take precedence; a choice persisted in the DPSR_TUNE_CACHE file
+// for this class size is used without timing.
 cudaError_t tune_kind(BatchClass& c, int kind, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
   const Solve dummy = {};
   const int n = (int)c.members.size();
@@ -129,6 +132,15 @@ cudaError_t tune_kind(BatchClass& c, int kind, cudaStream_t st, cudaEvent_t e0, 
     if (forced >= 0) c.C[kind] = forced;
     c.tuned[kind] = true;
     return dpsr::launch_plane(kind, c.r, c.C[kind], dummy, c.dtab, n, st);
+  }
+  {  // a choice persisted by an earlier process (DPSR_TUNE_CACHE)
+    const int cached = dpsr_internal_tc_lookup(kind, c.r, n);
+    const size_t sm = cached >= 0 ? dpsr::plane_smem_bytes(kind, c.r, cached) : 0;
+    if (sm != 0 && sm <= 227 * 1024 - 1024) {
+      c.C[kind] = cached;
+      c.tuned[kind] = true;
+      return dpsr::launch_plane(kind, c.r, cached, dummy, c.dtab, n, st);
+    }
   }
   const int cands[5] = {0, 1, 2, 4, 8};
   float best = 1e30f;
@@ -162,7 +174,9 @@ cudaError_t tune_kind(BatchClass& c, int kind, cudaStream_t st, cudaEvent_t e0, 
   }
   c.C[kind] = bestC;
   c.tuned[kind] = true;
-  return dpsr::launch_plane(kind, c.r, bestC, dummy, c.dtab, n, st);
+  cudaError_t e = dpsr::launch_plane(kind, c.r, bestC, dummy, c.dtab, n, st);
+  if (e == cudaSuccess && best < 1e30f) dpsr_internal_tc_store(kind, c.r, n, bestC, best);
+  return e;
 }
 
 // One eager forward (and backward) of every class on the batch stream, tuning
