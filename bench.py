@@ -268,6 +268,32 @@ def run_gpu(args):
     h2d = 2 * 12 * N + 4 * r ** 3
     d2h = 4 * r ** 3 + 2 * 12 * N
 
+    # ---------------- the same workload in an anisotropic box ----------------
+    # the ellipsoid cloud stretched into the periodic box (1, 0.75, 1.5): voxel
+    # size L_d / 128 per axis (dpsr_plan_create_box), same kernels and bytes
+    box_dims = (1.0, 0.75, 1.5)
+    bx = torch.tensor(box_dims, device=dev)
+    Pb = (P * bx).contiguous()
+    Nb = Nn / bx
+    Nb = (Nb / Nb.norm(dim=1, keepdim=True).clamp_min(1e-30)).contiguous()
+    plan_b = Plan(r, w["sigma"], device=dev, n_max=N, box=box_dims)
+    chib, dpb, dnb = torch.empty_like(chi), torch.empty_like(P), torch.empty_like(P)
+
+    def step_box():
+        plan_b.forward(Pb, Nb, chib)
+        plan_b.backward(G, dpb, dnb)
+
+    step_box()
+    if plan_b.sync() != 0:
+        raise RuntimeError("box device status")
+    ms_box, _ = timed(step_box, args.steps, args.warmup)
+    ms_box = _max_over_ranks(dist, ms_box)
+    box_block = {"workload": "r128 workload stretched into the periodic box (1, 0.75, 1.5), fwd+bwd",
+                 "box": list(box_dims), "solves_per_s": ws * args.steps / (ms_box / 1e3),
+                 "ms_per_step": ms_box / args.steps, "vs_cube": ms_max / ms_box,
+                 "paths": L.dpsr_plan_clusters(plan_b.handle)}
+    plan_b.close()
+
     # ---------------- r = 256 ----------------
     r256 = None
     if not args.no_r256:
@@ -377,6 +403,7 @@ def run_gpu(args):
             "paths": L.dpsr_plan_clusters(plan.handle),  # see r256["paths"]
             "clocks": clk,
             "r256": r256,
+            "box": box_block,
             "batched": batched,
             "train": train,
             "optimize": optim,

@@ -683,9 +683,17 @@ __global__ void __launch_bounds__(kNT, plane_minb<L, C>(2))
 // start; the Z channel's y-inverse is computed from the Q1 box in the Y
 // round (u_z is constant along a column, so it commutes with the y-inverse).
 // ===========================================================================
+// Threads of the adjoint plane kernel: with one CTA per plane (C = 1) the
+// CTA is alone on its SM (its two box buffers fill the shared memory), so it
+// runs 512 threads (16 warps, at most 128 registers each; from r = 64 on) to hide the
+// latency of its serial rounds; cluster CTAs keep 256.
+template <int L, int C>
+constexpr int binv_threads() { return C == 1 && L >= 64 ? 512 : kNT; }
+
 template <int L, int C>
 struct BinvGeo {
-  static constexpr int T = Shape<L>::T, R1 = Shape<L>::R1, G = kNT / T;
+  static constexpr int NT = binv_threads<L, C>();
+  static constexpr int T = Shape<L>::T, R1 = Shape<L>::R1, G = NT / T;
   static constexpr int R = L / C, H = L / 2, SPC = H / C;
   static constexpr int NB = (SPC + 15) / 16;
   static constexpr int BOX = L * 16;  // float2 per box [ky][16 kz]
@@ -742,9 +750,10 @@ __device__ __forceinline__ void c2r_pair_ip(int t, const Tw& tw, Acc acc) {
 }
 
 template <int L, int C>
-__global__ void __launch_bounds__(kNT, binv_smem<L, C>() <= 113 * 1024 ? 2 : 1)
+__global__ void __launch_bounds__(binv_threads<L, C>(), binv_smem<L, C>() <= 113 * 1024 ? 2 : 1)
     k_plane_binv(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
   using B = BinvGeo<L, C>;
+  constexpr int NT = B::NT;
   constexpr int H = B::H, R = B::R, SPC = B::SPC, T = B::T, R1 = B::R1, G = B::G;
   const Solve& S = tab ? tab[blockIdx.z] : s0;
   cg::cluster_group cl = cg::this_cluster();
@@ -761,7 +770,7 @@ __global__ void __launch_bounds__(kNT, binv_smem<L, C>() <= 113 * 1024 ? 2 : 1)
   __shared__ uint64_t barL[2], barR;
   __shared__ int list_n;
   pdl_trigger();
-  for (int i = tid; i < L; i += kNT) {
+  for (int i = tid; i < L; i += NT) {
     iu[i] = S.iu[L + i];  // y axis; the z axis is read from global memory
     twt[i] = S.tw[i];
   }
@@ -785,7 +794,7 @@ __global__ void __launch_bounds__(kNT, binv_smem<L, C>() <= 113 * 1024 ? 2 : 1)
   const PlanePoints pp(S, X);
   const int y_lo = c * R;
   // (overlaps the box loads in flight)
-  const int nlist = C > 1 ? plane_list<kNT>(S, pp, L, y_lo, R, false, list, &list_n) : -1;
+  const int nlist = C > 1 ? plane_list<NT>(S, pp, L, y_lo, R, false, list, &list_n) : -1;
   const int nvisit = nlist >= 0 ? nlist : pp.total();
   uint32_t phR = 0;
   bool alive = true;
@@ -870,7 +879,7 @@ __global__ void __launch_bounds__(kNT, binv_smem<L, C>() <= 113 * 1024 ? 2 : 1)
     // This channel's share of the point adjoint: dnormals_ch = gather of
     // V_ch, and d/dp of the weights times n_ch V_ch.
     if (alive) {
-      for (int i = tid; i < nvisit; i += kNT) {
+      for (int i = tid; i < nvisit; i += NT) {
         int dx;
         const int idx = visit_point(list, nlist, pp, i, dx);
         const float4 a = S.sorted[2 * idx];
@@ -954,6 +963,7 @@ static cudaError_t launch_plane_t(int kind, const Solve& s, const Solve* tab, in
   if constexpr (fwd_inst<L, C>()) {
     if (kind == 0) block = dim3(fwd_threads<L, C>());
   }
+  if (kind == 3) block = dim3(binv_threads<L, C>());
   return launch_k(fn, dim3(L * C, 1, count), block, smem, st, C, s, tab);
 }
 
