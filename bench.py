@@ -363,6 +363,8 @@ def run_gpu(args):
 
     # ---------------- L2 read bandwidth (the ceiling of the L2-resident r = 128 solve) ----
     l2 = measure_l2_read(dev)
+    # FP32 FMA throughput (the FFT butterflies' pipe), measured by the library's own kernel
+    fma_tflops = L.dpsr_fp32_fma_peak(1 << 16) / 1e12
     l2_ach = per[dom]["bytes"] / (per[dom]["ms"] / 1e3) / 1e9
     solve_gbs = solve_bytes_model(r, N) / (ms_max / args.steps / 1e3) / 1e9
 
@@ -396,6 +398,9 @@ def run_gpu(args):
                          "l2": {"achieved": l2_ach, "peak": l2, "unit": "GB/s",
                                 "frac": l2_ach / l2 if l2 else None,
                                 "peak_kind": "measured in this run: L2 read bandwidth, 64 reads of a 24 MiB buffer in one kernel"},
+                         "fp32": {"fma_tflops_measured": fma_tflops,
+                                  "nominal_tflops": 152 * 128 * 2 * 2.07e9 / 1e12,
+                                  "how": "8 independent FMA chains per thread, 8 x 256-thread CTAs per SM"},
                          "solve": {"model_bytes": solve_bytes_model(r, N), "achieved": solve_gbs,
                                    "frac_hbm": solve_gbs / hbm_peak,
                                    "frac_l2": solve_gbs / l2 if l2 else None}},

@@ -63,7 +63,8 @@ enum {
     DPSR_EDEGENERATE = -4, /* non-finite input or chi'(0) - mu == 0 (no finite scale) */
     DPSR_ESTATE = -5,      /* backward without a forward, or N above the reserved size */
     DPSR_ETIMEOUT = -6,    /* a bounded device wait gave up */
-    DPSR_EBUSY = -7        /* resource busy (serving admission) */
+    DPSR_EBUSY = -7,       /* resource busy (serving admission) */
+    DPSR_ECANCELED = -8    /* a serving request cancelled before admission */
 };
 
 /* Create a plan for grid size r (a power of two, 8 <= r <= 512) and Gaussian
@@ -388,6 +389,13 @@ DPSR_API int dpsr_server_submit(dpsr_server server, int r, const float *points,
 DPSR_API int dpsr_server_poll(dpsr_server server, int64_t ticket, int *done);
 /* Block until the ticket completes (or timeout_s passes: DPSR_ETIMEOUT). */
 DPSR_API int dpsr_server_wait(dpsr_server server, int64_t ticket, double timeout_s);
+/* Cancel a request that is still queued: it is taken out of the queue, no
+ * work for it reaches the GPU, its output buffers are not written, and its
+ * poll/wait returns DPSR_ECANCELED (which retires the ticket). Returns
+ * DPSR_OK when cancelled; DPSR_EBUSY when the request was already admitted
+ * or has completed (it then finishes normally and its poll/wait returns its
+ * own status); DPSR_EINVAL for an unknown or retired ticket. */
+DPSR_API int dpsr_server_cancel(dpsr_server server, int64_t ticket);
 /* Coalescing: requests of grid size up to 128 that wait in the queue with
  * the same grid size and mode (forward only / forward + backward) are
  * admitted together, up to max_group of them (1..8, default 8), and run as
@@ -412,6 +420,14 @@ DPSR_API const char *dpsr_strerror(int status);
  * DPSR_ETIMEOUT when the wait ran out as designed, DPSR_OK if it did not
  * (a defect), DPSR_EINVAL or DPSR_ECUDA on errors. */
 DPSR_API int dpsr_check_bounded_wait(double limit_s);
+
+/* Measurement utility (not part of the method): the FP32 FMA throughput of
+ * the current device in FLOP/s (2 per FMA), timed with events over a kernel
+ * of `iters` steps of 8 independent FMA chains per thread, 8 CTAs of 256
+ * threads per SM, fastest of three runs. Blocks the calling thread; uses
+ * its own stream and a small device buffer that it frees. Errors:
+ * DPSR_EINVAL (iters < 1 or NULL), DPSR_ECUDA. */
+DPSR_API int dpsr_fp32_fma_peak(int iters, double *flops_per_s);
 
 #ifdef __cplusplus
 }

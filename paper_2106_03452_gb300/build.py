@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdpsr.so")
-SOURCES = ["dpsr_api.cu", "k_plane.cu", "k_xpass.cu", "k_points.cu", "k_pencil.cu", "dpsr_static.cu", "dpsr_batch.cu", "dpsr_serve.cu", "k_mesh.cu", "k_opt.cu", "tune_cache.cu"]
+SOURCES = ["dpsr_api.cu", "k_plane.cu", "k_xpass.cu", "k_points.cu", "k_pencil.cu", "dpsr_static.cu", "dpsr_batch.cu", "dpsr_serve.cu", "k_mesh.cu", "k_opt.cu", "tune_cache.cu", "k_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

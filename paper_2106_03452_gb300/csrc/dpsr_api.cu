@@ -30,6 +30,7 @@
 #include "dpsr.h"
 #include "dpsr_dev.cuh"
 #include "launch.h"
+#include "nvtx.h"
 
 using dpsr::Solve;
 
@@ -397,6 +398,7 @@ const char* dpsr_strerror(int st) {
     case DPSR_ESTATE: return "invalid call order (backward without forward)";
     case DPSR_ETIMEOUT: return "bounded device wait timed out";
     case DPSR_EBUSY: return "resource busy";
+    case DPSR_ECANCELED: return "request cancelled";
     default: return "unknown status";
   }
 }
@@ -631,6 +633,7 @@ int dpsr_plan_profile_read(dpsr_plan p, double* ms, int* launches) {
 
 int dpsr_forward(dpsr_plan p, const float* points, const float* normals, int64_t N,
                  float* chi_out) {
+  dpsr::NvtxRange nvtx_call("dpsr_forward");
   if (!p || !points || !normals || !chi_out || N < 1 || N > INT32_MAX / 2) return DPSR_EINVAL;
   if (((uintptr_t)chi_out & 15) != 0) return DPSR_EINVAL;  // read back by vector loads
   DeviceGuard dg(p->device);
@@ -647,6 +650,7 @@ int dpsr_forward(dpsr_plan p, const float* points, const float* normals, int64_t
   cudaStream_t st = p->stream;
   cudaError_t e = cudaSuccess;
   auto run = [&](int kind, auto&& fn) {
+    dpsr::NvtxRange nr(dpsr::stage_name(kind));
     if (e == cudaSuccess) e = prof_mark(p, kind, true);
     if (e == cudaSuccess) e = fn();
     if (e == cudaSuccess) e = prof_mark(p, kind, false);
@@ -675,6 +679,7 @@ int dpsr_forward(dpsr_plan p, const float* points, const float* normals, int64_t
 }
 
 int dpsr_backward(dpsr_plan p, const float* dchi, float* dpoints, float* dnormals) {
+  dpsr::NvtxRange nvtx_call("dpsr_backward");
   if (!p || !dchi || !dpoints || !dnormals) return DPSR_EINVAL;
   if (((uintptr_t)dchi & 15) != 0) return DPSR_EINVAL;  // rows move by bulk copies
   if (!p->have_fwd) return DPSR_ESTATE;
@@ -689,6 +694,7 @@ int dpsr_backward(dpsr_plan p, const float* dchi, float* dpoints, float* dnormal
   cudaStream_t st = p->stream;
   cudaError_t e = cudaSuccess;
   auto run = [&](int kind, auto&& fn) {
+    dpsr::NvtxRange nr(dpsr::stage_name(kind));
     if (e == cudaSuccess) e = prof_mark(p, kind, true);
     if (e == cudaSuccess) e = fn();
     if (e == cudaSuccess) e = prof_mark(p, kind, false);
@@ -830,6 +836,7 @@ int dpsr_internal_io(dpsr_plan p, int64_t N, float** pts, float** nrm, float** c
 
 int dpsr_forward_host(dpsr_plan p, const float* points, const float* normals, int64_t N,
                       float* chi_out) {
+  dpsr::NvtxRange nvtx_call("dpsr_forward_host");
   if (!p || !points || !normals || !chi_out || N < 1 || N > INT32_MAX / 2) return DPSR_EINVAL;
   DeviceGuard dg(p->device);
   if (!dg.ok) return DPSR_ECUDA;
@@ -850,6 +857,7 @@ int dpsr_forward_host(dpsr_plan p, const float* points, const float* normals, in
 
 int dpsr_solve_host(dpsr_plan p, const float* points, const float* normals, int64_t N, const float* dchi,
                     float* chi_out, float* dpoints, float* dnormals) {
+  dpsr::NvtxRange nvtx_call("dpsr_solve_host");
   if (!p || !points || !normals || !dchi || !chi_out || !dpoints || !dnormals || N < 1 || N > INT32_MAX / 2)
     return DPSR_EINVAL;
   DeviceGuard dg(p->device);
@@ -895,6 +903,7 @@ int dpsr_solve_host(dpsr_plan p, const float* points, const float* normals, int6
 }
 
 int dpsr_backward_host(dpsr_plan p, const float* dchi, float* dpoints, float* dnormals) {
+  dpsr::NvtxRange nvtx_call("dpsr_backward_host");
   if (!p || !dchi || !dpoints || !dnormals) return DPSR_EINVAL;
   if (!p->have_fwd || p->s.points != (const float*)host_io_view(p, p->host_n).pts)
     return DPSR_ESTATE;

@@ -13,6 +13,7 @@
 #include "dpsr.h"
 #include "dpsr_dev.cuh"
 #include "launch.h"
+#include "nvtx.h"
 
 using dpsr::Solve;
 
@@ -325,6 +326,7 @@ int dpsr_batch_bind(dpsr_batch b, int i, const float* points, const float* norma
 }
 
 int dpsr_batch_forward(dpsr_batch b) {
+  dpsr::NvtxRange nvtx_call("dpsr_batch_forward");
   if (!b) return DPSR_EINVAL;
   int rc = upload(b);
   if (rc != DPSR_OK) return rc;
@@ -338,6 +340,7 @@ int dpsr_batch_forward(dpsr_batch b) {
 }
 
 int dpsr_batch_backward(dpsr_batch b) {
+  dpsr::NvtxRange nvtx_call("dpsr_batch_backward");
   if (!b) return DPSR_EINVAL;
   if (!b->have_fwd) return DPSR_ESTATE;
   for (int i = 0; i < b->count; ++i)
@@ -404,7 +407,10 @@ static int graph_launch(dpsr_batch b, int mode) {
   return DPSR_OK;
 }
 
-int dpsr_batch_graph_launch(dpsr_batch b, int with_bwd) { return graph_launch(b, with_bwd ? 1 : 0); }
+int dpsr_batch_graph_launch(dpsr_batch b, int with_bwd) {
+  dpsr::NvtxRange nvtx_call("dpsr_batch_graph_launch");
+  return graph_launch(b, with_bwd ? 1 : 0);
+}
 
 int dpsr_batch_bind_target(dpsr_batch b, int i, const float* target) {
   if (!b || i < 0 || i >= b->count || !target) return DPSR_EINVAL;
@@ -414,6 +420,7 @@ int dpsr_batch_bind_target(dpsr_batch b, int i, const float* target) {
 }
 
 int dpsr_batch_train_step(dpsr_batch b) {
+  dpsr::NvtxRange nvtx_call("dpsr_batch_train_step");
   if (!b) return DPSR_EINVAL;
   for (int i = 0; i < b->count; ++i)
     if (((uintptr_t)b->host[i].dchi_rw) & 15) return DPSR_EINVAL;

@@ -15,6 +15,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -25,6 +26,7 @@
 #include <vector>
 
 #include "dpsr.h"
+#include "nvtx.h"
 
 extern "C" int dpsr_internal_io(dpsr_plan p, int64_t N, float** pts, float** nrm, float** chi,
                                 float** dchi, float** dpts, float** dnrm);
@@ -196,6 +198,7 @@ int get_batch(dpsr_server s, int r, cudaStream_t st) {
 // Queue a coalesced group (same r and mode, 2..kMaxGroup requests) on a
 // slot's stream as one batched launch of its first g.size() instances.
 int launch_group(dpsr_server s, Slot& sl, std::vector<Request*>& g) {
+  dpsr::NvtxRange nvtx_call("dpsr_server.group");
   const int r = g[0]->r;
   const bool bwd = g[0]->dchi != nullptr;
   const int bi = get_batch(s, r, sl.stream);
@@ -241,6 +244,7 @@ int launch_group(dpsr_server s, Slot& sl, std::vector<Request*>& g) {
 
 // Queue one request on a slot's stream.
 int launch(dpsr_server s, Slot& sl, Request& q) {
+  dpsr::NvtxRange nvtx_call("dpsr_server.request");
   const int pi = get_plan(s, q.r, q.N);
   if (pi < 0) return DPSR_ENOMEM;
   PooledPlan& pp = s->pool[pi];
@@ -512,6 +516,24 @@ int dpsr_server_wait(dpsr_server s, int64_t ticket, double timeout_s) {
   const int st = f->second.status;
   s->reqs.erase(f);
   return st;
+}
+
+int dpsr_server_cancel(dpsr_server s, int64_t ticket) {
+  if (!s) return DPSR_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return DPSR_EINVAL;
+    // admission takes requests out of the queue under this lock: a ticket
+    // still queued here has no work on the GPU and none will be queued
+    auto q = std::find(s->queue.begin(), s->queue.end(), ticket);
+    if (it->second.done || q == s->queue.end()) return DPSR_EBUSY;
+    s->queue.erase(q);
+    it->second.status = DPSR_ECANCELED;
+    it->second.done = true;
+  }
+  s->cv_done.notify_all();
+  return DPSR_OK;
 }
 
 int dpsr_server_set_max_group(dpsr_server s, int max_group) {

@@ -24,10 +24,13 @@ DPSR_EDEGENERATE = -4
 DPSR_ESTATE = -5
 DPSR_ETIMEOUT = -6
 DPSR_EBUSY = -7
+DPSR_ECANCELED = -8
 
 _c_int, _c_i64, _c_sz, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p
 _PROTOS = {
     "dpsr_plan_create": (_c_int, [_c_int, ctypes.c_float, ctypes.POINTER(_vp)]),
+    "dpsr_server_cancel": (_c_int, [_vp, _c_i64]),
+    "dpsr_fp32_fma_peak": (_c_int, [_c_int, ctypes.POINTER(ctypes.c_double)]),
     "dpsr_plan_create_box": (_c_int, [_c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_vp)]),
     "dpsr_plan_destroy": (_c_int, [_vp]),
     "dpsr_plan_set_stream": (_c_int, [_vp, _vp]),
@@ -129,6 +132,22 @@ def dpsr_plan_create_box(r: int, sigma: float, box) -> int:
     b = None if box is None else (ctypes.c_float * 3)(*[float(v) for v in box])
     check(load().dpsr_plan_create_box(int(r), float(sigma), b, ctypes.byref(h)), "dpsr_plan_create_box")
     return h.value
+
+
+def dpsr_server_cancel(server: int, ticket: int) -> int:
+    """DPSR_OK (cancelled before admission) or DPSR_EBUSY (admitted or done:
+    it completes normally); raises for an unknown ticket."""
+    rc = load().dpsr_server_cancel(server, int(ticket))
+    if rc not in (DPSR_OK, DPSR_EBUSY):
+        raise DPSRError(rc, "dpsr_server_cancel")
+    return rc
+
+
+def dpsr_fp32_fma_peak(iters: int = 1 << 16) -> float:
+    """FP32 FMA throughput of the current device, FLOP/s."""
+    v = ctypes.c_double()
+    check(load().dpsr_fp32_fma_peak(int(iters), ctypes.byref(v)), "dpsr_fp32_fma_peak")
+    return v.value
 
 
 def dpsr_plan_destroy(plan: int) -> None:

@@ -43,6 +43,9 @@ class Server:
     def wait(self, ticket, timeout_s=0.0) -> int:
         return L.dpsr_server_wait(self.handle, ticket, timeout_s)
 
+    def cancel(self, ticket) -> int:
+        return L.dpsr_server_cancel(self.handle, ticket)
+
     def stats(self):
         d = L.dpsr_server_stats(self.handle)
         d.update(L.dpsr_server_group_stats(self.handle))

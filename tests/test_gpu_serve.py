@@ -133,3 +133,82 @@ def test_coalesced_groups_equal_alone_at_each_size(oracle):
             assert _rel(res["group"][i][0], ref) <= 1e-5
             rdp, rdn = oracle.backward(r, 2.0, p.numpy(), n.numpy(), G.numpy())
             assert _rel(res["group"][i][1], rdp) <= 1e-4 and _rel(res["group"][i][2], rdn) <= 1e-4
+
+
+def test_cancel_queued_request():
+    """A request still queued behind others is cancelled: its wait returns
+    DPSR_ECANCELED and its output buffer keeps its contents; an admitted or
+    finished request cannot be cancelled (DPSR_EBUSY) and completes normally;
+    a retired ticket is unknown (DPSR_EINVAL)."""
+    import torch
+    from paper_2106_03452_gb300 import libdpsr as L
+    from paper_2106_03452_gb300 import serve
+    pool = serve.InputPool(n_clouds=2, n_max=200000, rs=(256,))
+    srv = serve.Server(8 << 30, slots=1, max_group=1)
+    pts, nrm = pool.inputs(0, 200000)
+    outs = [torch.full((256, 256, 256), float("nan")).pin_memory() for _ in range(6)]
+    tickets = [srv.submit(256, pts, nrm, outs[i]) for i in range(6)]
+    # five 200 000-point r = 256 solves run one at a time ahead of the last
+    assert srv.cancel(tickets[5]) == L.DPSR_OK
+    assert srv.wait(tickets[5], 60.0) == L.DPSR_ECANCELED
+    assert srv.cancel(tickets[0]) == L.DPSR_EBUSY       # admitted first
+    for t in tickets[:5]:
+        assert srv.wait(t, 120.0) == 0
+    assert torch.isnan(outs[5]).all()                  # never written
+    assert all(torch.isfinite(o).all() for o in outs[:5])
+    with pytest.raises(L.DPSRError) as e:
+        srv.cancel(tickets[0])                         # retired by its wait
+    assert e.value.code == L.DPSR_EINVAL
+    st = srv.stats()
+    assert st["completed"] == 5
+    srv.close()
+
+
+def test_producer_thread_dies_mid_queue():
+    """A submitting thread that raises after queueing its requests (so that
+    nobody waits for them) leaves the server consistent: those requests still
+    run, another producer's requests complete, and the server shuts down
+    cleanly with the orphaned tickets never retired."""
+    import threading
+    import time
+
+    import torch
+    from paper_2106_03452_gb300 import serve
+    pool = serve.InputPool(n_clouds=2, n_max=50000, rs=(64, 128))
+    srv = serve.Server(8 << 30, slots=4)
+    keep = []
+
+    def dying_producer():
+        for i in range(6):
+            pts, nrm = pool.inputs(i, 50000)
+            chi = torch.empty((128, 128, 128)).pin_memory()
+            keep.append(chi)                            # the buffers outlive the thread
+            srv.submit(128, pts, nrm, chi)
+        raise RuntimeError("producer died with its requests in the queue")
+
+    errors = []
+    th = threading.Thread(target=lambda: errors.append(_run_catching(dying_producer)))
+    th.start()
+    mine = []
+    for i in range(6):
+        pts, nrm = pool.inputs(i + 1, 20000)
+        chi = torch.empty((64, 64, 64)).pin_memory()
+        mine.append((srv.submit(64, pts, nrm, chi), chi))
+    th.join()
+    assert errors and isinstance(errors[0], RuntimeError)
+    for t, chi in mine:
+        assert srv.wait(t, 120.0) == 0 and torch.isfinite(chi).all()
+    deadline = time.time() + 60.0
+    while srv.stats()["completed"] < 12 and time.time() < deadline:
+        time.sleep(0.01)
+    assert srv.stats()["completed"] == 12
+    assert all(torch.isfinite(c).all() for c in keep)
+    srv.close()
+
+
+def _run_catching(fn):
+    try:
+        fn()
+    except Exception as exc:  # the producer's own failure, recorded for the test
+        return exc
+    return None
