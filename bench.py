@@ -154,10 +154,12 @@ def kernel_bytes(r: int, N: int):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
 # plane kind's kernel at (grid size, plane path), from one ncu capture of the
-# current build on the same workload (profiles/sections_r128_plane_binv_xpass.md);
+# current build on the same workload (profiles/traffic_r128_kinds.md);
 # a kind, size or path not listed reports traffic as null.
 MEASURED_TRAFFIC = {
-    ("plane_binv", 128, 1): 21764352,   # k_plane_binv<128, 1>, r = 128 ellipsoids, N = 20000
+    # k_zfwd<128> + k_yfwd<128, 0> (the pencil forward plane kind), r = 128 ellipsoids, N = 20000
+    ("plane_fwd", 128, 0): 679936 + 37717760,
+    ("plane_binv", 128, 1): 21827840,   # k_plane_binv<128, 1> (512 threads), same workload
 }
 
 
