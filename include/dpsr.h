@@ -64,7 +64,8 @@ enum {
     DPSR_ESTATE = -5,      /* backward without a forward, or N above the reserved size */
     DPSR_ETIMEOUT = -6,    /* a bounded device wait gave up */
     DPSR_EBUSY = -7,       /* resource busy (serving admission) */
-    DPSR_ECANCELED = -8    /* a serving request cancelled before admission */
+    DPSR_ECANCELED = -8,   /* a serving request cancelled before admission */
+    DPSR_EBOUNDS = -9      /* debug builds: a data-dependent index failed its range check */
 };
 
 /* Create a plan for grid size r (a power of two, 8 <= r <= 512) and Gaussian
@@ -420,6 +421,20 @@ DPSR_API const char *dpsr_strerror(int status);
  * DPSR_ETIMEOUT when the wait ran out as designed, DPSR_OK if it did not
  * (a defect), DPSR_EINVAL or DPSR_ECUDA on errors. */
 DPSR_API int dpsr_check_bounded_wait(double limit_s);
+
+/* Debug builds. A library compiled with DPSR_DEBUG_CHECKS (the build
+ * script's debug variant; the Python binding loads it when the environment
+ * sets DPSR_DEBUG_CHECKS=1) checks every data-dependent index of the point
+ * kernels (bin keys, sorted positions, point indices read from the bins)
+ * before use: an index out of range skips its access and sets a status bit
+ * that dpsr_sync reports as DPSR_EBOUNDS. No check traps or aborts.
+ * dpsr_debug_checks returns 1 in such a build, 0 otherwise.
+ * dpsr_debug_check_selftest runs one kernel whose single access has an index
+ * outside its logical range but inside its allocation: DPSR_EBOUNDS in a
+ * debug build, DPSR_OK otherwise (DPSR_ECUDA if CUDA fails). It synchronises
+ * the device. */
+DPSR_API int dpsr_debug_checks(void);
+DPSR_API int dpsr_debug_check_selftest(void);
 
 /* Measurement utility (not part of the method): the FP32 FMA throughput of
  * the current device in FLOP/s (2 per FMA), timed with events over a kernel

@@ -349,6 +349,7 @@ static thread_local bool t_pdl_off = false;
 
 int status_code(unsigned st) {
   if (st & kStTimeout) return DPSR_ETIMEOUT;  // a wait gave up: the outputs are incomplete
+  if (st & kStBounds) return DPSR_EBOUNDS;    // a debug-build index check failed
   if (st) return DPSR_EDEGENERATE;
   return DPSR_OK;
 }
@@ -399,6 +400,7 @@ const char* dpsr_strerror(int st) {
     case DPSR_ETIMEOUT: return "bounded device wait timed out";
     case DPSR_EBUSY: return "resource busy";
     case DPSR_ECANCELED: return "request cancelled";
+    case DPSR_EBOUNDS: return "debug index check failed";
     default: return "unknown status";
   }
 }

@@ -461,7 +461,23 @@ inline void spectral_tables(int r, double sigma, const float* box, float2* tw, f
   }
 }
 
-enum : unsigned { kStBadInput = 1u, kStDegenerate = 2u, kStTimeout = 4u };
+enum : unsigned { kStBadInput = 1u, kStDegenerate = 2u, kStTimeout = 4u, kStBounds = 8u };
+
+// Debug builds (-DDPSR_DEBUG_CHECKS) check each data-dependent index of the
+// point kernels (bin keys, sorted positions, point indices read from the
+// bins) before it is used: an index outside [0, n) sets kStBounds in the
+// status word (reported as DPSR_EBOUNDS) and its access is skipped, so a
+// broken invariant shows up as a status instead of a stray access. Release
+// builds compile the checks away.
+#ifdef DPSR_DEBUG_CHECKS
+__device__ __forceinline__ bool dbg_in_range(unsigned* status, long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(status, kStBounds);
+  return false;
+}
+#else
+__device__ __forceinline__ bool dbg_in_range(unsigned*, long long, long long) { return true; }
+#endif
 
 // The point count of a solve and its reciprocal (used by the scalar pass).
 inline void set_count(Solve& s, int64_t N) {

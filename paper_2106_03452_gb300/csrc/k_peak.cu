@@ -65,3 +65,52 @@ extern "C" DPSR_API int dpsr_fp32_fma_peak(int iters, double* flops_per_s) {
   if (out) cudaFree(out);
   return rc;
 }
+
+// ---------------------------------------------------------------------------
+// Debug-build check of the index checks themselves: one access whose index
+// (40) lies outside its logical range [0, 32) but inside its 64-float
+// allocation, so that a build without the checks writes harmlessly and a
+// build with them skips the write and raises the status bit.
+// ---------------------------------------------------------------------------
+#include "dpsr_dev.cuh"
+
+namespace {
+
+__global__ void k_dbg_selftest(float* buf, unsigned* status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int i = 40;
+    if (dpsr::dbg_in_range(status, i, 32)) buf[i] = 1.f;
+  }
+}
+
+}  // namespace
+
+namespace dpsr {
+int status_code(unsigned st);
+}
+
+extern "C" DPSR_API int dpsr_debug_checks(void) {
+#ifdef DPSR_DEBUG_CHECKS
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+extern "C" DPSR_API int dpsr_debug_check_selftest(void) {
+  float* buf = nullptr;
+  unsigned* st = nullptr;
+  int rc = DPSR_ECUDA;
+  if (cudaMalloc(&buf, sizeof(float) * 64) == cudaSuccess && cudaMalloc(&st, sizeof(unsigned)) == cudaSuccess &&
+      cudaMemset(st, 0, sizeof(unsigned)) == cudaSuccess) {
+    k_dbg_selftest<<<1, 32>>>(buf, st);
+    unsigned h = 0;
+    if (cudaGetLastError() == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess &&
+        cudaMemcpy(&h, st, sizeof(unsigned), cudaMemcpyDeviceToHost) == cudaSuccess)
+      rc = dpsr::status_code(h);
+  }
+  cudaGetLastError();
+  if (buf) cudaFree(buf);
+  if (st) cudaFree(st);
+  return rc;
+}

@@ -229,6 +229,7 @@ __device__ __forceinline__ void zfwd_tile(const Solve& S, int X, int y0, float* 
     const int k = v < c1 ? 0 : (v < c2 ? 1 : (v < c3 ? 2 : 3));
     const int i = k == 0 ? q0 + v : (k == 1 ? q1 + (v - c1) : (k == 2 ? q2 + (v - c2) : q3 + (v - c3)));
     const int side = k >> 1, part = k & 1;
+    if (!dbg_in_range(S.status, i, S.N)) continue;
     const float4 a = S.sorted[2 * i], b = S.sorted[2 * i + 1];
     const Axis ay = axis_of(a.y, L);
     if (part == 1 && ay.i0 != ylast) continue;
@@ -674,8 +675,10 @@ __device__ __forceinline__ bool zinv_tile(const Solve& S, int tile, float2* sb, 
   float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa;
   if (tid < nv) {
     const int i = tid < n0 ? r0.x + tid : r1.x + (tid - n0);
-    pa = S.sorted[2 * i];
-    if constexpr (NCH == 3) pb = S.sorted[2 * i + 1];
+    if (dbg_in_range(S.status, i, S.N)) {
+      pa = S.sorted[2 * i];
+      if constexpr (NCH == 3) pb = S.sorted[2 * i + 1];
+    }
   }
   if (!wait_stage()) return false;
   TwTab<L> twr{twt, t};
@@ -710,6 +713,7 @@ __device__ __forceinline__ bool zinv_tile(const Solve& S, int tile, float2* sb, 
   for (int v = tid; v < nv; v += NT) {
     const int side = v < n0 ? 0 : 1;
     const int i = side ? r1.x + (v - n0) : r0.x + v;
+    if (!dbg_in_range(S.status, i, S.N)) continue;
     {
       const float4 a = v == tid ? pa : S.sorted[2 * i];
       const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);

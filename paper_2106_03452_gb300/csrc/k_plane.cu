@@ -108,8 +108,8 @@ __device__ int plane_list(const Solve& S, const PlanePoints& pp, int L, int y_lo
     const int i = i0 + (int)threadIdx.x;
     bool in = false;
     int idx = 0, dx = 0;
-    if (i < n) {
-      idx = pp.index(i, dx);
+    if (i < n) idx = pp.index(i, dx);
+    if (i < n && dbg_in_range(S.status, idx, S.N)) {
       const Axis ay = axis_of(pf[8 * (size_t)idx + 1], L);
       in = (unsigned)(ay.i0 - y_lo) < (unsigned)R || (both && (unsigned)(ay.i1 - y_lo) < (unsigned)R);
     }
@@ -351,6 +351,7 @@ __global__ void __launch_bounds__(fwd_threads<L, C>(), 512 / fwd_threads<L, C>()
     for (int i = tid; i < nvisit; i += F::NT) {
       int dx;
       const int idx = visit_point(list, nlist, pp, i, dx);
+      if (!dbg_in_range(S.status, idx, S.N)) continue;
       const float4 a = S.sorted[2 * idx], b = S.sorted[2 * idx + 1];
       const float val = ch == 0 ? a.w : (ch == 1 ? b.x : (ch == 2 ? b.y : 1.f));
       const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);
@@ -544,6 +545,7 @@ __global__ void __launch_bounds__(kNT, plane_minb<L, C>(1))
     for (int i = tid; i < pp.total(); i += kNT) {
       int dx;
       const int idx = pp.index(i, dx);
+      if (!dbg_in_range(S.status, idx, S.N)) continue;
       const float4 a = S.sorted[2 * idx];
       const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);
       if (ay.i0 - y_lo < 0 || ay.i0 - y_lo >= P::R) continue;
@@ -882,6 +884,7 @@ __global__ void __launch_bounds__(binv_threads<L, C>(), binv_smem<L, C>() <= 113
       for (int i = tid; i < nvisit; i += NT) {
         int dx;
         const int idx = visit_point(list, nlist, pp, i, dx);
+        if (!dbg_in_range(S.status, idx, S.N)) continue;
         const float4 a = S.sorted[2 * idx];
         const Axis ay = axis_of(a.y, L);
         if ((unsigned)(ay.i0 - y_lo) >= (unsigned)R) continue;

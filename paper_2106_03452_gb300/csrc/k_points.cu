@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(256) k_bin_count(const __grid_constant__ Solve
     }
     const int key = bin_key(x, y, r);
     S.cellx[p] = key;
+    if (!dbg_in_range(S.status, key, nb)) continue;
     atomicAdd(&h[key], 1);
   }
   if (bad) atomicOr(S.status, kStBadInput);
@@ -131,7 +132,9 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Sol
     if (!isfinite(ny)) ny = 0.f;
     if (!isfinite(nz)) nz = 0.f;
     const int key = S.cellx[p];  // key of k_bin_count
+    if (!dbg_in_range(S.status, key, nb)) continue;
     const int pos = h[scan_slot(key)] + atomicAdd(&cur[key], 1);
+    if (!dbg_in_range(S.status, pos, S.N)) continue;
     S.sorted[2 * pos] = make_float4(x, y, z, nx);
     S.sorted[2 * pos + 1] = make_float4(ny, nz, __int_as_float(p), 0.f);
   }
@@ -168,6 +171,7 @@ __global__ void __launch_bounds__(256) k_combine(const __grid_constant__ Solve s
   const size_t N = S.N;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.N; i += gridDim.x * blockDim.x) {
     const int orig = __float_as_int(S.sorted[2 * i + 1].z);
+    if (!dbg_in_range(S.status, orig, S.N)) continue;
     const float* a = S.slots + (size_t)i * 6;
     const float* b = S.slots + (N + i) * 6;
     const float4 ga = S.gfwd[i], gb = S.gfwd[N + i];

@@ -12,7 +12,10 @@ import os
 import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libdpsr.so")
+# DPSR_DEBUG_CHECKS=1 in the environment loads the bounds-checking build
+# (build.build(debug=True)) instead of the release one
+_DEBUG = os.environ.get("DPSR_DEBUG_CHECKS", "") == "1"
+LIB_PATH = os.path.join(_HERE, "_build_debug" if _DEBUG else "_build", "libdpsr.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -25,11 +28,14 @@ DPSR_ESTATE = -5
 DPSR_ETIMEOUT = -6
 DPSR_EBUSY = -7
 DPSR_ECANCELED = -8
+DPSR_EBOUNDS = -9
 
 _c_int, _c_i64, _c_sz, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p
 _PROTOS = {
     "dpsr_plan_create": (_c_int, [_c_int, ctypes.c_float, ctypes.POINTER(_vp)]),
     "dpsr_server_cancel": (_c_int, [_vp, _c_i64]),
+    "dpsr_debug_checks": (_c_int, []),
+    "dpsr_debug_check_selftest": (_c_int, []),
     "dpsr_fp32_fma_peak": (_c_int, [_c_int, ctypes.POINTER(ctypes.c_double)]),
     "dpsr_plan_create_box": (_c_int, [_c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_vp)]),
     "dpsr_plan_destroy": (_c_int, [_vp]),
@@ -105,7 +111,8 @@ def load():
             if not os.path.exists(LIB_PATH):
                 raise RuntimeError(
                     f"libdpsr is not built ({LIB_PATH} missing): run "
-                    "`python -m paper_2106_03452_gb300.build` (needs nvcc); there is no CPU fallback")
+                    f"`python -m paper_2106_03452_gb300.build{' --debug' if _DEBUG else ''}` (needs nvcc); "
+                    "there is no CPU fallback")
             lib = ctypes.CDLL(LIB_PATH)
             for name, (res, args) in _PROTOS.items():
                 f = getattr(lib, name)
@@ -141,6 +148,14 @@ def dpsr_server_cancel(server: int, ticket: int) -> int:
     if rc not in (DPSR_OK, DPSR_EBUSY):
         raise DPSRError(rc, "dpsr_server_cancel")
     return rc
+
+
+def dpsr_debug_checks() -> bool:
+    return bool(load().dpsr_debug_checks())
+
+
+def dpsr_debug_check_selftest() -> int:
+    return int(load().dpsr_debug_check_selftest())
 
 
 def dpsr_fp32_fma_peak(iters: int = 1 << 16) -> float:
