@@ -112,8 +112,14 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
+        import datetime
+
         import torch.distributed as dist
-        dist.init_process_group("gloo")
+        # a rank that dies ends the others' next collective with an error
+        # instead of a hang: gloo sees the closed connection, and at worst the
+        # group's timeout (DPSR_PG_TIMEOUT_S, default 300 s) expires
+        timeout = datetime.timedelta(seconds=float(os.environ.get("DPSR_PG_TIMEOUT_S", "300")))
+        dist.init_process_group("gloo", timeout=timeout)
         return dist, rank, ws, local
     return None, rank, ws, local
 
