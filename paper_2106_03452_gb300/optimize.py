@@ -19,6 +19,7 @@ from __future__ import annotations
 import math
 import time
 
+import numpy as np
 import torch
 
 from . import libdpsr as L
@@ -75,15 +76,47 @@ def resample_from(chi, n: int, seed: int):
     return sample(tris, nrm, n, seed)
 
 
+def _settings(levels, n_points, samples, lr0, decay, resample, seed):
+    return np.array([float(x) for lv in levels for x in lv] + [n_points, samples, lr0, decay, resample, seed],
+                    np.float64)
+
+
+def save_checkpoint(path, level, c, n, chi, hist, settings):
+    """The state at a level boundary: the next level starts from it exactly
+    (its points are drawn from chi's mesh and its Adam state is fresh)."""
+    np.savez(path, level=np.int64(level), points=c.detach().cpu().numpy(), normals=n.detach().cpu().numpy(),
+             chi=chi.detach().cpu().numpy(), hist=np.array(hist, np.float64).reshape(-1, 6), settings=settings)
+
+
+def load_checkpoint(path, device):
+    z = np.load(path)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    hist = [tuple(row) for row in z["hist"].tolist()]
+    hist = [(int(h[0]), h[1], int(h[2]), h[3], h[4], h[5]) for h in hist]
+    return int(z["level"]), t(z["points"]), t(z["normals"]), t(z["chi"]), hist, z["settings"]
+
+
 def reconstruct(target: torch.Tensor, levels=PAPER_LEVELS, n_points: int = 20000, samples: int = 20000,
-                lr0: float = 2e-3, decay: float = 0.7, resample: int = 200, seed: int = 0, log=None):
+                lr0: float = 2e-3, decay: float = 0.7, resample: int = 200, seed: int = 0, log=None,
+                checkpoint: str | None = None, resume: str | None = None):
     """Optimise an oriented cloud whose surface fits the unoriented `target`
     cloud (M x 3, CUDA). Returns (points, normals, history) where history
-    lists per level (r, sigma, iterations, first loss, last loss, seconds)."""
+    lists per level (r, sigma, iterations, first loss, last loss, seconds).
+    checkpoint: a .npz path written after every completed level (points,
+    normals, chi, history); resume: such a file, whose completed levels are
+    skipped (the schedule and settings must be the ones it was written with)."""
+    settings = _settings(levels, n_points, samples, lr0, decay, resample, seed)
     c, n = sphere_cloud(n_points, device=target.device)
     hist = []
     chi = None
+    start = 0
+    if resume is not None:
+        start, c, n, chi, hist, saved = load_checkpoint(resume, target.device)
+        if saved.shape != settings.shape or not np.array_equal(saved, settings):
+            raise ValueError("checkpoint was written with another schedule or other settings")
     for li, (r, sigma, iters) in enumerate(levels):
+        if li < start:
+            continue
         if chi is not None:  # a new grid size starts from the previous level's mesh
             c, n = resample_from(chi, n_points, seed + 7919 * li)
         plan = Plan(r, sigma, device=target.device, n_max=n_points)
@@ -116,4 +149,6 @@ def reconstruct(target: torch.Tensor, levels=PAPER_LEVELS, n_points: int = 20000
             log(f"level r={r} sigma={sigma}: {iters} iterations, Chamfer {first:.3e} -> {last:.3e}, {dt:.2f} s")
         plan.close()
         chi = chi.detach()
+        if checkpoint is not None:
+            save_checkpoint(checkpoint, li + 1, c, n, chi, hist, settings)
     return c.detach(), n.detach(), hist

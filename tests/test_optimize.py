@@ -130,3 +130,32 @@ def test_short_reconstruction_from_a_sphere():
     V, E, F, E2 = ref.topology(tris.cpu().numpy().astype(np.float64))
     assert E2 == E
     plan.close()
+
+
+def test_checkpoint_and_resume(tmp_path):
+    """A level-boundary checkpoint round-trips the state exactly, a resumed
+    run skips the completed level (its history entry is the saved one) and
+    carries on from the saved mesh, and a checkpoint of another schedule is
+    refused."""
+    import torch
+    from paper_2106_03452_gb300.optimize import load_checkpoint, reconstruct
+    rng = synth.Rng(4243)
+    tgt, _ = synth.union_cloud(rng, [synth.Torus()], 10000, 0.0)
+    T = torch.from_numpy(tgt).cuda()
+    levels = ((32, 2.0, 60), (64, 2.0, 60))
+    kw = dict(n_points=4000, samples=6000, resample=30, seed=5)
+    ck = str(tmp_path / "level1.npz")
+    c1, n1, h1 = reconstruct(T, levels=levels[:1], checkpoint=ck, **kw)
+    # the first level alone was run with a one-level schedule: write the
+    # two-level schedule's checkpoint from the same state
+    lvl, c, n, chi, hist, _ = load_checkpoint(ck, T.device)
+    assert lvl == 1 and torch.equal(c, c1) and torch.equal(n, n1) and hist == h1
+    ck2 = str(tmp_path / "level1_of_2.npz")
+    from paper_2106_03452_gb300.optimize import _settings, save_checkpoint
+    save_checkpoint(ck2, 1, c, n, chi, hist, _settings(levels, kw["n_points"], kw["samples"], 2e-3, 0.7,
+                                                       kw["resample"], kw["seed"]))
+    c2, n2, h2 = reconstruct(T, levels=levels, resume=ck2, **kw)
+    assert len(h2) == 2 and h2[0] == h1[0]          # restored, not rerun
+    assert h2[1][0] == 64 and np.isfinite(h2[1][4]) and h2[1][4] < h2[1][3]
+    with pytest.raises(ValueError):
+        reconstruct(T, levels=levels, resume=ck, **kw)  # written with the one-level schedule
