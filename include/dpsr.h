@@ -390,6 +390,15 @@ DPSR_API int dpsr_server_submit(dpsr_server server, int r, const float *points,
 DPSR_API int dpsr_server_poll(dpsr_server server, int64_t ticket, int *done);
 /* Block until the ticket completes (or timeout_s passes: DPSR_ETIMEOUT). */
 DPSR_API int dpsr_server_wait(dpsr_server server, int64_t ticket, double timeout_s);
+/* Block until at least one request has completed (or timeout_s passes:
+ * DPSR_ETIMEOUT, *count = 0), then retire up to `max` completed requests in
+ * completion order: their tickets and statuses go to tickets[i] and
+ * statuses[i], i < *count. Tickets already retired by poll or wait are
+ * skipped. One call replaces a poll of every outstanding ticket: a client
+ * with many requests in flight retires them without holding the server's
+ * lock once per ticket. Errors: DPSR_EINVAL (NULL or max < 1). */
+DPSR_API int dpsr_server_wait_any(dpsr_server server, int64_t *tickets, int *statuses, int max,
+                                  double timeout_s, int *count);
 /* Cancel a request that is still queued: it is taken out of the queue, no
  * work for it reaches the GPU, its output buffers are not written, and its
  * poll/wait returns DPSR_ECANCELED (which retires the ticket). Returns

@@ -87,6 +87,7 @@ struct dpsr_server_s {
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<int64_t> queue;
+  std::deque<int64_t> done_q;  // completed tickets in completion order (dpsr_server_wait_any)
   std::map<int64_t, Request> reqs;
   std::vector<Slot> slots;
   std::vector<PooledPlan> pool;
@@ -102,6 +103,21 @@ struct dpsr_server_s {
 };
 
 namespace {
+
+// A request's result is final (caller holds s->mu).
+void finish(dpsr_server s, Request& rq, int status) {
+  rq.status = status;
+  rq.done = true;
+  s->done_q.push_back(rq.ticket);
+  // tickets retired by poll or wait stay in the queue until wait_any passes
+  // them: drop them once they outnumber the live requests (amortised O(1))
+  if (s->done_q.size() > 4096 && s->done_q.size() > 2 * s->reqs.size()) {
+    std::deque<int64_t> keep;
+    for (int64_t t : s->done_q)
+      if (s->reqs.find(t) != s->reqs.end()) keep.push_back(t);
+    s->done_q.swap(keep);
+  }
+}
 
 size_t request_bytes(int r, int64_t N, bool bwd) {
   const size_t grid = (size_t)r * r * r * sizeof(float);
@@ -296,8 +312,7 @@ void worker_main(dpsr_server s) {
         PooledBatch& pb = s->bpool[sl.pbatch];
         for (size_t i = 0; i < sl.group.size(); ++i) {
           Request& rq = s->reqs[sl.group[i]];
-          rq.status = q == cudaSuccess ? dpsr_sync(dpsr_internal_batch_plan(pb.batch, (int)i)) : DPSR_ECUDA;
-          rq.done = true;
+          finish(s, rq, q == cudaSuccess ? dpsr_sync(dpsr_internal_batch_plan(pb.batch, (int)i)) : DPSR_ECUDA);
           s->used -= rq.bytes;
           ++s->completed;
         }
@@ -308,8 +323,7 @@ void worker_main(dpsr_server s) {
       } else {
         Request& rq = s->reqs[sl.ticket];
         PooledPlan& pp = s->pool[sl.pooled];
-        rq.status = q == cudaSuccess ? dpsr_sync(pp.plan) : DPSR_ECUDA;
-        rq.done = true;
+        finish(s, rq, q == cudaSuccess ? dpsr_sync(pp.plan) : DPSR_ECUDA);
         pp.busy = false;
         dpsr_plan_set_stream(pp.plan, nullptr);
         s->used -= rq.bytes;
@@ -332,8 +346,7 @@ void worker_main(dpsr_server s) {
     while (!s->queue.empty()) {
       Request& q = s->reqs[s->queue.front()];
       if (q.bytes > s->budget) {
-        q.status = DPSR_EBUSY;
-        q.done = true;
+        finish(s, q, DPSR_EBUSY);
         s->queue.pop_front();
         s->cv_done.notify_all();
         continue;
@@ -378,8 +391,7 @@ void worker_main(dpsr_server s) {
         sl.claimed = false;
         if (rcs[i] != DPSR_OK) {
           for (Request* q : admit[i].second) {
-            q->status = rcs[i];
-            q->done = true;
+            finish(s, *q, rcs[i]);
             s->used -= q->bytes;
           }
           s->cv_done.notify_all();
@@ -518,6 +530,33 @@ int dpsr_server_wait(dpsr_server s, int64_t ticket, double timeout_s) {
   return st;
 }
 
+int dpsr_server_wait_any(dpsr_server s, int64_t* tickets, int* statuses, int max, double timeout_s,
+                         int* count) {
+  if (!s || !tickets || !statuses || !count || max < 1) return DPSR_EINVAL;
+  *count = 0;
+  std::unique_lock<std::mutex> lk(s->mu);
+  // tickets retired meanwhile by poll or wait are skipped
+  auto ready = [&] {
+    while (!s->done_q.empty() && s->reqs.find(s->done_q.front()) == s->reqs.end()) s->done_q.pop_front();
+    return !s->done_q.empty();
+  };
+  if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 1e9), ready))
+    return DPSR_ETIMEOUT;
+  int n = 0;
+  while (n < max && !s->done_q.empty()) {
+    const int64_t t = s->done_q.front();
+    s->done_q.pop_front();
+    auto it = s->reqs.find(t);
+    if (it == s->reqs.end()) continue;
+    tickets[n] = t;
+    statuses[n] = it->second.status;
+    s->reqs.erase(it);
+    ++n;
+  }
+  *count = n;
+  return DPSR_OK;
+}
+
 int dpsr_server_cancel(dpsr_server s, int64_t ticket) {
   if (!s) return DPSR_EINVAL;
   {
@@ -529,8 +568,7 @@ int dpsr_server_cancel(dpsr_server s, int64_t ticket) {
     auto q = std::find(s->queue.begin(), s->queue.end(), ticket);
     if (it->second.done || q == s->queue.end()) return DPSR_EBUSY;
     s->queue.erase(q);
-    it->second.status = DPSR_ECANCELED;
-    it->second.done = true;
+    finish(s, it->second, DPSR_ECANCELED);
   }
   s->cv_done.notify_all();
   return DPSR_OK;

@@ -34,6 +34,8 @@ _c_int, _c_i64, _c_sz, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_size_t, ctyp
 _PROTOS = {
     "dpsr_plan_create": (_c_int, [_c_int, ctypes.c_float, ctypes.POINTER(_vp)]),
     "dpsr_server_cancel": (_c_int, [_vp, _c_i64]),
+    "dpsr_server_wait_any": (_c_int, [_vp, ctypes.POINTER(_c_i64), ctypes.POINTER(_c_int), _c_int,
+                                      ctypes.c_double, ctypes.POINTER(_c_int)]),
     "dpsr_debug_checks": (_c_int, []),
     "dpsr_debug_check_selftest": (_c_int, []),
     "dpsr_fp32_fma_peak": (_c_int, [_c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -139,6 +141,19 @@ def dpsr_plan_create_box(r: int, sigma: float, box) -> int:
     b = None if box is None else (ctypes.c_float * 3)(*[float(v) for v in box])
     check(load().dpsr_plan_create_box(int(r), float(sigma), b, ctypes.byref(h)), "dpsr_plan_create_box")
     return h.value
+
+
+def dpsr_server_wait_any(server: int, max_n: int = 64, timeout_s: float = 0.0):
+    """[(ticket, status), ...] of up to max_n completed requests, retired in
+    completion order; [] when timeout_s passes first."""
+    t = (_c_i64 * max_n)()
+    st = (_c_int * max_n)()
+    n = _c_int()
+    rc = load().dpsr_server_wait_any(server, t, st, int(max_n), float(timeout_s), ctypes.byref(n))
+    if rc == DPSR_ETIMEOUT:
+        return []
+    check(rc, "dpsr_server_wait_any")
+    return [(int(t[i]), int(st[i])) for i in range(n.value)]
 
 
 def dpsr_server_cancel(server: int, ticket: int) -> int:

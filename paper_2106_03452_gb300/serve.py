@@ -43,6 +43,9 @@ class Server:
     def wait(self, ticket, timeout_s=0.0) -> int:
         return L.dpsr_server_wait(self.handle, ticket, timeout_s)
 
+    def wait_any(self, max_n=64, timeout_s=0.0):
+        return L.dpsr_server_wait_any(self.handle, max_n, timeout_s)
+
     def cancel(self, ticket) -> int:
         return L.dpsr_server_cancel(self.handle, ticket)
 
@@ -121,27 +124,23 @@ def replay(trace, server: Server, pool: InputPool, realtime=True, n_max=200000, 
     stop = threading.Event()
 
     def completer():
+        # completed requests come back in batches from one blocking call
+        # (dpsr_server_wait_any), not from a poll of every outstanding ticket
         while not stop.is_set() or pending:
-            with lock:
-                items = list(pending.items())
-            if not items:
-                time.sleep(0.0002)
-                continue
-            any_done = False
-            for t, rec in items:
-                done, st = server.poll(t)
-                if done:
-                    rec["done"] = time.perf_counter() - t0
-                    rec["status"] = st
-                    ring.put(rec["r"], rec["bwd"], rec.pop("bufs"))
-                    if on_done is not None:
-                        on_done(rec)
-                    with lock:
-                        del pending[t]
-                        results.append(rec)
-                    any_done = True
-            if not any_done:
-                time.sleep(0.0001)
+            got = server.wait_any(64, 0.02)
+            now = time.perf_counter() - t0
+            for t, st in got:
+                with lock:
+                    rec = pending.pop(t, None)
+                if rec is None:  # not one of this replay's requests
+                    continue
+                rec["done"] = now
+                rec["status"] = st
+                ring.put(rec["r"], rec["bwd"], rec.pop("bufs"))
+                if on_done is not None:
+                    on_done(rec)
+                with lock:
+                    results.append(rec)
 
     th = threading.Thread(target=completer, daemon=True)
     t0 = time.perf_counter()

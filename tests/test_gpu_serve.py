@@ -212,3 +212,35 @@ def _run_catching(fn):
     except Exception as exc:  # the producer's own failure, recorded for the test
         return exc
     return None
+
+
+def test_wait_any_retires_in_completion_batches():
+    """dpsr_server_wait_any hands back every completed request once, with its
+    status, and skips tickets that poll or wait already retired."""
+    import torch
+    from paper_2106_03452_gb300 import libdpsr as L
+    from paper_2106_03452_gb300 import serve
+    pool = serve.InputPool(n_clouds=2, n_max=30000, rs=(64, 128))
+    srv = serve.Server(8 << 30, slots=4)
+    keep, tickets = [], []
+    for i in range(12):
+        r = 64 if i % 2 else 128
+        pts, nrm = pool.inputs(i, 30000)
+        chi = torch.empty((r, r, r)).pin_memory()
+        keep.append(chi)
+        tickets.append(srv.submit(r, pts, nrm, chi))
+    assert srv.wait(tickets[0], 120.0) == 0          # retired by wait: never returned below
+    seen = {}
+    while len(seen) < 11:
+        got = srv.wait_any(5, 60.0)
+        assert got, "timed out"
+        assert len(got) <= 5
+        for t, st in got:
+            assert t not in seen and st == 0
+            seen[t] = st
+    assert sorted(seen) == sorted(tickets[1:])
+    assert srv.wait_any(5, 0.05) == []               # nothing left
+    with pytest.raises(L.DPSRError):
+        L.check(L.dpsr_server_wait(srv.handle, tickets[3], 1.0), "wait")   # already retired
+    assert all(torch.isfinite(c).all() for c in keep)
+    srv.close()
