@@ -678,8 +678,24 @@ def oracle_baseline(w, budget_s=12.0):
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "solves/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{n} whole fwd+bwd solves of the r=128 workload (FP64, OpenMP over FFT pencils)"}
+    out = {"value": n / dt, "unit": "solves/s", "cores": oracle.threads(), "kind": "oracle",
+           "sample": f"{n} whole fwd+bwd solves of the r=128 workload (FP64, OpenMP over FFT pencils)"}
+    # the same on one core (a shorter sample: at least one whole solve)
+    all_cores = oracle.threads()
+    oracle.set_threads(1)
+    n1 = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.forward(r, sigma, w["points"], w["normals"])
+        oracle.backward(r, sigma, w["points"], w["normals"], w["dchi"])
+        n1 += 1
+        if time.perf_counter() - t0 >= budget_s / 2:
+            break
+    dt1 = time.perf_counter() - t0
+    oracle.set_threads(all_cores)
+    out["single_thread"] = {"value": n1 / dt1, "unit": "solves/s", "cores": 1,
+                            "sample": f"{n1} whole fwd+bwd solves of the r=128 workload on one thread"}
+    return out
 
 
 def run_reference(args):

@@ -69,9 +69,11 @@ def _load():
             lib.oracle_dpsr_backward_box.argtypes = [ctypes.c_int, ctypes.c_double, i64, dp, dp, dp,
                                                      dp, dp, dp]
             for f in ("oracle_dpsr_forward_box", "oracle_dpsr_backward_box", "oracle_dpsr_backward_terms", "oracle_fft3", "oracle_splat", "oracle_gather", "oracle_dpsr_forward",
-                      "oracle_dpsr_backward", "oracle_threads"):
+                      "oracle_dpsr_backward", "oracle_threads", "oracle_set_threads"):
                 getattr(lib, f).restype = ctypes.c_int
             lib.oracle_threads.argtypes = []
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_set_threads.restype = None
             _lib = lib
     return _lib
 
@@ -97,6 +99,11 @@ def _check(code, what):
 def threads() -> int:
     """OpenMP threads the oracle uses (its FFT pencils run in parallel)."""
     return int(_load().oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads for the oracle's parallel loops from now on."""
+    _load().oracle_set_threads(int(n))
 
 
 def fft3(g: np.ndarray, inverse: bool = False) -> np.ndarray:

@@ -79,6 +79,17 @@ int oracle_threads(void)
 #endif
 }
 
+/* Threads for the oracle's parallel loops from now on (n >= 1); for timing
+ * the oracle on one core and on all of them. */
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* 1D complex FFT: textbook iterative radix-2 Cooley-Tukey, in place.        */
 /* sign = -1 is the forward transform of Eq. A3, +1 the inverse kernel of    */

@@ -402,3 +402,79 @@ def test_box_backward_finite_differences(oracle):
         nmi[i, d] -= h
         fd = (L(pts, npl) - L(pts, nmi)) / (2 * h)
         assert abs(fd - dn[i, d]) <= 1e-6 * scale_n, (i, d, fd, dn[i, d])
+
+
+# --------------------------------------------------------------------------
+# One point on a vertex with n = e_a: V_a is a unit impulse there, so chi'
+# is the circular shift of the kernel K_a = Re IDFT(H_a) (Eq. 3), written
+# out here as direct sums over every frequency.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("a", [0, 1, 2])
+def test_single_point_kernel(oracle, a):
+    r, sigma = 8, 1.5
+    j0 = np.array([3, 5, 6])
+    pts = (j0 / r)[None, :]
+    nrm = np.zeros((1, 3))
+    nrm[0, a] = 1.0
+    _, chip, _, _ = oracle.forward(r, sigma, pts, nrm, full=True)
+    f = np.where(np.arange(r) < r // 2, np.arange(r), np.arange(r) - r).astype(float)
+    K = np.zeros((r, r, r))
+    idx = np.arange(r)
+    for kx in range(r):
+        for ky in range(r):
+            for kz in range(r):
+                k = (kx, ky, kz)
+                if k == (0, 0, 0) or k[a] == r // 2:
+                    continue
+                u = np.array([r // 2 if k[d] == r // 2 else f[k[d]] for d in range(3)], float)
+                g = math.exp(-2 * sigma ** 2 * float(u @ u) / r ** 2)
+                H = g * 1j * u[a] / (-2 * math.pi * float(u @ u))
+                ph = np.exp(2j * math.pi * (kx * idx[:, None, None] + ky * idx[None, :, None]
+                                            + kz * idx[None, None, :]) / r)
+                K += np.real(H * ph) / r ** 3
+    expect = np.roll(K, tuple(j0), axis=(0, 1, 2))
+    assert np.max(np.abs(chip - expect)) <= 1e-12 * np.max(np.abs(expect))
+
+
+# --------------------------------------------------------------------------
+# The spectral identity of Eq. 1 / Eq. 3 on the oracle's own chi': for
+# k != 0 and no axis at Nyquist, -4 pi^2 |u|^2 chi~'(k) = 2 pi i g(k) u . V~(k),
+# with chi~' and V~ taken by numpy's FFT of chi' and of the rasterized field.
+# --------------------------------------------------------------------------
+def test_spectral_identity(oracle):
+    r, sigma = 16, 2.0
+    pts, nrm = _cloud(61, 200, -0.1, 1.1)
+    _, chip, _, _ = oracle.forward(r, sigma, pts, nrm, full=True)
+    V = oracle.splat(r, pts, nrm)                       # 3 x r^3
+    C = np.fft.fftn(chip)
+    Vh = [np.fft.fftn(V[d]) for d in range(3)]
+    f = np.fft.fftfreq(r, 1.0 / r)
+    U = np.stack(np.meshgrid(f, f, f, indexing="ij"))
+    u2 = (U ** 2).sum(0)
+    g = np.exp(-2 * sigma ** 2 * u2 / r ** 2)
+    lhs = -4 * math.pi ** 2 * u2 * C
+    rhs = 2j * math.pi * g * sum(U[d] * Vh[d] for d in range(3))
+    ok = (u2 > 0) & np.all(np.abs(U) < r // 2, axis=0)
+    assert np.max(np.abs(lhs - rhs)[ok]) <= 1e-10 * np.max(np.abs(rhs[ok]))
+
+
+# --------------------------------------------------------------------------
+# The whole linearisation at once: the directional derivative of
+# L = <dchi, chi> along a random direction in (points, normals), by central
+# differences, equals <grad, direction> from the backward pass.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("r,sigma,N", [(8, 1.0, 30), (16, 2.0, 60)])
+def test_jvp_matches_vjp(oracle, r, sigma, N):
+    rng = synth.Rng(71 + r)
+    u = 0.15 + 0.7 * rng.uniform(N, 3)
+    f = u * r - np.floor(u * r)
+    pts = (np.floor(u * r) + np.clip(f, 0.01, 0.99)) / r
+    nrm = rng.normal(N, 3)
+    G = rng.normal(r, r, r)
+    dp, dn = oracle.backward(r, sigma, pts, nrm, G)
+    Dp, Dn = rng.normal(N, 3), rng.normal(N, 3)
+    h = 1e-7
+    L = lambda p, n: float(np.sum(G * oracle.forward(r, sigma, p, n)))
+    fd = (L(pts + h * Dp, nrm + h * Dn) - L(pts - h * Dp, nrm - h * Dn)) / (2 * h)
+    an = float(np.sum(dp * Dp) + np.sum(dn * Dn))
+    assert abs(fd - an) <= 1e-6 * max(abs(an), np.sum(np.abs(dp * Dp)) + np.sum(np.abs(dn * Dn)))
