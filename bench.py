@@ -376,6 +376,11 @@ def run_gpu(args):
     l2_ach = per[dom]["bytes"] / (per[dom]["ms"] / 1e3) / 1e9
     solve_gbs = solve_bytes_model(r, N) / (ms_max / args.steps / 1e3) / 1e9
 
+    # ---------------- context: the same layer in plain PyTorch ops ----------------
+    torch_ctx = None
+    if not args.no_torch_context and rank == 0:
+        torch_ctx = torch_ops_context(dev)
+
     # ---------------- serving: Poisson arrivals at 200 req/s ----------------
     serving = None
     if not args.no_serve and rank == 0:
@@ -420,6 +425,7 @@ def run_gpu(args):
             "batched": batched,
             "train": train,
             "optimize": optim,
+            "torch_ops_context": torch_ctx,
             "serving": serving,
             "cpu_baseline": cpu,
         }
@@ -663,6 +669,114 @@ def bench_serving(args):
     return out
 
 
+def torch_ops_dpsr(points, normals, r: int, sigma: float):
+    """Context baseline only (never a product path): the DPSR layer written
+    with plain PyTorch GPU ops from Sec. 3.1 (Eq. A1-A2 splat by index_add,
+    Eq. A3 torch.fft.rfftn, the solve of Eq. 3, Eq. A8 irfftn, Eq. 4
+    normalisation with a trilinear gather), differentiated by autograd. The
+    readings are the library's: periodic unit cube, integer frequencies, DC
+    zero, the a-th term zero at a Nyquist index with |u_a| = r/2 there, the
+    shifted scale s = chi'(0) - mu."""
+    import math
+
+    import torch
+    dev = points.device
+    x = points * r
+    fl = torch.floor(x)
+    t = x - fl
+    i0 = fl.long() % r
+    i1 = (i0 + 1) % r
+    corners = []
+    for d in range(8):
+        dx, dy, dz = d >> 2, (d >> 1) & 1, d & 1
+        w = ((t[:, 0] if dx else 1 - t[:, 0]) * (t[:, 1] if dy else 1 - t[:, 1]) *
+             (t[:, 2] if dz else 1 - t[:, 2]))
+        idx = ((i1[:, 0] if dx else i0[:, 0]) * r + (i1[:, 1] if dy else i0[:, 1])) * r + \
+              (i1[:, 2] if dz else i0[:, 2])
+        corners.append((w, idx))
+    V = torch.zeros(3, r ** 3, device=dev, dtype=points.dtype)
+    for w, idx in corners:
+        V = V.index_add(1, idx, (w[:, None] * normals).t())
+    Vh = torch.fft.rfftn(V.view(3, r, r, r), dim=(1, 2, 3))
+    k = torch.arange(r, device=dev)
+    f = torch.where(k < r // 2, k, k - r).float()
+    fa = torch.where(k == r // 2, torch.full_like(f, r // 2), f)     # |u| at Nyquist
+    kz = torch.arange(r // 2 + 1, device=dev)
+    fz = kz.float()
+    U = [f.view(r, 1, 1), f.view(1, r, 1), torch.where(kz == r // 2, torch.zeros_like(fz), fz).view(1, 1, -1)]
+    A = [fa.view(r, 1, 1), fa.view(1, r, 1), fz.view(1, 1, -1)]
+    U[0] = torch.where((k == r // 2).view(r, 1, 1), torch.zeros_like(U[0]), U[0])
+    U[1] = torch.where((k == r // 2).view(1, r, 1), torch.zeros_like(U[1]), U[1])
+    u2 = A[0] ** 2 + A[1] ** 2 + A[2] ** 2
+    g = torch.exp(-2.0 * sigma ** 2 * u2 / r ** 2)
+    div = U[0] * Vh[0] + U[1] * Vh[1] + U[2] * Vh[2]
+    H = g / (-2.0 * math.pi * torch.where(u2 > 0, u2, torch.ones_like(u2)))
+    H = torch.where(u2 > 0, H, torch.zeros_like(H))
+    chih = 1j * div * H
+    chip = torch.fft.irfftn(chih, s=(r, r, r), dim=(0, 1, 2))
+    flat = chip.reshape(-1)
+    mu = sum(w * flat[idx] for w, idx in corners).mean()
+    s = flat[0] - mu
+    return 0.5 / s.abs() * (chip - mu)
+
+
+def torch_ops_context(dev, steps=10, warmup=3):
+    """Fwd+bwd solves/s of torch_ops_dpsr on this GPU at the r = 128 and
+    r = 256 workloads (L2 flushed between steps, CUDA events)."""
+    import torch
+
+    from paper_2106_03452_gb300 import synth
+    out = {"what": "the DPSR layer in plain PyTorch ops (cuFFT rfftn/irfftn, index_add splat, "
+                   "autograd backward): context, not a product path"}
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    for name, w in (("r128", synth.workload_ellipsoids_r128()), ("r256", synth.workload_torus_r256())):
+        r, sigma = w["r"], w["sigma"]
+        P = torch.from_numpy(w["points"]).to(dev).requires_grad_(True)
+        Nn = torch.from_numpy(w["normals"]).to(dev).requires_grad_(True)
+        G = torch.randn((r,) * 3, device=dev)
+
+        def step():
+            chi = torch_ops_dpsr(P, Nn, r, sigma)
+            dp, dn = torch.autograd.grad((chi * G).sum(), (P, Nn))
+            return dp, dn
+
+        def timed_ms(fn):
+            for _ in range(warmup):
+                fn()
+            torch.cuda.synchronize()
+            ms = 0.0
+            for _ in range(steps):
+                flush.fill_(1.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                b.record()
+                torch.cuda.synchronize()
+                ms += a.elapsed_time(b)
+            return ms / steps
+
+        res = {}
+        ms = timed_ms(step)
+        res["eager"] = {"solves_per_s": 1e3 / ms, "ms_per_step": ms}
+        # the same step captured as one CUDA graph (removes the per-op launch cost)
+        try:
+            side = torch.cuda.Stream(dev)
+            side.wait_stream(torch.cuda.current_stream(dev))
+            with torch.cuda.stream(side):
+                for _ in range(warmup):
+                    step()
+            torch.cuda.current_stream(dev).wait_stream(side)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                step()
+            ms = timed_ms(graph.replay)
+            res["graph"] = {"solves_per_s": 1e3 / ms, "ms_per_step": ms}
+        except Exception as exc:  # the context number is optional: say why it is missing
+            res["graph"] = {"unavailable": f"{type(exc).__name__}: {exc}"[:200]}
+        out[name] = res
+    return out
+
+
 def oracle_baseline(w, budget_s=12.0):
     """The FP64 oracle as it stands, forward + backward, on this host's cores:
     repeats whole solves of the workload until budget_s has passed."""
@@ -747,6 +861,7 @@ def main():
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-optimize", action="store_true")
     ap.add_argument("--no-loop", action="store_true")
+    ap.add_argument("--no-torch-context", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-loop-seconds", type=float, default=15.0)
     ap.add_argument("--serve-slots", type=int, default=8)
