@@ -431,6 +431,21 @@ DPSR_API const char *dpsr_strerror(int status);
  * (a defect), DPSR_EINVAL or DPSR_ECUDA on errors. */
 DPSR_API int dpsr_check_bounded_wait(double limit_s);
 
+/* Stage read-back for tests (Sec. 3.1 / Eq. A3, Eq. 3): copies one of the
+ * forward pass's intermediate spectra to the host buffer out_host, which
+ * receives r * r * (r/2 + 1) complex64 values laid out [x][ky][kz] (kz =
+ * 0 .. r/2, the z half spectrum; x a grid coordinate, not transformed):
+ *   which = 0: D = i u_y FFT_yz(V_y) + i u_z FFT_yz(V_z) (u in integer
+ *              cycles, zero at a Nyquist index);
+ *   which = 1: C = FFT_yz(V_x);
+ *   which = 2: W~ = FFT_yz(w), w the splat of ones (the weights of Eq. 4);
+ *   which = 3: r * FFT_yz(chi'), the unnormalised x-inverse of chi~.
+ * FFT_yz: unnormalised DFT over y (length r) and the z half spectrum. Valid
+ * after dpsr_forward and until the next dpsr_backward on the plan, which
+ * reuses the buffers (DPSR_ESTATE otherwise). Synchronises the plan's
+ * stream. Errors: DPSR_EINVAL (which outside 0..3, NULL), DPSR_ECUDA. */
+DPSR_API int dpsr_debug_read_spectrum(dpsr_plan plan, int which, void *out_host);
+
 /* Debug builds. A library compiled with DPSR_DEBUG_CHECKS (the build
  * script's debug variant; the Python binding loads it when the environment
  * sets DPSR_DEBUG_CHECKS=1) checks every data-dependent index of the point

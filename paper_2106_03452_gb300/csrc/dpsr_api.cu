@@ -49,6 +49,7 @@ struct dpsr_plan_s {
   int64_t n_cap = 0;
   Solve s = {};
   bool have_fwd = false;
+  bool spectra_fresh = false;  // the forward's spectra are intact (no backward since)
   int last_launches = 0;
   // device staging for the host-buffer variants
   void* host_io = nullptr;
@@ -677,6 +678,7 @@ int dpsr_forward(dpsr_plan p, const float* points, const float* normals, int64_t
   p->s.normals = normals;
   p->s.chi = chi_out;
   p->have_fwd = true;
+  p->spectra_fresh = true;
   return DPSR_OK;
 }
 
@@ -687,6 +689,7 @@ int dpsr_backward(dpsr_plan p, const float* dchi, float* dpoints, float* dnormal
   if (!p->have_fwd) return DPSR_ESTATE;
   DeviceGuard dg(p->device);
   if (!dg.ok) return DPSR_ECUDA;
+  p->spectra_fresh = false;  // the backward reuses the forward's spectral buffers
   PdlScope pdl(p->profile);
   Solve s = p->s;
   s.dchi = dchi;
@@ -767,6 +770,22 @@ int dpsr_get_loss(dpsr_plan p, double* loss) {
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) return DPSR_ECUDA;
   if (cudaMemcpy(loss, &p->s.sc->loss, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
     return DPSR_ECUDA;
+  return DPSR_OK;
+}
+
+int dpsr_debug_read_spectrum(dpsr_plan p, int which, void* out_host) {
+  if (!p || !out_host || which < 0 || which > 3) return DPSR_EINVAL;
+  if (!p->have_fwd || !p->spectra_fresh) return DPSR_ESTATE;
+  DeviceGuard dg(p->device);
+  if (!dg.ok || cudaStreamSynchronize(p->stream) != cudaSuccess) return DPSR_ECUDA;
+  static const int buf[4] = {dpsr::kSpD, dpsr::kSpC, dpsr::kSpW, dpsr::kSpChi};
+  const int r = p->r;
+  const size_t w = sizeof(float2) * (size_t)(r / 2 + 1);
+  if (cudaMemcpy2D(out_host, w, p->s.spec[buf[which]], sizeof(float2) * (size_t)dpsr::kpitch(r), w,
+                   (size_t)r * r, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return DPSR_ECUDA;
+  }
   return DPSR_OK;
 }
 

@@ -37,6 +37,7 @@ _PROTOS = {
     "dpsr_server_wait_any": (_c_int, [_vp, ctypes.POINTER(_c_i64), ctypes.POINTER(_c_int), _c_int,
                                       ctypes.c_double, ctypes.POINTER(_c_int)]),
     "dpsr_debug_checks": (_c_int, []),
+    "dpsr_debug_read_spectrum": (_c_int, [_vp, _c_int, _vp]),
     "dpsr_debug_check_selftest": (_c_int, []),
     "dpsr_fp32_fma_peak": (_c_int, [_c_int, ctypes.POINTER(ctypes.c_double)]),
     "dpsr_plan_create_box": (_c_int, [_c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_vp)]),
@@ -163,6 +164,15 @@ def dpsr_server_cancel(server: int, ticket: int) -> int:
     if rc not in (DPSR_OK, DPSR_EBUSY):
         raise DPSRError(rc, "dpsr_server_cancel")
     return rc
+
+
+def dpsr_debug_read_spectrum(plan: int, which: int, r: int):
+    """One of the forward's intermediate spectra as a complex64 numpy array
+    [x][ky][kz], kz = 0 .. r/2 (see include/dpsr.h)."""
+    import numpy as np
+    out = np.empty((r, r, r // 2 + 1), np.complex64)
+    check(load().dpsr_debug_read_spectrum(plan, int(which), out.ctypes.data), "dpsr_debug_read_spectrum")
+    return out
 
 
 def dpsr_debug_checks() -> bool:
