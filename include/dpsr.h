@@ -439,11 +439,16 @@ DPSR_API int dpsr_check_bounded_wait(double limit_s);
  *              cycles, zero at a Nyquist index);
  *   which = 1: C = FFT_yz(V_x);
  *   which = 2: W~ = FFT_yz(w), w the splat of ones (the weights of Eq. 4);
- *   which = 3: r * FFT_yz(chi'), the unnormalised x-inverse of chi~.
- * FFT_yz: unnormalised DFT over y (length r) and the z half spectrum. Valid
- * after dpsr_forward and until the next dpsr_backward on the plan, which
- * reuses the buffers (DPSR_ESTATE otherwise). Synchronises the plan's
- * stream. Errors: DPSR_EINVAL (which outside 0..3, NULL), DPSR_ECUDA. */
+ *   which = 3: r * FFT_yz(chi'), the unnormalised x-inverse of chi~;
+ * after dpsr_backward, the adjoint spectrum of Eq. 3 (G_bar of Eq. 4's
+ * adjoint, F = G(k) FFT3(G_bar) / r^3 with G(k) = g(k) / (-2 pi |u|^2)):
+ *   which = 4: Q1 = the unnormalised x-inverse of F;
+ *   which = 5: Q2 = the unnormalised x-inverse of -i u_x F.
+ * FFT_yz: unnormalised DFT over y (length r) and the z half spectrum. 0..3
+ * are valid after dpsr_forward until the next dpsr_backward, 4..5 after
+ * dpsr_backward until the next dpsr_forward (DPSR_ESTATE otherwise).
+ * Synchronises the plan's stream. Errors: DPSR_EINVAL (which outside 0..5,
+ * NULL), DPSR_ECUDA. */
 DPSR_API int dpsr_debug_read_spectrum(dpsr_plan plan, int which, void *out_host);
 
 /* Debug builds. A library compiled with DPSR_DEBUG_CHECKS (the build

@@ -49,7 +49,7 @@ struct dpsr_plan_s {
   int64_t n_cap = 0;
   Solve s = {};
   bool have_fwd = false;
-  bool spectra_fresh = false;  // the forward's spectra are intact (no backward since)
+  int spectra = 0;  // what the spectral buffers hold: 1 the forward's, 2 the backward's
   int last_launches = 0;
   // device staging for the host-buffer variants
   void* host_io = nullptr;
@@ -641,6 +641,7 @@ int dpsr_forward(dpsr_plan p, const float* points, const float* normals, int64_t
   if (((uintptr_t)chi_out & 15) != 0) return DPSR_EINVAL;  // read back by vector loads
   DeviceGuard dg(p->device);
   if (!dg.ok) return DPSR_ECUDA;
+  p->spectra = 0;
   int rc = grow_points(p, N);
   if (rc != DPSR_OK) return rc;
   PdlScope pdl(p->profile);
@@ -678,7 +679,7 @@ int dpsr_forward(dpsr_plan p, const float* points, const float* normals, int64_t
   p->s.normals = normals;
   p->s.chi = chi_out;
   p->have_fwd = true;
-  p->spectra_fresh = true;
+  p->spectra = 1;
   return DPSR_OK;
 }
 
@@ -689,7 +690,7 @@ int dpsr_backward(dpsr_plan p, const float* dchi, float* dpoints, float* dnormal
   if (!p->have_fwd) return DPSR_ESTATE;
   DeviceGuard dg(p->device);
   if (!dg.ok) return DPSR_ECUDA;
-  p->spectra_fresh = false;  // the backward reuses the forward's spectral buffers
+  p->spectra = 0;  // the backward reuses the forward's spectral buffers
   PdlScope pdl(p->profile);
   Solve s = p->s;
   s.dchi = dchi;
@@ -714,6 +715,7 @@ int dpsr_backward(dpsr_plan p, const float* dchi, float* dpoints, float* dnormal
   }
   // plane pass(es) (+ scalars), x-pass, inverse plane pass(es), combine
   p->last_launches = 2 + dpsr::plane_launches(p->C[2]) + dpsr::plane_launches(p->C[3]);
+  p->spectra = 2;
   cudaEventRecord(p->done_ev, st);
   return DPSR_OK;
 }
@@ -774,11 +776,11 @@ int dpsr_get_loss(dpsr_plan p, double* loss) {
 }
 
 int dpsr_debug_read_spectrum(dpsr_plan p, int which, void* out_host) {
-  if (!p || !out_host || which < 0 || which > 3) return DPSR_EINVAL;
-  if (!p->have_fwd || !p->spectra_fresh) return DPSR_ESTATE;
+  if (!p || !out_host || which < 0 || which > 5) return DPSR_EINVAL;
+  if (p->spectra != (which < 4 ? 1 : 2)) return DPSR_ESTATE;
   DeviceGuard dg(p->device);
   if (!dg.ok || cudaStreamSynchronize(p->stream) != cudaSuccess) return DPSR_ECUDA;
-  static const int buf[4] = {dpsr::kSpD, dpsr::kSpC, dpsr::kSpW, dpsr::kSpChi};
+  static const int buf[6] = {dpsr::kSpD, dpsr::kSpC, dpsr::kSpW, dpsr::kSpChi, dpsr::kSpD, dpsr::kSpChi};
   const int r = p->r;
   const size_t w = sizeof(float2) * (size_t)(r / 2 + 1);
   if (cudaMemcpy2D(out_host, w, p->s.spec[buf[which]], sizeof(float2) * (size_t)dpsr::kpitch(r), w,

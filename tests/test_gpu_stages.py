@@ -60,10 +60,38 @@ def test_forward_stages(oracle, monkeypatch, path, r, N):
     P = r * _fft_yz(chip)
     for name, g, e in (("D", got[0], D), ("C", got[1], C), ("W", got[2], W), ("P", got[3], P)):
         assert _rel(g, e) <= (5e-6 if name != "P" else 1e-5), (name, _rel(g, e))
-    # the backward reuses these buffers: read-back refused after it
-    plan.backward(torch.from_numpy(rng.normal(r, r, r).astype(np.float32)).cuda())
+    # Backward: G_bar = alpha dchi + s_bar e_0 + (mu_bar / N) w (the adjoint
+    # of Eq. 4), F = G(k) FFT3(G_bar) / r^3, Q1 = r IFFT_x(F), Q2 = r IFFT_x(-i u_x F)
+    with pytest.raises(L.DPSRError) as e:
+        L.dpsr_debug_read_spectrum(plan.handle, 4, r)  # no backward yet
+    assert e.value.code == L.DPSR_ESTATE
+    dchi = rng.normal(r, r, r).astype(np.float32)
+    plan.backward(torch.from_numpy(dchi).cuda())
     assert plan.sync() == 0
     with pytest.raises(L.DPSRError) as e:
-        L.dpsr_debug_read_spectrum(plan.handle, 0, r)
+        L.dpsr_debug_read_spectrum(plan.handle, 0, r)   # the backward reused the buffers
     assert e.value.code == L.DPSR_ESTATE
+    q1, q2 = (L.dpsr_debug_read_spectrum(plan.handle, k, r).astype(np.complex128) for k in (4, 5))
+    _, chip, mu, s_ = oracle.forward(r, sigma, p64, n64, full=True)
+    g = dchi.astype(np.float64)
+    alpha = 0.5 / abs(s_)
+    s_bar = -0.5 * np.sign(s_) * float(np.sum(g * (chip - mu))) / s_ ** 2
+    mu_bar = -alpha * float(np.sum(g)) - s_bar
+    Gb = alpha * g + (mu_bar / N) * w
+    Gb[0, 0, 0] += s_bar
+    Gh = np.fft.fftn(np.fft.rfft(Gb, axis=2), axes=(0, 1))
+    ua = np.where(k < r // 2, k, k - r).astype(float)
+    ua2 = ua.copy()
+    ua2[r // 2] = r // 2
+    uzz = np.arange(r // 2 + 1, dtype=float)
+    U2 = ua2[:, None, None] ** 2 + ua2[None, :, None] ** 2 + uzz[None, None, :] ** 2
+    Gk = np.exp(-2 * sigma ** 2 * U2 / r ** 2) / (-2 * np.pi * np.where(U2 > 0, U2, 1.0))
+    Gk[0, 0, 0] = 0.0
+    F = Gk * Gh / r ** 3
+    ux = ua.copy()
+    ux[r // 2] = 0.0
+    Q1 = r * np.fft.ifft(F, axis=0)
+    Q2 = r * np.fft.ifft(-1j * ux[:, None, None] * F, axis=0)
+    assert _rel(q1, Q1) <= 2e-5, ("Q1", _rel(q1, Q1))
+    assert _rel(q2, Q2) <= 2e-5, ("Q2", _rel(q2, Q2))
     plan.close()
