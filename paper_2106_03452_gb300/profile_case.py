@@ -4,7 +4,7 @@
     python -m paper_2106_03452_gb300.profile_case --batch --reps 3
 
 Workloads: r=32 sphere (N=3000), r=128 ellipsoids (N=20000), r=256 torus +
-ellipsoids (N=100000), all sigma = 2. Prints the event-timed ms per solve and
+ellipsoids (N=100000; --r 512 solves the same cloud on a 512^3 grid), all sigma = 2. Prints the event-timed ms per solve and
 the per-kernel profile of the library. --batch runs the batched workload
 instead (32 clouds, r in {64, 128}, fwd+bwd): one eager run (which tunes),
 then --reps plain (not graph) runs, each launch visible to a profiler.
@@ -24,7 +24,7 @@ def main():
     from paper_2106_03452_gb300.dpsr import Plan
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--r", type=int, default=256, choices=[32, 128, 256])
+    ap.add_argument("--r", type=int, default=256, choices=[32, 128, 256, 512])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--fwd-only", action="store_true")
     ap.add_argument("--batch", action="store_true")
@@ -32,8 +32,8 @@ def main():
     if a.batch:
         return run_batch(a.reps)
     w = {32: synth.workload_sphere_r32, 128: synth.workload_ellipsoids_r128,
-         256: synth.workload_torus_r256}[a.r]()
-    r = w["r"]
+         256: synth.workload_torus_r256, 512: synth.workload_torus_r256}[a.r]()
+    r = a.r  # 512: the r = 256 torus workload (N = 100 000) on a 512^3 grid
     plan = Plan(r, w["sigma"], n_max=w["points"].shape[0])
     P = torch.from_numpy(w["points"]).cuda()
     Nn = torch.from_numpy(w["normals"]).cuda()
