@@ -83,8 +83,9 @@ DPSR_API int dpsr_plan_create(int r, float sigma, dpsr_plan *out);
  * and the Gaussian keeps sigma in grid units on every axis,
  * g = exp(-2 sigma^2 sum_d f_d^2 / r^2). dL/dpoints come back in box
  * coordinates. The normalisation of Eq. 4 is unchanged. Errors: DPSR_EINVAL
- * for a bad box, else as dpsr_plan_create. The batched, serving, static and
- * mesh entry points work on the unit cube. */
+ * for a bad box, else as dpsr_plan_create. Batches take a box per instance
+ * (dpsr_batch_create_box); the serving, static and mesh entry points work on
+ * the unit cube. */
 DPSR_API int dpsr_plan_create_box(int r, float sigma, const float *box, dpsr_plan *out);
 
 /* Free the plan and its workspace (synchronises its stream first). */
@@ -324,6 +325,12 @@ DPSR_API int dpsr_forward_static(int r, float sigma, const float *points, const 
 typedef struct dpsr_batch_s *dpsr_batch;
 DPSR_API int dpsr_batch_create(int count, const int *r, const float *sigma, const int64_t *n_max,
                                dpsr_batch *out);
+/* The same with a periodic box per instance (as dpsr_plan_create_box):
+ * box holds 3 side lengths per instance, count x 3 floats (NULL: every
+ * instance on the unit cube). Instances of one grid size still share every
+ * launch; each keeps its own spectral tables and coordinate scaling. */
+DPSR_API int dpsr_batch_create_box(int count, const int *r, const float *sigma, const float *box,
+                                   const int64_t *n_max, dpsr_batch *out);
 DPSR_API int dpsr_batch_destroy(dpsr_batch batch);
 /* A non-default stream is required for dpsr_batch_graph_launch (capture). */
 DPSR_API int dpsr_batch_set_stream(dpsr_batch batch, void *stream);

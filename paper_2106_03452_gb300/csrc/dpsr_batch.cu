@@ -229,6 +229,11 @@ extern "C" {
 
 int dpsr_batch_create(int count, const int* r, const float* sigma, const int64_t* n_max,
                       dpsr_batch* out) {
+  return dpsr_batch_create_box(count, r, sigma, nullptr, n_max, out);
+}
+
+int dpsr_batch_create_box(int count, const int* r, const float* sigma, const float* box,
+                          const int64_t* n_max, dpsr_batch* out) {
   if (!out || count < 1 || !r || !sigma || !n_max) return DPSR_EINVAL;
   *out = nullptr;
   dpsr_batch b = new (std::nothrow) dpsr_batch_s();
@@ -240,7 +245,7 @@ int dpsr_batch_create(int count, const int* r, const float* sigma, const int64_t
   b->nmax.assign(n_max, n_max + count);
   int rc = DPSR_OK;
   for (int i = 0; i < count && rc == DPSR_OK; ++i) {
-    rc = dpsr_plan_create(r[i], sigma[i], &b->plans[i]);
+    rc = dpsr_plan_create_box(r[i], sigma[i], box ? box + 3 * i : nullptr, &b->plans[i]);
     if (rc == DPSR_OK) rc = dpsr_plan_reserve(b->plans[i], n_max[i]);
     if (rc == DPSR_OK) memcpy(&b->host[i], dpsr_internal_solve(b->plans[i]), sizeof(Solve));
   }

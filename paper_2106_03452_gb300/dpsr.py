@@ -143,13 +143,18 @@ class Batch:
     """Many independent solves (mixed r, uneven N) run together: every kernel
     launches once per grid size for all instances of that size, and with
     graph=True the whole forward (+ backward) sequence is one CUDA graph
-    launch. Instances bind caller-owned CUDA tensors."""
+    launch. Instances bind caller-owned CUDA tensors. boxes: one periodic box
+    (3 side lengths) per instance, None for the unit cube."""
 
-    def __init__(self, rs, sigmas, n_max, device=None):
+    def __init__(self, rs, sigmas, n_max, device=None, boxes=None):
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.rs = [int(r) for r in rs]
         with torch.cuda.device(self.device):
-            self.handle = L.dpsr_batch_create(self.rs, [float(s) for s in sigmas], [int(n) for n in n_max])
+            if boxes is None:
+                self.handle = L.dpsr_batch_create(self.rs, [float(s) for s in sigmas], [int(n) for n in n_max])
+            else:
+                self.handle = L.dpsr_batch_create_box(self.rs, [float(s) for s in sigmas], boxes,
+                                                      [int(n) for n in n_max])
             self.stream = torch.cuda.Stream(self.device)
         L.dpsr_batch_set_stream(self.handle, self.stream.cuda_stream)
         self._bound = [None] * len(self.rs)

@@ -77,6 +77,9 @@ _PROTOS = {
     "dpsr_mesh_sample": (_c_int, [_vp, _vp, _c_i64, _c_i64, ctypes.c_uint64, _vp, _vp, _vp, _vp]),
     "dpsr_batch_create": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(_c_i64), ctypes.POINTER(_vp)]),
+    "dpsr_batch_create_box": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float),
+                                       ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(_vp)]),
     "dpsr_batch_destroy": (_c_int, [_vp]),
     "dpsr_batch_set_stream": (_c_int, [_vp, _vp]),
     "dpsr_batch_bind": (_c_int, [_vp, _c_int, _vp, _vp, _c_i64, _vp, _vp, _vp, _vp]),
@@ -292,6 +295,18 @@ def dpsr_batch_create(r, sigma, n_max) -> int:
     sa = (ctypes.c_float * n)(*[float(x) for x in sigma])
     na = (ctypes.c_int64 * n)(*[int(x) for x in n_max])
     check(load().dpsr_batch_create(n, ra, sa, na, ctypes.byref(h)), "dpsr_batch_create")
+    return h.value
+
+
+def dpsr_batch_create_box(r, sigma, box, n_max) -> int:
+    """box: count x 3 side lengths (one periodic box per instance)."""
+    n = len(r)
+    h = _vp()
+    ra = (ctypes.c_int * n)(*[int(x) for x in r])
+    sa = (ctypes.c_float * n)(*[float(x) for x in sigma])
+    ba = (ctypes.c_float * (3 * n))(*[float(v) for b in box for v in b])
+    na = (ctypes.c_int64 * n)(*[int(x) for x in n_max])
+    check(load().dpsr_batch_create_box(n, ra, sa, ba, na, ctypes.byref(h)), "dpsr_batch_create_box")
     return h.value
 
 
