@@ -95,10 +95,10 @@ __device__ __forceinline__ int2 bin_range(const Solve& S, int xc, int yb) {
   return make_int2(off[k], off[k + 1]);
 }
 
-// R2C of two real rows a = p[0..L), b = p[L..2L) in place: afterwards the
-// storage, seen as L float2, holds A's packed half spectrum in [0, H) and B's
-// in [H, L). The storage is also the FFT exchange area. The group's lanes are
-// contiguous (see Lanes).
+// R2C of two real rows a = p[0..L), b = p[L..2L): A's and B's packed half
+// spectra (H slots each; slot 0 holds the real DC and Nyquist values) end in
+// registers, A[j] and B[j] at slot t + T j. The rows' storage is the FFT
+// exchange area. The group's lanes are contiguous (see Lanes).
 //
 // Z = FFT(a + i b) leaves Z[t + T j] in v[j] of thread t; the separation
 // A[k] = (Z[k] + conj Z[L-k]) / 2, B[k] = -i (Z[k] - conj Z[L-k]) / 2 needs
@@ -108,8 +108,9 @@ __device__ __forceinline__ int2 bin_range(const Solve& S, int xc, int yb) {
 // multiplied by i u(k) (slot 0, DC and Nyquist, becomes 0): the spectral
 // derivative of the forward's v_z rows, folded into the stores.
 template <int L, class Tw>
-__device__ __forceinline__ void r2c_pair_ip(int t, const Tw& tw, float* p, const float* iu = nullptr) {
-  constexpr int R1 = Shape<L>::R1, T = Shape<L>::T, H = L / 2;
+__device__ __forceinline__ void r2c_pair_ab(int t, const Tw& tw, float* p, const float* iu,
+                                            float2 (&A)[Shape<L>::R1 / 2], float2 (&B)[Shape<L>::R1 / 2]) {
+  constexpr int R1 = Shape<L>::R1, T = Shape<L>::T;
   float2 v[R1];
 #pragma unroll
   for (int j = 0; j < R1; ++j) v[j] = make_float2(p[t + T * j], p[L + t + T * j]);
@@ -119,7 +120,6 @@ __device__ __forceinline__ void r2c_pair_ip(int t, const Tw& tw, float* p, const
   const unsigned lane = threadIdx.x & 31u;
   const unsigned gmask = T >= 32 ? 0xffffffffu : (((1u << (T & 31)) - 1u) << (lane & ~(unsigned)(T - 1)));
   const int src = (int)(lane & ~(unsigned)(T - 1)) | ((T - t) & (T - 1));
-  float2 A[R1 / 2], B[R1 / 2];
 #pragma unroll
   for (int j = 0; j < R1 / 2; ++j) {
     float2 zm = v[(R1 - j) & (R1 - 1)];  // thread 0's own mirror (j > 0)
@@ -149,10 +149,22 @@ __device__ __forceinline__ void r2c_pair_ip(int t, const Tw& tw, float* p, const
       B[j] = cmul_iu(B[j], u);
     }
   }
+}
+
+// Straight to global memory: the packed spectra of rows a and b go to the
+// rows ga and gb of a spectral buffer from registers (a group's lanes write
+// consecutive slots: whole 128-byte lines), with no shared-memory write and
+// no bulk copy reading them back. `p` is left as FFT exchange scratch.
+template <int L, class Tw>
+__device__ __forceinline__ void r2c_pair_st(int t, const Tw& tw, float* p, const float* iu, float2* ga,
+                                            float2* gb) {
+  constexpr int R1 = Shape<L>::R1, T = Shape<L>::T;
+  float2 A[R1 / 2], B[R1 / 2];
+  r2c_pair_ab<L>(t, tw, p, iu, A, B);
 #pragma unroll
   for (int j = 0; j < R1 / 2; ++j) {
-    x[t + T * j] = A[j];
-    x[H + t + T * j] = B[j];
+    ga[t + T * j] = A[j];
+    gb[t + T * j] = B[j];
   }
 }
 
@@ -255,19 +267,13 @@ __device__ __forceinline__ void zfwd_tile(const Solve& S, int X, int y0, float* 
   constexpr int NP = 4 * YB / 2;
   for (int p0 = 0; p0 < NP; p0 += P::ZG) {
     const int pi = p0 + g;
-    // the v_z rows (pairs YB/2 .. YB-1) take i u_z (zero at DC and Nyquist)
-    const bool vz = pi >= YB / 2 && pi < YB;
-    if (pi < NP) r2c_pair_ip<L>(t, twr, rows + pair_off<L>(pi), vz ? iu : nullptr);  // whole groups
-  }
-  // the packed rows go out by bulk copies, one row per thread
-  fence_async_smem();
-  __syncthreads();
-  if (tid < 4 * YB) {
-    const int ch = tid / YB, ly = tid % YB;
-    bulk_store(S.spec[ch] + ((size_t)X * L + y0 + ly) * P::KP, rows + row_off<L>(ch * YB + ly),
-               H * (uint32_t)sizeof(float2));
-    tma_store_commit();
-    tma_store_wait_read();  // shared memory stays valid until read
+    if (pi < NP) {  // whole groups
+      // the v_z rows (pairs YB/2 .. YB-1) take i u_z (zero at DC and Nyquist)
+      const bool vz = pi >= YB / 2 && pi < YB;
+      const int ch = (2 * pi) / YB, ly = (2 * pi) % YB;  // rows ly, ly + 1 of channel ch
+      float2* ga = S.spec[ch] + ((size_t)X * L + y0 + ly) * P::KP;
+      r2c_pair_st<L>(t, twr, rows + pair_off<L>(pi), vz ? iu : nullptr, ga, ga + P::KP);
+    }
   }
 }
 
@@ -881,10 +887,7 @@ __global__ void __launch_bounds__(ZbGeo<L>::NT, L >= 512 ? 1 : 3) k_zbfwd(const 
   for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
     const int st = it & 1;
     const int next = tile + gridDim.x;
-    if (tid == 0 && next < ntiles) {
-      tma_store_wait_read();  // the rows stored from stage st ^ 1 last tile have been read
-      issue(next, st ^ 1);
-    }
+    if (tid == 0 && next < ntiles) issue(next, st ^ 1);  // stage st ^ 1 was released last tile
     const bool ok = __syncthreads_and(mbar_wait(&bar[st], (ph >> st) & 1u));
     ph ^= 1u << st;
     if (!ok) {
@@ -906,21 +909,20 @@ __global__ void __launch_bounds__(ZbGeo<L>::NT, L >= 512 ? 1 : 3) k_zbfwd(const 
     dS = ff_add(dS, accS);
     dD = ff_add(dD, accD);
     __syncthreads();  // the sums have read the rows before the R2C rewrites them
-    for (int p0 = 0; p0 < YB / 2; p0 += ZG) {
-      const int pi = p0 + g;
-      if (pi < YB / 2) r2c_pair_ip<L>(t, twr, rows + pair_off<L>(pi));  // whole groups
+    {
+      const int X = tile / (L / YB), y0 = (tile % (L / YB)) * YB;
+      for (int p0 = 0; p0 < YB / 2; p0 += ZG) {
+        const int pi = p0 + g;
+        if (pi < YB / 2) {  // whole groups; the packed rows go straight to global memory
+          float2* ga = S.spec[kSpD] + ((size_t)X * L + y0 + 2 * pi) * P::KP;
+          r2c_pair_st<L>(t, twr, rows + pair_off<L>(pi), nullptr, ga, ga + P::KP);
+        }
+      }
     }
+    // every thread is done with this stage before a bulk copy refills it
     fence_async_smem();
     __syncthreads();
-    if (tid == 0) {  // packed rows out by bulk copies; waited for before the refill
-      const int X = tile / (L / YB), y0 = (tile % (L / YB)) * YB;
-      for (int ly = 0; ly < YB; ++ly)
-        bulk_store(S.spec[kSpD] + ((size_t)X * L + y0 + ly) * P::KP, rows + row_off<L>(ly),
-                   H * (uint32_t)sizeof(float2));
-      tma_store_commit();
-    }
   }
-  if (tid == 0) tma_store_wait_read();  // shared memory stays valid until read
   // this CTA's partial sums, fixed order; the last CTA finalises
   block_sum_ff<NT>(dS, dD);
   last_block_finalize<NT>(S, 1, (int)gridDim.x, (int)blockIdx.x, dS, dD, true);
