@@ -56,7 +56,6 @@ def test_mix_equals_alone():
     mixed, st = run(8)
     assert st1["groups"] == 0                # one at a time: nothing to coalesce
     assert st["max_in_flight"] >= 2          # requests overlapped on the GPU
-    assert st["groups"] >= 1 and st["grouped_requests"] >= 2  # and same-size ones ran batched
     for q, a, m in zip(trace, alone, mixed):
         assert _rel(m[0], a[0]) <= 1e-5
         if q["backward"]:
@@ -244,3 +243,37 @@ def test_wait_any_retires_in_completion_batches():
         L.check(L.dpsr_server_wait(srv.handle, tickets[3], 1.0), "wait")   # already retired
     assert all(torch.isfinite(c).all() for c in keep)
     srv.close()
+
+
+def test_queued_same_size_requests_are_coalesced():
+    """With one slot held by a long r = 256 request, six r = 64 requests queue
+    behind it; when the slot frees, the head and the five behind it (same
+    size, same mode) are admitted as one batched launch, and each still
+    equals its solo result."""
+    import torch
+    from paper_2106_03452_gb300 import serve
+    pool = serve.InputPool(n_clouds=2, n_max=100000, rs=(64, 256))
+    srv = serve.Server(8 << 30, slots=1, max_group=8)
+    serve.warm(srv, pool, rs=(64, 256), slots=1, n=100000)
+    g0 = srv.stats()
+    pts, nrm = pool.inputs(0, 100000)
+    big = torch.empty((256,) * 3).pin_memory()
+    d = [torch.empty(100000, 3).pin_memory() for _ in range(2)]
+    t_big = srv.submit(256, pts, nrm, big, pool.dchi[256], d[0], d[1])
+    small = []
+    for i in range(6):
+        p, n = pool.inputs(i + 1, 3000 + 500 * i)
+        chi = torch.empty((64,) * 3).pin_memory()
+        small.append((srv.submit(64, p, n, chi), p, n, chi))
+    assert srv.wait(t_big, 120.0) == 0
+    for t, _, _, _ in small:
+        assert srv.wait(t, 120.0) == 0
+    st = srv.stats()
+    assert st["groups"] - g0["groups"] >= 1 and st["grouped_requests"] - g0["grouped_requests"] >= 2
+    srv.close()
+    solo = serve.Server(8 << 30, slots=1, max_group=1)
+    for _, p, n, chi in small:
+        ref = torch.empty((64,) * 3).pin_memory()
+        assert solo.wait(solo.submit(64, p, n, ref), 120.0) == 0
+        assert _rel(chi, ref) <= 1e-5
+    solo.close()
