@@ -147,9 +147,13 @@ def replay(trace, server: Server, pool: InputPool, realtime=True, n_max=200000, 
     th.start()
     for i, q in enumerate(trace):
         if realtime:
+            # sleep to just short of the arrival time, then spin: a plain
+            # sleep overshoots by a scheduler tick, which would count as latency
             dt = q["t"] - (time.perf_counter() - t0)
-            if dt > 0:
-                time.sleep(dt)
+            if dt > 0.0005:
+                time.sleep(dt - 0.0005)
+            while time.perf_counter() - t0 < q["t"]:
+                pass
         r, N, bwd = q["r"], q["N"], q["backward"]
         pts, nrm = pool.inputs(i, N)
         bufs = ring.get(r, n_max, bwd)
