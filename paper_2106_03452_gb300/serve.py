@@ -153,7 +153,7 @@ def replay(trace, server: Server, pool: InputPool, realtime=True, n_max=200000, 
             if dt > 0.0005:
                 time.sleep(dt - 0.0005)
             while time.perf_counter() - t0 < q["t"]:
-                pass
+                time.sleep(0)  # yields the interpreter lock to the completion thread
         r, N, bwd = q["r"], q["N"], q["backward"]
         pts, nrm = pool.inputs(i, N)
         bufs = ring.get(r, n_max, bwd)
