@@ -459,11 +459,12 @@ int dpsr_plan_create_box(int r, float sigma, const float* box, dpsr_plan* out) {
     return DPSR_ENOMEM;
   }
   Solve& s = p->s;
-  s.r = r;
   for (int d = 0; d < 3; ++d) {
     p->box[d] = box ? box[d] : 1.f;
     s.inv_box[d] = box ? (float)(1.0 / (double)box[d]) : 1.f;
+    s.box[d] = box ? (double)box[d] : 1.0;
   }
+  dpsr::set_grid(s, r);
   char* q = (char*)p->grid_ws;
   for (int k = 0; k < dpsr::kNSpec; ++k) {
     s.spec[k] = (float2*)q;

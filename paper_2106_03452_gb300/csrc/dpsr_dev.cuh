@@ -412,10 +412,13 @@ struct Solve {
   int r;
   int N;
   double inv_N;  // 1 / N (set with N by set_count)
-  // 1 / L_d for a periodic box of side lengths L (voxel size L_d / r along
-  // axis d, Eq. A1 with a per-axis s): the binning turns box coordinates
-  // into unit-cube ones and the combine turns unit-cube gradients back.
+  // A periodic box of side lengths L (voxel size L_d / r along axis d, Eq.
+  // A1 with a per-axis s): the binning finds each point's cell and in-cell
+  // fraction from c r / L_d in FP64 (box), the combine turns unit-cube
+  // gradients into box ones (times 1 / L_d, inv_box).
   float inv_box[3] = {1.f, 1.f, 1.f};
+  double box[3] = {1.0, 1.0, 1.0};
+  double gscale[3] = {0.0, 0.0, 0.0};  // r / L_d, set with r (set_grid)
   // per call (caller-owned)
   const float* points;
   const float* normals;
@@ -426,7 +429,7 @@ struct Solve {
   const float* target;  // L_DPSR target grid (r^3), and where its gradient goes
   float* dchi_rw;
   // plan workspace
-  float4* sorted;   // 2 records per point: (x, y, z, nx), (ny, nz, orig, 0)
+  float4* sorted;   // 2 records per point: (tx, ty, tz, nx), (ny, nz, orig, cells) (see axis_rec)
   int* cellx;       // N
   int* bins;        // count[r*r], off[r*r + 1], cursor[r*r] (see nbins)
   float2* spec[kNSpec];  // r * r * (r/2 + 2) complex each
@@ -479,6 +482,12 @@ __device__ __forceinline__ bool dbg_in_range(unsigned* status, long long i, long
 __device__ __forceinline__ bool dbg_in_range(unsigned*, long long, long long) { return true; }
 #endif
 
+// The grid size of a solve and its per-axis scales r / L_d (host side).
+inline void set_grid(Solve& s, int r) {
+  s.r = r;
+  for (int d = 0; d < 3; ++d) s.gscale[d] = (double)r / s.box[d];
+}
+
 // The point count of a solve and its reciprocal (used by the scalar pass).
 inline void set_count(Solve& s, int64_t N) {
   s.N = (int)N;
@@ -528,6 +537,43 @@ __device__ __forceinline__ Axis axis_of(float c, int r) {
   const int i = (int)f;
   a.i0 = i & (r - 1);
   a.i1 = (i + 1) & (r - 1);
+  return a;
+}
+
+// The cell of a point along axis d from its coordinate c in the periodic
+// box [0, L_d), given scale = r / L_d (FP64): on the unit cube (L_d = 1)
+// exactly axis_of (c r is exact in FP32); in a box the grid coordinate
+// c r / L_d in FP64, its floor (wrapped to the grid) and the fraction in
+// [0, 1) rounded once to FP32, which avoids the extra rounding of an FP32
+// c / L_d (up to r 2^-24 voxel). One FP64 multiply per coordinate.
+__device__ __forceinline__ Axis axis_in_box(float c, double scale, bool unit, int r) {
+  if (unit) return axis_of(c, r);
+  const double g = (double)c * scale;
+  double f = floor(g);
+  float t = (float)(g - f);
+  if (t >= 1.f) {  // g - f within half an FP32 ulp of 1
+    t = 0.f;
+    f += 1.0;
+  }
+  Axis a;
+  a.t = t;
+  const long long i = (long long)f;
+  a.i0 = (int)(i & (long long)(r - 1));
+  a.i1 = (a.i0 + 1) & (r - 1);
+  return a;
+}
+
+// Sorted point records (the binning's output): (tx, ty, tz, nx) and
+// (ny, nz, original index, cells), t the fraction within the cell along each
+// axis and cells = i0x | i0y << 10 | i0z << 20 (r <= 512).
+__device__ __forceinline__ unsigned pack_cells(int ix, int iy, int iz) {
+  return (unsigned)ix | ((unsigned)iy << 10) | ((unsigned)iz << 20);
+}
+__device__ __forceinline__ Axis axis_rec(float t, float cells_bits, int d, int r) {
+  Axis a;
+  a.t = t;
+  a.i0 = (int)((__float_as_uint(cells_bits) >> (10 * d)) & 1023u);
+  a.i1 = (a.i0 + 1) & (r - 1);
   return a;
 }
 

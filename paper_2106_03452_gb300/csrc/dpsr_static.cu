@@ -149,7 +149,7 @@ extern "C" DPSR_API int dpsr_forward_static(int r, float sigma, const float* poi
   float htab[7 * kMaxR];
   dpsr::spectral_tables(r, (double)sigma, nullptr, htw, htab);
   dpsr::Solve s = {};
-  s.r = r;
+  dpsr::set_grid(s, r);
   dpsr::set_count(s, N);
   s.points = points;
   s.normals = normals;

@@ -243,9 +243,9 @@ __device__ __forceinline__ void zfwd_tile(const Solve& S, int X, int y0, float* 
     const int side = k >> 1, part = k & 1;
     if (!dbg_in_range(S.status, i, S.N)) continue;
     const float4 a = S.sorted[2 * i], b = S.sorted[2 * i + 1];
-    const Axis ay = axis_of(a.y, L);
+    const Axis ay = axis_rec(a.y, b.w, 1, L);
     if (part == 1 && ay.i0 != ylast) continue;
-    const Axis ax = axis_of(a.x, L), az = axis_of(a.z, L);
+    const Axis ax = axis_rec(a.x, b.w, 0, L), az = axis_rec(a.z, b.w, 2, L);
     const float wx = tri_w(side, ax.t);
     const float val[4] = {b.x, b.y, a.w, 1.f};
 #pragma unroll
@@ -683,7 +683,7 @@ __device__ __forceinline__ bool zinv_tile(const Solve& S, int tile, float2* sb, 
     const int i = tid < n0 ? r0.x + tid : r1.x + (tid - n0);
     if (dbg_in_range(S.status, i, S.N)) {
       pa = S.sorted[2 * i];
-      if constexpr (NCH == 3) pb = S.sorted[2 * i + 1];
+      pb = S.sorted[2 * i + 1];  // normals (adjoint) and the packed cells
     }
   }
   if (!wait_stage()) return false;
@@ -722,7 +722,8 @@ __device__ __forceinline__ bool zinv_tile(const Solve& S, int tile, float2* sb, 
     if (!dbg_in_range(S.status, i, S.N)) continue;
     {
       const float4 a = v == tid ? pa : S.sorted[2 * i];
-      const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);
+      const float4 b = v == tid ? pb : S.sorted[2 * i + 1];
+      const Axis ax = axis_rec(a.x, b.w, 0, L), ay = axis_rec(a.y, b.w, 1, L), az = axis_rec(a.z, b.w, 2, L);
       const int ly0 = ay.i0 - y0;  // in [0, YB); row i1 is ly0 + 1 (a halo row at most)
       const float fx = tri_w(side, ax.t), dfx = side ? (float)L : -(float)L;
       if constexpr (NCH == 1) {
@@ -742,7 +743,6 @@ __device__ __forceinline__ bool zinv_tile(const Solve& S, int tile, float2* sb, 
         }
         S.gfwd[(size_t)side * S.N + i] = make_float4(gx, gy, gz, 0.f);
       } else {
-        const float4 b = v == tid ? pb : S.sorted[2 * i + 1];
         const float n0_ = a.w, n1 = b.x, n2 = b.y;
         float nb0 = 0.f, nb1 = 0.f, nb2 = 0.f, cb0 = 0.f, cb1 = 0.f, cb2 = 0.f;
 #pragma unroll

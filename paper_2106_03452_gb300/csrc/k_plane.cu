@@ -110,7 +110,7 @@ __device__ int plane_list(const Solve& S, const PlanePoints& pp, int L, int y_lo
     int idx = 0, dx = 0;
     if (i < n) idx = pp.index(i, dx);
     if (i < n && dbg_in_range(S.status, idx, S.N)) {
-      const Axis ay = axis_of(pf[8 * (size_t)idx + 1], L);
+      const Axis ay = axis_rec(pf[8 * (size_t)idx + 1], pf[8 * (size_t)idx + 7], 1, L);
       in = (unsigned)(ay.i0 - y_lo) < (unsigned)R || (both && (unsigned)(ay.i1 - y_lo) < (unsigned)R);
     }
     const unsigned m = __ballot_sync(0xffffffffu, in);
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(fwd_threads<L, C>(), 512 / fwd_threads<L, C>()
       if (!dbg_in_range(S.status, idx, S.N)) continue;
       const float4 a = S.sorted[2 * idx], b = S.sorted[2 * idx + 1];
       const float val = ch == 0 ? a.w : (ch == 1 ? b.x : (ch == 2 ? b.y : 1.f));
-      const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);
+      const Axis ax = axis_rec(a.x, b.w, 0, L), ay = axis_rec(a.y, b.w, 1, L), az = axis_rec(a.z, b.w, 2, L);
       const float fx = wsel(dx, ax.t) * val;
 #pragma unroll
       for (int dy = 0; dy < 2; ++dy) {
@@ -547,7 +547,8 @@ __global__ void __launch_bounds__(kNT, plane_minb<L, C>(1))
       const int idx = pp.index(i, dx);
       if (!dbg_in_range(S.status, idx, S.N)) continue;
       const float4 a = S.sorted[2 * idx];
-      const Axis ax = axis_of(a.x, L), ay = axis_of(a.y, L), az = axis_of(a.z, L);
+      const float cells = S.sorted[2 * idx + 1].w;
+      const Axis ax = axis_rec(a.x, cells, 0, L), ay = axis_rec(a.y, cells, 1, L), az = axis_rec(a.z, cells, 2, L);
       if (ay.i0 - y_lo < 0 || ay.i0 - y_lo >= P::R) continue;
       const float fx = wsel(dx, ax.t), dfx = dx ? (float)L : -(float)L;
       float gx = 0.f, gy = 0.f, gz = 0.f;
@@ -885,11 +886,11 @@ __global__ void __launch_bounds__(binv_threads<L, C>(), binv_smem<L, C>() <= 113
         int dx;
         const int idx = visit_point(list, nlist, pp, i, dx);
         if (!dbg_in_range(S.status, idx, S.N)) continue;
-        const float4 a = S.sorted[2 * idx];
-        const Axis ay = axis_of(a.y, L);
+        const float4 a = S.sorted[2 * idx], b = S.sorted[2 * idx + 1];
+        const Axis ay = axis_rec(a.y, b.w, 1, L);
         if ((unsigned)(ay.i0 - y_lo) >= (unsigned)R) continue;
-        const Axis ax = axis_of(a.x, L), az = axis_of(a.z, L);
-        const float nch = ch == 0 ? a.w : (ch == 1 ? S.sorted[2 * idx + 1].x : S.sorted[2 * idx + 1].y);
+        const Axis ax = axis_rec(a.x, b.w, 0, L), az = axis_rec(a.z, b.w, 2, L);
+        const float nch = ch == 0 ? a.w : (ch == 1 ? b.x : b.y);
         const float fx = wsel(dx, ax.t), dfx = dx ? (float)L : -(float)L;
         float nb = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
 #pragma unroll

@@ -14,10 +14,8 @@ __device__ __forceinline__ bool coord_ok(float c, int r) {
   return isfinite(c) && fabsf(c * (float)r) < 1073741824.f;  // |c r| < 2^30
 }
 
-// Bin key of a point (see nbins).
-__device__ __forceinline__ int bin_key(float x, float y, int r) {
-  return axis_of(x, r).i0 * nybins(r) + axis_of(y, r).i0 / ybin(r);
-}
+// Bin key of a point from its x and y cells (see nbins).
+__device__ __forceinline__ int bin_key(int ix, int iy, int r) { return ix * nybins(r) + iy / ybin(r); }
 
 // count[key]++ per point (see nbins for the key); validates the inputs
 // (non-finite or huge values raise kStBadInput and are replaced by 0 so that
@@ -35,17 +33,21 @@ __global__ void __launch_bounds__(256) k_bin_count(const __grid_constant__ Solve
   pdl_wait();
   __syncthreads();
   bool bad = false;
+  // r / L_d per axis (FP64 cell arithmetic only off the unit cube)
+  const double sx = S.gscale[0], sy = S.gscale[1];
+  const bool unit[2] = {S.box[0] == 1.0, S.box[1] == 1.0};
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < S.N; p += gridDim.x * blockDim.x) {
-    float x = S.points[3 * p] * S.inv_box[0], y = S.points[3 * p + 1] * S.inv_box[1];
-    const float z = S.points[3 * p + 2] * S.inv_box[2];
+    // box coordinates; the check uses their unit-cube size
+    float x = S.points[3 * p], y = S.points[3 * p + 1];
+    const float z = S.points[3 * p + 2];
     const float nx = S.normals[3 * p], ny = S.normals[3 * p + 1], nz = S.normals[3 * p + 2];
-    if (!(coord_ok(x, r) && coord_ok(y, r) && coord_ok(z, r) && isfinite(nx) && isfinite(ny) &&
-          isfinite(nz))) {
+    const bool okx = coord_ok(x * S.inv_box[0], r), oky = coord_ok(y * S.inv_box[1], r);
+    if (!(okx && oky && coord_ok(z * S.inv_box[2], r) && isfinite(nx) && isfinite(ny) && isfinite(nz))) {
       bad = true;
-      if (!coord_ok(x, r)) x = 0.f;
-      if (!coord_ok(y, r)) y = 0.f;
+      if (!okx) x = 0.f;
+      if (!oky) y = 0.f;
     }
-    const int key = bin_key(x, y, r);
+    const int key = bin_key(axis_in_box(x, sx, unit[0], r).i0, axis_in_box(y, sy, unit[1], r).i0, r);
     S.cellx[p] = key;
     if (!dbg_in_range(S.status, key, nb)) continue;
     atomicAdd(&h[key], 1);
@@ -120,14 +122,16 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Sol
       S.sc->ticket[2] = 0;
     }
   }
+  const double sx = S.gscale[0], sy = S.gscale[1], sz = S.gscale[2];
+  const bool unit[3] = {S.box[0] == 1.0, S.box[1] == 1.0, S.box[2] == 1.0};
   for (int p = blockIdx.x * NT + tid; p < S.N; p += gridDim.x * NT) {
-    // unit-cube coordinates from here on (exact for the unit cube)
-    float x = S.points[3 * p] * S.inv_box[0], y = S.points[3 * p + 1] * S.inv_box[1],
-          z = S.points[3 * p + 2] * S.inv_box[2];
+    // box coordinates; the records hold each point's cells and in-cell
+    // fractions (the same FP64 arithmetic as the count's key)
+    float x = S.points[3 * p], y = S.points[3 * p + 1], z = S.points[3 * p + 2];
     float nx = S.normals[3 * p], ny = S.normals[3 * p + 1], nz = S.normals[3 * p + 2];
-    if (!coord_ok(x, r)) x = 0.f;
-    if (!coord_ok(y, r)) y = 0.f;
-    if (!coord_ok(z, r)) z = 0.f;
+    if (!coord_ok(x * S.inv_box[0], r)) x = 0.f;
+    if (!coord_ok(y * S.inv_box[1], r)) y = 0.f;
+    if (!coord_ok(z * S.inv_box[2], r)) z = 0.f;
     if (!isfinite(nx)) nx = 0.f;
     if (!isfinite(ny)) ny = 0.f;
     if (!isfinite(nz)) nz = 0.f;
@@ -135,8 +139,10 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Sol
     if (!dbg_in_range(S.status, key, nb)) continue;
     const int pos = h[scan_slot(key)] + atomicAdd(&cur[key], 1);
     if (!dbg_in_range(S.status, pos, S.N)) continue;
-    S.sorted[2 * pos] = make_float4(x, y, z, nx);
-    S.sorted[2 * pos + 1] = make_float4(ny, nz, __int_as_float(p), 0.f);
+    const Axis ax = axis_in_box(x, sx, unit[0], r), ay = axis_in_box(y, sy, unit[1], r),
+               az = axis_in_box(z, sz, unit[2], r);
+    S.sorted[2 * pos] = make_float4(ax.t, ay.t, az.t, nx);
+    S.sorted[2 * pos + 1] = make_float4(ny, nz, __int_as_float(p), __uint_as_float(pack_cells(ax.i0, ay.i0, az.i0)));
   }
 }
 

@@ -71,7 +71,10 @@ def _check_box(oracle, r, sigma, box, pts, nrm, dchi):
 def test_random_clouds_in_box(oracle, monkeypatch, path, box, r, N, sigma):
     _set_path(monkeypatch, path, r)
     rng = synth.Rng(5000 + 10 * r + N)
-    pts = (rng.uniform(N, 3) * 1.4 - 0.2) * np.asarray(box)     # wraps around the box
+    pts = rng.uniform(N, 3) * 1.4 - 0.2
+    f = pts * r - np.floor(pts * r)                  # 1e-4 voxel off the cell faces: the
+    pts = (np.floor(pts * r) + np.clip(f, 1e-4, 1 - 1e-4)) / r   # two sides round x / L differently
+    pts = pts * np.asarray(box)                      # wraps around the box
     nrm = rng.normal(N, 3)
     dchi = rng.normal(r, r, r).astype(np.float32)
     _check_box(oracle, r, sigma, box, pts.astype(np.float32), nrm.astype(np.float32), dchi)
@@ -83,6 +86,9 @@ def test_ellipsoids_in_box_r128(oracle, monkeypatch, path):
     w = synth.workload_ellipsoids_r128()
     box = BOXES[0]
     pts, nrm = _in_box(w["points"], w["normals"], box)
+    u = pts.astype(np.float64) / np.asarray(box) * 128
+    f = u - np.floor(u)                              # 1e-4 voxel off the cell faces (see above)
+    pts = ((np.floor(u) + np.clip(f, 1e-4, 1 - 1e-4)) / 128 * np.asarray(box)).astype(np.float32)
     _check_box(oracle, 128, w["sigma"], box, pts, nrm, w["dchi"])
 
 
