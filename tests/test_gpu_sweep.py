@@ -87,3 +87,50 @@ def test_sweep(oracle, monkeypatch, i):
     err = np.max(np.abs(g["dpoints"] - dp))
     bound = tol_g * np.max(np.abs(dp)) + (2e-6 * scale if box is None else 0.0)
     assert err <= bound, (i, r, N, sigma, box, path, "dpoints", err / np.max(np.abs(dp)))
+
+
+@pytest.mark.parametrize("j", range(6))
+def test_batch_sweep(j):
+    """Seeded random batches (3 to 10 instances of mixed r, N, sigma and box):
+    every instance equals a solo plan's solve of the same inputs, to the
+    rounding of the splat's addition order (amplified, for near-degenerate
+    draws, by the conditioning of the scale s)."""
+    import torch
+    from gpu_util import relmax
+    from paper_2106_03452_gb300.dpsr import Batch, Plan
+    rng = synth.Rng(70000 + j)
+    count = 3 + int(rng.uniform() * 8)
+    rs, sig, boxes, clouds = [], [], [], []
+    for _ in range(count):
+        u = rng.uniform(4)
+        r = [16, 32, 64, 128][min(int(u[0] * 4), 3)]
+        N = int(round(np.exp(np.log(50.0) + (np.log(20000.0) - np.log(50.0)) * u[1])))
+        box = (1.0, 1.0, 1.0) if u[2] < 0.5 else tuple(float(v) for v in np.round(0.5 + 1.5 * rng.uniform(3), 3))
+        pts = ((rng.uniform(N, 3) * 1.3 - 0.15) * np.asarray(box)).astype(np.float32)
+        rs.append(r)
+        sig.append(round(float(4.0 * u[3]), 2))
+        boxes.append(box)
+        clouds.append((pts, rng.normal(N, 3).astype(np.float32), rng.normal(r, r, r).astype(np.float32)))
+    batch = Batch(rs, sig, [c[0].shape[0] for c in clouds], boxes=boxes)
+    out = []
+    for i, (p, n, g) in enumerate(clouds):
+        r = rs[i]
+        P, Nn, G = (torch.from_numpy(a).cuda() for a in (p, n, g))
+        chi = torch.empty((r, r, r), device="cuda")
+        dp, dn = torch.empty_like(P), torch.empty_like(P)
+        batch.bind(i, P, Nn, chi, G, dp, dn)
+        out.append((P, Nn, G, chi, dp, dn))
+    batch.run(with_bwd=True, graph=True)
+    assert batch.sync() == 0
+    for i, (P, Nn, G, chi, dp, dn) in enumerate(out):
+        plan = Plan(rs[i], sig[i], box=boxes[i])
+        c0 = plan.forward(P, Nn).clone()
+        d0, n0 = plan.backward(G)
+        assert plan.sync() == 0
+        cond = 2.0 * float(c0.abs().max())            # max|chi'| / |s| = 2 max|chi|
+        tol = 1e-5 + 4 * 2.0 ** -24 * cond
+        assert relmax(chi.cpu().numpy(), c0.cpu().numpy()) <= tol, (j, i, rs[i], sig[i], boxes[i])
+        assert relmax(dn.cpu().numpy(), n0.cpu().numpy()) <= 10 * tol, (j, i, "dnormals")
+        assert relmax(dp.cpu().numpy(), d0.cpu().numpy()) <= 10 * tol, (j, i, "dpoints")
+        plan.close()
+    batch.close()
