@@ -76,8 +76,9 @@ DPSR_API int dpsr_plan_create(int r, float sigma, dpsr_plan *out);
 
 /* The same over a periodic box [0, L0) x [0, L1) x [0, L2) instead of the
  * unit cube: the r^3 grid's voxel size is L_d / r along axis d (Eq. A1 with
- * a per-axis voxel size s, Sec. 3.1). box: 3 side lengths, each finite and
- * > 0, read during the call (NULL: the unit cube). Points are then given in
+ * a per-axis voxel size s, Sec. 3.1). box: 3 side lengths in FP64 (the
+ * binning's cell arithmetic uses them unrounded), each finite and > 0, read
+ * during the call (NULL: the unit cube). Points are then given in
  * box coordinates (wrapped with period L_d); the spectral operator of Eq. 3
  * uses the physical frequency u_d = f_d / L_d of the integer frequency f_d,
  * and the Gaussian keeps sigma in grid units on every axis,
@@ -86,7 +87,7 @@ DPSR_API int dpsr_plan_create(int r, float sigma, dpsr_plan *out);
  * for a bad box, else as dpsr_plan_create. Batches take a box per instance
  * (dpsr_batch_create_box); the serving, static and mesh entry points work on
  * the unit cube. */
-DPSR_API int dpsr_plan_create_box(int r, float sigma, const float *box, dpsr_plan *out);
+DPSR_API int dpsr_plan_create_box(int r, float sigma, const double *box, dpsr_plan *out);
 
 /* Free the plan and its workspace (synchronises its stream first). */
 DPSR_API int dpsr_plan_destroy(dpsr_plan plan);
@@ -327,9 +328,9 @@ DPSR_API int dpsr_batch_create(int count, const int *r, const float *sigma, cons
                                dpsr_batch *out);
 /* The same with a periodic box per instance (as dpsr_plan_create_box):
  * box holds 3 side lengths per instance, count x 3 floats (NULL: every
- * instance on the unit cube). Instances of one grid size still share every
+ * instance on the unit cube), FP64 as for dpsr_plan_create_box. Instances of one grid size still share every
  * launch; each keeps its own spectral tables and coordinate scaling. */
-DPSR_API int dpsr_batch_create_box(int count, const int *r, const float *sigma, const float *box,
+DPSR_API int dpsr_batch_create_box(int count, const int *r, const float *sigma, const double *box,
                                    const int64_t *n_max, dpsr_batch *out);
 DPSR_API int dpsr_batch_destroy(dpsr_batch batch);
 /* A non-default stream is required for dpsr_batch_graph_launch (capture). */

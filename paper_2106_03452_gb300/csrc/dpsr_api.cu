@@ -37,7 +37,7 @@ using dpsr::Solve;
 struct dpsr_plan_s {
   int r = 0;
   float sigma = 0.f;
-  float box[3] = {1.f, 1.f, 1.f};  // side lengths of the periodic domain
+  double box[3] = {1.0, 1.0, 1.0};  // side lengths of the periodic domain
   int device = 0;
   cudaStream_t stream = nullptr;
   int C[4] = {1, 1, 1, 1};
@@ -431,16 +431,16 @@ size_t dpsr_plan_workspace_bytes(int r, int64_t n_max, int with_bwd) {
   return grid_ws_bytes(r) + pts_ws_bytes(n_max > 0 ? n_max : 1);
 }
 
-static bool valid_box(const float* box) {
+static bool valid_box(const double* box) {
   if (!box) return true;
   for (int d = 0; d < 3; ++d)
-    if (!(box[d] > 0.f) || !isfinite(box[d])) return false;
+    if (!(box[d] > 0.0) || !isfinite(box[d])) return false;
   return true;
 }
 
 int dpsr_plan_create(int r, float sigma, dpsr_plan* out) { return dpsr_plan_create_box(r, sigma, nullptr, out); }
 
-int dpsr_plan_create_box(int r, float sigma, const float* box, dpsr_plan* out) {
+int dpsr_plan_create_box(int r, float sigma, const double* box, dpsr_plan* out) {
   if (!out || !valid_r(r) || !(sigma >= 0.f) || !isfinite(sigma) || !valid_box(box)) return DPSR_EINVAL;
   *out = nullptr;
   dpsr_plan p = new (std::nothrow) dpsr_plan_s();
@@ -460,9 +460,9 @@ int dpsr_plan_create_box(int r, float sigma, const float* box, dpsr_plan* out) {
   }
   Solve& s = p->s;
   for (int d = 0; d < 3; ++d) {
-    p->box[d] = box ? box[d] : 1.f;
-    s.inv_box[d] = box ? (float)(1.0 / (double)box[d]) : 1.f;
-    s.box[d] = box ? (double)box[d] : 1.0;
+    p->box[d] = box ? box[d] : 1.0;
+    s.inv_box[d] = box ? (float)(1.0 / box[d]) : 1.f;
+    s.box[d] = box ? box[d] : 1.0;
   }
   dpsr::set_grid(s, r);
   char* q = (char*)p->grid_ws;

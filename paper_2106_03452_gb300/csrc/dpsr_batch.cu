@@ -232,7 +232,7 @@ int dpsr_batch_create(int count, const int* r, const float* sigma, const int64_t
   return dpsr_batch_create_box(count, r, sigma, nullptr, n_max, out);
 }
 
-int dpsr_batch_create_box(int count, const int* r, const float* sigma, const float* box,
+int dpsr_batch_create_box(int count, const int* r, const float* sigma, const double* box,
                           const int64_t* n_max, dpsr_batch* out) {
   if (!out || count < 1 || !r || !sigma || !n_max) return DPSR_EINVAL;
   *out = nullptr;

@@ -449,7 +449,7 @@ struct Solve {
 // Host side: the spectral tables of one plan, computed in FP64 and rounded
 // to FP32. tw[r]: twiddles exp(-2 pi i m / r); tab[7r]: g1 (r), u2 (3r) and
 // iu (3r) as laid out in Solve. box: side lengths L_d (nullptr: unit cube).
-inline void spectral_tables(int r, double sigma, const float* box, float2* tw, float* tab) {
+inline void spectral_tables(int r, double sigma, const double* box, float2* tw, float* tab) {
   const double pi = 3.14159265358979323846264338327950288;
   for (int m = 0; m < r; ++m) {
     const double ang = -2.0 * pi * (double)m / (double)r;
@@ -457,7 +457,7 @@ inline void spectral_tables(int r, double sigma, const float* box, float2* tw, f
     const double f = m < r / 2 ? (double)m : (m == r / 2 ? (double)(r / 2) : (double)(m - r));
     tab[m] = (float)exp(-2.0 * sigma * sigma * f * f / ((double)r * r));
     for (int d = 0; d < 3; ++d) {
-      const double u = f / (box ? (double)box[d] : 1.0);
+      const double u = f / (box ? box[d] : 1.0);
       tab[(1 + d) * r + m] = (float)(u * u);
       tab[(4 + d) * r + m] = m == r / 2 ? 0.f : (float)u;
     }

@@ -40,7 +40,7 @@ _PROTOS = {
     "dpsr_debug_read_spectrum": (_c_int, [_vp, _c_int, _vp]),
     "dpsr_debug_check_selftest": (_c_int, []),
     "dpsr_fp32_fma_peak": (_c_int, [_c_int, ctypes.POINTER(ctypes.c_double)]),
-    "dpsr_plan_create_box": (_c_int, [_c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_vp)]),
+    "dpsr_plan_create_box": (_c_int, [_c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_vp)]),
     "dpsr_plan_destroy": (_c_int, [_vp]),
     "dpsr_plan_set_stream": (_c_int, [_vp, _vp]),
     "dpsr_plan_reserve": (_c_int, [_vp, _c_i64]),
@@ -78,7 +78,7 @@ _PROTOS = {
     "dpsr_batch_create": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(_c_i64), ctypes.POINTER(_vp)]),
     "dpsr_batch_create_box": (_c_int, [_c_int, ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_float),
-                                       ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(_vp)]),
     "dpsr_batch_destroy": (_c_int, [_vp]),
     "dpsr_batch_set_stream": (_c_int, [_vp, _vp]),
@@ -142,7 +142,7 @@ def dpsr_plan_create(r: int, sigma: float) -> int:
 
 def dpsr_plan_create_box(r: int, sigma: float, box) -> int:
     h = _vp()
-    b = None if box is None else (ctypes.c_float * 3)(*[float(v) for v in box])
+    b = None if box is None else (ctypes.c_double * 3)(*[float(v) for v in box])
     check(load().dpsr_plan_create_box(int(r), float(sigma), b, ctypes.byref(h)), "dpsr_plan_create_box")
     return h.value
 
@@ -304,7 +304,7 @@ def dpsr_batch_create_box(r, sigma, box, n_max) -> int:
     h = _vp()
     ra = (ctypes.c_int * n)(*[int(x) for x in r])
     sa = (ctypes.c_float * n)(*[float(x) for x in sigma])
-    ba = (ctypes.c_float * (3 * n))(*[float(v) for b in box for v in b])
+    ba = (ctypes.c_double * (3 * n))(*[float(v) for b in box for v in b])
     na = (ctypes.c_int64 * n)(*[int(x) for x in n_max])
     check(load().dpsr_batch_create_box(n, ra, sa, ba, na, ctypes.byref(h)), "dpsr_batch_create_box")
     return h.value
