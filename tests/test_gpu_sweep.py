@@ -134,3 +134,65 @@ def test_batch_sweep(j):
         assert relmax(dp.cpu().numpy(), d0.cpu().numpy()) <= 10 * tol, (j, i, "dpoints")
         plan.close()
     batch.close()
+
+
+@pytest.mark.parametrize("k", range(8))
+def test_mesh_extraction_sweep(k):
+    """Seeded random periodic fields (a few random Fourier modes, r in
+    {16, 32, 64}) at random levels, a quarter of them a level equal to a
+    grid value (exact ties at vertices): the kernel's triangles equal the
+    numpy reference's (count, centroids and area vectors). Topology: a
+    level away from every grid value gives a closed surface (every edge in
+    exactly two triangles); a tie puts vertices of several edges on one grid
+    point, where the tetrahedra leave a fan that is not a manifold in exact
+    arithmetic too, so there the kernel's vertex, edge and face counts must
+    equal the reference's. Topology is compared only where no vertex lies
+    within 2e-5 voxel of a grid point without being on it: closer than that,
+    FP32 coordinates (an ulp of 1.0 is 3.8e-6 voxel at r = 64) may merge a
+    vertex with the grid point's, a near-tie the FP64 reference resolves."""
+    import torch
+    from scipy.spatial import cKDTree
+    from oracle import mesh as ref
+    from paper_2106_03452_gb300 import mesh
+    rng = synth.Rng(74000 + k)
+    u = rng.uniform(3)
+    r = [16, 32, 64][min(int(u[0] * 3), 2)]
+    j = np.arange(r) / r
+    X, Y, Z = np.meshgrid(j, j, j, indexing="ij")
+    f = np.zeros((r, r, r))
+    for _ in range(5):
+        m = np.floor(rng.uniform(3) * 4).astype(int)
+        ph = rng.uniform(3)
+        f += rng.normal() * np.cos(2 * np.pi * (m[0] * X + ph[0])) * np.cos(2 * np.pi * (m[1] * Y + ph[1])) \
+            * np.cos(2 * np.pi * (m[2] * Z + ph[2]))
+    chi = f.astype(np.float32)
+    if u[1] < 0.25:
+        level = float(chi.flat[int(u[2] * chi.size) % chi.size])   # a tie at one vertex at least
+    else:
+        # the midpoint of the widest gap among 64 neighbouring grid values
+        srt = np.unique(chi).astype(np.float64)
+        w = srt[int((0.2 + 0.6 * u[2]) * (len(srt) - 1)):][:64]
+        g = int(np.argmax(np.diff(w)))
+        level = float(np.float32(0.5 * (w[g] + w[g + 1])))
+    tris, nrm = mesh.extract(torch.from_numpy(chi).cuda(), level)
+    tris_c, _ = ref.extract(chi.astype(np.float64), level)
+    assert tris.shape[0] == len(tris_c), (k, r, level)
+    if len(tris_c) == 0:
+        return
+    t = tris.cpu().numpy().astype(np.float64)
+    area = lambda q: np.cross(q[:, 1] - q[:, 0], q[:, 2] - q[:, 0])
+    a = np.concatenate([t.mean(1), r * area(t)], 1)
+    b = np.concatenate([tris_c.mean(1), r * area(tris_c)], 1)
+    da, _ = cKDTree(b).query(a)
+    db, _ = cKDTree(a).query(b)
+    assert max(da.max(), db.max()) <= 1e-5, (k, r, level, da.max(), db.max())
+    wr = tris_c.reshape(-1, 3) * r
+    d = np.max(np.abs(wr - np.round(wr)), axis=1)  # distance of each vertex to its nearest grid point
+    if np.any((d > 0) & (d < 2e-5)):
+        return
+    got = ref.topology(np.mod(t, 1.0))           # vertices identified across the periodic faces
+    want = ref.topology(np.mod(tris_c, 1.0))
+    if np.any(d == 0):
+        assert got == want, (k, r, level, got, want)
+    else:
+        assert want[1] == want[3] and got[1] == got[3], (k, r, level, got, want)
