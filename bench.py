@@ -166,6 +166,7 @@ MEASURED_TRAFFIC = {
     # k_zfwd<128> + k_yfwd<128, 0> (the pencil forward plane kind), r = 128 ellipsoids, N = 20000
     ("plane_fwd", 128, 0): 682240 + 37711872,
     ("plane_binv", 128, 1): 21772288,   # k_plane_binv<128, 1> (512 threads), same workload
+    ("plane_binv", 128, 3): 21667072,   # k_plane_binv_ch<128> (one CTA per plane and channel)
 }
 
 

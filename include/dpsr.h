@@ -281,12 +281,16 @@ DPSR_API int dpsr_plan_profile(dpsr_plan plan, int enable);
 
 /* Plane paths the plan currently uses for its four plane kinds, in the
  * order forward, forward inverse, backward, backward inverse: 0 = two pencil
- * passes of independent CTAs, else the cluster size (CTAs per x-plane). An
+ * passes of independent CTAs, 1, 2, 4 or 8 = the cluster size (CTAs per
+ * x-plane), 3 = the backward inverse as three independent CTAs per x-plane,
+ * one per adjoint channel (r = 64 and 128; backward inverse only). An
  * autotuner sets them on the first solve of each grid size in a process
  * (DPSR_TUNE=0 keeps the static choice). The environment can fix them:
  * DPSR_PLANE_PATHS_<r>="a,b,c,d" for grid size r, or DPSR_PLANE_PATH=c for
  * every kind and size (c in 0, 1, 2, 4, 8). At r = 512 only the pencil
- * passes exist (a plane no longer fits a cluster's shared memory). */
+ * passes exist (a plane no longer fits a cluster's shared memory). A path
+ * that does not exist for a kind and size makes the solve fail with
+ * DPSR_ECUDA. */
 DPSR_API int dpsr_plan_clusters(dpsr_plan plan, int *C4);
 DPSR_API int dpsr_plan_profile_read(dpsr_plan plan, double *ms, int *launches);
 
@@ -364,7 +368,8 @@ DPSR_API int dpsr_batch_sync(dpsr_batch batch);
 /* Kernel launches in one forward (+ backward) of the batch. */
 DPSR_API int dpsr_batch_launches(dpsr_batch batch, int with_bwd);
 /* Plane paths of the batch's instances of grid size r, in the order of
- * dpsr_plan_clusters (0 = pencil passes, else the cluster size). A batch
+ * dpsr_plan_clusters (0 = pencil passes, 3 = the backward inverse split by
+ * channel, else the cluster size). A batch
  * tunes them on its first eager run (dpsr_batch_forward / _backward, or the
  * first dpsr_batch_graph_launch, which runs the sequence once before it
  * captures it): each plane kind of each grid size is timed over every path on

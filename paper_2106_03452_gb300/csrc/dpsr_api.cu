@@ -121,7 +121,7 @@ size_t pts_ws_bytes(int64_t n) {
   size_t b = align256(sizeof(float4) * 2 * n);  // sorted
   b += align256(sizeof(int) * n);              // cellx
   b += align256(sizeof(float4) * 2 * n);       // gfwd
-  b += align256(sizeof(float) * 12 * n);       // slots
+  b += align256(sizeof(float) * 24 * n);       // slots ([2][3][n] float4 on the split adjoint path)
   return b;
 }
 
@@ -190,9 +190,10 @@ bool tuning_enabled() {
 // DPSR_PLANE_PATHS_<r> = "a,b,c,d" fixes the four kinds at grid size r (for
 // instance the choices an autotuned run reported, to profile the same
 // kernels), else DPSR_PLANE_PATH fixes every kind at every r; 0 = pencil
-// passes, 1/2/4/8 = cluster size. Returns -1 when neither applies.
+// passes, 1/2/4/8 = cluster size, 3 = the adjoint kind split by channel
+// (kind 3 only). Returns -1 when neither applies.
 int forced_path(int kind, int r) {
-  auto valid = [](int c) { return c == 0 || c == 1 || c == 2 || c == 4 || c == 8; };
+  auto valid = [](int c) { return dpsr::valid_path(c); };
   char name[32];
   snprintf(name, sizeof(name), "DPSR_PLANE_PATHS_%d", r);
   if (const char* e = getenv(name)) {
@@ -204,7 +205,7 @@ int forced_path(int kind, int r) {
   const char* e = getenv("DPSR_PLANE_PATH");
   if (!e || !*e) return -1;
   const int c = atoi(e);
-  return valid(c) ? c : -1;
+  return valid(c) && c != dpsr::kPathSplit ? c : -1;  // the split path exists for one kind only
 }
 
 // Launch plane kernel `kind` for every candidate C, time each with events
@@ -212,7 +213,7 @@ int forced_path(int kind, int r) {
 // run does not decide), record the fastest. Returns the last launch error.
 cudaError_t tune_plane(dpsr_plan p, int kind, const Solve& s, cudaStream_t st) {
   const int r = p->r;
-  const int cands[5] = {0, 1, 2, 4, 8};  // 0: the z/y pencil passes
+  const int cands[6] = {0, 1, 2, 4, 8, dpsr::kPathSplit};  // 0: the z/y pencil passes
   float best = 1e30f;
   int bestC = p->C[kind];
   cudaEvent_t e0, e1;
@@ -709,7 +710,7 @@ int dpsr_backward(dpsr_plan p, const float* dchi, float* dpoints, float* dnormal
   run(DPSR_K_PLANE_BFWD, [&] { return run_plane(p, 2, s, st); });
   run(DPSR_K_XPASS_BWD, [&] { return dpsr::launch_xpass(true, r, s, nullptr, 1, st); });
   run(DPSR_K_PLANE_BINV, [&] { return run_plane(p, 3, s, st); });
-  run(DPSR_K_COMBINE, [&] { return dpsr::launch_combine(s, nullptr, 1, s.N, st); });
+  run(DPSR_K_COMBINE, [&] { return dpsr::launch_combine(s, nullptr, 1, s.N, p->C[3] == dpsr::kPathSplit, st); });
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_err(e);

@@ -110,7 +110,7 @@ cudaError_t launch_bwd(dpsr_batch b) {
     cudaError_t e = dpsr::launch_plane(2, c.r, c.C[2], dummy, c.dtab, n, st);
     if (e == cudaSuccess) e = dpsr::launch_xpass(true, c.r, dummy, c.dtab, n, st);
     if (e == cudaSuccess) e = dpsr::launch_plane(3, c.r, c.C[3], dummy, c.dtab, n, st);
-    if (e == cudaSuccess) e = dpsr::launch_combine(dummy, c.dtab, n, c.nmax, st);
+    if (e == cudaSuccess) e = dpsr::launch_combine(dummy, c.dtab, n, c.nmax, c.C[3] == dpsr::kPathSplit, st);
     return e;
   });
 }
@@ -143,7 +143,7 @@ cudaError_t tune_kind(BatchClass& c, int kind, cudaStream_t st, cudaEvent_t e0, 
       return dpsr::launch_plane(kind, c.r, cached, dummy, c.dtab, n, st);
     }
   }
-  const int cands[5] = {0, 1, 2, 4, 8};
+  const int cands[6] = {0, 1, 2, 4, 8, dpsr::kPathSplit};
   float best = 1e30f;
   int bestC = c.C[kind];
   for (int C : cands) {
@@ -202,7 +202,7 @@ cudaError_t tune_batch(dpsr_batch b, bool with_bwd) {
       if (e == cudaSuccess) e = plane(2);
       if (e == cudaSuccess) e = dpsr::launch_xpass(true, c.r, dummy, c.dtab, n, st);
       if (e == cudaSuccess) e = plane(3);
-      if (e == cudaSuccess) e = dpsr::launch_combine(dummy, c.dtab, n, c.nmax, st);
+      if (e == cudaSuccess) e = dpsr::launch_combine(dummy, c.dtab, n, c.nmax, c.C[3] == dpsr::kPathSplit, st);
     }
   }
   if (e0) cudaEventDestroy(e0);
@@ -494,7 +494,7 @@ int dpsr_internal_batch_run(dpsr_batch b, int k, int with_bwd) {
     if (e == cudaSuccess) e = dpsr::launch_plane(2, c.r, c.C[2], dummy, c.dtab, k, st);
     if (e == cudaSuccess) e = dpsr::launch_xpass(true, c.r, dummy, c.dtab, k, st);
     if (e == cudaSuccess) e = dpsr::launch_plane(3, c.r, c.C[3], dummy, c.dtab, k, st);
-    if (e == cudaSuccess) e = dpsr::launch_combine(dummy, c.dtab, k, c.nmax, st);
+    if (e == cudaSuccess) e = dpsr::launch_combine(dummy, c.dtab, k, c.nmax, c.C[3] == dpsr::kPathSplit, st);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -929,6 +929,168 @@ __global__ void __launch_bounds__(binv_threads<L, C>(), binv_smem<L, C>() <= 113
   if constexpr (C > 1) cl.sync();  // peers may still read this CTA's rows
 }
 
+// ===========================================================================
+// The adjoint plane kind split by channel (path code 3): one CTA per (plane
+// X, channel) instead of one per plane. A CTA holds one channel's boxes, a
+// third of k_plane_binv<L, 1>'s shared memory, so three CTAs share an SM and
+// 3r CTAs fill the GPU where the r CTAs of the one-CTA kernel leave SMs idle
+// and run their three channels back to back. A channel's arithmetic is that
+// of k_plane_binv<L, 1> (the same transforms in the same order: the same
+// bits). Its per-point results go to slots of their own, [side][channel]
+// [point] as float4 (gather, three weight-derivative terms), which k_combine
+// adds in the one-CTA kernel's order.
+// ===========================================================================
+template <int L>
+struct BinvChGeo {
+  static constexpr int NT = kNT;
+  static constexpr int T = Shape<L>::T, R1 = Shape<L>::R1, G = NT / T;
+  static constexpr int H = L / 2;
+  static constexpr int NB = (H + 15) / 16;  // boxes of 16 slots
+  static constexpr int BOX = L * 16;        // float2 per box [ky][16 kz]
+  static constexpr int BUF = NB * BOX;
+};
+
+template <int L>
+constexpr bool binv_ch_inst() { return L == 64 || L == 128; }
+
+template <int L>
+constexpr size_t binv_ch_smem() {
+  using B = BinvChGeo<L>;
+  return 1024 + sizeof(float2) * ((size_t)B::BUF + L) + sizeof(float) * L;
+}
+
+template <int L>
+__global__ void __launch_bounds__(BinvChGeo<L>::NT, 3)
+    k_plane_binv_ch(const __grid_constant__ Solve s0, const Solve* __restrict__ tab) {
+  using B = BinvChGeo<L>;
+  constexpr int NT = B::NT, H = B::H, T = B::T, R1 = B::R1, G = B::G;
+  const Solve& S = tab ? tab[blockIdx.z] : s0;
+  const int X = blockIdx.x, ch = blockIdx.y;
+  const int tid = threadIdx.x, g = tid / T, t = tid % T;
+  extern __shared__ unsigned char smem_raw[];
+  float2* buf = aligned_smem(smem_raw);
+  float2* twt = buf + B::BUF;
+  float* iu = reinterpret_cast<float*>(twt + L);
+  __shared__ uint64_t bar;
+  pdl_trigger();
+  for (int i = tid; i < L; i += NT) {
+    iu[i] = S.iu[L + i];  // y axis; the z axis is read from global memory
+    twt[i] = S.tw[i];
+  }
+  pdl_wait();
+  // X channel from Q2 = IFFT_x(-i u_x F), Y and Z from Q1 = IFFT_x(F)
+  const int sp = ch == 0 ? kSpChi : kSpD;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(&bar, B::NB * B::BOX * (uint32_t)sizeof(float2));
+    for (int b = 0; b < B::NB; ++b) tma_load_3d(buf + b * B::BOX, &S.tmy[sp], 16 * b, 0, X, &bar);
+  }
+  __syncthreads();
+  TwTab<L> twr{twt, t};
+  const PlanePoints pp(S, X);
+  auto col = [&](int sl, int e) -> float2& { return buf[(sl >> 4) * B::BOX + bx(e, sl & 15)]; };
+  const bool alive = chunk_wait(&bar, 0, S.status);
+  if (alive) {
+    if (g == 0) {
+      // column kz = 0 becomes P = X0 + i Xn (Xn: the Nyquist column); the
+      // same lanes read these elements again in the y pass below
+      const float2* nq = S.spec[sp] + (size_t)X * L * kpitch(L) + H;
+      for (int j = 0; j < R1; ++j) {
+        const int ky = t + T * j;
+        const float2 n = nq[(size_t)ky * kpitch(L)];
+        const float2 x0 = col(0, ky);
+        col(0, ky) = make_float2(x0.x - n.y, x0.y + n.x);
+      }
+    }
+    // IFFT along y of the H columns (Y: times -i u_y first; Z: times -i u_z
+    // after, which commutes with the y transform; zero at DC and Nyquist)
+    for (int sl0 = 0; sl0 < H; sl0 += G) {
+      const int sl = sl0 + g;
+      if (sl < H) {  // whole groups; T-lane syncs only
+        float2 v[R1];
+#pragma unroll
+        for (int j = 0; j < R1; ++j) v[j] = col(sl, t + T * j);
+        if (ch == 1) {
+#pragma unroll
+          for (int j = 0; j < R1; ++j) v[j] = cmul_iu(v[j], -iu[t + T * j]);
+        }
+        fft_r<L, +1>(v, t, [&](int e) -> float2& { return col(sl, e); }, twr);
+        if (ch == 2) {
+          const float ez = sl == 0 ? 0.f : -__ldg(S.iu + 2 * L + sl);  // z axis
+#pragma unroll
+          for (int j = 0; j < R1; ++j) v[j] = cmul_iu(v[j], ez);
+        }
+#pragma unroll
+        for (int j = 0; j < R1; ++j) col(sl, t + T * j) = v[j];
+      }
+    }
+  }
+  __syncthreads();
+  // C2R along z of row pairs, in place.
+  if (alive) {
+    for (int p0 = 0; p0 < L / 2; p0 += G) {
+      const int p = p0 + g;
+      if (p < L / 2) {
+        c2r_pair_ip<L>(t, twr, [&](int i) -> float2& { return buf[rb<B::BOX>(2 * p + i / H, i % H)]; });
+      }
+    }
+  }
+  __syncthreads();
+  // This channel's share of the point adjoint: the gather of V_ch, and d/dp
+  // of the weights times n_ch V_ch.
+  if (!alive) return;
+  float4* out = reinterpret_cast<float4*>(S.slots);
+  const int nvisit = pp.total();
+  for (int i = tid; i < nvisit; i += NT) {
+    int dx;
+    const int idx = pp.index(i, dx);
+    if (!dbg_in_range(S.status, idx, S.N)) continue;
+    const float4 a = S.sorted[2 * idx], b = S.sorted[2 * idx + 1];
+    const Axis ay = axis_rec(a.y, b.w, 1, L);
+    const Axis ax = axis_rec(a.x, b.w, 0, L), az = axis_rec(a.z, b.w, 2, L);
+    const float nch = ch == 0 ? a.w : (ch == 1 ? b.x : b.y);
+    const float fx = wsel(dx, ax.t), dfx = dx ? (float)L : -(float)L;
+    float nb = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const int y = dy ? ay.i1 : ay.i0;
+      const int p2 = y & ~1;
+      const float fy = wsel(dy, ay.t), dfy = dy ? (float)L : -(float)L;
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz) {
+        const int z = dz ? az.i1 : az.i0;
+        const float fz = wsel(dz, az.t), dfz = dz ? (float)L : -(float)L;
+        const float2 f = buf[rb<B::BOX>(p2 + z / H, z % H)];
+        const float V = (y & 1) ? f.y : f.x;
+        const float sv = nch * V;
+        nb += fx * fy * fz * V;
+        c0 += dfx * fy * fz * sv;
+        c1 += fx * dfy * fz * sv;
+        c2 += fx * fy * dfz * sv;
+      }
+    }
+    out[((size_t)dx * 3 + ch) * S.N + idx] = make_float4(nb, c0, c1, c2);
+  }
+}
+
+template <int L>
+static cudaError_t launch_binv_ch_t(const Solve& s, const Solve* tab, int count, cudaStream_t st) {
+  if constexpr (!binv_ch_inst<L>()) {
+    return cudaErrorInvalidValue;
+  } else {
+    constexpr size_t smem = binv_ch_smem<L>();
+    static bool attr_set = false;
+    if (!attr_set) {
+      const cudaError_t e =
+          cudaFuncSetAttribute(k_plane_binv_ch<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+    return launch_k(k_plane_binv_ch<L>, dim3(L, 3, count), dim3(BinvChGeo<L>::NT), smem, st, 1, s, tab);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
@@ -987,6 +1149,12 @@ static cudaError_t launch_plane_L(int kind, int C, const Solve& s, const Solve* 
 cudaError_t launch_plane(int kind, int r, int C, const Solve& s, const Solve* tab, int count,
                          cudaStream_t st) {
   if (C == 0) return launch_pencil(kind, r, s, tab, count, st);
+  if (C == kPathSplit) {
+    if (kind != 3) return cudaErrorInvalidValue;
+    if (r == 64) return launch_binv_ch_t<64>(s, tab, count, st);
+    if (r == 128) return launch_binv_ch_t<128>(s, tab, count, st);
+    return cudaErrorInvalidValue;
+  }
   switch (r) {
     case 8: return launch_plane_L<8>(kind, C, s, tab, count, st);
     case 16: return launch_plane_L<16>(kind, C, s, tab, count, st);
@@ -1017,6 +1185,12 @@ static size_t kind_smem(int kind) {
 
 size_t plane_smem_bytes(int kind, int r, int C) {
   if (C == 0) return pencil_smem_bytes(kind, r);
+  if (C == kPathSplit) {
+    if (kind != 3) return 0;
+    if (r == 64) return binv_ch_smem<64>();
+    if (r == 128) return binv_ch_smem<128>();
+    return 0;
+  }
   auto pick = [&](auto Lc) -> size_t {
     constexpr int L = decltype(Lc)::value;
     switch (C) {

@@ -167,7 +167,10 @@ cudaError_t launch_bin(const Solve& s, const Solve* tab, int count, int nmax, in
 // dpoints = (sum of the two plane sides of the weight-derivative terms
 //            + (mu_bar / (N n)) * gradient of the lookup of y (Eq. 4 adjoint)) / L_d;
 // dnormals = sum of the two plane sides of the gather. Written in the
-// caller's point order.
+// caller's point order. SPLIT: the adjoint kind left [side][channel][point]
+// float4 slots (gather, three derivative terms), summed over the channels in
+// the order the one-CTA adjoint accumulates them; else [side][point][6].
+template <bool SPLIT>
 __global__ void __launch_bounds__(256) k_combine(const __grid_constant__ Solve s0,
                                                  const Solve* __restrict__ tab) {
   pdl_trigger();
@@ -178,8 +181,33 @@ __global__ void __launch_bounds__(256) k_combine(const __grid_constant__ Solve s
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.N; i += gridDim.x * blockDim.x) {
     const int orig = __float_as_int(S.sorted[2 * i + 1].z);
     if (!dbg_in_range(S.status, orig, S.N)) continue;
-    const float* a = S.slots + (size_t)i * 6;
-    const float* b = S.slots + (N + i) * 6;
+    float a[6], b[6];
+    if constexpr (SPLIT) {
+      const float4* q = reinterpret_cast<const float4*>(S.slots);
+      float4 u[3], w[3];
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        u[ch] = q[(size_t)ch * N + i];
+        w[ch] = q[(size_t)(3 + ch) * N + i];
+      }
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        a[ch] = u[ch].x;
+        b[ch] = w[ch].x;
+      }
+      a[3] = (u[0].y + u[1].y) + u[2].y;
+      a[4] = (u[0].z + u[1].z) + u[2].z;
+      a[5] = (u[0].w + u[1].w) + u[2].w;
+      b[3] = (w[0].y + w[1].y) + w[2].y;
+      b[4] = (w[0].z + w[1].z) + w[2].z;
+      b[5] = (w[0].w + w[1].w) + w[2].w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        a[k] = S.slots[(size_t)i * 6 + k];
+        b[k] = S.slots[(N + i) * 6 + k];
+      }
+    }
     const float4 ga = S.gfwd[i], gb = S.gfwd[N + i];
     S.dnormals[3 * orig] = a[0] + b[0];
     S.dnormals[3 * orig + 1] = a[1] + b[1];
@@ -191,10 +219,11 @@ __global__ void __launch_bounds__(256) k_combine(const __grid_constant__ Solve s
   }
 }
 
-cudaError_t launch_combine(const Solve& s, const Solve* tab, int count, int nmax,
+cudaError_t launch_combine(const Solve& s, const Solve* tab, int count, int nmax, bool split,
                            cudaStream_t st) {
   const int blocks = min(max((nmax + 255) / 256, 1), 1184);
-  return launch_k(k_combine, dim3(blocks, 1, count), dim3(256), 0, st, 0, s, tab);
+  return split ? launch_k(k_combine<true>, dim3(blocks, 1, count), dim3(256), 0, st, 0, s, tab)
+               : launch_k(k_combine<false>, dim3(blocks, 1, count), dim3(256), 0, st, 0, s, tab);
 }
 
 // ---------------------------------------------------------------------------

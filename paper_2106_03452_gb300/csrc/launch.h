@@ -69,6 +69,11 @@ inline int persistent_ctas(K fn, int nthreads, size_t smem, int tiles, int count
   return n < 1 ? 1 : (n < tiles ? n : tiles);
 }
 
+// Plane path codes: 0 the two pencil passes, 1/2/4/8 the cluster size of the
+// plane kernels, kPathSplit the adjoint kind as one CTA per plane and
+// channel (k_plane_binv_ch; r = 64 and 128).
+constexpr int kPathSplit = 3;
+inline bool valid_path(int C) { return C == 0 || C == 1 || C == 2 || C == kPathSplit || C == 4 || C == 8; }
 // Kernel launches of one plane kind with path C (0: two pencil passes).
 inline int plane_launches(int C) { return C == 0 ? 2 : 1; }
 cudaError_t launch_xpass(bool bwd, int r, const Solve& s, const Solve* tab, int count,
@@ -80,7 +85,8 @@ int xpass_blocks(int r);
 int make_tensor_maps(Solve& s, int r);
 // Points: x-plane bucketing (count, scan, scatter) and the backward combine.
 cudaError_t launch_bin(const Solve& s, const Solve* tab, int count, int nmax, int r, cudaStream_t st);
-cudaError_t launch_combine(const Solve& s, const Solve* tab, int count, int nmax,
+// split: the adjoint kind ran on path kPathSplit (per-channel slots).
+cudaError_t launch_combine(const Solve& s, const Solve* tab, int count, int nmax, bool split,
                            cudaStream_t st);
 
 // Trilinear lookup of a grid at query points and its adjoint (atomic adds).

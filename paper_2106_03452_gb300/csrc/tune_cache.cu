@@ -64,7 +64,8 @@ bool parse(const char* line, Entry* e) {
              "\"path\": %d, \"ms\": %f}%n",
              &e->cc, &e->sms, &e->driver, &e->r, &e->kind, &e->batch, &e->path, &e->ms, &n) != 8)
     return false;
-  const bool valid_path = e->path == 0 || e->path == 1 || e->path == 2 || e->path == 4 || e->path == 8;
+  // 0 pencil passes, 1/2/4/8 cluster size, 3 the adjoint kind split by channel
+  const bool valid_path = e->path == 0 || e->path == 1 || e->path == 2 || e->path == 3 || e->path == 4 || e->path == 8;
   return n > 0 && valid_path && e->kind >= 0 && e->kind < 4 && e->r >= 8 && e->batch >= 0;
 }
 

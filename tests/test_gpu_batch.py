@@ -21,13 +21,16 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
-@pytest.mark.parametrize("path", ["pencil", "tuned"])
+@pytest.mark.parametrize("path", ["pencil", "tuned", "split"])
 def test_batch_equals_solo_and_oracle(oracle, monkeypatch, path):
     import torch
     if path == "pencil":
         monkeypatch.setenv("DPSR_PLANE_PATH", "0")
     else:
         monkeypatch.delenv("DPSR_PLANE_PATH", raising=False)
+    if path == "split":  # the adjoint kind as one CTA per plane and channel, batch and solo
+        monkeypatch.setenv("DPSR_PLANE_PATHS_64", "1,1,1,3")
+        monkeypatch.setenv("DPSR_PLANE_PATHS_128", "1,1,1,3")
     from paper_2106_03452_gb300 import synth
     from paper_2106_03452_gb300.dpsr import Batch, Plan
     inst = synth.workload_batch(count=32)
@@ -68,6 +71,8 @@ def test_batch_equals_solo_and_oracle(oracle, monkeypatch, path):
     # (pencil) launches for each of the four plane kinds
     n = batch.launches(True)
     assert 2 * 9 <= n <= 2 * 13 and (path != "pencil" or n == 2 * 13)
+    if path == "split":
+        assert batch.paths(64) == [1, 1, 1, 3] and batch.paths(128) == [1, 1, 1, 3]
     batch.close()
 
 

@@ -47,9 +47,12 @@ def _cuda():
     build.build(debug=True)
 
 
-@pytest.mark.parametrize("path", ["0", "1"])
+@pytest.mark.parametrize("path", ["0", "1", "split"])
 def test_debug_build_checks(path):
-    env = dict(os.environ, DPSR_DEBUG_CHECKS="1", DPSR_PLANE_PATH=path, PYTHONPATH=ROOT)
+    env = dict(os.environ, DPSR_DEBUG_CHECKS="1", DPSR_PLANE_PATH="1" if path == "split" else path,
+               PYTHONPATH=ROOT)
+    if path == "split":  # one-CTA planes, the adjoint kind split by channel where it exists
+        env.update(DPSR_PLANE_PATHS_64="1,1,1,3", DPSR_PLANE_PATHS_128="1,1,1,3")
     res = subprocess.run([sys.executable, "-c", CHILD], cwd=ROOT, env=env, capture_output=True, text=True,
                          timeout=900)
     assert res.returncode == 0, res.stderr[-3000:]

@@ -141,6 +141,48 @@ def test_ellipsoids_r128_mixed_paths(oracle, monkeypatch):
     assert L.dpsr_plan_clusters(g["plan"].handle) == [0, 2, 1, 4]
 
 
+@pytest.mark.parametrize("r", [64, 128])
+def test_split_adjoint(oracle, monkeypatch, r):
+    """The adjoint plane kind as one CTA per plane and channel (path 3): the
+    oracle's gradients, and the same bits as the one-CTA adjoint kernel (the
+    same transforms; the channel sums in the same order)."""
+    from paper_2106_03452_gb300 import libdpsr as L
+    from gpu_util import gpu_fwd_bwd
+    if r == 128:
+        w = synth.workload_ellipsoids_r128()
+        pts, nrm, dchi, sigma, key = w["points"], w["normals"], w["dchi"], w["sigma"], "ellipsoids_r128"
+    else:
+        rng = synth.Rng(6403)
+        pts = (rng.uniform(5000, 3) * 1.4 - 0.2).astype(np.float32)   # wrapping the cube
+        nrm = rng.normal(5000, 3).astype(np.float32)
+        dchi = rng.normal(r, r, r).astype(np.float32)
+        sigma, key = 1.5, None
+    monkeypatch.delenv("DPSR_PLANE_PATH", raising=False)
+    env = f"DPSR_PLANE_PATHS_{r}"
+    monkeypatch.setenv(env, "1,1,1,3")
+    _check(oracle, r, sigma, pts, nrm, dchi, key=key)
+    # one forward, then the backward on each adjoint path: the adjoint
+    # kinds see the same inputs and agree to rounding (the backward's other
+    # kernels reduce with atomics, whose order can differ between runs)
+    import torch
+    from gpu_util import relmax
+    from paper_2106_03452_gb300.dpsr import Plan
+    plan = Plan(r, sigma)
+    plan.forward(torch.from_numpy(pts).cuda(), torch.from_numpy(nrm).cuda())
+    assert plan.sync() == 0
+    G = torch.from_numpy(dchi).cuda()
+    out = {}
+    for paths in ("1,1,1,3", "1,1,1,1"):
+        monkeypatch.setenv(env, paths)
+        dp, dn = plan.backward(G)
+        assert plan.sync() == 0
+        out[paths] = (dp.cpu().numpy(), dn.cpu().numpy(), L.dpsr_plan_clusters(plan.handle))
+    (dp3, dn3, c3), (dp1, dn1, c1) = out["1,1,1,3"], out["1,1,1,1"]
+    assert c3 == [1, 1, 1, 3] and c1 == [1, 1, 1, 1]
+    assert relmax(dn3, dn1) <= 1e-6 and relmax(dp3, dp1) <= 1e-6, (relmax(dn3, dn1), relmax(dp3, dp1))
+    plan.close()
+
+
 @pytest.mark.parametrize("path", PATHS + ["tuned"])
 def test_torus_r256(oracle, monkeypatch, path):
     w = synth.workload_torus_r256()
